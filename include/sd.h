@@ -1,0 +1,195 @@
+/*
+ * sd.h -- C ABI of the GB300-native leading-order Stokesian-dynamics library.
+ *
+ * Method: Kopp & Hoefling, "GPU-accelerated simulation of colloidal suspensions
+ * with direct hydrodynamic interactions" (arXiv:1205.6333).
+ *
+ *   v_i = sum_j mu_ij F_j = mu0 F_i + sum_{j != i} T(r_i - r_j) F_j        (Sec. 2.2, Eq. rotneMobility)
+ *   mu0 = 1/(6 pi eta a)                                                  (Sec. 2.2)
+ *   T(r) = mu0 3a/(4r) (I + rr) + mu0 a^3/(2 r^3) (I - 3 rr)  Rotne-Prager  (Sec. 2.2, Eq. rotneMobility)
+ *   G(r) = (I + rr) / (8 pi eta r)                            Oseen        (Sec. 2.2, Eq. oseenTensor)
+ *   r_i <- r_i + dt v_i                                       Euler        (Sec. 3.1, step 1)
+ *
+ * The mobility matrix is never stored (Sec. 3.1): every apply is a matrix-free
+ * all-pairs sum on the GPU.
+ *
+ * Conventions for every entry point:
+ *   - Arrays of vectors are n x 3 row-major (x0 y0 z0 x1 y1 z1 ...).
+ *   - `on_device` = 1: the pointer is CUDA device memory of the handle's device;
+ *     the call is asynchronous on the handle's stream and device-side errors
+ *     (non-finite input, coincident particles, watchdog) surface at the next
+ *     synchronising call (sd_synchronize or any host-pointer call).
+ *     `on_device` = 0: the pointer is host memory; the call copies, runs, and
+ *     synchronises the stream before returning.
+ *   - Caller pointers are borrowed for the duration of the call only.
+ *   - The handle owns its device buffers, allocated through cfg.alloc/cfg.free
+ *     when given (e.g. bound to a framework's caching allocator), else cudaMalloc.
+ *   - Every call returns an sd_status; nothing aborts and no C++ exception
+ *     crosses this boundary.  sd_last_error() gives a thread-local message.
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef SD_H
+#define SD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SD_OK = 0,
+    SD_ERR_ARG = 1,          /* invalid argument (null pointer, n < 0, a <= 0, ...)            */
+    SD_ERR_CUDA = 2,         /* a CUDA runtime call failed                                       */
+    SD_ERR_OOM = 3,          /* device allocation failed (cudaMalloc or cfg.alloc returned NULL) */
+    SD_ERR_COINCIDENT = 4,   /* two distinct particles at r = 0 in RP or Oseen mode              */
+    SD_ERR_NONFINITE = 5,    /* NaN or Inf in positions or forces                                */
+    SD_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up (results of that call invalid) */
+    SD_ERR_STATE = 7,        /* call out of order (e.g. step before positions were set)          */
+    SD_ERR_UNSUPPORTED = 8   /* valid request this build does not implement                      */
+} sd_status;
+
+/* Pair tensor.  RPY = Rotne-Prager for r >= 2a continued inside r < 2a by the
+ * Yamakawa form mu0[(1 - 9r/(32a)) I + (3r/(32a)) rr] (not in the paper; the
+ * textbook regularisation of overlapping spheres, finite at r = 0).
+ * RP = the paper's Rotne-Prager form for every r > 0.  OSEEN = Eq. oseenTensor. */
+typedef enum { SD_TENSOR_RPY = 0, SD_TENSOR_RP = 1, SD_TENSOR_OSEEN = 2 } sd_tensor;
+
+/* Arithmetic of the all-pairs sum (Sec. 3.2, last paragraph: pair terms in single
+ * precision, accumulation in higher precision).
+ *   FP32C: FP32 pair terms, compensated (two-float) accumulation, FP64 near/self
+ *          terms and FP64 position state.
+ *   FP64 : everything in FP64 (reference path).
+ *   FP32 : FP32 pair terms and plain FP32 accumulation (ablation only).        */
+typedef enum { SD_PREC_FP32C = 0, SD_PREC_FP64 = 1, SD_PREC_FP32 = 2 } sd_precision;
+
+typedef enum { SD_DTYPE_F32 = 0, SD_DTYPE_F64 = 1 } sd_dtype;
+
+typedef struct sd_config {
+    int32_t n;               /* particles; 0 <= n <= 2^24                                  */
+    double a;                /* sphere radius, > 0                                          */
+    double eta;              /* viscosity, > 0                                              */
+    int32_t tensor;          /* sd_tensor                                                   */
+    int32_t prec;            /* sd_precision                                                */
+    double box[3];           /* 0 = unbounded (default); > 0 = periodic, nearest image only
+                                (Sec. 3.1 footnote).  This build returns SD_ERR_UNSUPPORTED
+                                for a periodic box.                                         */
+    double r_near;           /* pairs closer than r_near get their term in FP64; 0 = 2.5a;
+                                must be >= 2.2a                                             */
+    double rep_eps;          /* soft repulsion U = rep_eps (2a/r)^12 for r < rep_rc; 0 = off */
+    double rep_rc;           /* repulsion cutoff (0 = 2.5a)                                 */
+    double gravity[3];       /* uniform force added to every particle                       */
+    int32_t device;          /* CUDA device ordinal                                         */
+    void *stream;            /* cudaStream_t to run on; NULL = the legacy default stream    */
+    void *(*alloc)(size_t bytes, void *ctx);   /* optional device allocator              */
+    void (*free)(void *ptr, void *ctx);        /* its matching free                      */
+    void *alloc_ctx;
+} sd_config;
+
+typedef struct sd_handle sd_handle;
+typedef struct sd_batch sd_batch;
+
+/* Fill *cfg with defaults: a = eta = 1, RPY, FP32C, unbounded, r_near = 2.5a,
+ * no repulsion (rep_rc = 2.5a), no gravity, device 0, default stream, cudaMalloc. */
+void sd_config_init(sd_config *cfg);
+
+/* Create a system of cfg->n particles.  Positions must be set before use; forces
+ * default to zero.  *out receives the handle (NULL on failure). */
+sd_status sd_create(const sd_config *cfg, sd_handle **out);
+void sd_destroy(sd_handle *h);
+
+/* Positions r_i (n x 3 doubles), copied into the handle's FP64 state; also
+ * refreshes the FP32 mirror the all-pairs kernel reads.  Non-finite values give
+ * SD_ERR_NONFINITE (host pointers: from this call; device pointers: deferred). */
+sd_status sd_set_positions(sd_handle *h, const double *xyz, int on_device);
+sd_status sd_get_positions(sd_handle *h, double *xyz, int on_device);
+
+/* Per-particle external forces F_ext,i (n x 3 doubles), held constant by sd_step.
+ * The force used in a step is F_ext,i + gravity + repulsion (Sec. 3.1, step 2). */
+sd_status sd_set_forces(sd_handle *h, const double *f, int on_device);
+
+/* Velocities V = mu(x) F at the current positions for the given forces F
+ * (n x 3, dtype sd_dtype for both F and V) -- Sec. 2.2, Eq. rotneMobility;
+ * Sec. 3.1, step 3.  Does not change the handle's state. */
+sd_status sd_mobility_apply(sd_handle *h, const void *F, void *V, int dtype, int on_device);
+
+/* nsteps explicit Euler steps (Sec. 3.1): F = F(x_n), v = mu(x_n) F, x_{n+1} = x_n + dt v.
+ * Position state is FP64.  Steps run as a replayed CUDA graph on the handle's stream
+ * (asynchronous; errors surface at the next synchronising call).  nsteps >= 0. */
+sd_status sd_step(sd_handle *h, double dt, int64_t nsteps);
+
+/* Synchronise the handle's stream and report deferred device-side errors. */
+sd_status sd_synchronize(sd_handle *h);
+
+/* Vector-Jacobian products of v(x, F) = mu(x) F at the current positions:
+ *   gX = (dv/dx)^T W,   gF = mu(x)^T W = mu(x) W     (derivative of Eq. rotneMobility)
+ * F, W inputs; gX, gF outputs (n x 3, dtype). */
+sd_status sd_mobility_vjp(sd_handle *h, const void *F, const void *W, void *gX, void *gF, int dtype,
+                          int on_device);
+
+/* Gradient through nsteps Euler steps from the current positions x0 with the
+ * handle's forces (F_ext + gravity; repulsion unsupported -> SD_ERR_UNSUPPORTED):
+ *   lambda_T = gxT;  lambda_n = lambda_{n+1} + dt (dv/dx(x_n))^T lambda_{n+1};
+ *   gx0 = lambda_0;  gF = dL/dF_ext = sum_n dt mu(x_n) lambda_{n+1}.
+ * The forward pass is re-run with FP64 checkpoints every ckpt_every steps
+ * (ckpt_every >= 1) and each segment is recomputed once.  The handle's positions
+ * are restored to x0 on return.  gxT input, gx0 and gF outputs (n x 3 doubles). */
+sd_status sd_adjoint(sd_handle *h, double dt, int64_t nsteps, int32_t ckpt_every, const double *gxT, double *gx0,
+                     double *gF, int on_device);
+
+/* Many independent clusters in one launch per step.  Cluster c holds particles
+ * offsets[c] .. offsets[c+1]-1 (offsets: nclusters+1 int32, host memory,
+ * non-decreasing, offsets[0] = 0, cluster sizes 0..256).  cfg->n is ignored; the
+ * tensor, a, eta, gravity and prec (FP32C or FP64) of cfg apply.  Particles of
+ * different clusters do not interact. */
+sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t nclusters, sd_batch **out);
+void sd_batch_destroy(sd_batch *b);
+sd_status sd_batch_set_positions(sd_batch *b, const double *xyz, int on_device);
+sd_status sd_batch_get_positions(sd_batch *b, double *xyz, int on_device);
+sd_status sd_batch_set_forces(sd_batch *b, const double *f, int on_device);
+/* nsteps Euler steps of every cluster: one persistent kernel launch per step,
+ * replayed from a CUDA graph.  The launch shape is picked by the built-in
+ * autotuner on first use (or by sd_batch_autotune). */
+sd_status sd_step_batched(sd_batch *b, double dt, int64_t nsteps);
+/* Time the candidate launch shapes on the current state (state unchanged) and keep
+ * the fastest.  *choice (may be NULL) receives the index of the chosen shape. */
+sd_status sd_batch_autotune(sd_batch *b, int32_t *choice);
+sd_status sd_batch_synchronize(sd_batch *b);
+
+/* ---- instrumentation (used by benchmarks and tests) ---------------------- */
+
+/* Kernel families that can be timed with CUDA events on the handle's stream. */
+typedef enum {
+    SD_KERNEL_DENSE = 0,     /* all-pairs sum (the hot loop, Sec. 3.1 step 3)  */
+    SD_KERNEL_EPILOGUE = 1,  /* split reduction + FP64 near/self terms + Euler */
+    SD_KERNEL_CELLS = 2,     /* cell-list build                                */
+    SD_KERNEL_FORCES = 3,    /* force assembly (Sec. 3.1 step 2)               */
+    SD_KERNEL_BATCHED = 4,   /* batched persistent kernel                      */
+    SD_KERNEL_VJP = 5,       /* adjoint all-pairs kernel                       */
+    SD_KERNEL_COUNT = 6
+} sd_kernel;
+
+/* on = 1: record a CUDA event pair around every launch of each kernel family (steps
+ * then run without graph replay).  Enabling clears the accumulated times. */
+sd_status sd_profile(sd_handle *h, int on);
+sd_status sd_batch_profile(sd_batch *b, int on);
+/* Synchronise and return the summed event time (ms) and launch count of a family. */
+sd_status sd_profile_read(sd_handle *h, int kernel, double *ms, int64_t *launches);
+sd_status sd_batch_profile_read(sd_batch *b, int kernel, double *ms, int64_t *launches);
+/* Number of kernel launches this handle has issued so far (graph replays count
+ * every kernel node). */
+int64_t sd_launch_count(const sd_handle *h);
+int64_t sd_batch_launch_count(const sd_batch *b);
+/* Iteration limit of every bounded device-side wait (default 1 << 22). */
+sd_status sd_set_watchdog(sd_handle *h, int64_t iterations);
+
+/* Thread-local message describing the last non-OK status ("" if none). */
+const char *sd_last_error(void);
+/* Library version string. */
+const char *sd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SD_H */

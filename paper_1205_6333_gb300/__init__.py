@@ -1,0 +1,371 @@
+"""GB300-native leading-order Stokesian dynamics (Kopp & Hoefling, arXiv:1205.6333).
+
+Python binding of the C ABI in include/sd.h.  Every step of the computation
+runs in the CUDA kernels of libsd_gb300.so; this module only marshals
+arguments (numpy arrays and torch tensors -> pointers, torch's current stream
+and caching allocator -> the handle's stream and allocator callbacks).
+
+Two layers:
+  * the C names (``sd_create``, ``sd_set_positions``, ``sd_mobility_apply``,
+    ``sd_step``, ``sd_step_batched``, ``sd_adjoint``, ...), taking the same
+    arguments as in C (pointers as ints) and raising SDError on a non-OK status;
+  * ``System`` and ``Batch``, which accept numpy arrays (host memory) or torch
+    tensors (CUDA tensors are passed as device pointers, no copy).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import (SD_TENSOR_RPY, SD_TENSOR_RP, SD_TENSOR_OSEEN, SD_PREC_FP32C, SD_PREC_FP64, SD_PREC_FP32,
+                   SD_DTYPE_F32, SD_DTYPE_F64, SD_KERNEL_DENSE, SD_KERNEL_EPILOGUE, SD_KERNEL_CELLS,
+                   SD_KERNEL_FORCES, SD_KERNEL_BATCHED, SD_KERNEL_VJP, sd_config)
+
+TENSORS = {"rpy": SD_TENSOR_RPY, "rp": SD_TENSOR_RP, "oseen": SD_TENSOR_OSEEN}
+PRECISIONS = {"fp32c": SD_PREC_FP32C, "fp64": SD_PREC_FP64, "fp32": SD_PREC_FP32}
+
+
+class SDError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        self.status_name = L.STATUS_NAMES[status] if 0 <= status < len(L.STATUS_NAMES) else str(status)
+        super().__init__("%s: %s (%s)" % (where, self.status_name, message))
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise SDError(st, where, L.load().sd_last_error().decode())
+
+
+def lib():
+    return L.load()
+
+
+# ---------------------------------------------------------------- C names
+
+def sd_config_init() -> sd_config:
+    cfg = sd_config()
+    lib().sd_config_init(ctypes.byref(cfg))
+    return cfg
+
+
+def sd_create(cfg: sd_config) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sd_create(ctypes.byref(cfg), ctypes.byref(h)), "sd_create")
+    return h.value
+
+
+def sd_destroy(h: int):
+    lib().sd_destroy(h)
+
+
+def sd_set_positions(h, xyz_ptr, on_device):
+    _check(lib().sd_set_positions(h, xyz_ptr, on_device), "sd_set_positions")
+
+
+def sd_get_positions(h, xyz_ptr, on_device):
+    _check(lib().sd_get_positions(h, xyz_ptr, on_device), "sd_get_positions")
+
+
+def sd_set_forces(h, f_ptr, on_device):
+    _check(lib().sd_set_forces(h, f_ptr, on_device), "sd_set_forces")
+
+
+def sd_mobility_apply(h, F_ptr, V_ptr, dtype, on_device):
+    _check(lib().sd_mobility_apply(h, F_ptr, V_ptr, dtype, on_device), "sd_mobility_apply")
+
+
+def sd_step(h, dt, nsteps):
+    _check(lib().sd_step(h, float(dt), int(nsteps)), "sd_step")
+
+
+def sd_synchronize(h):
+    _check(lib().sd_synchronize(h), "sd_synchronize")
+
+
+def sd_mobility_vjp(h, F_ptr, W_ptr, gX_ptr, gF_ptr, dtype, on_device):
+    _check(lib().sd_mobility_vjp(h, F_ptr, W_ptr, gX_ptr, gF_ptr, dtype, on_device), "sd_mobility_vjp")
+
+
+def sd_adjoint(h, dt, nsteps, ckpt_every, gxT_ptr, gx0_ptr, gF_ptr, on_device):
+    _check(lib().sd_adjoint(h, float(dt), int(nsteps), int(ckpt_every), gxT_ptr, gx0_ptr, gF_ptr, on_device),
+           "sd_adjoint")
+
+
+def sd_batch_create(cfg: sd_config, offsets) -> int:
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    b = ctypes.c_void_p()
+    _check(lib().sd_batch_create(ctypes.byref(cfg), off.ctypes.data, off.size - 1, ctypes.byref(b)),
+           "sd_batch_create")
+    return b.value
+
+
+def sd_batch_destroy(b):
+    lib().sd_batch_destroy(b)
+
+
+def sd_batch_set_positions(b, ptr, on_device):
+    _check(lib().sd_batch_set_positions(b, ptr, on_device), "sd_batch_set_positions")
+
+
+def sd_batch_get_positions(b, ptr, on_device):
+    _check(lib().sd_batch_get_positions(b, ptr, on_device), "sd_batch_get_positions")
+
+
+def sd_batch_set_forces(b, ptr, on_device):
+    _check(lib().sd_batch_set_forces(b, ptr, on_device), "sd_batch_set_forces")
+
+
+def sd_step_batched(b, dt, nsteps):
+    _check(lib().sd_step_batched(b, float(dt), int(nsteps)), "sd_step_batched")
+
+
+def sd_batch_autotune(b) -> int:
+    c = ctypes.c_int32(-1)
+    _check(lib().sd_batch_autotune(b, ctypes.byref(c)), "sd_batch_autotune")
+    return c.value
+
+
+def sd_last_error() -> str:
+    return lib().sd_last_error().decode()
+
+
+def sd_version() -> str:
+    return lib().sd_version().decode()
+
+
+# ---------------------------------------------------------------- array helpers
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _as_arg(x, dtype):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor of n x 3 values."""
+    if _is_torch(x):
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.float32
+        t = x.detach()
+        if t.dtype != want or not t.is_contiguous():
+            t = t.to(want).contiguous()
+        return t.data_ptr(), int(t.is_cuda), t
+    a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
+    return a.ctypes.data, 0, a
+
+
+def _out_like(x, n, dtype):
+    if _is_torch(x):
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.float32
+        t = torch.empty((n, 3), dtype=want, device=x.device)
+        return t.data_ptr(), int(t.is_cuda), t
+    a = np.empty((n, 3), dtype=dtype)
+    return a.ctypes.data, 0, a
+
+
+def _dtype_of(x):
+    if _is_torch(x):
+        import torch
+        return np.float32 if x.dtype == torch.float32 else np.float64
+    return np.float32 if np.asarray(x).dtype == np.float32 else np.float64
+
+
+def _torch_allocator(device: int):
+    """Allocator callbacks backed by torch's CUDA caching allocator."""
+    import torch
+
+    def _alloc(nbytes, ctx):
+        try:
+            s = torch.cuda.current_stream(device)
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, s)
+        except Exception:
+            return None
+
+    def _free(ptr, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:
+            pass
+
+    return L.ALLOC_FN(_alloc), L.FREE_FN(_free)
+
+
+def _make_config(n=0, a=1.0, eta=1.0, tensor="rpy", prec="fp32c", r_near=None, rep_eps=0.0, rep_rc=None,
+                 gravity=(0.0, 0.0, 0.0), device=0, stream=None, torch_allocator=False):
+    cfg = sd_config_init()
+    cfg.n = int(n)
+    cfg.a = float(a)
+    cfg.eta = float(eta)
+    cfg.tensor = TENSORS[tensor] if isinstance(tensor, str) else int(tensor)
+    cfg.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    cfg.r_near = float(r_near) if r_near else 2.5 * float(a)
+    cfg.rep_eps = float(rep_eps)
+    cfg.rep_rc = float(rep_rc) if rep_rc else 2.5 * float(a)
+    for d in range(3):
+        cfg.gravity[d] = float(gravity[d])
+    cfg.device = int(device)
+    keep = ()
+    if stream == "torch":
+        import torch
+        cfg.stream = torch.cuda.current_stream(device).cuda_stream
+    elif stream is not None:
+        cfg.stream = int(stream)
+    if torch_allocator:
+        fa, ff = _torch_allocator(int(device))
+        cfg.alloc, cfg.free = fa, ff
+        keep = (fa, ff)
+    return cfg, keep
+
+
+# ---------------------------------------------------------------- System
+
+class System:
+    """A system of n spheres: positions (FP64 state), per-particle forces, and the
+    all-pairs mobility on the GPU.  Arrays are n x 3; numpy arrays are host
+    memory, CUDA torch tensors device memory."""
+
+    def __init__(self, n, a=1.0, eta=1.0, tensor="rpy", prec="fp32c", r_near=None, rep_eps=0.0, rep_rc=None,
+                 gravity=(0.0, 0.0, 0.0), device=0, stream=None, torch_allocator=False):
+        self.cfg, self._keep = _make_config(n, a, eta, tensor, prec, r_near, rep_eps, rep_rc, gravity, device,
+                                            stream, torch_allocator)
+        self.n = int(n)
+        self.h = sd_create(self.cfg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_positions(self, x):
+        p, dev, _k = _as_arg(x, np.float64)
+        sd_set_positions(self.h, p, dev)
+
+    def get_positions(self, out=None):
+        if out is None:
+            out = np.empty((self.n, 3))
+        p, dev, _k = _as_arg(out, np.float64)
+        sd_get_positions(self.h, p, dev)
+        return out
+
+    def set_forces(self, f):
+        p, dev, _k = _as_arg(f, np.float64)
+        sd_set_forces(self.h, p, dev)
+
+    def mobility_apply(self, F):
+        dt = _dtype_of(F)
+        pf, dev, _kf = _as_arg(F, dt)
+        pv, devv, V = _out_like(F, self.n, dt)
+        sd_mobility_apply(self.h, pf, pv, SD_DTYPE_F32 if dt == np.float32 else SD_DTYPE_F64, dev)
+        return V
+
+    def step(self, dt, nsteps=1):
+        sd_step(self.h, dt, nsteps)
+
+    def synchronize(self):
+        sd_synchronize(self.h)
+
+    def vjp(self, F, W):
+        dt = _dtype_of(F)
+        pf, dev, _kf = _as_arg(F, dt)
+        pw, _, _kw = _as_arg(W, dt)
+        pgx, _, gX = _out_like(F, self.n, dt)
+        pgf, _, gF = _out_like(F, self.n, dt)
+        sd_mobility_vjp(self.h, pf, pw, pgx, pgf, SD_DTYPE_F32 if dt == np.float32 else SD_DTYPE_F64, dev)
+        return gX, gF
+
+    def adjoint(self, dt, nsteps, ckpt_every, gxT):
+        pg, dev, _kg = _as_arg(gxT, np.float64)
+        p0, _, gx0 = _out_like(gxT, self.n, np.float64)
+        pF, _, gF = _out_like(gxT, self.n, np.float64)
+        sd_adjoint(self.h, dt, nsteps, ckpt_every, pg, p0, pF, dev)
+        return gx0, gF
+
+    def profile(self, on=True):
+        _check(lib().sd_profile(self.h, int(on)), "sd_profile")
+
+    def profile_read(self, kernel):
+        ms = ctypes.c_double()
+        cnt = ctypes.c_int64()
+        _check(lib().sd_profile_read(self.h, int(kernel), ctypes.byref(ms), ctypes.byref(cnt)), "sd_profile_read")
+        return ms.value, cnt.value
+
+    def launch_count(self) -> int:
+        return int(lib().sd_launch_count(self.h))
+
+    def set_watchdog(self, iterations):
+        _check(lib().sd_set_watchdog(self.h, int(iterations)), "sd_set_watchdog")
+
+
+class Batch:
+    """Independent clusters (CSR offsets, sizes 0..256) stepped by one persistent
+    kernel launch per Euler step."""
+
+    def __init__(self, offsets, a=1.0, eta=1.0, tensor="rpy", prec="fp32c", gravity=(0.0, 0.0, 0.0), device=0,
+                 stream=None, torch_allocator=False):
+        self.cfg, self._keep = _make_config(0, a, eta, tensor, prec, None, 0.0, None, gravity, device, stream,
+                                            torch_allocator)
+        self.offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+        self.P = int(self.offsets[-1]) if self.offsets.size else 0
+        self.b = sd_batch_create(self.cfg, self.offsets)
+
+    def close(self):
+        if getattr(self, "b", None):
+            sd_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_positions(self, x):
+        p, dev, _k = _as_arg(x, np.float64)
+        sd_batch_set_positions(self.b, p, dev)
+
+    def get_positions(self, out=None):
+        if out is None:
+            out = np.empty((self.P, 3))
+        p, dev, _k = _as_arg(out, np.float64)
+        sd_batch_get_positions(self.b, p, dev)
+        return out
+
+    def set_forces(self, f):
+        p, dev, _k = _as_arg(f, np.float64)
+        sd_batch_set_forces(self.b, p, dev)
+
+    def step(self, dt, nsteps=1):
+        sd_step_batched(self.b, dt, nsteps)
+
+    def autotune(self) -> int:
+        return sd_batch_autotune(self.b)
+
+    def synchronize(self):
+        _check(lib().sd_batch_synchronize(self.b), "sd_batch_synchronize")
+
+    def profile(self, on=True):
+        _check(lib().sd_batch_profile(self.b, int(on)), "sd_batch_profile")
+
+    def profile_read(self, kernel=SD_KERNEL_BATCHED):
+        ms = ctypes.c_double()
+        cnt = ctypes.c_int64()
+        _check(lib().sd_batch_profile_read(self.b, int(kernel), ctypes.byref(ms), ctypes.byref(cnt)),
+               "sd_batch_profile_read")
+        return ms.value, cnt.value
+
+    def launch_count(self) -> int:
+        return int(lib().sd_batch_launch_count(self.b))

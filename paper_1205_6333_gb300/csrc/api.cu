@@ -1,0 +1,651 @@
+// api.cu -- the C ABI of include/sd.h for single systems: handle life cycle,
+// argument checks, buffers, error reporting, CUDA-graph replay of Euler steps
+// (Sec. 3.1), the adjoint sweep, and the per-kernel event profiler.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sd_internal.h"
+
+namespace sd {
+
+static thread_local std::string g_last_error;
+
+sd_status set_error(sd_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+sd_status cuda_status(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return set_error(SD_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    return set_error(SD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------- profiler
+
+void prof_begin(sd_handle *h, int kind, cudaStream_t st) {
+    Profiler &p = h->prof;
+    if (!p.on || h->capturing || p.npending >= Profiler::kMaxPending) return;
+    const int k = p.npending;
+    if (k >= p.nevents) {
+        cudaEventCreate(&p.ev0[k]);
+        cudaEventCreate(&p.ev1[k]);
+        p.nevents = k + 1;
+    }
+    p.kind[k] = kind;
+    cudaEventRecord(p.ev0[k], st);
+}
+
+void prof_end(sd_handle *h, int kind, cudaStream_t st) {
+    Profiler &p = h->prof;
+    if (!p.on || h->capturing || p.npending >= Profiler::kMaxPending) return;
+    (void)kind;
+    cudaEventRecord(p.ev1[p.npending], st);
+    ++p.npending;
+}
+
+static cudaError_t prof_collect(Profiler &p) {
+    for (int k = 0; k < p.npending; ++k) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(p.ev1[k]);
+        if (e != cudaSuccess) return e;
+        e = cudaEventElapsedTime(&ms, p.ev0[k], p.ev1[k]);
+        if (e != cudaSuccess) return e;
+        p.ms[p.kind[k]] += ms;
+        p.launches[p.kind[k]] += 1;
+    }
+    p.npending = 0;
+    return cudaSuccess;
+}
+
+static void prof_destroy(Profiler &p) {
+    for (int k = 0; k < p.nevents; ++k) {
+        cudaEventDestroy(p.ev0[k]);
+        cudaEventDestroy(p.ev1[k]);
+    }
+    p.nevents = p.npending = 0;
+}
+
+// ---------------------------------------------------------------- memory
+
+static void *dalloc(sd_handle *h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (h->al.alloc) return h->al.alloc(bytes, h->al.ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void dfree(sd_handle *h, void *p) {
+    if (!p) return;
+    if (h->al.free)
+        h->al.free(p, h->al.ctx);
+    else
+        cudaFree(p);
+}
+
+template <typename T>
+static bool dalloc_t(sd_handle *h, T *&p, size_t count) {
+    p = static_cast<T *>(dalloc(h, count * sizeof(T)));
+    return p != nullptr;
+}
+
+static size_t v4size(const sd_handle *h) { return h->mode == MODE_FP64 ? sizeof(dbl4) : sizeof(float4); }
+
+// ---------------------------------------------------------------- device status
+
+static sd_status status_from_bits(int bits) {
+    if (bits & DEV_ERR_TIMEOUT) return set_error(SD_ERR_TIMEOUT, "a bounded device-side wait timed out");
+    if (bits & DEV_ERR_QUEUE) return set_error(SD_ERR_TIMEOUT, "batched work queue inconsistent");
+    if (bits & DEV_ERR_COINCIDENT)
+        return set_error(SD_ERR_COINCIDENT, "two distinct particles at zero separation (RP/Oseen tensor undefined)");
+    if (bits & DEV_ERR_NONFINITE) return set_error(SD_ERR_NONFINITE, "non-finite value in positions or forces");
+    return SD_OK;
+}
+
+// Synchronise the stream, read and clear the device error word.
+static sd_status sync_check(sd_handle *h) {
+    SD_CUDA(cudaStreamSynchronize(h->stream));
+    int bits = 0;
+    SD_CUDA(cudaMemcpy(&bits, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bits) SD_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+    return status_from_bits(bits);
+}
+
+static sd_status launch_check(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) return cuda_status(e, what);
+    return SD_OK;
+}
+
+// ---------------------------------------------------------------- one Euler step
+
+// x_out = x_in + dt mu(x_in) F(x_in); the cell-list build also writes the mirror of x_in.
+static cudaError_t launch_step(sd_handle *h, cudaStream_t st, double dt, const double *x_in, double *x_out) {
+    cudaError_t e = launch_build_cells(h, st, x_in, h->posm);
+    if (e == cudaSuccess && !h->forces_const) e = launch_forces_rep(h, st, x_in);
+    if (e == cudaSuccess) e = launch_dense(h, st, h->posm, h->frcm, h->part);
+    if (e == cudaSuccess) e = launch_epilogue(h, st, OUT_EULER, x_in, h->posm, h->F64, h->frcm, nullptr, dt, x_out);
+    return e;
+}
+
+static void drop_graphs(sd_handle *h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->g_steps = 0;
+}
+
+constexpr int kGraphSteps = 16;   // steps per captured graph (even: ends on the starting buffer)
+
+static sd_status capture_steps(sd_handle *h, double dt, int cur) {
+    drop_graphs(h);
+    cudaGraph_t graph = nullptr;
+    SD_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    const int64_t l0 = h->launches;
+    cudaError_t e = cudaSuccess;
+    int c = cur;
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+        e = launch_step(h, h->cap, dt, h->x64[c], h->x64[1 - c]);
+        c = 1 - c;
+    }
+    h->capturing = false;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
+    h->g_kernels = h->launches - l0;
+    h->launches = l0;
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_status(e, "capture of Euler steps");
+    }
+    if (e2 != cudaSuccess) return cuda_status(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate");
+    h->g_steps = kGraphSteps;
+    h->g_dt = dt;
+    h->g_cur = cur;
+    return SD_OK;
+}
+
+}  // namespace sd
+
+using namespace sd;
+
+extern "C" {
+
+const char *sd_last_error(void) { return g_last_error.c_str(); }
+
+const char *sd_version(void) { return "sd-gb300 1.0 (sm_103a)"; }
+
+void sd_config_init(sd_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->a = 1.0;
+    cfg->eta = 1.0;
+    cfg->tensor = SD_TENSOR_RPY;
+    cfg->prec = SD_PREC_FP32C;
+    cfg->r_near = 2.5;
+    cfg->rep_rc = 2.5;
+}
+
+static sd_status validate_common(const sd_config *cfg) {
+    if (!cfg) return set_error(SD_ERR_ARG, "cfg is NULL");
+    if (!(cfg->a > 0.0) || !std::isfinite(cfg->a)) return set_error(SD_ERR_ARG, "radius a must be finite and > 0");
+    if (!(cfg->eta > 0.0) || !std::isfinite(cfg->eta)) return set_error(SD_ERR_ARG, "viscosity eta must be > 0");
+    if (cfg->tensor < 0 || cfg->tensor > 2) return set_error(SD_ERR_ARG, "unknown tensor");
+    if (cfg->prec < 0 || cfg->prec > 2) return set_error(SD_ERR_ARG, "unknown precision");
+    for (int d = 0; d < 3; ++d) {
+        if (cfg->box[d] < 0.0 || !std::isfinite(cfg->box[d])) return set_error(SD_ERR_ARG, "box must be >= 0");
+        if (cfg->box[d] > 0.0)
+            return set_error(SD_ERR_UNSUPPORTED, "periodic boxes (nearest image) are not implemented in this build");
+        if (!std::isfinite(cfg->gravity[d])) return set_error(SD_ERR_ARG, "gravity must be finite");
+    }
+    if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
+        return set_error(SD_ERR_ARG, "alloc and free callbacks must be given together");
+    return SD_OK;
+}
+
+sd_status sd_create(const sd_config *cfg, sd_handle **out) {
+    if (!out) return set_error(SD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    sd_status s = validate_common(cfg);
+    if (s != SD_OK) return s;
+    if (cfg->n < 0 || cfg->n > (1 << 24)) return set_error(SD_ERR_ARG, "n must be in [0, 2^24]");
+    const double a = cfg->a;
+    const double r_near = cfg->r_near > 0.0 ? cfg->r_near : 2.5 * a;
+    if (!(r_near >= 2.2 * a) || !std::isfinite(r_near)) return set_error(SD_ERR_ARG, "r_near must be >= 2.2 a");
+    const double rep_rc = cfg->rep_rc > 0.0 ? cfg->rep_rc : 2.5 * a;
+    if (!std::isfinite(cfg->rep_eps) || !std::isfinite(rep_rc)) return set_error(SD_ERR_ARG, "repulsion parameters");
+
+    sd_handle *h = new (std::nothrow) sd_handle();
+    if (!h) return set_error(SD_ERR_OOM, "host allocation");
+    h->cfg = *cfg;
+    h->n = cfg->n;
+    h->npad = ((cfg->n + kPadTo - 1) / kPadTo) * kPadTo;
+    h->mode = cfg->prec == SD_PREC_FP64 ? MODE_FP64 : (cfg->prec == SD_PREC_FP32 ? MODE_FP32 : MODE_FP32C);
+    h->tensor = cfg->tensor;
+    h->device = cfg->device;
+    h->stream = static_cast<cudaStream_t>(cfg->stream);
+    h->al.alloc = cfg->alloc;
+    h->al.free = cfg->free;
+    h->al.ctx = cfg->alloc_ctx;
+    h->r_near = r_near;
+    h->rep_rc = rep_rc;
+    h->forces_const = (cfg->rep_eps == 0.0);
+
+    PairConst &pc = h->pc;
+    pc.a = a;
+    pc.two_a = 2.0 * a;
+    pc.mu0 = 1.0 / (6.0 * 3.14159265358979323846 * cfg->eta * a);
+    pc.r2min_d = 4.0 * a * a;
+    pc.c1_d = 0.75 * a;
+    pc.c3_d = 0.5 * a * a * a;
+    pc.m3c3_d = -1.5 * a * a * a;
+    pc.r2min_f = static_cast<float>(pc.r2min_d);
+    pc.c1_f = static_cast<float>(pc.c1_d);
+    pc.c3_f = static_cast<float>(pc.c3_d);
+    pc.m3c3_f = static_cast<float>(pc.m3c3_d);
+
+    auto fail = [&](sd_status st, const std::string &m) {
+        sd_destroy(h);
+        return set_error(st, m);
+    };
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail(SD_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    int major = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return fail(SD_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
+    e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(SD_ERR_CUDA, "stream creation");
+
+    const size_t n3 = 3 * static_cast<size_t>(std::max(h->n, 1));
+    const size_t np = static_cast<size_t>(std::max(h->npad, kPadTo));
+    const size_t vb = v4size(h);
+    bool ok = dalloc_t(h, h->d_err, 1);
+    for (int b = 0; b < 2 && ok; ++b) ok = dalloc_t(h, h->x64[b], n3);
+    h->posm = ok ? dalloc(h, np * vb) : nullptr;
+    ok = ok && h->posm;
+    ok = ok && dalloc_t(h, h->fext64, n3) && dalloc_t(h, h->F64, n3) && dalloc_t(h, h->Fa64, n3) &&
+         dalloc_t(h, h->Wa64, n3);
+    if (ok) {
+        h->frcm = dalloc(h, np * vb);
+        h->frcam = dalloc(h, np * vb);
+        h->wam = dalloc(h, np * vb);
+        ok = h->frcm && h->frcam && h->wam;
+    }
+    if (!ok) return fail(SD_ERR_OOM, "device allocation of particle buffers");
+
+    // cell list
+    CellList &c = h->cl;
+    c.h = std::max(r_near, h->forces_const ? 0.0 : rep_rc);
+    c.inv_h = 1.0 / c.h;
+    int H = 1024;
+    while (H < 2 * h->n) H <<= 1;
+    c.H = H;
+    c.nblk = (H + 4095) / 4096;
+    ok = dalloc_t(h, c.cell, n3 / 3) && dalloc_t(h, c.key, n3 / 3) && dalloc_t(h, c.cnt, H) &&
+         dalloc_t(h, c.fill, H) && dalloc_t(h, c.start, H + 1) && dalloc_t(h, c.bsum, c.nblk) &&
+         dalloc_t(h, c.sorted, n3 / 3);
+    if (!ok) return fail(SD_ERR_OOM, "device allocation of the cell list");
+
+    if (h->n > 0) {
+        e = dense_setup(h);
+        if (e == cudaSuccess) e = vjp_setup(h);
+        if (e != cudaSuccess) return fail(SD_ERR_CUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
+        const int slots = std::max(h->geom.maxSlots, h->geomv.maxSlots);
+        h->part_bytes = static_cast<size_t>(slots) * 3 * h->npad * sizeof(double);
+        h->part2_bytes = static_cast<size_t>(h->geomv.maxSlots) * 3 * h->npad * sizeof(double);
+        h->part = static_cast<double *>(dalloc(h, h->part_bytes));
+        h->part2 = static_cast<double *>(dalloc(h, h->part2_bytes));
+        if (!h->part || !h->part2) return fail(SD_ERR_OOM, "device allocation of partial sums");
+    }
+
+    // zero everything that padding or defaults rely on
+    cudaStream_t st = h->stream;
+    e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->posm, 0, np * vb, st);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(h->x64[b], 0, n3 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->frcm, 0, np * vb, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->frcam, 0, np * vb, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->wam, 0, np * vb, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->fext64, 0, n3 * sizeof(double), st);
+    if (e == cudaSuccess) e = launch_stage_forces(h, st, nullptr, SD_DTYPE_F64, 1, h->F64, h->frcm);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(SD_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+    *out = h;
+    return SD_OK;
+}
+
+void sd_destroy(sd_handle *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    prof_destroy(h->prof);
+    for (int b = 0; b < 2; ++b) dfree(h, h->x64[b]);
+    dfree(h, h->posm);
+    void *bufs[] = {h->fext64, h->F64, h->frcm, h->Fa64, h->frcam, h->Wa64, h->wam, h->part, h->part2,
+                    h->cl.cell, h->cl.key, h->cl.cnt, h->cl.fill, h->cl.start, h->cl.bsum, h->cl.sorted,
+                    h->ckpt, h->seg, h->lam, h->gFacc, h->d_err};
+    for (void *p : bufs) dfree(h, p);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+}
+
+sd_status sd_set_positions(sd_handle *h, const double *xyz, int on_device) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    if (!xyz && h->n > 0) return set_error(SD_ERR_ARG, "positions pointer is NULL");
+    cudaSetDevice(h->device);
+    if (!on_device) {
+        for (size_t k = 0; k < 3 * static_cast<size_t>(h->n); ++k)
+            if (!std::isfinite(xyz[k])) return set_error(SD_ERR_NONFINITE, "non-finite position");
+    }
+    if (h->n > 0) {
+        SD_CUDA(cudaMemcpyAsync(h->x64[h->cur], xyz, 3 * sizeof(double) * h->n,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        sd_status s = launch_check(launch_stage_pos(h, h->stream, h->x64[h->cur], h->posm), "stage positions");
+        if (s != SD_OK) return s;
+    }
+    h->pos_set = true;
+    h->cells_valid = false;
+    return on_device ? SD_OK : sync_check(h);
+}
+
+sd_status sd_get_positions(sd_handle *h, double *xyz, int on_device) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    if (!xyz && h->n > 0) return set_error(SD_ERR_ARG, "positions pointer is NULL");
+    if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
+    cudaSetDevice(h->device);
+    if (h->n > 0)
+        SD_CUDA(cudaMemcpyAsync(xyz, h->x64[h->cur], 3 * sizeof(double) * h->n,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    return on_device ? SD_OK : sync_check(h);
+}
+
+sd_status sd_set_forces(sd_handle *h, const double *f, int on_device) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    if (!f && h->n > 0) return set_error(SD_ERR_ARG, "forces pointer is NULL");
+    cudaSetDevice(h->device);
+    if (!on_device) {
+        for (size_t k = 0; k < 3 * static_cast<size_t>(h->n); ++k)
+            if (!std::isfinite(f[k])) return set_error(SD_ERR_NONFINITE, "non-finite force");
+    }
+    if (h->n > 0) {
+        SD_CUDA(cudaMemcpyAsync(h->fext64, f, 3 * sizeof(double) * h->n,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        sd_status s =
+            launch_check(launch_stage_forces(h, h->stream, nullptr, SD_DTYPE_F64, 1, h->F64, h->frcm), "stage forces");
+        if (s != SD_OK) return s;
+    }
+    return on_device ? SD_OK : sync_check(h);
+}
+
+sd_status sd_synchronize(sd_handle *h) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    cudaSetDevice(h->device);
+    return sync_check(h);
+}
+
+// Device staging buffers for host-pointer calls.
+static sd_status host_io(sd_handle *h, void *&in, void *&out) {
+    const size_t bytes = 3 * sizeof(double) * static_cast<size_t>(std::max(h->n, 1));
+    if (!h->seg || h->seg_bytes < 2 * bytes) {
+        dfree(h, h->seg);
+        h->seg = static_cast<double *>(dalloc(h, 2 * bytes));
+        h->seg_bytes = h->seg ? 2 * bytes : 0;
+        if (!h->seg) return set_error(SD_ERR_OOM, "device allocation of staging buffers");
+    }
+    in = h->seg;
+    out = reinterpret_cast<char *>(h->seg) + bytes;
+    return SD_OK;
+}
+
+static sd_status ensure_cells(sd_handle *h) {
+    if (h->cells_valid) return SD_OK;
+    sd_status s = launch_check(launch_build_cells(h, h->stream, h->x64[h->cur], h->posm), "cell list");
+    if (s == SD_OK) h->cells_valid = true;
+    return s;
+}
+
+sd_status sd_mobility_apply(sd_handle *h, const void *F, void *V, int dtype, int on_device) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    if (dtype != SD_DTYPE_F32 && dtype != SD_DTYPE_F64) return set_error(SD_ERR_ARG, "dtype must be F32 or F64");
+    if (h->n > 0 && (!F || !V)) return set_error(SD_ERR_ARG, "F or V is NULL");
+    if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
+    if (h->n == 0) return SD_OK;
+    cudaSetDevice(h->device);
+    const size_t es = dtype == SD_DTYPE_F32 ? sizeof(float) : sizeof(double);
+    const size_t bytes = 3 * es * h->n;
+    const void *Fd = F;
+    void *Vd = V;
+    if (!on_device) {
+        void *in = nullptr, *out = nullptr;
+        sd_status s = host_io(h, in, out);
+        if (s != SD_OK) return s;
+        SD_CUDA(cudaMemcpyAsync(in, F, bytes, cudaMemcpyHostToDevice, h->stream));
+        Fd = in;
+        Vd = out;
+    }
+    sd_status s = launch_check(launch_stage_forces(h, h->stream, Fd, dtype, 0, h->Fa64, h->frcam), "stage F");
+    if (s == SD_OK) s = ensure_cells(h);
+    if (s == SD_OK) s = launch_check(launch_dense(h, h->stream, h->posm, h->frcam, h->part), "dense kernel");
+    if (s == SD_OK)
+        s = launch_check(launch_epilogue(h, h->stream, dtype == SD_DTYPE_F32 ? OUT_F32 : OUT_F64, h->x64[h->cur],
+                                         h->posm, h->Fa64, h->frcam, Vd, 0.0, nullptr),
+                         "epilogue");
+    if (s != SD_OK) return s;
+    if (!on_device) {
+        SD_CUDA(cudaMemcpyAsync(V, Vd, bytes, cudaMemcpyDeviceToHost, h->stream));
+        return sync_check(h);
+    }
+    return SD_OK;
+}
+
+sd_status sd_step(sd_handle *h, double dt, int64_t nsteps) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    if (nsteps < 0 || !std::isfinite(dt)) return set_error(SD_ERR_ARG, "nsteps must be >= 0 and dt finite");
+    if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
+    if (h->n == 0 || nsteps == 0) return SD_OK;
+    cudaSetDevice(h->device);
+    int64_t left = nsteps;
+    if (!h->prof.on) {
+        while (left >= kGraphSteps) {
+            if (!h->gexec || h->g_dt != dt || h->g_cur != h->cur) {
+                sd_status s = capture_steps(h, dt, h->cur);
+                if (s != SD_OK) return s;
+            }
+            SD_CUDA(cudaGraphLaunch(h->gexec, h->stream));
+            h->launches += h->g_kernels;
+            left -= kGraphSteps;   // even count: the state ends in buffer h->cur again
+        }
+    }
+    for (; left > 0; --left) {
+        const int c = h->cur;
+        sd_status s = launch_check(launch_step(h, h->stream, dt, h->x64[c], h->x64[1 - c]), "Euler step");
+        if (s != SD_OK) return s;
+        h->cur = 1 - c;
+    }
+    h->cells_valid = false;
+    return SD_OK;
+}
+
+sd_status sd_mobility_vjp(sd_handle *h, const void *F, const void *W, void *gX, void *gF, int dtype, int on_device) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    if (dtype != SD_DTYPE_F32 && dtype != SD_DTYPE_F64) return set_error(SD_ERR_ARG, "dtype must be F32 or F64");
+    if (h->n > 0 && (!F || !W || (!gX && !gF))) return set_error(SD_ERR_ARG, "null argument");
+    if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
+    if (h->n == 0) return SD_OK;
+    cudaSetDevice(h->device);
+    const size_t es = dtype == SD_DTYPE_F32 ? sizeof(float) : sizeof(double);
+    const size_t bytes = 3 * es * h->n;
+    const void *Fd = F, *Wd = W;
+    void *gXd = gX, *gFd = gF;
+    if (!on_device) {
+        // four n x 3 arrays: F, W in; gX, gF out
+        const size_t need = 4 * 3 * sizeof(double) * static_cast<size_t>(h->n);
+        if (!h->seg || h->seg_bytes < need) {
+            dfree(h, h->seg);
+            h->seg = static_cast<double *>(dalloc(h, need));
+            h->seg_bytes = h->seg ? need : 0;
+            if (!h->seg) return set_error(SD_ERR_OOM, "device allocation of staging buffers");
+        }
+        char *b = reinterpret_cast<char *>(h->seg);
+        SD_CUDA(cudaMemcpyAsync(b, F, bytes, cudaMemcpyHostToDevice, h->stream));
+        SD_CUDA(cudaMemcpyAsync(b + bytes, W, bytes, cudaMemcpyHostToDevice, h->stream));
+        Fd = b;
+        Wd = b + bytes;
+        gXd = gX ? b + 2 * bytes : nullptr;
+        gFd = gF ? b + 3 * bytes : nullptr;
+    }
+    sd_status s = launch_check(launch_stage_forces(h, h->stream, Fd, dtype, 0, h->Fa64, h->frcam), "stage F");
+    if (s == SD_OK) s = launch_check(launch_stage_forces(h, h->stream, Wd, dtype, 0, h->Wa64, h->wam), "stage W");
+    if (s == SD_OK) s = ensure_cells(h);
+    if (s == SD_OK)
+        s = launch_check(launch_vjp_dense(h, h->stream, h->posm, h->frcam, h->wam, h->part, h->part2),
+                         "vjp kernel");
+    if (s == SD_OK)
+        s = launch_check(launch_vjp_epilogue(h, h->stream, h->x64[h->cur], h->posm, h->Fa64, h->frcam,
+                                             h->Wa64, h->wam, dtype, gXd, gFd, 0.0, nullptr, nullptr),
+                         "vjp epilogue");
+    if (s != SD_OK) return s;
+    if (!on_device) {
+        if (gX) SD_CUDA(cudaMemcpyAsync(gX, gXd, bytes, cudaMemcpyDeviceToHost, h->stream));
+        if (gF) SD_CUDA(cudaMemcpyAsync(gF, gFd, bytes, cudaMemcpyDeviceToHost, h->stream));
+        return sync_check(h);
+    }
+    return SD_OK;
+}
+
+sd_status sd_adjoint(sd_handle *h, double dt, int64_t nsteps, int32_t ckpt_every, const double *gxT, double *gx0,
+                     double *gF, int on_device) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    if (nsteps < 0 || ckpt_every < 1 || !std::isfinite(dt)) return set_error(SD_ERR_ARG, "nsteps, ckpt_every or dt");
+    if (h->n > 0 && (!gxT || !gx0 || !gF)) return set_error(SD_ERR_ARG, "null argument");
+    if (!h->forces_const) return set_error(SD_ERR_UNSUPPORTED, "adjoint with soft repulsion is not implemented");
+    if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
+    if (h->n == 0) return SD_OK;
+    cudaSetDevice(h->device);
+    cudaStream_t st = h->stream;
+    const size_t n3 = 3 * static_cast<size_t>(h->n);
+    const size_t xb = n3 * sizeof(double);
+    const size_t mb = static_cast<size_t>(h->npad) * v4size(h);
+    const int64_t K = ckpt_every;
+    const int64_t nck = nsteps / K + 1;
+    // storage: checkpoints, one segment of positions + mirrors, lambda, gF accumulator
+    const size_t ck_need = static_cast<size_t>(nck) * xb;
+    if (!h->ckpt || h->ckpt_bytes < ck_need) {
+        dfree(h, h->ckpt);
+        h->ckpt = static_cast<double *>(dalloc(h, ck_need));
+        h->ckpt_bytes = h->ckpt ? ck_need : 0;
+        if (!h->ckpt) return set_error(SD_ERR_OOM, "device allocation of checkpoints");
+    }
+    const size_t seg_need = static_cast<size_t>(K) * xb;
+    if (!h->seg || h->seg_bytes < seg_need) {
+        dfree(h, h->seg);
+        h->seg = static_cast<double *>(dalloc(h, seg_need));
+        h->seg_bytes = h->seg ? seg_need : 0;
+        if (!h->seg) return set_error(SD_ERR_OOM, "device allocation of the recompute segment");
+    }
+    if (!h->lam) {
+        if (!dalloc_t(h, h->lam, n3) || !dalloc_t(h, h->gFacc, n3))
+            return set_error(SD_ERR_OOM, "device allocation of adjoint vectors");
+    }
+    auto segx = [&](int64_t k) { return h->seg + static_cast<size_t>(k) * n3; };
+
+    const int c0 = h->cur;
+    // forward with checkpoints (the state ping-pongs through x64[0], x64[1])
+    SD_CUDA(cudaMemcpyAsync(h->ckpt, h->x64[c0], xb, cudaMemcpyDeviceToDevice, st));
+    int c = c0;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        sd_status ss = launch_check(launch_step(h, st, dt, h->x64[c], h->x64[1 - c]), "adjoint forward");
+        if (ss != SD_OK) return ss;
+        c = 1 - c;
+        if ((s + 1) % K == 0 && (s + 1) / K < nck)
+            SD_CUDA(cudaMemcpyAsync(h->ckpt + static_cast<size_t>((s + 1) / K) * n3, h->x64[c], xb,
+                                    cudaMemcpyDeviceToDevice, st));
+    }
+    // lambda_T
+    if (on_device)
+        SD_CUDA(cudaMemcpyAsync(h->lam, gxT, xb, cudaMemcpyDeviceToDevice, st));
+    else
+        SD_CUDA(cudaMemcpyAsync(h->lam, gxT, xb, cudaMemcpyHostToDevice, st));
+    SD_CUDA(cudaMemsetAsync(h->gFacc, 0, xb, st));
+    const int64_t nseg = (nsteps + K - 1) / K;
+    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+        const int64_t s0 = sg * K, s1 = std::min(s0 + K, nsteps);
+        SD_CUDA(cudaMemcpyAsync(segx(0), h->ckpt + static_cast<size_t>(sg) * n3, xb, cudaMemcpyDeviceToDevice, st));
+        sd_status ss = SD_OK;
+        for (int64_t k = 0; k + 1 < s1 - s0 && ss == SD_OK; ++k)
+            ss = launch_check(launch_step(h, st, dt, segx(k), segx(k + 1)), "recompute");
+        for (int64_t k = s1 - s0 - 1; k >= 0 && ss == SD_OK; --k) {
+            // W = lambda_{n+1} (FP64 copy + mirror); lambda_n = W + dt gX; gF += dt mu W
+            ss = launch_check(launch_stage_forces(h, st, h->lam, SD_DTYPE_F64, 0, h->Wa64, h->wam), "stage lambda");
+            if (ss == SD_OK) ss = launch_check(launch_build_cells(h, st, segx(k), h->posm), "cells");
+            if (ss == SD_OK)
+                ss = launch_check(launch_vjp_dense(h, st, h->posm, h->frcm, h->wam, h->part, h->part2), "vjp");
+            if (ss == SD_OK)
+                ss = launch_check(launch_vjp_epilogue(h, st, segx(k), h->posm, h->F64, h->frcm, h->Wa64, h->wam, -1,
+                                                      nullptr, nullptr, dt, h->lam, h->gFacc),
+                                  "vjp epilogue");
+        }
+        if (ss != SD_OK) return ss;
+    }
+    // restore x0 into the current buffers
+    SD_CUDA(cudaMemcpyAsync(h->x64[c0], h->ckpt, xb, cudaMemcpyDeviceToDevice, st));
+    sd_status ss = launch_check(launch_stage_pos(h, st, h->x64[c0], h->posm), "restore positions");
+    if (ss != SD_OK) return ss;
+    h->cur = c0;
+    h->cells_valid = false;
+    if (on_device) {
+        SD_CUDA(cudaMemcpyAsync(gx0, h->lam, xb, cudaMemcpyDeviceToDevice, st));
+        SD_CUDA(cudaMemcpyAsync(gF, h->gFacc, xb, cudaMemcpyDeviceToDevice, st));
+        return SD_OK;
+    }
+    SD_CUDA(cudaMemcpyAsync(gx0, h->lam, xb, cudaMemcpyDeviceToHost, st));
+    SD_CUDA(cudaMemcpyAsync(gF, h->gFacc, xb, cudaMemcpyDeviceToHost, st));
+    return sync_check(h);
+}
+
+sd_status sd_profile(sd_handle *h, int on) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    cudaSetDevice(h->device);
+    SD_CUDA(cudaStreamSynchronize(h->stream));
+    Profiler &p = h->prof;
+    p.on = on != 0;
+    p.npending = 0;
+    for (int k = 0; k < SD_KERNEL_COUNT; ++k) {
+        p.ms[k] = 0.0;
+        p.launches[k] = 0;
+    }
+    return SD_OK;
+}
+
+sd_status sd_profile_read(sd_handle *h, int kernel, double *ms, int64_t *launches) {
+    if (!h || kernel < 0 || kernel >= SD_KERNEL_COUNT) return set_error(SD_ERR_ARG, "bad handle or kernel id");
+    cudaSetDevice(h->device);
+    SD_CUDA(prof_collect(h->prof));
+    if (ms) *ms = h->prof.ms[kernel];
+    if (launches) *launches = h->prof.launches[kernel];
+    return SD_OK;
+}
+
+int64_t sd_launch_count(const sd_handle *h) { return h ? h->launches : 0; }
+
+sd_status sd_set_watchdog(sd_handle *h, int64_t iterations) {
+    if (!h || iterations < 1) return set_error(SD_ERR_ARG, "bad handle or iteration limit");
+    h->watchdog = iterations;
+    drop_graphs(h);   // graphs captured the old limit
+    return SD_OK;
+}
+
+}  // extern "C"

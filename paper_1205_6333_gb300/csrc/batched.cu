@@ -1,0 +1,749 @@
+// batched.cu -- many independent clusters, one persistent launch per Euler step.
+//
+// Each cluster c (particles off[c] .. off[c+1]-1, at most 256) evolves by
+//   v_i = mu0 [F_i + sum_{j != i in c} T^(r_i - r_j) F_j],  x_i <- x_i + dt v_i
+// (Sec. 2.2, Eq. rotneMobility; Sec. 3.1, steps 1 and 3).
+//
+// Work distribution: a persistent grid; every warp pops cluster tickets from a
+// global atomic counter (reset by a memset node before each step) and takes the
+// clusters in largest-first order (a longest-processing-time schedule), so the
+// small clusters fill the tail.  A warp stages its cluster in shared memory --
+// FP64 positions minus the cluster's first particle, rounded to FP32, so FP32
+// separations keep full relative precision and no FP64 near-pair pass is needed
+// -- and lane l owns particles l, l+32, ..., l+32(R-1), R = ceil(n/32).
+//
+// The j loop runs over 32-particle chunks in a lane-rotated order
+// (j = 32 jb + ((l + m) mod 32)), so a particle meets itself exactly at m = 0 of
+// its own chunk and that pair is skipped without a per-pair test.  Pairs use the
+// dense kernel's clamped pair term; a running minimum of r^2 flags overlaps
+// (r < 2a), and only then does a second pass replace the clamped terms of the
+// overlapping pairs by their exact values.  FP32C keeps per-lane (hi, lo)
+// accumulators in shared memory and folds each chunk's FP32 partial into them
+// with TwoSum.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sd_internal.h"
+
+namespace sd {
+
+constexpr int kMaxCluster = 256;
+constexpr int kMaxR = kMaxCluster / 32;
+
+struct BatchShape {
+    int warps;        // warps per CTA
+    int ctas_per_sm;  // resident CTAs per SM requested
+};
+
+}  // namespace sd
+
+struct sd_batch {
+    sd_config cfg{};
+    int C = 0, P = 0, maxn = 0;
+    int mode = 0, tensor = 0, device = 0, num_sms = 0;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    sd::Allocator al;
+    sd::PairConst pc{};
+    int32_t *d_off = nullptr, *d_order = nullptr;
+    double *x64 = nullptr, *F64 = nullptr, *fext64 = nullptr;
+    void *frcm = nullptr;
+    unsigned long long *ctr = nullptr;
+    int *d_err = nullptr;
+    bool pos_set = false;
+    std::vector<sd::BatchShape> shapes;
+    int choice = -1;
+    cudaGraphExec_t gexec = nullptr;
+    double g_dt = 0.0;
+    int g_choice = -1;
+    int64_t launches = 0;
+    sd::Profiler prof;
+    long long watchdog = sd::kDefaultWatchdog;
+};
+
+namespace sd {
+
+template <int MODE>
+struct BT {
+    using V4 = float4;
+    using S = float;
+};
+template <>
+struct BT<MODE_FP64> {
+    using V4 = dbl4;
+    using S = double;
+};
+
+struct BatchArgs {
+    const int32_t *off, *order;
+    double *x64;
+    const double *F64;
+    const void *frcm;
+    unsigned long long *ctr;
+    int C;
+    PairConst pc;
+    double dt;
+    int *err;
+};
+
+// Exact pair term (overlap branch included) in the working precision, from zero.
+template <int TENSOR, typename S>
+__device__ __forceinline__ void exact_pair(S dx, S dy, S dz, S fx, S fy, S fz, const PairConst &c, S &ox, S &oy,
+                                           S &oz, bool &coincident) {
+    const S r2 = dx * dx + dy * dy + dz * dz;
+    ox = oy = oz = S(0);
+    if (r2 == S(0)) {
+        if (TENSOR != T_RPY) coincident = true;
+        else { ox = fx; oy = fy; oz = fz; }   // T^(0) = I for the RPY overlap form
+        return;
+    }
+    const S r = sqrt(r2);
+    S A, B;
+    if (TENSOR == T_RPY && r < S(c.two_a)) {
+        A = S(1) - S(9) * r / (S(32) * S(c.a));
+        B = S(3) / (S(32) * S(c.a) * r);
+    } else if (TENSOR == T_OSEEN) {
+        A = S(c.c1_d) / r;
+        B = A / r2;
+    } else {
+        const S ri = S(1) / r, ri2 = ri * ri;
+        A = ri * (S(c.c1_d) + S(c.c3_d) * ri2);
+        B = ri * ri2 * (S(c.c1_d) + S(c.m3c3_d) * ri2);
+    }
+    const S s = B * (dx * fx + dy * fy + dz * fz);
+    ox = A * fx + s * dx;
+    oy = A * fy + s * dy;
+    oz = A * fz + s * dz;
+}
+
+template <int TENSOR, int MODE, int R>
+__device__ __forceinline__ void cluster_compute(const BatchArgs &a, int o, int n, double3 anchor,
+                                                const typename BT<MODE>::V4 *s_pos,
+                                                const typename BT<MODE>::V4 *s_frc, float *s_acc, int lane) {
+    using V4 = typename BT<MODE>::V4;
+    using S = typename BT<MODE>::S;
+    constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
+    constexpr bool COMP = (MODE == MODE_FP32C);
+    S xi[R], yi[R], zi[R], ax[R], ay[R], az[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        // slots beyond n sit far from everything (their results are discarded)
+        const V4 p = s_pos[lane + 32 * k];
+        const bool real = lane + 32 * k < n;
+        xi[k] = real ? S(p.x) : S(-1.0e15);
+        yi[k] = real ? S(p.y) : S(0);
+        zi[k] = real ? S(p.z) : S(0);
+        ax[k] = ay[k] = az[k] = S(0);
+        if (COMP)
+            for (int d = 0; d < 6; ++d) s_acc[(k * 6 + d) * 32 + lane] = 0.0f;
+    }
+    S mn = S(1e30);
+    const int nchunk = (n + 31) >> 5;
+    for (int jb = 0; jb < nchunk; ++jb) {
+        // m = 0: the diagonal slot k == jb meets itself; skip that pair only
+        {
+            const int j = 32 * jb + lane;
+            const V4 p = s_pos[j], f = s_frc[j];
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                if (k == jb) continue;
+                const S dx = xi[k] - p.x, dy = yi[k] - p.y, dz = zi[k] - p.z;
+                mn = fmin(mn, dx * dx + dy * dy + dz * dz);
+                if constexpr (MODE == MODE_FP64)
+                    pair_f64<TD>(xi[k], yi[k], zi[k], p, f, a.pc, ax[k], ay[k], az[k]);
+                else
+                    pair_f32<TD>(xi[k], yi[k], zi[k], p, f, a.pc, ax[k], ay[k], az[k]);
+            }
+        }
+        for (int m = 1; m < 32; ++m) {
+            const int j = 32 * jb + ((lane + m) & 31);
+            const V4 p = s_pos[j], f = s_frc[j];
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                if constexpr (MODE == MODE_FP64) {
+                    const double dx = xi[k] - p.x, dy = yi[k] - p.y, dz = zi[k] - p.z;
+                    mn = fmin(mn, dx * dx + dy * dy + dz * dz);
+                    pair_f64<TD>(xi[k], yi[k], zi[k], p, f, a.pc, ax[k], ay[k], az[k]);
+                } else {
+                    // the clamp in pair_f32 sees the same r^2; track it for the overlap test
+                    const float dx = __fsub_rn(xi[k], p.x), dy = __fsub_rn(yi[k], p.y), dz = __fsub_rn(zi[k], p.z);
+                    mn = fminf(mn, __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
+                    pair_f32<TD>(xi[k], yi[k], zi[k], p, f, a.pc, ax[k], ay[k], az[k]);
+                }
+            }
+        }
+        if constexpr (COMP) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                float *q = s_acc + k * 6 * 32 + lane;
+                float hx = q[0], hy = q[32], hz = q[64], lx = q[96], ly = q[128], lz = q[160];
+                fold2(hx, lx, ax[k]);
+                fold2(hy, ly, ay[k]);
+                fold2(hz, lz, az[k]);
+                q[0] = hx; q[32] = hy; q[64] = hz; q[96] = lx; q[128] = ly; q[160] = lz;
+                ax[k] = ay[k] = az[k] = 0.0f;
+            }
+        }
+    }
+    // per slot: compensated dense sum, exact terms for overlapping pairs (only
+    // when some lane saw r < 2a), self term mu_ii = mu0 I, Euler update in FP64
+    const bool overlap = __any_sync(0xffffffffu, mn < S(a.pc.r2min_d));
+    bool coincident = false;
+    const double m0 = a.pc.mu0, dt = a.dt;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int i = lane + 32 * k;
+        if (i >= n) continue;
+        double V0, V1, V2;
+        if constexpr (COMP) {
+            const float *q = s_acc + k * 6 * 32 + lane;
+            V0 = static_cast<double>(q[0]) + q[96];
+            V1 = static_cast<double>(q[32]) + q[128];
+            V2 = static_cast<double>(q[64]) + q[160];
+        } else {
+            V0 = ax[k];
+            V1 = ay[k];
+            V2 = az[k];
+        }
+        if (overlap) {
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                const V4 p = s_pos[j], f = s_frc[j];
+                S dx, dy, dz;
+                if constexpr (MODE == MODE_FP64) {
+                    dx = xi[k] - p.x; dy = yi[k] - p.y; dz = zi[k] - p.z;
+                } else {
+                    dx = __fsub_rn(xi[k], p.x); dy = __fsub_rn(yi[k], p.y); dz = __fsub_rn(zi[k], p.z);
+                }
+                const S r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < S(a.pc.r2min_d))) continue;
+                S cx = S(0), cy = S(0), cz = S(0);
+                if constexpr (MODE == MODE_FP64)
+                    pair_f64<TD>(xi[k], yi[k], zi[k], p, f, a.pc, cx, cy, cz);
+                else
+                    pair_f32<TD>(xi[k], yi[k], zi[k], p, f, a.pc, cx, cy, cz);
+                S ex, ey, ez;
+                exact_pair<TENSOR, S>(dx, dy, dz, S(f.x), S(f.y), S(f.z), a.pc, ex, ey, ez, coincident);
+                V0 += static_cast<double>(ex) - static_cast<double>(cx);
+                V1 += static_cast<double>(ey) - static_cast<double>(cy);
+                V2 += static_cast<double>(ez) - static_cast<double>(cz);
+            }
+        }
+        const size_t g = static_cast<size_t>(o + i);
+        const double vx = m0 * (V0 + a.F64[3 * g]);
+        const double vy = m0 * (V1 + a.F64[3 * g + 1]);
+        const double vz = m0 * (V2 + a.F64[3 * g + 2]);
+        const double nx = a.x64[3 * g] + dt * vx, ny = a.x64[3 * g + 1] + dt * vy, nz = a.x64[3 * g + 2] + dt * vz;
+        if (!isfinite(nx) || !isfinite(ny) || !isfinite(nz)) atomicOr(a.err, DEV_ERR_NONFINITE);
+        a.x64[3 * g] = nx;
+        a.x64[3 * g + 1] = ny;
+        a.x64[3 * g + 2] = nz;
+    }
+    if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
+    (void)anchor;
+}
+
+template <int TENSOR, int MODE>
+__global__ void batched_kernel(BatchArgs a) {
+    using V4 = typename BT<MODE>::V4;
+    constexpr int stage_bytes = 2 * kMaxCluster * sizeof(V4) + (MODE == MODE_FP32C ? kMaxR * 6 * 32 * 4 : 0);
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned char *mine = smem + static_cast<size_t>(wid) * stage_bytes;
+    V4 *s_pos = reinterpret_cast<V4 *>(mine);
+    V4 *s_frc = s_pos + kMaxCluster;
+    float *s_acc = reinterpret_cast<float *>(s_frc + kMaxCluster);
+    const V4 *frcm = static_cast<const V4 *>(a.frcm);
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(a.ctr, 1ULL);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= static_cast<unsigned long long>(a.C)) break;
+        const int c = a.order[t];
+        const int o = a.off[c];
+        const int n = a.off[c + 1] - o;
+        if (n <= 0) continue;
+        if (n > kMaxCluster) {   // rejected at creation; never reached
+            if (lane == 0) atomicOr(a.err, DEV_ERR_QUEUE);
+            continue;
+        }
+        const double3 anchor = make_double3(a.x64[3 * o], a.x64[3 * o + 1], a.x64[3 * o + 2]);
+        const int R = (n + 31) >> 5;
+        for (int p = lane; p < 32 * R; p += 32) {
+            V4 q, f;
+            if (p < n) {
+                const size_t g = static_cast<size_t>(o + p);
+                q.x = a.x64[3 * g] - anchor.x;
+                q.y = a.x64[3 * g + 1] - anchor.y;
+                q.z = a.x64[3 * g + 2] - anchor.z;
+                f = frcm[g];
+            } else {
+                // padding: far away (and far from the unused i-slots at -1e15), zero force
+                q.x = 1.0e15;
+                q.y = 0;
+                q.z = 0;
+                f.x = f.y = f.z = 0;
+            }
+            q.w = 0;
+            f.w = 0;
+            s_pos[p] = q;
+            s_frc[p] = f;
+        }
+        __syncwarp();
+        switch (R) {
+#define SD_BR(RR) \
+    case RR: cluster_compute<TENSOR, MODE, RR>(a, o, n, anchor, s_pos, s_frc, s_acc, lane); break
+            SD_BR(1); SD_BR(2); SD_BR(3); SD_BR(4); SD_BR(5); SD_BR(6); SD_BR(7); SD_BR(8);
+#undef SD_BR
+            default: break;
+        }
+        __syncwarp();
+    }
+}
+
+template <int MODE>
+static size_t warp_stage_bytes() {
+    return 2 * kMaxCluster * sizeof(typename BT<MODE>::V4) + (MODE == MODE_FP32C ? kMaxR * 6 * 32 * 4 : 0);
+}
+
+static size_t stage_bytes(int mode) {
+    return mode == MODE_FP64 ? warp_stage_bytes<MODE_FP64>() : warp_stage_bytes<MODE_FP32C>();
+}
+
+static void *batched_fn(int tensor, int mode) {
+    if (mode == MODE_FP64) {
+        if (tensor == T_RPY) return reinterpret_cast<void *>(&batched_kernel<T_RPY, MODE_FP64>);
+        if (tensor == T_RP) return reinterpret_cast<void *>(&batched_kernel<T_RP, MODE_FP64>);
+        return reinterpret_cast<void *>(&batched_kernel<T_OSEEN, MODE_FP64>);
+    }
+    if (tensor == T_RPY) return reinterpret_cast<void *>(&batched_kernel<T_RPY, MODE_FP32C>);
+    if (tensor == T_RP) return reinterpret_cast<void *>(&batched_kernel<T_RP, MODE_FP32C>);
+    return reinterpret_cast<void *>(&batched_kernel<T_OSEEN, MODE_FP32C>);
+}
+
+static cudaError_t batch_launch(sd_batch *b, cudaStream_t st, double dt, const BatchShape &sh, bool prof) {
+    cudaError_t e = cudaMemsetAsync(b->ctr, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    BatchArgs a;
+    a.off = b->d_off;
+    a.order = b->d_order;
+    a.x64 = b->x64;
+    a.F64 = b->F64;
+    a.frcm = b->frcm;
+    a.ctr = b->ctr;
+    a.C = b->C;
+    a.pc = b->pc;
+    a.dt = dt;
+    a.err = b->d_err;
+    const size_t smem = static_cast<size_t>(sh.warps) * stage_bytes(b->mode);
+    const int grid = b->num_sms * sh.ctas_per_sm;
+    void *fn = batched_fn(b->tensor, b->mode);
+    int kk = -1;
+    if (prof && b->prof.on && b->prof.npending < Profiler::kMaxPending) {
+        kk = b->prof.npending;
+        if (kk >= b->prof.nevents) {
+            cudaEventCreate(&b->prof.ev0[kk]);
+            cudaEventCreate(&b->prof.ev1[kk]);
+            b->prof.nevents = kk + 1;
+        }
+        b->prof.kind[kk] = SD_KERNEL_BATCHED;
+        cudaEventRecord(b->prof.ev0[kk], st);
+    }
+    void *args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(32 * sh.warps), args, smem, st);
+    if (kk >= 0) {
+        cudaEventRecord(b->prof.ev1[kk], st);
+        ++b->prof.npending;
+    }
+    ++b->launches;
+    return e;
+}
+
+static sd_status batch_sync_check(sd_batch *b) {
+    SD_CUDA(cudaStreamSynchronize(b->stream));
+    int bits = 0;
+    SD_CUDA(cudaMemcpy(&bits, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bits) SD_CUDA(cudaMemset(b->d_err, 0, sizeof(int)));
+    if (bits & (DEV_ERR_TIMEOUT | DEV_ERR_QUEUE)) return set_error(SD_ERR_TIMEOUT, "batched kernel gave up");
+    if (bits & DEV_ERR_COINCIDENT) return set_error(SD_ERR_COINCIDENT, "two distinct particles at zero separation");
+    if (bits & DEV_ERR_NONFINITE) return set_error(SD_ERR_NONFINITE, "non-finite value in positions or forces");
+    return SD_OK;
+}
+
+static void *balloc(sd_batch *b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b->al.alloc) return b->al.alloc(bytes, b->al.ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void bfree(sd_batch *b, void *p) {
+    if (!p) return;
+    if (b->al.free) b->al.free(p, b->al.ctx);
+    else cudaFree(p);
+}
+
+template <typename V4>
+__global__ void batch_stage_forces_kernel(const double *__restrict__ fext, double gx, double gy, double gz,
+                                          double *__restrict__ F, V4 *__restrict__ m, int P, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const double f0 = fext[3 * i] + gx, f1 = fext[3 * i + 1] + gy, f2 = fext[3 * i + 2] + gz;
+    if (!isfinite(f0) || !isfinite(f1) || !isfinite(f2)) atomicOr(err, DEV_ERR_NONFINITE);
+    F[3 * i] = f0;
+    F[3 * i + 1] = f1;
+    F[3 * i + 2] = f2;
+    V4 v;
+    v.x = f0;
+    v.y = f1;
+    v.z = f2;
+    v.w = 0;
+    m[i] = v;
+}
+
+__global__ void batch_check_pos_kernel(const double *__restrict__ x, int P, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * P) return;
+    if (!isfinite(x[i])) atomicOr(err, DEV_ERR_NONFINITE);
+}
+
+static cudaError_t batch_stage_forces(sd_batch *b) {
+    if (b->P == 0) return cudaSuccess;
+    const int nb = (b->P + 255) / 256;
+    const double *g = b->cfg.gravity;
+    if (b->mode == MODE_FP64)
+        batch_stage_forces_kernel<dbl4><<<nb, 256, 0, b->stream>>>(b->fext64, g[0], g[1], g[2], b->F64,
+                                                                   static_cast<dbl4 *>(b->frcm), b->P, b->d_err);
+    else
+        batch_stage_forces_kernel<float4><<<nb, 256, 0, b->stream>>>(b->fext64, g[0], g[1], g[2], b->F64,
+                                                                     static_cast<float4 *>(b->frcm), b->P, b->d_err);
+    ++b->launches;
+    return cudaGetLastError();
+}
+
+static void drop_batch_graph(sd_batch *b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+}
+
+constexpr int kBatchGraphSteps = 16;
+
+static sd_status capture_batch(sd_batch *b, double dt) {
+    drop_batch_graph(b);
+    cudaGraph_t graph = nullptr;
+    SD_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    const int64_t l0 = b->launches;
+    for (int k = 0; k < kBatchGraphSteps && e == cudaSuccess; ++k) e = batch_launch(b, b->cap, dt, b->shapes[b->choice], false);
+    b->launches = l0;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_status(e, "capture of batched steps");
+    }
+    if (e2 != cudaSuccess) return cuda_status(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate");
+    b->g_dt = dt;
+    b->g_choice = b->choice;
+    return SD_OK;
+}
+
+}  // namespace sd
+
+using namespace sd;
+
+extern "C" {
+
+sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t nclusters, sd_batch **out) {
+    if (!out) return set_error(SD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return set_error(SD_ERR_ARG, "cfg is NULL");
+    if (nclusters < 0 || (nclusters > 0 && !offsets)) return set_error(SD_ERR_ARG, "offsets / nclusters");
+    if (!(cfg->a > 0.0) || !(cfg->eta > 0.0) || !std::isfinite(cfg->a) || !std::isfinite(cfg->eta))
+        return set_error(SD_ERR_ARG, "a and eta must be finite and > 0");
+    if (cfg->tensor < 0 || cfg->tensor > 2) return set_error(SD_ERR_ARG, "unknown tensor");
+    if (cfg->prec < 0 || cfg->prec > 2) return set_error(SD_ERR_ARG, "unknown precision");
+    for (int d = 0; d < 3; ++d) {
+        if (cfg->box[d] != 0.0) return set_error(SD_ERR_UNSUPPORTED, "periodic boxes are not implemented for batches");
+        if (!std::isfinite(cfg->gravity[d])) return set_error(SD_ERR_ARG, "gravity must be finite");
+    }
+    if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
+        return set_error(SD_ERR_ARG, "alloc and free callbacks must be given together");
+    if (nclusters > 0 && offsets[0] != 0) return set_error(SD_ERR_ARG, "offsets[0] must be 0");
+    int maxn = 0;
+    for (int c = 0; c < nclusters; ++c) {
+        const int nc = offsets[c + 1] - offsets[c];
+        if (nc < 0 || nc > kMaxCluster) return set_error(SD_ERR_ARG, "cluster sizes must be in [0, 256]");
+        maxn = std::max(maxn, nc);
+    }
+    const int P = nclusters > 0 ? offsets[nclusters] : 0;
+
+    sd_batch *b = new (std::nothrow) sd_batch();
+    if (!b) return set_error(SD_ERR_OOM, "host allocation");
+    b->cfg = *cfg;
+    b->C = nclusters;
+    b->P = P;
+    b->maxn = maxn;
+    b->mode = cfg->prec == SD_PREC_FP64 ? MODE_FP64 : MODE_FP32C;
+    b->tensor = cfg->tensor;
+    b->device = cfg->device;
+    b->stream = static_cast<cudaStream_t>(cfg->stream);
+    b->al.alloc = cfg->alloc;
+    b->al.free = cfg->free;
+    b->al.ctx = cfg->alloc_ctx;
+    const double a = cfg->a;
+    PairConst &pc = b->pc;
+    pc.a = a;
+    pc.two_a = 2 * a;
+    pc.mu0 = 1.0 / (6.0 * 3.14159265358979323846 * cfg->eta * a);
+    pc.r2min_d = 4 * a * a;
+    pc.c1_d = 0.75 * a;
+    pc.c3_d = 0.5 * a * a * a;
+    pc.m3c3_d = -1.5 * a * a * a;
+    pc.r2min_f = static_cast<float>(pc.r2min_d);
+    pc.c1_f = static_cast<float>(pc.c1_d);
+    pc.c3_f = static_cast<float>(pc.c3_d);
+    pc.m3c3_f = static_cast<float>(pc.m3c3_d);
+
+    auto fail = [&](sd_status st, const std::string &m) {
+        sd_batch_destroy(b);
+        return set_error(st, m);
+    };
+    if (cudaSetDevice(b->device) != cudaSuccess) return fail(SD_ERR_CUDA, "cudaSetDevice");
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(SD_ERR_CUDA, "stream");
+    const size_t p3 = 3 * static_cast<size_t>(std::max(P, 1));
+    const size_t vb = b->mode == MODE_FP64 ? sizeof(dbl4) : sizeof(float4);
+    b->d_off = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * (nclusters + 1)));
+    b->d_order = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * std::max(nclusters, 1)));
+    b->x64 = static_cast<double *>(balloc(b, p3 * sizeof(double)));
+    b->F64 = static_cast<double *>(balloc(b, p3 * sizeof(double)));
+    b->fext64 = static_cast<double *>(balloc(b, p3 * sizeof(double)));
+    b->frcm = balloc(b, std::max(P, 1) * vb);
+    b->ctr = static_cast<unsigned long long *>(balloc(b, sizeof(unsigned long long)));
+    b->d_err = static_cast<int *>(balloc(b, sizeof(int)));
+    if (!b->d_off || !b->d_order || !b->x64 || !b->F64 || !b->fext64 || !b->frcm || !b->ctr || !b->d_err)
+        return fail(SD_ERR_OOM, "device allocation of batch buffers");
+
+    // largest-first order (stable in the cluster index)
+    std::vector<int32_t> order(nclusters);
+    for (int c = 0; c < nclusters; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return offsets[x + 1] - offsets[x] > offsets[y + 1] - offsets[y];
+    });
+    cudaStream_t st = b->stream;
+    cudaError_t e = cudaMemcpyAsync(b->d_off, offsets, sizeof(int32_t) * (nclusters + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nclusters > 0)
+        e = cudaMemcpyAsync(b->d_order, order.data(), sizeof(int32_t) * nclusters, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->fext64, 0, p3 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->x64, 0, p3 * sizeof(double), st);
+    if (e == cudaSuccess) e = batch_stage_forces(b);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(SD_ERR_CUDA, std::string("batch initialisation: ") + cudaGetErrorString(e));
+
+    // candidate launch shapes: warps per CTA x resident CTAs per SM that fit
+    void *fn = batched_fn(b->tensor, b->mode);
+    const size_t sb = stage_bytes(b->mode);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(8 * sb)) != cudaSuccess)
+        return fail(SD_ERR_CUDA, "shared-memory opt-in for the batched kernel");
+    for (int w : {4, 8, 2}) {
+        const size_t smem = w * sb;
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * w, smem) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        for (int c = 1; c <= occ; ++c) b->shapes.push_back({w, c});
+    }
+    if (b->shapes.empty()) return fail(SD_ERR_CUDA, "no launch shape fits the device");
+    // default: the shape with the most resident warps (ties: fewer warps per CTA)
+    int best = 0;
+    for (int k = 1; k < static_cast<int>(b->shapes.size()); ++k) {
+        const int wk = b->shapes[k].warps * b->shapes[k].ctas_per_sm;
+        const int wb = b->shapes[best].warps * b->shapes[best].ctas_per_sm;
+        if (wk > wb) best = k;
+    }
+    b->choice = -1;   // autotune on first step
+    (void)best;
+    *out = b;
+    return SD_OK;
+}
+
+void sd_batch_destroy(sd_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_batch_graph(b);
+    for (int k = 0; k < b->prof.nevents; ++k) {
+        cudaEventDestroy(b->prof.ev0[k]);
+        cudaEventDestroy(b->prof.ev1[k]);
+    }
+    void *bufs[] = {b->d_off, b->d_order, b->x64, b->F64, b->fext64, b->frcm, b->ctr, b->d_err};
+    for (void *p : bufs) bfree(b, p);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+sd_status sd_batch_set_positions(sd_batch *b, const double *xyz, int on_device) {
+    if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    if (b->P > 0 && !xyz) return set_error(SD_ERR_ARG, "positions pointer is NULL");
+    cudaSetDevice(b->device);
+    if (!on_device)
+        for (size_t k = 0; k < 3 * static_cast<size_t>(b->P); ++k)
+            if (!std::isfinite(xyz[k])) return set_error(SD_ERR_NONFINITE, "non-finite position");
+    if (b->P > 0) {
+        SD_CUDA(cudaMemcpyAsync(b->x64, xyz, 3 * sizeof(double) * b->P,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+        batch_check_pos_kernel<<<(3 * b->P + 255) / 256, 256, 0, b->stream>>>(b->x64, b->P, b->d_err);
+        ++b->launches;
+        SD_CUDA(cudaGetLastError());
+    }
+    b->pos_set = true;
+    return on_device ? SD_OK : batch_sync_check(b);
+}
+
+sd_status sd_batch_get_positions(sd_batch *b, double *xyz, int on_device) {
+    if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    if (b->P > 0 && !xyz) return set_error(SD_ERR_ARG, "positions pointer is NULL");
+    if (!b->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
+    cudaSetDevice(b->device);
+    if (b->P > 0)
+        SD_CUDA(cudaMemcpyAsync(xyz, b->x64, 3 * sizeof(double) * b->P,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+    return on_device ? SD_OK : batch_sync_check(b);
+}
+
+sd_status sd_batch_set_forces(sd_batch *b, const double *f, int on_device) {
+    if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    if (b->P > 0 && !f) return set_error(SD_ERR_ARG, "forces pointer is NULL");
+    cudaSetDevice(b->device);
+    if (!on_device)
+        for (size_t k = 0; k < 3 * static_cast<size_t>(b->P); ++k)
+            if (!std::isfinite(f[k])) return set_error(SD_ERR_NONFINITE, "non-finite force");
+    if (b->P > 0) {
+        SD_CUDA(cudaMemcpyAsync(b->fext64, f, 3 * sizeof(double) * b->P,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+        SD_CUDA(batch_stage_forces(b));
+    }
+    return on_device ? SD_OK : batch_sync_check(b);
+}
+
+sd_status sd_batch_synchronize(sd_batch *b) {
+    if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    cudaSetDevice(b->device);
+    return batch_sync_check(b);
+}
+
+sd_status sd_batch_autotune(sd_batch *b, int32_t *choice) {
+    if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    if (!b->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
+    cudaSetDevice(b->device);
+    if (b->C == 0 || b->P == 0) {
+        b->choice = 0;
+        if (choice) *choice = 0;
+        return SD_OK;
+    }
+    // time every shape on a scratch copy of the positions (dt = 0 keeps them fixed)
+    cudaEvent_t e0, e1;
+    SD_CUDA(cudaEventCreate(&e0));
+    SD_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best = 0;
+    const int64_t l0 = b->launches;
+    for (int k = 0; k < static_cast<int>(b->shapes.size()); ++k) {
+        const BatchShape &sh = b->shapes[k];
+        cudaError_t e = cudaSuccess;
+        for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = batch_launch(b, b->stream, 0.0, sh, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = batch_launch(b, b->stream, 0.0, sh, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_status(e, "autotune launch");
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = k;
+        }
+    }
+    b->launches = l0;   // tuning launches are not part of the user's work
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->choice = best;
+    drop_batch_graph(b);
+    if (choice) *choice = best;
+    return batch_sync_check(b);
+}
+
+sd_status sd_step_batched(sd_batch *b, double dt, int64_t nsteps) {
+    if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    if (nsteps < 0 || !std::isfinite(dt)) return set_error(SD_ERR_ARG, "nsteps must be >= 0 and dt finite");
+    if (!b->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
+    if (b->C == 0 || b->P == 0 || nsteps == 0) return SD_OK;
+    cudaSetDevice(b->device);
+    if (b->choice < 0) {
+        sd_status s = sd_batch_autotune(b, nullptr);
+        if (s != SD_OK) return s;
+    }
+    int64_t left = nsteps;
+    if (!b->prof.on) {
+        while (left >= kBatchGraphSteps) {
+            if (!b->gexec || b->g_dt != dt || b->g_choice != b->choice) {
+                sd_status s = capture_batch(b, dt);
+                if (s != SD_OK) return s;
+            }
+            SD_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+            b->launches += kBatchGraphSteps;
+            left -= kBatchGraphSteps;
+        }
+    }
+    for (; left > 0; --left) SD_CUDA(batch_launch(b, b->stream, dt, b->shapes[b->choice], true));
+    return SD_OK;
+}
+
+sd_status sd_batch_profile(sd_batch *b, int on) {
+    if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    cudaSetDevice(b->device);
+    SD_CUDA(cudaStreamSynchronize(b->stream));
+    b->prof.on = on != 0;
+    b->prof.npending = 0;
+    for (int k = 0; k < SD_KERNEL_COUNT; ++k) {
+        b->prof.ms[k] = 0;
+        b->prof.launches[k] = 0;
+    }
+    return SD_OK;
+}
+
+sd_status sd_batch_profile_read(sd_batch *b, int kernel, double *ms, int64_t *launches) {
+    if (!b || kernel < 0 || kernel >= SD_KERNEL_COUNT) return set_error(SD_ERR_ARG, "bad batch or kernel id");
+    cudaSetDevice(b->device);
+    Profiler &p = b->prof;
+    for (int k = 0; k < p.npending; ++k) {
+        float t = 0.0f;
+        SD_CUDA(cudaEventSynchronize(p.ev1[k]));
+        SD_CUDA(cudaEventElapsedTime(&t, p.ev0[k], p.ev1[k]));
+        p.ms[p.kind[k]] += t;
+        p.launches[p.kind[k]] += 1;
+    }
+    p.npending = 0;
+    if (ms) *ms = p.ms[kernel];
+    if (launches) *launches = p.launches[kernel];
+    return SD_OK;
+}
+
+int64_t sd_batch_launch_count(const sd_batch *b) { return b ? b->launches : 0; }
+
+}  // extern "C"

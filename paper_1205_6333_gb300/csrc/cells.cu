@@ -1,0 +1,319 @@
+// cells.cu -- staging of FP64 state into the dense kernels' mirrors, the hashed
+// cell list, and force assembly (Sec. 3.1, step 2: F_ext + pair interactions,
+// the primed sums accelerated by neighbour lists; the paper notes that particle
+// sorting is needed for these short-ranged parts but not for the all-pairs sum,
+// Sec. 3.2).
+//
+// Cell list: cells of side h >= max(r_near, repulsion cutoff) over FP64
+// positions; the integer cell (cx, cy, cz) is hashed into H = 2^k >= 2n buckets,
+// so unbounded domains need no bounding box.  Build = count, exclusive scan,
+// scatter, and an insertion sort of each bucket by particle index (makes every
+// neighbour walk, hence every FP64 near-pair sum, independent of atomics order).
+#include "neighbours.cuh"
+
+namespace sd {
+
+// ---------------------------------------------------------------- staging
+
+template <typename V4>
+__global__ void stage_pos_kernel(const double *__restrict__ x, V4 *__restrict__ m, int n, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+    if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicOr(err, DEV_ERR_NONFINITE);
+    // mirror relative to particle 0: only differences enter the pair terms, and
+    // small coordinates keep FP32 separations accurate
+    V4 v;
+    v.x = px - x[0];
+    v.y = py - x[1];
+    v.z = pz - x[2];
+    v.w = 0;
+    m[i] = v;
+}
+
+cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, void *posm) {
+    if (h->n == 0) return cudaSuccess;
+    const int nb = (h->n + 255) / 256;
+    if (h->mode == MODE_FP64)
+        stage_pos_kernel<dbl4><<<nb, 256, 0, st>>>(x64, static_cast<dbl4 *>(posm), h->n, h->d_err);
+    else
+        stage_pos_kernel<float4><<<nb, 256, 0, st>>>(x64, static_cast<float4 *>(posm), h->n, h->d_err);
+    ++h->launches;
+    return cudaGetLastError();
+}
+
+// dst64 = src (+ fext + gravity when add_ext) and its mirror; src is n x 3 float or double.
+template <typename V4, typename Src>
+__global__ void stage_forces_kernel(const Src *__restrict__ src, const double *__restrict__ fext, double gx,
+                                    double gy, double gz, double *__restrict__ dst, V4 *__restrict__ m, int n,
+                                    int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double f[3];
+    for (int d = 0; d < 3; ++d) f[d] = src ? static_cast<double>(src[3 * i + d]) : 0.0;
+    if (fext) {
+        f[0] += fext[3 * i] + gx;
+        f[1] += fext[3 * i + 1] + gy;
+        f[2] += fext[3 * i + 2] + gz;
+    }
+    if (!isfinite(f[0]) || !isfinite(f[1]) || !isfinite(f[2])) atomicOr(err, DEV_ERR_NONFINITE);
+    dst[3 * i] = f[0];
+    dst[3 * i + 1] = f[1];
+    dst[3 * i + 2] = f[2];
+    V4 v;
+    v.x = f[0];
+    v.y = f[1];
+    v.z = f[2];
+    v.w = 0;
+    m[i] = v;
+}
+
+// src_dtype: SD_DTYPE_F32 / SD_DTYPE_F64 (src may be NULL = zeros); add_ext: add
+// the handle's F_ext and gravity.
+cudaError_t launch_stage_forces(sd_handle *h, cudaStream_t st, const void *src, int src_dtype, int add_ext,
+                                double *dst64, void *dstm) {
+    if (h->n == 0) return cudaSuccess;
+    const int nb = (h->n + 255) / 256;
+    const double *fe = add_ext ? h->fext64 : nullptr;
+    const double *g = h->cfg.gravity;
+    if (h->mode == MODE_FP64) {
+        if (src_dtype == SD_DTYPE_F32)
+            stage_forces_kernel<dbl4, float><<<nb, 256, 0, st>>>(static_cast<const float *>(src), fe, g[0], g[1],
+                                                                 g[2], dst64, static_cast<dbl4 *>(dstm), h->n,
+                                                                 h->d_err);
+        else
+            stage_forces_kernel<dbl4, double><<<nb, 256, 0, st>>>(static_cast<const double *>(src), fe, g[0], g[1],
+                                                                  g[2], dst64, static_cast<dbl4 *>(dstm), h->n,
+                                                                  h->d_err);
+    } else {
+        if (src_dtype == SD_DTYPE_F32)
+            stage_forces_kernel<float4, float><<<nb, 256, 0, st>>>(static_cast<const float *>(src), fe, g[0], g[1],
+                                                                   g[2], dst64, static_cast<float4 *>(dstm), h->n,
+                                                                   h->d_err);
+        else
+            stage_forces_kernel<float4, double><<<nb, 256, 0, st>>>(static_cast<const double *>(src), fe, g[0],
+                                                                    g[1], g[2], dst64, static_cast<float4 *>(dstm),
+                                                                    h->n, h->d_err);
+    }
+    ++h->launches;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- cell list
+
+__device__ __forceinline__ int cell_coord(double x, double inv_h) {
+    double c = floor(x * inv_h);
+    c = fmin(fmax(c, -1.0e9), 1.0e9);  // keep the integer in range for absurd coordinates
+    return static_cast<int>(c);
+}
+
+// Bins particle i and writes its mirror (position relative to particle 0, in the
+// dense kernels' precision), so the mirror is a pure function of the FP64 state.
+template <typename V4>
+__global__ void cells_hash_kernel(const double *__restrict__ x, int n, double inv_h, int H, int4 *__restrict__ cell,
+                                  uint32_t *__restrict__ key, int *__restrict__ cnt, V4 *__restrict__ m, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+    if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicOr(err, DEV_ERR_NONFINITE);
+    V4 v;
+    v.x = px - x[0];
+    v.y = py - x[1];
+    v.z = pz - x[2];
+    v.w = 0;
+    m[i] = v;
+    const int cx = cell_coord(px, inv_h);
+    const int cy = cell_coord(py, inv_h);
+    const int cz = cell_coord(pz, inv_h);
+    cell[i] = make_int4(cx, cy, cz, 0);
+    const uint32_t k = cell_hash(cx, cy, cz, H);
+    key[i] = k;
+    atomicAdd(&cnt[k], 1);
+}
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanBlock = kScanThreads * kScanPer;
+
+// Exclusive scan of kScanPer values per thread across a block; returns the
+// block total.  Warp shuffles within warps, shared memory across warps.
+__device__ __forceinline__ int block_exclusive_scan(int v[kScanPer], int *s_warp) {
+    int tsum = 0;
+    for (int k = 0; k < kScanPer; ++k) {
+        const int t = v[k];
+        v[k] = tsum;
+        tsum += t;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = tsum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = (lane < kScanThreads / 32) ? s_warp[lane] : 0;
+        int wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        s_warp[lane] = wi - w;  // exclusive warp offsets
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const int off = s_warp[wid] + incl - tsum;
+    for (int k = 0; k < kScanPer; ++k) v[k] += off;
+    const int total = s_warp[32];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(const int *__restrict__ in, int *__restrict__ out,
+                                                                   int *__restrict__ bsum, int H) {
+    __shared__ int s_warp[33];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+    int v[kScanPer];
+    for (int k = 0; k < kScanPer; ++k) v[k] = (base + k < H) ? in[base + k] : 0;
+    const int total = block_exclusive_scan(v, s_warp);
+    for (int k = 0; k < kScanPer; ++k)
+        if (base + k < H) out[base + k] = v[k];
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the block totals in place (nblk <= kScanBlock
+// per pass, looping with a carry), then start[H] = grand total.
+__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(int *__restrict__ bsum, int nblk,
+                                                                int *__restrict__ start, int H) {
+    __shared__ int s_warp[33];
+    int carry = 0;
+    for (int b0 = 0; b0 < nblk; b0 += kScanBlock) {
+        const int base = b0 + threadIdx.x * kScanPer;
+        int v[kScanPer];
+        for (int k = 0; k < kScanPer; ++k) v[k] = (base + k < nblk) ? bsum[base + k] : 0;
+        const int total = block_exclusive_scan(v, s_warp);
+        for (int k = 0; k < kScanPer; ++k)
+            if (base + k < nblk) bsum[base + k] = v[k] + carry;
+        carry += total;
+    }
+    if (threadIdx.x == 0) start[H] = carry;
+}
+
+__global__ void scan_add_kernel(int *__restrict__ start, const int *__restrict__ bsum, int H) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < H) start[e] += bsum[e / kScanBlock];
+}
+
+__global__ void cells_scatter_kernel(const uint32_t *__restrict__ key, int n, const int *__restrict__ start,
+                                     int *__restrict__ fill, int *__restrict__ sorted) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = key[i];
+    sorted[start[k] + atomicAdd(&fill[k], 1)] = i;
+}
+
+// Sort each bucket by particle index (buckets hold ~1 particle; a bucket larger
+// than 256 -- only possible for unphysically dense input -- stays unsorted, which
+// changes only the FP64 summation order of its near pairs).
+__global__ void cells_sort_kernel(const int *__restrict__ start, int *__restrict__ sorted, int H) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= H) return;
+    const int s0 = start[b], s1 = start[b + 1];
+    if (s1 - s0 < 2 || s1 - s0 > 256) return;
+    for (int p = s0 + 1; p < s1; ++p) {
+        const int v = sorted[p];
+        int q = p - 1;
+        while (q >= s0 && sorted[q] > v) {
+            sorted[q + 1] = sorted[q];
+            --q;
+        }
+        sorted[q + 1] = v;
+    }
+}
+
+cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, void *posm) {
+    CellList &c = h->cl;
+    if (h->n == 0) return cudaSuccess;
+    prof_begin(h, SD_KERNEL_CELLS, st);
+    cudaError_t e = cudaMemsetAsync(c.cnt, 0, sizeof(int) * static_cast<size_t>(c.H), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.fill, 0, sizeof(int) * static_cast<size_t>(c.H), st);
+    if (e != cudaSuccess) return e;
+    const int nb = (h->n + 255) / 256;
+    if (h->mode == MODE_FP64)
+        cells_hash_kernel<dbl4><<<nb, 256, 0, st>>>(x64, h->n, c.inv_h, c.H, c.cell, c.key, c.cnt,
+                                                    static_cast<dbl4 *>(posm), h->d_err);
+    else
+        cells_hash_kernel<float4><<<nb, 256, 0, st>>>(x64, h->n, c.inv_h, c.H, c.cell, c.key, c.cnt,
+                                                      static_cast<float4 *>(posm), h->d_err);
+    scan_blocks_kernel<<<c.nblk, kScanThreads, 0, st>>>(c.cnt, c.start, c.bsum, c.H);
+    scan_top_kernel<<<1, kScanThreads, 0, st>>>(c.bsum, c.nblk, c.start, c.H);
+    scan_add_kernel<<<(c.H + 255) / 256, 256, 0, st>>>(c.start, c.bsum, c.H);
+    cells_scatter_kernel<<<nb, 256, 0, st>>>(c.key, h->n, c.start, c.fill, c.sorted);
+    cells_sort_kernel<<<(c.H + 255) / 256, 256, 0, st>>>(c.start, c.sorted, c.H);
+    prof_end(h, SD_KERNEL_CELLS, st);
+    h->launches += 6;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- forces (Sec. 3.1, step 2)
+
+// F_i = F_ext,i + g + sum_{j: r_ij < r_c} 12 eps (2a)^12 r^-14 (r_i - r_j)
+// (U = eps (2a/r)^12, truncated at r_c, F = -grad U), in FP64; writes F64 and its mirror.
+template <typename V4>
+__global__ void forces_rep_kernel(const double *__restrict__ x, const double *__restrict__ fext, double gx, double gy,
+                                  double gz, double eps, double rc, double s12, CellList c, int n,
+                                  double *__restrict__ F, V4 *__restrict__ m, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
+    double f0 = fext[3 * i] + gx, f1 = fext[3 * i + 1] + gy, f2 = fext[3 * i + 2] + gz;
+    const double rc2 = rc * rc;
+    bool coincident = false;
+    for_each_neighbour(c, i, c.cell[i], [&](int j) {
+        const double dx = xi - x[3 * j], dy = yi - x[3 * j + 1], dz = zi - x[3 * j + 2];
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= rc2) return;
+        if (r2 == 0.0) {
+            coincident = true;
+            return;
+        }
+        const double ir2 = 1.0 / r2;
+        const double ir6 = ir2 * ir2 * ir2;
+        const double coef = 12.0 * eps * s12 * ir6 * ir6 * ir2;
+        f0 += coef * dx;
+        f1 += coef * dy;
+        f2 += coef * dz;
+    });
+    if (coincident) atomicOr(err, DEV_ERR_COINCIDENT);
+    if (!isfinite(f0) || !isfinite(f1) || !isfinite(f2)) atomicOr(err, DEV_ERR_NONFINITE);
+    F[3 * i] = f0;
+    F[3 * i + 1] = f1;
+    F[3 * i + 2] = f2;
+    V4 v;
+    v.x = f0;
+    v.y = f1;
+    v.z = f2;
+    v.w = 0;
+    m[i] = v;
+}
+
+cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64) {
+    if (h->n == 0) return cudaSuccess;
+    const int nb = (h->n + 127) / 128;
+    const double *g = h->cfg.gravity;
+    const double s12 = pow(2.0 * h->cfg.a, 12.0);
+    prof_begin(h, SD_KERNEL_FORCES, st);
+    if (h->mode == MODE_FP64)
+        forces_rep_kernel<dbl4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, h->rep_rc, s12,
+                                                    h->cl, h->n, h->F64, static_cast<dbl4 *>(h->frcm), h->d_err);
+    else
+        forces_rep_kernel<float4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, h->rep_rc,
+                                                      s12, h->cl, h->n, h->F64, static_cast<float4 *>(h->frcm),
+                                                      h->d_err);
+    prof_end(h, SD_KERNEL_FORCES, st);
+    ++h->launches;
+    return cudaGetLastError();
+}
+
+}  // namespace sd

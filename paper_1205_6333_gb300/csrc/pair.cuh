@@ -1,0 +1,235 @@
+// pair.cuh -- the pair term of the mobility sum, in the scalar form
+//
+//   T(r) / mu0 = A(r) I + B(r) r r^T        (r unnormalised)
+//
+// which is Eq. rotneMobility (Sec. 2.2) regrouped with rr = r r^T / r^2:
+//   Rotne-Prager, r >= 2a : A = c1/r + c3/r^3,   B = c1/r^3 - 3 c3/r^5,   c1 = 3a/4, c3 = a^3/2
+//   Oseen (Eq. oseenTensor): A = c1/r,           B = c1/r^3          ((I+rr)/(8 pi eta r) = mu0 (3a/4r)(I+rr))
+//   RPY overlap, r < 2a   : A = 1 - 9r/(32a),    B = 3/(32 a r)      (Yamakawa continuation)
+// so that T(r) F = mu0 [A F + B (r.F) r].  mu0 is applied once per particle in
+// the epilogue, never per pair.
+//
+// The all-pairs ("dense") kernels evaluate the Rotne-Prager / Oseen branch for
+// every pair with r^2 clamped to >= (2a)^2 -- one FMNMX instead of a branch on the
+// self pair or on overlaps -- and the FP64 epilogue replaces the self term and
+// every pair closer than r_near by its exact value.  Every FP32 operation is an
+// explicit round-to-nearest intrinsic, so the epilogue can re-evaluate exactly
+// the value a dense kernel used for a pair.
+#pragma once
+#include <cuda_runtime.h>
+#include "ptx.cuh"
+
+namespace sd {
+
+enum { T_RPY = 0, T_RP = 1, T_OSEEN = 2 };
+
+// 32-byte aligned four-double vector (position or force + padding).
+using dbl4 = double4_32a;
+
+struct PairConst {
+    float r2min_f, c1_f, c3_f, m3c3_f;   // (2a)^2, 3a/4, a^3/2, -3a^3/2
+    double r2min_d, c1_d, c3_d, m3c3_d;
+    double a, two_a, mu0;
+};
+
+// ---------------------------------------------------------------- dense FP32
+
+// One pair of the dense sum, accumulated into (ax, ay, az): 22 FP32-pipe ops
+// (RP) or 20 (Oseen), one FMNMX, one MUFU.RSQ.
+template <int TENSOR>
+__device__ __forceinline__ void pair_f32(float xi, float yi, float zi, float4 p, float4 f, const PairConst &c,
+                                         float &ax, float &ay, float &az) {
+    const float dx = __fsub_rn(xi, p.x);
+    const float dy = __fsub_rn(yi, p.y);
+    const float dz = __fsub_rn(zi, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    r2 = fmaxf(r2, c.r2min_f);
+    const float ri = rsqrt_sfu(r2);
+    const float ri2 = __fmul_rn(ri, ri);
+    float A, B;
+    if (TENSOR == T_OSEEN) {
+        A = __fmul_rn(c.c1_f, ri);
+        B = __fmul_rn(A, ri2);
+    } else {
+        A = __fmul_rn(ri, __fmaf_rn(c.c3_f, ri2, c.c1_f));
+        const float ri3 = __fmul_rn(ri, ri2);
+        B = __fmul_rn(ri3, __fmaf_rn(c.m3c3_f, ri2, c.c1_f));
+    }
+    const float dF = __fmaf_rn(dz, f.z, __fmaf_rn(dy, f.y, __fmul_rn(dx, f.x)));
+    const float s = __fmul_rn(B, dF);
+    ax = __fmaf_rn(s, dx, __fmaf_rn(A, f.x, ax));
+    ay = __fmaf_rn(s, dy, __fmaf_rn(A, f.y, ay));
+    az = __fmaf_rn(s, dz, __fmaf_rn(A, f.z, az));
+}
+
+// ---------------------------------------------------------------- dense FP64
+
+template <int TENSOR>
+__device__ __forceinline__ void pair_f64(double xi, double yi, double zi, dbl4 p, dbl4 f, const PairConst &c,
+                                         double &ax, double &ay, double &az) {
+    const double dx = __dsub_rn(xi, p.x);
+    const double dy = __dsub_rn(yi, p.y);
+    const double dz = __dsub_rn(zi, p.z);
+    double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+    r2 = fmax(r2, c.r2min_d);
+    const double ri = rsqrt_nr64(r2);
+    const double ri2 = __dmul_rn(ri, ri);
+    double A, B;
+    if (TENSOR == T_OSEEN) {
+        A = __dmul_rn(c.c1_d, ri);
+        B = __dmul_rn(A, ri2);
+    } else {
+        A = __dmul_rn(ri, __fma_rn(c.c3_d, ri2, c.c1_d));
+        const double ri3 = __dmul_rn(ri, ri2);
+        B = __dmul_rn(ri3, __fma_rn(c.m3c3_d, ri2, c.c1_d));
+    }
+    const double dF = __fma_rn(dz, f.z, __fma_rn(dy, f.y, __dmul_rn(dx, f.x)));
+    const double s = __dmul_rn(B, dF);
+    ax = __fma_rn(s, dx, __fma_rn(A, f.x, ax));
+    ay = __fma_rn(s, dy, __fma_rn(A, f.y, ay));
+    az = __fma_rn(s, dz, __fma_rn(A, f.z, az));
+}
+
+// ---------------------------------------------------------------- exact FP64 profile
+
+// A(r), B(r) and the radial derivatives divided by r, dA = A'(r)/r, dB = B'(r)/r,
+// of the tensor actually in use at separation |r| = sqrt(r2) (r2 > 0, or r2 = 0 for RPY).
+template <int TENSOR>
+__device__ __forceinline__ void profile_exact(double r2, const PairConst &c, double &A, double &B, double &dA,
+                                              double &dB) {
+    if (TENSOR == T_RPY && r2 < c.two_a * c.two_a) {
+        const double r = sqrt(r2);
+        A = 1.0 - 9.0 * r / (32.0 * c.a);
+        if (r2 > 0.0) {
+            B = 3.0 / (32.0 * c.a * r);
+            dA = -9.0 / (32.0 * c.a * r);
+            dB = -3.0 / (32.0 * c.a * r * r2);
+        } else {
+            B = dA = dB = 0.0;  // the terms they multiply carry a factor r
+        }
+        return;
+    }
+    const double ri = 1.0 / sqrt(r2);
+    const double ri2 = ri * ri;
+    const double ri3 = ri * ri2;
+    const double ri5 = ri3 * ri2;
+    if (TENSOR == T_OSEEN) {
+        A = c.c1_d * ri;
+        B = c.c1_d * ri3;
+        dA = -c.c1_d * ri3;
+        dB = -3.0 * c.c1_d * ri5;
+    } else {
+        A = c.c1_d * ri + c.c3_d * ri3;
+        B = c.c1_d * ri3 - 3.0 * c.c3_d * ri5;
+        dA = -c.c1_d * ri3 - 3.0 * c.c3_d * ri5;
+        dB = -3.0 * c.c1_d * ri5 + 15.0 * c.c3_d * ri5 * ri2;
+    }
+}
+
+// ---------------------------------------------------------------- VJP pair terms
+
+// For the pair (i, j) at r = x_i - x_j with forces Fi, Fj and cotangents Wi, Wj:
+//   m += A Wj + B (r.Wj) r                                  (row i of mu W)
+//   g += (dA U + dB Q) r + B [Wi (Fj.r) + Fj (Wi.r) + Wj (Fi.r) + Fi (Wj.r)]
+// with U = Wi.Fj + Wj.Fi and Q = (Wi.r)(Fj.r) + (Wj.r)(Fi.r)  -- the gradient of
+// Wi.T(r)Fj + Wj.T(r)Fi with respect to x_i.  FP32, r^2 clamped like pair_f32.
+template <int TENSOR>
+__device__ __forceinline__ void vjp_pair_f32(float xi, float yi, float zi, float3 Fi, float3 Wi, float4 p, float4 f,
+                                             float4 w, const PairConst &c, float3 &m, float3 &g) {
+    const float dx = __fsub_rn(xi, p.x);
+    const float dy = __fsub_rn(yi, p.y);
+    const float dz = __fsub_rn(zi, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    r2 = fmaxf(r2, c.r2min_f);
+    const float ri = rsqrt_sfu(r2);
+    const float ri2 = __fmul_rn(ri, ri);
+    const float ri3 = __fmul_rn(ri, ri2);
+    const float ri5 = __fmul_rn(ri3, ri2);
+    float A, B, dA, dB;
+    if (TENSOR == T_OSEEN) {
+        A = __fmul_rn(c.c1_f, ri);
+        B = __fmul_rn(c.c1_f, ri3);
+        dA = __fmul_rn(-c.c1_f, ri3);
+        dB = __fmul_rn(-3.0f * c.c1_f, ri5);
+    } else {
+        A = __fmul_rn(ri, __fmaf_rn(c.c3_f, ri2, c.c1_f));
+        B = __fmul_rn(ri3, __fmaf_rn(c.m3c3_f, ri2, c.c1_f));
+        dA = __fmul_rn(ri3, __fmaf_rn(c.m3c3_f, ri2, -c.c1_f));                 // -c1/r^3 - 3c3/r^5
+        dB = __fmul_rn(ri5, __fmaf_rn(-5.0f * c.m3c3_f, ri2, -3.0f * c.c1_f));  // -3c1/r^5 + 15c3/r^7
+    }
+    const float Wir = __fmaf_rn(dz, Wi.z, __fmaf_rn(dy, Wi.y, __fmul_rn(dx, Wi.x)));
+    const float Fir = __fmaf_rn(dz, Fi.z, __fmaf_rn(dy, Fi.y, __fmul_rn(dx, Fi.x)));
+    const float Wjr = __fmaf_rn(dz, w.z, __fmaf_rn(dy, w.y, __fmul_rn(dx, w.x)));
+    const float Fjr = __fmaf_rn(dz, f.z, __fmaf_rn(dy, f.y, __fmul_rn(dx, f.x)));
+    const float WiFj = __fmaf_rn(Wi.z, f.z, __fmaf_rn(Wi.y, f.y, __fmul_rn(Wi.x, f.x)));
+    const float U = __fmaf_rn(w.z, Fi.z, __fmaf_rn(w.y, Fi.y, __fmaf_rn(w.x, Fi.x, WiFj)));
+    const float Q = __fmaf_rn(Wjr, Fir, __fmul_rn(Wir, Fjr));
+    const float cr = __fmaf_rn(dB, Q, __fmul_rn(dA, U));
+    const float bFj = __fmul_rn(B, Fjr), bWi = __fmul_rn(B, Wir), bFi = __fmul_rn(B, Fir), bWj = __fmul_rn(B, Wjr);
+    g.x = __fmaf_rn(cr, dx, __fmaf_rn(Wi.x, bFj, __fmaf_rn(f.x, bWi, __fmaf_rn(w.x, bFi, __fmaf_rn(Fi.x, bWj, g.x)))));
+    g.y = __fmaf_rn(cr, dy, __fmaf_rn(Wi.y, bFj, __fmaf_rn(f.y, bWi, __fmaf_rn(w.y, bFi, __fmaf_rn(Fi.y, bWj, g.y)))));
+    g.z = __fmaf_rn(cr, dz, __fmaf_rn(Wi.z, bFj, __fmaf_rn(f.z, bWi, __fmaf_rn(w.z, bFi, __fmaf_rn(Fi.z, bWj, g.z)))));
+    m.x = __fmaf_rn(bWj, dx, __fmaf_rn(A, w.x, m.x));
+    m.y = __fmaf_rn(bWj, dy, __fmaf_rn(A, w.y, m.y));
+    m.z = __fmaf_rn(bWj, dz, __fmaf_rn(A, w.z, m.z));
+}
+
+// The same pair in FP64 with the clamp (what the FP64 dense VJP kernel adds).
+template <int TENSOR>
+__device__ __forceinline__ void vjp_pair_f64(double xi, double yi, double zi, double3 Fi, double3 Wi, dbl4 p,
+                                             dbl4 f, dbl4 w, const PairConst &c, double3 &m, double3 &g) {
+    const double dx = __dsub_rn(xi, p.x);
+    const double dy = __dsub_rn(yi, p.y);
+    const double dz = __dsub_rn(zi, p.z);
+    double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+    r2 = fmax(r2, c.r2min_d);
+    const double ri = rsqrt_nr64(r2);
+    const double ri2 = ri * ri;
+    const double ri3 = ri * ri2;
+    const double ri5 = ri3 * ri2;
+    double A, B, dA, dB;
+    if (TENSOR == T_OSEEN) {
+        A = c.c1_d * ri;
+        B = c.c1_d * ri3;
+        dA = -c.c1_d * ri3;
+        dB = -3.0 * c.c1_d * ri5;
+    } else {
+        A = ri * fma(c.c3_d, ri2, c.c1_d);
+        B = ri3 * fma(c.m3c3_d, ri2, c.c1_d);
+        dA = ri3 * fma(c.m3c3_d, ri2, -c.c1_d);
+        dB = ri5 * fma(-5.0 * c.m3c3_d, ri2, -3.0 * c.c1_d);
+    }
+    const double Wir = dx * Wi.x + dy * Wi.y + dz * Wi.z;
+    const double Fir = dx * Fi.x + dy * Fi.y + dz * Fi.z;
+    const double Wjr = dx * w.x + dy * w.y + dz * w.z;
+    const double Fjr = dx * f.x + dy * f.y + dz * f.z;
+    const double U = Wi.x * f.x + Wi.y * f.y + Wi.z * f.z + w.x * Fi.x + w.y * Fi.y + w.z * Fi.z;
+    const double Q = Wir * Fjr + Wjr * Fir;
+    const double cr = dA * U + dB * Q;
+    const double bFj = B * Fjr, bWi = B * Wir, bFi = B * Fir, bWj = B * Wjr;
+    g.x += cr * dx + Wi.x * bFj + f.x * bWi + w.x * bFi + Fi.x * bWj;
+    g.y += cr * dy + Wi.y * bFj + f.y * bWi + w.y * bFi + Fi.y * bWj;
+    g.z += cr * dz + Wi.z * bFj + f.z * bWi + w.z * bFi + Fi.z * bWj;
+    m.x += A * w.x + bWj * dx;
+    m.y += A * w.y + bWj * dy;
+    m.z += A * w.z + bWj * dz;
+}
+
+// ---------------------------------------------------------------- compensated sums
+
+// Knuth's TwoSum: s + e == a + b exactly (round-to-nearest, no FMA contraction).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Fold a tile partial p into the two-float accumulator (hi, lo).
+__device__ __forceinline__ void fold2(float &hi, float &lo, float p) {
+    float s, e;
+    two_sum(hi, p, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+}  // namespace sd

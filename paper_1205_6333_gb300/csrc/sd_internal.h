@@ -1,0 +1,189 @@
+// sd_internal.h -- handle layout and kernel launchers shared by the .cu files
+// of the library (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/sd.h"
+#include "pair.cuh"
+
+namespace sd {
+
+// Device error word bits (atomicOr'ed by kernels, read at synchronising calls).
+enum : int {
+    DEV_ERR_NONFINITE = 1,
+    DEV_ERR_COINCIDENT = 2,
+    DEV_ERR_TIMEOUT = 4,
+    DEV_ERR_QUEUE = 8,
+};
+
+enum { MODE_FP32C = 0, MODE_FP64 = 1, MODE_FP32 = 2 };
+enum { OUT_F32 = 0, OUT_F64 = 1, OUT_EULER = 2 };
+
+constexpr int kPadTo = 512;      // particle arrays are padded to a multiple of this
+constexpr int kNT = 128;         // threads per CTA of the dense kernels
+constexpr int kR32 = 4;          // i-particles per thread, FP32 dense kernel
+constexpr int kR64 = 2;          // i-particles per thread, FP64 dense kernel
+constexpr int kRV = 2;           // i-particles per thread, VJP dense kernel
+constexpr int kJmax = 256;       // largest j-tile
+constexpr long long kDefaultWatchdog = 1LL << 22;
+
+// Partition of the (i-block, j-tile) plane over a persistent grid: CTA b takes
+// the row-major tile range [b*chunk, min((b+1)*chunk, nIB*nJT)).  The CTAs that
+// touch i-block ib are first(ib) .. last(ib); each writes its partial sum for ib
+// into slot (b - first(ib)), and the epilogue adds slots in ascending order.
+struct DenseGeom {
+    int I;          // i-particles per CTA (threads x R)
+    int J;          // j-particles per tile
+    int nIB, nJT;   // i-blocks, j-tiles
+    long long chunk;
+    int grid;
+    int maxSlots;
+};
+
+__host__ __device__ inline int geom_first(const DenseGeom &g, int ib) {
+    return static_cast<int>((static_cast<long long>(ib) * g.nJT) / g.chunk);
+}
+__host__ __device__ inline int geom_last(const DenseGeom &g, int ib) {
+    return static_cast<int>((static_cast<long long>(ib + 1) * g.nJT - 1) / g.chunk);
+}
+
+// Hashed cell list over FP64 positions (unbounded domains): cells of side h,
+// H buckets (power of two), particles sorted by bucket, each bucket ascending.
+struct CellList {
+    double h = 0.0, inv_h = 0.0;
+    int H = 0;
+    int nblk = 0;          // scan blocks
+    int4 *cell = nullptr;  // [n] integer cell coordinates (w unused)
+    uint32_t *key = nullptr;  // [n] bucket of each particle
+    int *cnt = nullptr;    // [H] occupancy, then fill counters
+    int *fill = nullptr;   // [H]
+    int *start = nullptr;  // [H+1]
+    int *bsum = nullptr;   // [nblk]
+    int *sorted = nullptr; // [n]
+};
+
+__device__ __forceinline__ uint32_t cell_hash(int cx, int cy, int cz, int H) {
+    return ((static_cast<uint32_t>(cx) * 73856093u) ^ (static_cast<uint32_t>(cy) * 19349663u) ^
+            (static_cast<uint32_t>(cz) * 83492791u)) &
+           static_cast<uint32_t>(H - 1);
+}
+
+struct Profiler {
+    bool on = false;
+    double ms[SD_KERNEL_COUNT] = {};
+    int64_t launches[SD_KERNEL_COUNT] = {};
+    static constexpr int kMaxPending = 4096;
+    cudaEvent_t ev0[kMaxPending] = {}, ev1[kMaxPending] = {};
+    int kind[kMaxPending] = {};
+    int npending = 0;
+    int nevents = 0;  // created event pairs
+};
+
+struct Allocator {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*free)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+};
+
+}  // namespace sd
+
+struct sd_handle {
+    sd_config cfg{};
+    int n = 0, npad = 0;
+    int mode = 0;      // MODE_*
+    int tensor = 0;    // T_*
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;   // caller's stream
+    cudaStream_t cap = nullptr;      // private stream used for graph capture
+    sd::Allocator al;
+    sd::PairConst pc{};
+    double r_near = 0.0, rep_rc = 0.0;
+    long long watchdog = sd::kDefaultWatchdog;
+
+    // FP64 state (ping-pong) and the mirror the dense kernel reads: float4 or
+    // double4 [npad], positions relative to particle 0 of the state, rewritten by
+    // the cell-list build of every step (a pure function of the FP64 state)
+    double *x64[2] = {nullptr, nullptr};
+    void *posm = nullptr;
+    int cur = 0;
+    bool pos_set = false;
+    bool cells_valid = false;             // cell list matches x64[cur]
+
+    double *fext64 = nullptr;   // [n*3] per-particle external forces
+    double *F64 = nullptr;      // [n*3] total force of the current step
+    void *frcm = nullptr;       // mirror of F64
+    bool forces_const = true;   // no repulsion: F64 depends on nothing that changes
+
+    // apply / vjp scratch
+    double *Fa64 = nullptr;  void *frcam = nullptr;
+    double *Wa64 = nullptr;  void *wam = nullptr;
+    double *part = nullptr;  size_t part_bytes = 0;   // dense partial sums
+    double *part2 = nullptr; size_t part2_bytes = 0;  // second output of the VJP kernel
+    sd::DenseGeom geom{}, geomv{};
+    int dense_occ = 0, vjp_occ = 0;
+
+    sd::CellList cl;
+    int *d_err = nullptr;
+
+    // graph cache for sd_step
+    cudaGraphExec_t gexec = nullptr;
+    int g_steps = 0;
+    double g_dt = 0.0;
+    int g_cur = -1;
+    int64_t g_kernels = 0;   // kernel nodes in the cached graph
+    cudaGraphExec_t gexec1 = nullptr;   // single-step graph (odd remainder)
+    int g1_cur = -1;
+    double g1_dt = 0.0;
+    int64_t g1_kernels = 0;
+
+    // adjoint storage (allocated on first use)
+    double *ckpt = nullptr; size_t ckpt_bytes = 0;
+    double *seg = nullptr;  size_t seg_bytes = 0;
+    double *lam = nullptr;  double *gFacc = nullptr;
+
+    sd::Profiler prof;
+    int64_t launches = 0;
+    bool capturing = false;
+};
+
+namespace sd {
+
+// errors
+sd_status set_error(sd_status st, const std::string &msg);
+sd_status cuda_status(cudaError_t e, const char *what);
+#define SD_CUDA(call)                                                  \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return ::sd::cuda_status(e_, #call);    \
+    } while (0)
+
+// profiling hooks around launches on `st`
+void prof_begin(sd_handle *h, int kind, cudaStream_t st);
+void prof_end(sd_handle *h, int kind, cudaStream_t st);
+
+// ---- launchers (return cudaGetLastError of the launch)
+// cells.cu
+cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, void *posm);
+cudaError_t launch_stage_forces(sd_handle *h, cudaStream_t st, const void *src, int src_dtype, int add_ext,
+                                double *dst64, void *dstm);
+cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, void *posm);
+cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64);
+// dense.cu
+cudaError_t dense_setup(sd_handle *h);
+cudaError_t launch_dense(sd_handle *h, cudaStream_t st, const void *posm, const void *frcm, double *part);
+// epilogue.cu
+cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double *x64, const void *posm,
+                            const double *F64, const void *frcm, void *vout, double dt, double *x64n);
+// vjp.cu
+cudaError_t vjp_setup(sd_handle *h);
+cudaError_t launch_vjp_dense(sd_handle *h, cudaStream_t st, const void *posm, const void *frcm, const void *wm,
+                             double *partM, double *partG);
+cudaError_t launch_vjp_epilogue(sd_handle *h, cudaStream_t st, const double *x64, const void *posm,
+                                const double *F64, const void *frcm, const double *W64, const void *wm,
+                                int out_dtype, void *gx_out, void *gF_out, double dt, double *lam_acc,
+                                double *gF_acc);
+
+}  // namespace sd

@@ -1,0 +1,418 @@
+// vjp.cu -- vector-Jacobian products of v(x, F) = mu(x) F (derivative of
+// Sec. 2.2, Eq. rotneMobility; the paper has no adjoint):
+//
+//   (mu W)_i  = mu0 [ W_i + sum_{j != i} (A W_j + B (r.W_j) r) ]
+//   gX_i      = mu0 sum_{j != i} grad_r [ W_i.T^(r) F_j + W_j.T^(r) F_i ],  r = x_i - x_j
+//
+// with T^ = T/mu0 = A I + B r r^T (pair.cuh).  mu is symmetric, so mu^T W = mu W
+// is the force gradient.  One all-pairs kernel evaluates both sums from the same
+// r, 1/r and tensor profile; the layout is the dense kernel's (persistent grid,
+// bulk-copied j-tiles of positions, forces and cotangents, per-tile TwoSum folds,
+// fixed-order slots), and the epilogue again swaps the self term and the pairs
+// closer than r_near for their exact FP64 values.
+#include <algorithm>
+#include "neighbours.cuh"
+
+namespace sd {
+
+template <int MODE>
+struct VjpT {
+    using V4 = float4;
+    using V3 = float3;
+    using S = float;
+};
+template <>
+struct VjpT<MODE_FP64> {
+    using V4 = dbl4;
+    using V3 = double3;
+    using S = double;
+};
+
+template <int TENSOR, int MODE>
+__device__ __forceinline__ void vjp_term(typename VjpT<MODE>::S xi, typename VjpT<MODE>::S yi,
+                                         typename VjpT<MODE>::S zi, const typename VjpT<MODE>::V3 &Fi,
+                                         const typename VjpT<MODE>::V3 &Wi, const typename VjpT<MODE>::V4 &p,
+                                         const typename VjpT<MODE>::V4 &f, const typename VjpT<MODE>::V4 &w,
+                                         const PairConst &c, typename VjpT<MODE>::V3 &m,
+                                         typename VjpT<MODE>::V3 &g) {
+    if constexpr (MODE == MODE_FP64)
+        vjp_pair_f64<TENSOR>(xi, yi, zi, Fi, Wi, p, f, w, c, m, g);
+    else
+        vjp_pair_f32<TENSOR>(xi, yi, zi, Fi, Wi, p, f, w, c, m, g);
+}
+
+template <int TENSOR, int MODE>
+__global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 *__restrict__ pos,
+                                                  const typename VjpT<MODE>::V4 *__restrict__ frc,
+                                                  const typename VjpT<MODE>::V4 *__restrict__ wv,
+                                                  double *__restrict__ partM, double *__restrict__ partG, int npad,
+                                                  DenseGeom g, PairConst c, int *__restrict__ err, long long wd) {
+    using V4 = typename VjpT<MODE>::V4;
+    using V3 = typename VjpT<MODE>::V3;
+    using S = typename VjpT<MODE>::S;
+    constexpr int R = kRV;
+    constexpr bool COMP = (MODE != MODE_FP64);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+    V4 *s_pos = reinterpret_cast<V4 *>(smem);
+    V4 *s_frc = s_pos + 2 * g.J;
+    V4 *s_w = s_frc + 2 * g.J;
+
+    const int tid = threadIdx.x;
+    const long long T = static_cast<long long>(g.nIB) * g.nJT;
+    const long long t0 = static_cast<long long>(blockIdx.x) * g.chunk;
+    const long long t1 = (t0 + g.chunk < T) ? t0 + g.chunk : T;
+    if (t0 >= t1) return;
+    const uint32_t tile_bytes = static_cast<uint32_t>(g.J * sizeof(V4));
+
+    int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    auto issue = [&](long long t, int stg) {
+        const size_t jt = static_cast<size_t>(t % g.nJT);
+        mbar_arrive_expect_tx(&bars[stg], 3 * tile_bytes);
+        bulk_g2s(s_pos + stg * g.J, pos + jt * g.J, tile_bytes, &bars[stg]);
+        bulk_g2s(s_frc + stg * g.J, frc + jt * g.J, tile_bytes, &bars[stg]);
+        bulk_g2s(s_w + stg * g.J, wv + jt * g.J, tile_bytes, &bars[stg]);
+        if (stg == 0) ++issued0; else ++issued1;
+    };
+    if (tid == 0)
+        for (int q = 0; q < 2 && t0 + q < t1; ++q) issue(t0 + q, q);
+
+    S xi[R], yi[R], zi[R];
+    V3 Fi[R], Wi[R], m[R], gg[R];
+    float mh[R][3], ml[R][3], gh[R][3], gl[R][3];
+    int cur_ib = -1;
+    bool aborted = false;
+
+    auto flush = [&](int ib) {
+        const int slot = static_cast<int>(blockIdx.x) - geom_first(g, ib);
+        double *dM = partM + static_cast<size_t>(slot) * 3 * npad;
+        double *dG = partG + static_cast<size_t>(slot) * 3 * npad;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const size_t i = static_cast<size_t>(ib) * g.I + tid + k * kNT;
+            if constexpr (COMP) {
+                for (int d = 0; d < 3; ++d) {
+                    dM[d * static_cast<size_t>(npad) + i] = static_cast<double>(mh[k][d]) + ml[k][d];
+                    dG[d * static_cast<size_t>(npad) + i] = static_cast<double>(gh[k][d]) + gl[k][d];
+                }
+            } else {
+                dM[i] = m[k].x;
+                dM[npad + i] = m[k].y;
+                dM[2 * static_cast<size_t>(npad) + i] = m[k].z;
+                dG[i] = gg[k].x;
+                dG[npad + i] = gg[k].y;
+                dG[2 * static_cast<size_t>(npad) + i] = gg[k].z;
+            }
+        }
+    };
+
+    for (long long t = t0; t < t1; ++t) {
+        const int ib = static_cast<int>(t / g.nJT);
+        if (ib != cur_ib) {
+            if (cur_ib >= 0) flush(cur_ib);
+            cur_ib = ib;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const size_t i = static_cast<size_t>(ib) * g.I + tid + k * kNT;
+                const V4 p = pos[i], f = frc[i], w = wv[i];
+                xi[k] = p.x;
+                yi[k] = p.y;
+                zi[k] = p.z;
+                Fi[k].x = f.x; Fi[k].y = f.y; Fi[k].z = f.z;
+                Wi[k].x = w.x; Wi[k].y = w.y; Wi[k].z = w.z;
+                m[k].x = m[k].y = m[k].z = S(0);
+                gg[k].x = gg[k].y = gg[k].z = S(0);
+                for (int d = 0; d < 3; ++d) mh[k][d] = ml[k][d] = gh[k][d] = gl[k][d] = 0.0f;
+            }
+        }
+        const int q = static_cast<int>(t - t0);
+        const int st = q & 1;
+        if (!aborted) {
+            if (mbar_wait_bounded(&bars[st], (q >> 1) & 1, wd)) {
+                if (tid == 0) { if (st == 0) ++waited0; else ++waited1; }
+            } else {
+                atomicOr(err, DEV_ERR_TIMEOUT);
+                s_abort = 1;
+            }
+        }
+        const V4 *P = s_pos + st * g.J;
+        const V4 *Fq = s_frc + st * g.J;
+        const V4 *Wq = s_w + st * g.J;
+        for (int jj = 0; jj < g.J; ++jj) {
+            const V4 p = P[jj], f = Fq[jj], w = Wq[jj];
+#pragma unroll
+            for (int k = 0; k < R; ++k) vjp_term<TENSOR, MODE>(xi[k], yi[k], zi[k], Fi[k], Wi[k], p, f, w, c, m[k], gg[k]);
+        }
+        if constexpr (COMP) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                fold2(mh[k][0], ml[k][0], m[k].x);
+                fold2(mh[k][1], ml[k][1], m[k].y);
+                fold2(mh[k][2], ml[k][2], m[k].z);
+                fold2(gh[k][0], gl[k][0], gg[k].x);
+                fold2(gh[k][1], gl[k][1], gg[k].y);
+                fold2(gh[k][2], gl[k][2], gg[k].z);
+                m[k].x = m[k].y = m[k].z = S(0);
+                gg[k].x = gg[k].y = gg[k].z = S(0);
+            }
+        }
+        __syncthreads();
+        aborted = s_abort != 0;
+        if (tid == 0 && !aborted && t + 2 < t1) issue(t + 2, st);
+    }
+    flush(cur_ib);
+    if (tid == 0) {
+        for (int k = waited0; k < issued0; ++k)
+            if (!mbar_wait_bounded(&bars[0], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+        for (int k = waited1; k < issued1; ++k)
+            if (!mbar_wait_bounded(&bars[1], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+    }
+}
+
+static size_t v4b(int mode) { return mode == MODE_FP64 ? sizeof(dbl4) : sizeof(float4); }
+
+template <int TT, int MM>
+static void *vjp_fn() {
+    return reinterpret_cast<void *>(&vjp_kernel<TT, MM>);
+}
+
+static void *pick_vjp(int tensor, int mode) {
+    const int dt = (tensor == T_OSEEN) ? T_OSEEN : T_RP;
+    if (mode == MODE_FP64) return dt == T_OSEEN ? vjp_fn<T_OSEEN, MODE_FP64>() : vjp_fn<T_RP, MODE_FP64>();
+    return dt == T_OSEEN ? vjp_fn<T_OSEEN, MODE_FP32C>() : vjp_fn<T_RP, MODE_FP32C>();
+}
+
+cudaError_t vjp_setup(sd_handle *h) {
+    DenseGeom g{};
+    g.I = kNT * kRV;
+    g.nIB = h->npad / g.I;
+    const int mode = (h->mode == MODE_FP64) ? MODE_FP64 : MODE_FP32C;
+    void *fn = pick_vjp(h->tensor, mode);
+    int occ = 0;
+    const int Jc[3] = {kJmax, 128, 64};
+    for (int ci = 0; ci < 3; ++ci) {
+        const int J = Jc[ci];
+        if (mode == MODE_FP64 && J > 128) continue;
+        const size_t smem = 6 * static_cast<size_t>(J) * v4b(mode);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kNT, smem);
+        if (e != cudaSuccess) return e;
+        g.J = J;
+        g.nJT = h->npad / J;
+        if (static_cast<long long>(g.nIB) * g.nJT >= 4LL * h->num_sms * std::max(occ, 1)) break;
+    }
+    occ = std::max(occ, 1);
+    const long long T = static_cast<long long>(g.nIB) * g.nJT;
+    const long long want = static_cast<long long>(h->num_sms) * occ;
+    g.chunk = std::max(1LL, (T + want - 1) / want);
+    g.grid = static_cast<int>((T + g.chunk - 1) / g.chunk);
+    int ms = 0;
+    for (int ib = 0; ib < g.nIB; ++ib) ms = std::max(ms, geom_last(g, ib) - geom_first(g, ib) + 1);
+    g.maxSlots = ms;
+    h->geomv = g;
+    h->vjp_occ = occ;
+    return cudaSuccess;
+}
+
+cudaError_t launch_vjp_dense(sd_handle *h, cudaStream_t st, const void *posm, const void *frcm, const void *wm,
+                             double *partM, double *partG) {
+    const DenseGeom &g = h->geomv;
+    const bool f64 = h->mode == MODE_FP64;
+    const size_t smem = 6 * static_cast<size_t>(g.J) * v4b(f64 ? MODE_FP64 : MODE_FP32C);
+    const bool oseen = h->tensor == T_OSEEN;
+    prof_begin(h, SD_KERNEL_VJP, st);
+#define SD_VJP_LAUNCH(TT, MM)                                                                                 \
+    vjp_kernel<TT, MM><<<g.grid, kNT, smem, st>>>(                                                            \
+        static_cast<const typename VjpT<MM>::V4 *>(posm), static_cast<const typename VjpT<MM>::V4 *>(frcm),   \
+        static_cast<const typename VjpT<MM>::V4 *>(wm), partM, partG, h->npad, g, h->pc, h->d_err, h->watchdog)
+    if (f64) {
+        if (oseen) SD_VJP_LAUNCH(T_OSEEN, MODE_FP64); else SD_VJP_LAUNCH(T_RP, MODE_FP64);
+    } else {
+        if (oseen) SD_VJP_LAUNCH(T_OSEEN, MODE_FP32C); else SD_VJP_LAUNCH(T_RP, MODE_FP32C);
+    }
+#undef SD_VJP_LAUNCH
+    prof_end(h, SD_KERNEL_VJP, st);
+    ++h->launches;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- VJP epilogue
+
+struct VjpEpiArgs {
+    const double *partM, *partG;
+    int npad;
+    DenseGeom g;
+    const double *x64;
+    const void *posm;
+    const double *F64;
+    const void *frcm;
+    const double *W64;
+    const void *wm;
+    CellList cl;
+    double rnear2;
+    PairConst pc;
+    int n;
+    int out_dtype;   // SD_DTYPE_F32 / SD_DTYPE_F64 for gX / gF, or -1 = adjoint update
+    void *gx_out, *gF_out;
+    double dt;
+    double *lam_out;   // adjoint: lam_out = W + dt gX
+    double *gF_acc;    // adjoint: gF_acc += dt mu W
+    int *err;
+};
+
+template <int TENSOR, int MODE>
+__global__ void __launch_bounds__(128) vjp_epilogue_kernel(VjpEpiArgs a) {
+    using V4 = typename VjpT<MODE>::V4;
+    using V3 = typename VjpT<MODE>::V3;
+    using S = typename VjpT<MODE>::S;
+    constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const V4 *pm = static_cast<const V4 *>(a.posm);
+    const V4 *fm = static_cast<const V4 *>(a.frcm);
+    const V4 *wm = static_cast<const V4 *>(a.wm);
+    double M[3] = {0.0, 0.0, 0.0}, G[3] = {0.0, 0.0, 0.0};
+    {
+        const int ib = i / a.g.I;
+        const int ns = geom_last(a.g, ib) - geom_first(a.g, ib) + 1;
+        for (int s = 0; s < ns; ++s)
+            for (int d = 0; d < 3; ++d) {
+                M[d] += a.partM[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+                G[d] += a.partG[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+            }
+    }
+    const V4 pi = pm[i], fi4 = fm[i], wi4 = wm[i];
+    V3 Fi, Wi;
+    Fi.x = fi4.x; Fi.y = fi4.y; Fi.z = fi4.z;
+    Wi.x = wi4.x; Wi.y = wi4.y; Wi.z = wi4.z;
+    auto dense = [&](const V4 &pj, const V4 &fj, const V4 &wj, double tm[3], double tg[3]) {
+        V3 m, g;
+        m.x = m.y = m.z = S(0);
+        g.x = g.y = g.z = S(0);
+        vjp_term<TD, MODE>(pi.x, pi.y, pi.z, Fi, Wi, pj, fj, wj, a.pc, m, g);
+        tm[0] = m.x; tm[1] = m.y; tm[2] = m.z;
+        tg[0] = g.x; tg[1] = g.y; tg[2] = g.z;
+    };
+    {   // self: mu_ii W_i / mu0 = W_i; its x-derivative is zero
+        double tm[3], tg[3];
+        dense(pi, fi4, wi4, tm, tg);
+        for (int d = 0; d < 3; ++d) {
+            M[d] += a.W64[3 * i + d] - tm[d];
+            G[d] -= tg[d];
+        }
+    }
+    const double xi = a.x64[3 * i], yi = a.x64[3 * i + 1], zi = a.x64[3 * i + 2];
+    const double Fx = a.F64[3 * i], Fy = a.F64[3 * i + 1], Fz = a.F64[3 * i + 2];
+    const double Wx = a.W64[3 * i], Wy = a.W64[3 * i + 1], Wz = a.W64[3 * i + 2];
+    bool coincident = false;
+    for_each_neighbour(a.cl, i, a.cl.cell[i], [&](int j) {
+        const double dx = xi - a.x64[3 * j], dy = yi - a.x64[3 * j + 1], dz = zi - a.x64[3 * j + 2];
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= a.rnear2) return;
+        if (r2 == 0.0 && TENSOR != T_RPY) {
+            coincident = true;
+            return;
+        }
+        double A, B, dA, dB;
+        profile_exact<TENSOR>(r2, a.pc, A, B, dA, dB);
+        const double fx = a.F64[3 * j], fy = a.F64[3 * j + 1], fz = a.F64[3 * j + 2];
+        const double wx = a.W64[3 * j], wy = a.W64[3 * j + 1], wz = a.W64[3 * j + 2];
+        const double Wir = dx * Wx + dy * Wy + dz * Wz, Fir = dx * Fx + dy * Fy + dz * Fz;
+        const double Wjr = dx * wx + dy * wy + dz * wz, Fjr = dx * fx + dy * fy + dz * fz;
+        const double U = Wx * fx + Wy * fy + Wz * fz + wx * Fx + wy * Fy + wz * Fz;
+        const double Q = Wir * Fjr + Wjr * Fir;
+        const double cr = dA * U + dB * Q;
+        double tm[3], tg[3];
+        dense(pm[j], fm[j], wm[j], tm, tg);
+        M[0] += A * wx + B * Wjr * dx - tm[0];
+        M[1] += A * wy + B * Wjr * dy - tm[1];
+        M[2] += A * wz + B * Wjr * dz - tm[2];
+        G[0] += cr * dx + B * (Wx * Fjr + fx * Wir + wx * Fir + Fx * Wjr) - tg[0];
+        G[1] += cr * dy + B * (Wy * Fjr + fy * Wir + wy * Fir + Fy * Wjr) - tg[1];
+        G[2] += cr * dz + B * (Wz * Fjr + fz * Wir + wz * Fir + Fz * Wjr) - tg[2];
+    });
+    if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
+    const double m0 = a.pc.mu0;
+    for (int d = 0; d < 3; ++d) {
+        M[d] *= m0;
+        G[d] *= m0;
+    }
+    if (a.out_dtype == SD_DTYPE_F32) {
+        float *gx = static_cast<float *>(a.gx_out), *gF = static_cast<float *>(a.gF_out);
+        for (int d = 0; d < 3; ++d) {
+            if (gx) gx[3 * i + d] = static_cast<float>(G[d]);
+            if (gF) gF[3 * i + d] = static_cast<float>(M[d]);
+        }
+    } else if (a.out_dtype == SD_DTYPE_F64) {
+        double *gx = static_cast<double *>(a.gx_out), *gF = static_cast<double *>(a.gF_out);
+        for (int d = 0; d < 3; ++d) {
+            if (gx) gx[3 * i + d] = G[d];
+            if (gF) gF[3 * i + d] = M[d];
+        }
+    } else {
+        for (int d = 0; d < 3; ++d) {
+            a.lam_out[3 * i + d] = a.W64[3 * i + d] + a.dt * G[d];
+            a.gF_acc[3 * i + d] += a.dt * M[d];
+        }
+    }
+}
+
+cudaError_t launch_vjp_epilogue(sd_handle *h, cudaStream_t st, const double *x64, const void *posm,
+                                const double *F64, const void *frcm, const double *W64, const void *wm,
+                                int out_dtype, void *gx_out, void *gF_out, double dt, double *lam_out,
+                                double *gF_acc) {
+    if (h->n == 0) return cudaSuccess;
+    VjpEpiArgs a;
+    a.partM = h->part;
+    a.partG = h->part2;
+    a.npad = h->npad;
+    a.g = h->geomv;
+    a.x64 = x64;
+    a.posm = posm;
+    a.F64 = F64;
+    a.frcm = frcm;
+    a.W64 = W64;
+    a.wm = wm;
+    a.cl = h->cl;
+    a.rnear2 = h->r_near * h->r_near;
+    a.pc = h->pc;
+    a.n = h->n;
+    a.out_dtype = out_dtype;
+    a.gx_out = gx_out;
+    a.gF_out = gF_out;
+    a.dt = dt;
+    a.lam_out = lam_out;
+    a.gF_acc = gF_acc;
+    a.err = h->d_err;
+    const int nb = (h->n + 127) / 128;
+    prof_begin(h, SD_KERNEL_EPILOGUE, st);
+    const bool f64 = h->mode == MODE_FP64;
+    switch (h->tensor) {
+        case T_RPY:
+            if (f64) vjp_epilogue_kernel<T_RPY, MODE_FP64><<<nb, 128, 0, st>>>(a);
+            else vjp_epilogue_kernel<T_RPY, MODE_FP32C><<<nb, 128, 0, st>>>(a);
+            break;
+        case T_RP:
+            if (f64) vjp_epilogue_kernel<T_RP, MODE_FP64><<<nb, 128, 0, st>>>(a);
+            else vjp_epilogue_kernel<T_RP, MODE_FP32C><<<nb, 128, 0, st>>>(a);
+            break;
+        default:
+            if (f64) vjp_epilogue_kernel<T_OSEEN, MODE_FP64><<<nb, 128, 0, st>>>(a);
+            else vjp_epilogue_kernel<T_OSEEN, MODE_FP32C><<<nb, 128, 0, st>>>(a);
+            break;
+    }
+    prof_end(h, SD_KERNEL_EPILOGUE, st);
+    ++h->launches;
+    return cudaGetLastError();
+}
+
+}  // namespace sd

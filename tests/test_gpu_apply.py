@@ -1,0 +1,168 @@
+"""GPU mobility apply (Sec. 2.2 Eq. rotneMobility, Sec. 3.1 step 3) against the
+FP64 oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1205_6333_gb300 as sd
+from paper_1205_6333_gb300 import inputs
+from helpers import TOL, rel_err, system_with_overlaps
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64", "fp32"])
+@pytest.mark.parametrize("tensor", ["rpy", "rp", "oseen"])
+@pytest.mark.parametrize("n", [1, 2, 3, 33, 513, 1500])
+def test_apply_matches_oracle(prec, tensor, n):
+    x, _ = system_with_overlaps(n, 0.05, seed=100 + n)
+    F = inputs.normal_forces(n, seed=200 + n)
+    with sd.System(n, tensor=tensor, prec=prec) as s:
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+    ref = oracle.mobility_apply(x, F, tensor)
+    assert rel_err(v, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_apply_float32_inputs(prec):
+    """Workload 2 shape at a size the full oracle finishes quickly: float32 positions
+    and forces, widened exactly on both sides."""
+    n = 4096
+    x, _ = inputs.cube_rsa(n, 0.05, inputs.SEED_BASE + 2)
+    x = x.astype(np.float32)
+    F = inputs.normal_forces(n, inputs.SEED_BASE + 1002).astype(np.float32)
+    with sd.System(n, prec=prec) as s:
+        s.set_positions(x.astype(np.float64))
+        v = s.mobility_apply(F)
+        assert v.dtype == np.float32
+        v64 = s.mobility_apply(F.astype(np.float64))
+    ref = oracle.mobility_apply(x, F, "rpy")
+    assert rel_err(v64, ref) <= TOL[prec]
+    assert rel_err(v, ref) <= max(TOL[prec], 2e-7)   # output rounded to float32
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_apply_full_size_sampled_rows(prec):
+    """N = 65,536 at volume fraction 0.05 (the benchmark's size and launch shape),
+    checked on 384 seeded rows that the oracle computes one by one."""
+    w = inputs.config_inputs(2)
+    x, F = w["x"], w["F"]
+    n = x.shape[0]
+    with sd.System(n, prec=prec) as s:
+        s.set_positions(x.astype(np.float64))
+        v = s.mobility_apply(F.astype(np.float64))
+    rows = np.random.default_rng(5).choice(n, 384, replace=False)
+    rows = np.concatenate([rows, [0, 1, n - 1]]).astype(np.int32)
+    ref = oracle.mobility_rows(x, F, rows, "rpy", nthreads=8)
+    den = np.linalg.norm(oracle.mobility_rows(x, F, rows, "rpy", nthreads=8), axis=1).max()
+    err = np.linalg.norm(v[rows] - ref, axis=1).max() / den
+    assert err <= TOL[prec]
+
+
+def test_plain_fp32_accumulation_is_less_accurate():
+    """Ablation: the compensated sum beats plain FP32 accumulation at large N."""
+    w = inputs.config_inputs(2, n=32768)
+    x, F = w["x"].astype(np.float64), w["F"].astype(np.float64)
+    rows = np.arange(0, 32768, 97, dtype=np.int32)
+    ref = oracle.mobility_rows(x, F, rows, "rpy", nthreads=8)
+    errs = {}
+    for prec in ["fp32c", "fp32"]:
+        with sd.System(32768, prec=prec) as s:
+            s.set_positions(x)
+            errs[prec] = rel_err(s.mobility_apply(F)[rows], ref)
+    assert errs["fp32c"] <= TOL["fp32c"]
+    assert errs["fp32c"] < errs["fp32"]
+
+
+def test_far_from_origin():
+    """Large absolute coordinates: separations stay accurate (mirror relative to a
+    particle, near pairs in FP64)."""
+    n = 2000
+    x, _ = system_with_overlaps(n, 0.1, seed=3)
+    x = x + np.array([1.0e4, -3.0e4, 5.0e3])
+    F = inputs.normal_forces(n, seed=4)
+    with sd.System(n) as s:
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+    assert rel_err(v, oracle.mobility_apply(x, F, "rpy")) <= TOL["fp32c"]
+
+
+def test_single_sphere_and_empty():
+    with sd.System(1, a=0.7, eta=1.3) as s:
+        s.set_positions([[1.0, 2.0, 3.0]])
+        v = s.mobility_apply(np.array([[0.5, -1.0, 2.0]]))
+    np.testing.assert_allclose(v, np.array([[0.5, -1.0, 2.0]]) / (6 * np.pi * 1.3 * 0.7), rtol=1e-6)
+    with sd.System(0) as s:
+        s.set_positions(np.zeros((0, 3)))
+        assert s.mobility_apply(np.zeros((0, 3))).shape == (0, 3)
+
+
+def test_coincident_particles():
+    x = np.array([[0.0, 0.0, 0.0], [3.0, 0.0, 0.0], [3.0, 0.0, 0.0]])
+    F = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    with sd.System(3, tensor="rpy", prec="fp64") as s:
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+    assert rel_err(v, oracle.mobility_apply(x, F, "rpy")) <= 1e-12
+    for tensor in ["rp", "oseen"]:
+        with sd.System(3, tensor=tensor) as s:
+            s.set_positions(x)
+            with pytest.raises(sd.SDError) as ei:
+                s.mobility_apply(F)
+            assert ei.value.status_name == "SD_ERR_COINCIDENT"
+
+
+def test_nonfinite_inputs_are_reported():
+    with sd.System(4) as s:
+        with pytest.raises(sd.SDError) as ei:
+            s.set_positions(np.array([[0, 0, 0], [5, 0, 0], [np.nan, 0, 0], [0, 5, 0]], float))
+        assert ei.value.status_name == "SD_ERR_NONFINITE"
+        s.set_positions(np.array([[0, 0, 0], [5, 0, 0], [10, 0, 0], [0, 5, 0]], float))
+        with pytest.raises(sd.SDError) as ei:
+            s.mobility_apply(np.array([[0, 0, 0], [1, 0, 0], [np.inf, 0, 0], [0, 0, 1]], float))
+        assert ei.value.status_name == "SD_ERR_NONFINITE"
+        # the handle stays usable
+        v = s.mobility_apply(np.ones((4, 3)))
+        assert np.all(np.isfinite(v))
+
+
+def test_device_pointers_and_torch_stream():
+    import torch
+    n = 1200
+    x, _ = system_with_overlaps(n, 0.05, seed=9)
+    F = inputs.normal_forces(n, seed=10)
+    with sd.System(n, stream="torch", torch_allocator=True) as s:
+        xt = torch.tensor(x, device="cuda")
+        s.set_positions(xt)
+        Ft = torch.tensor(F, device="cuda", dtype=torch.float32)
+        vt = s.mobility_apply(Ft)
+        s.synchronize()
+        assert vt.is_cuda and vt.dtype == torch.float32
+        v_dev = vt.cpu().numpy()
+        v_host = s.mobility_apply(F.astype(np.float32))
+        np.testing.assert_array_equal(v_dev, v_host)
+    assert rel_err(v_dev, oracle.mobility_apply(x, F.astype(np.float32), "rpy")) <= TOL["fp32c"]
+
+
+def test_repeatable_bitwise():
+    n = 3000
+    x, _ = system_with_overlaps(n, 0.05, seed=11)
+    F = inputs.normal_forces(n, seed=12)
+    with sd.System(n) as s:
+        s.set_positions(x)
+        a = s.mobility_apply(F)
+        b = s.mobility_apply(F)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_linearity_and_time_reversal_on_gpu():
+    n = 800
+    x, _ = system_with_overlaps(n, 0.05, seed=13)
+    F = inputs.normal_forces(n, seed=14)
+    with sd.System(n, prec="fp64") as s:
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+        np.testing.assert_allclose(s.mobility_apply(-2.0 * F), -2.0 * v, rtol=1e-13, atol=1e-15)
+        s.set_positions(-x)
+        np.testing.assert_allclose(s.mobility_apply(-F), -v, rtol=1e-12, atol=1e-14)

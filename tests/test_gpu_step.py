@@ -1,0 +1,136 @@
+"""Euler time stepping on the GPU (Sec. 3.1: positions, forces, velocities) against
+the FP64 oracle; the four-sphere orbit of Sec. 4."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1205_6333_gb300 as sd
+from paper_1205_6333_gb300 import inputs
+from helpers import system_with_overlaps
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _run(x0, nsteps, dt, prec, gravity=(0, 0, -1.0), fext=None, rep_eps=0.0, tensor="rpy"):
+    n = x0.shape[0]
+    with sd.System(n, prec=prec, gravity=gravity, rep_eps=rep_eps, rep_rc=2.5, tensor=tensor) as s:
+        s.set_positions(x0)
+        if fext is not None:
+            s.set_forces(fext)
+        s.step(dt, nsteps)
+        return s.get_positions()
+
+
+@pytest.mark.parametrize("dt_unit", ["tau_s", "raw"])
+def test_square_cluster_matches_oracle(dt_unit):
+    """Four spheres on a horizontal square (side 4a, +-0.01a jitter), F=(0,0,-1),
+    20,000 Euler steps; dt = 0.01 in units of tau_s = a/(mu0 F) (Sec. 3.3) or raw."""
+    x0 = inputs.config_inputs(1)["x"]
+    tau = 1.0 / oracle.mu0()
+    dt = 0.01 * tau if dt_unit == "tau_s" else 0.01
+    ref = oracle.euler(x0, 20000, dt, gravity=(0, 0, -1.0))
+    g64 = _run(x0, 20000, dt, "fp64")
+    assert np.abs(g64 - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max())
+    g32 = _run(x0, 20000, dt, "fp32c")
+    assert np.abs(g32 - ref).max() <= 1e-6 * np.abs(ref - x0).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_four_sphere_orbit_on_gpu(prec):
+    """Tory's orbit (Sec. 4): period ~517 tau_s, particles 1 and 3 stay in the xz plane."""
+    g = json.load(open(os.path.join(GOLDEN, "four_sphere_orbit.json")))
+    tau = 1.0 / oracle.mu0()
+    dt = g["dt_tau_s"] * tau
+    x = np.array(g["start"])
+    traj = []
+    chunk = 100
+    with sd.System(4, prec=prec, tensor="rp", gravity=g["force"]) as s:
+        s.set_positions(x)
+        for _ in range(int(1000.0 / g["dt_tau_s"]) // chunk):
+            s.step(dt, chunk)
+            traj.append(s.get_positions())
+    traj = np.array(traj)
+    x1 = traj[:, 0, 0]
+    k = np.nonzero((x1[1:-1] > x1[:-2]) & (x1[1:-1] >= x1[2:]))[0] + 1
+    t = (k + 1) * chunk * g["dt_tau_s"]
+    assert len(t) >= 2
+    assert np.diff(t) == pytest.approx(np.full(len(t) - 1, g["period_tau_s"]), rel=0.01)
+    drift = np.abs(traj[:, [0, 2], 1]).max()
+    assert drift <= (1e-12 if prec == "fp64" else 1e-5)
+    # and the oracle's trajectory at the sampled times
+    ref = oracle.euler(np.array(g["start"]), len(traj) * chunk, dt, gravity=g["force"], tensor="rp", every=chunk)[1]
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    assert np.abs(traj - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32c", 1e-5)])
+def test_repulsion_gravity_matches_oracle(prec, tol):
+    """Workload-3 physics at a size the oracle integrates in seconds: phi = 0.10,
+    gravity + eps (2a/r)^12 repulsion cut at 2.5a, dt = 1e-3, 100 steps."""
+    n = 2048
+    x0, _ = inputs.cube_rsa(n, 0.10, inputs.SEED_BASE + 3)
+    ref = oracle.euler(x0, 100, 1e-3, gravity=(0, 0, -1.0), rep_eps=1.0, rep_rc=2.5, nthreads=8)
+    got = _run(x0, 100, 1e-3, prec, rep_eps=1.0)
+    assert np.abs(got - ref).max() <= tol * np.abs(ref - x0).max()
+
+
+def test_external_forces_and_overlaps_step():
+    n = 900
+    x0, _ = system_with_overlaps(n, 0.05, seed=21, overlaps=5)
+    fe = inputs.normal_forces(n, seed=22)
+    ref = oracle.euler(x0, 7, 0.05, fext=fe, gravity=(0.1, 0, -0.5))
+    got = _run(x0, 7, 0.05, "fp32c", gravity=(0.1, 0, -0.5), fext=fe)
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref - x0).max()
+
+
+def test_graph_replay_equals_eager_steps():
+    n = 1000
+    x0, _ = inputs.cube_rsa(n, 0.05, 31)
+    with sd.System(n, gravity=(0, 0, -1.0), rep_eps=1.0) as s:
+        s.set_positions(x0)
+        s.step(0.01, 35)          # two graph replays + 3 eager steps
+        a = s.get_positions()
+        s.set_positions(x0)
+        for _ in range(35):
+            s.step(0.01, 1)
+        b = s.get_positions()
+        c0 = s.launch_count()
+        s.step(0.01, 16)
+        s.synchronize()
+        assert s.launch_count() > c0
+    np.testing.assert_array_equal(a, b)
+
+
+def test_profiler_times_kernels():
+    n = 4096
+    x0, _ = inputs.cube_rsa(n, 0.05, 41)
+    with sd.System(n, gravity=(0, 0, -1.0)) as s:
+        s.set_positions(x0)
+        s.profile(True)
+        s.step(0.01, 3)
+        ms, cnt = s.profile_read(sd.SD_KERNEL_DENSE)
+        assert cnt == 3 and ms > 0
+        ms_e, cnt_e = s.profile_read(sd.SD_KERNEL_EPILOGUE)
+        assert cnt_e == 3 and ms_e > 0
+        s.profile(False)
+
+
+def test_checkpoint_resume_is_exact():
+    """Positions read back and set again resume the trajectory bit for bit."""
+    n = 700
+    x0, _ = inputs.cube_rsa(n, 0.05, 51)
+    with sd.System(n, gravity=(0, 0, -1.0)) as s:
+        s.set_positions(x0)
+        s.step(0.02, 40)
+        full = s.get_positions()
+        s.set_positions(x0)
+        s.step(0.02, 17)
+        mid = s.get_positions()
+    with sd.System(n, gravity=(0, 0, -1.0)) as s2:
+        s2.set_positions(mid)
+        s2.step(0.02, 23)
+        np.testing.assert_array_equal(s2.get_positions(), full)

@@ -1,0 +1,90 @@
+"""Adjoint on the GPU: vector-Jacobian products of v = mu(x) F and the reverse
+sweep through Euler steps with checkpoints, against the FP64 oracle and central
+finite differences."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1205_6333_gb300 as sd
+from paper_1205_6333_gb300 import inputs
+from helpers import rel_err, system_with_overlaps
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("tensor", ["rpy", "rp", "oseen"])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32c", 1e-5)])
+def test_vjp_matches_oracle(tensor, prec, tol):
+    n = 700
+    x, _ = system_with_overlaps(n, 0.05, seed=61 + n, overlaps=4)
+    F = inputs.normal_forces(n, 62)
+    W = inputs.normal_forces(n, 63)
+    with sd.System(n, tensor=tensor, prec=prec) as s:
+        s.set_positions(x)
+        gx, gF = s.vjp(F, W)
+    rx, rF = oracle.vjp(x, F, W, tensor)
+    assert rel_err(gF, rF) <= tol
+    assert rel_err(gx, rx) <= 10 * tol
+
+
+def _adjoint_case(n=64, seed=inputs.SEED_BASE + 5):
+    x0, L = inputs.cube_rsa(n, 0.05, seed)
+    target = x0 + np.random.default_rng(seed + 3).standard_normal(x0.shape)
+    return x0, target
+
+
+def test_adjoint_matches_oracle_n64():
+    """Workload 5 protocol on an N=64 system: gravity, dt = 0.01, 1000 steps,
+    L = sum |x(T) - x*|^2, checkpoints every 50 steps; full gradients."""
+    x0, target = _adjoint_case()
+    nsteps, dt, K = 1000, 0.01, 50
+    g = (0.0, 0.0, -1.0)
+    fe = np.zeros_like(x0)
+    xT = oracle.euler(x0, nsteps, dt, fe, g)
+    gxT = 2.0 * (xT - target)
+    rx0, rF = oracle.adjoint(x0, fe, gxT, nsteps, dt, g)
+    for prec, tol in [("fp64", 1e-9), ("fp32c", 1e-4)]:
+        with sd.System(64, prec=prec, gravity=g) as s:
+            s.set_positions(x0)
+            gx0, gF = s.adjoint(dt, nsteps, K, gxT)
+            np.testing.assert_array_equal(s.get_positions(), x0)   # state restored
+        assert rel_err(gx0, rx0) <= tol, prec
+        assert rel_err(gF, rF) <= tol, prec
+
+
+def test_adjoint_finite_differences_fp64():
+    """Central differences (h = 1e-4) of the GPU FP64 trajectory loss."""
+    x0, target = _adjoint_case()
+    nsteps, dt, K, h = 1000, 0.01, 50, 1e-4
+    g = (0.0, 0.0, -1.0)
+    with sd.System(64, prec="fp64", gravity=g) as s:
+        def loss(x, f):
+            s.set_positions(x)
+            s.set_forces(f)
+            s.step(dt, nsteps)
+            return float(((s.get_positions() - target) ** 2).sum())
+
+        fe = np.zeros_like(x0)
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(dt, nsteps)
+        xT = s.get_positions()
+        s.set_positions(x0)
+        gx0, gF = s.adjoint(dt, nsteps, K, 2.0 * (xT - target))
+        rng = np.random.default_rng(7)
+        for comp in rng.choice(64 * 3, 6, replace=False):
+            i, d = divmod(int(comp), 3)
+            e = np.zeros_like(x0)
+            e[i, d] = h
+            fdx = (loss(x0 + e, fe) - loss(x0 - e, fe)) / (2 * h)
+            fdF = (loss(x0, fe + e) - loss(x0, fe - e)) / (2 * h)
+            assert abs(gx0[i, d] - fdx) <= 1e-6 * max(abs(fdx), np.abs(gx0).max() * 1e-3)
+            assert abs(gF[i, d] - fdF) <= 1e-6 * max(abs(fdF), np.abs(gF).max() * 1e-3)
+
+
+def test_adjoint_rejects_repulsion():
+    with sd.System(8, rep_eps=1.0) as s:
+        s.set_positions(np.arange(24, dtype=float).reshape(8, 3) * 3)
+        with pytest.raises(sd.SDError) as ei:
+            s.adjoint(0.01, 2, 1, np.ones((8, 3)))
+        assert ei.value.status_name == "SD_ERR_UNSUPPORTED"
