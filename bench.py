@@ -1,0 +1,404 @@
+"""Benchmark of the all-pairs Stokesian-dynamics hot path on GB300.
+
+One JSON line on rank 0.  A step is one explicit Euler step (Sec. 3.1) of the
+N = 65,536 system at volume fraction 0.05 with per-particle N(0,1) forces,
+float32 inputs, RPY tensor, FP32-compensated pair sums, FP64 positions:
+cell-list build + FP32 mirror, all-pairs kernel, FP64 near/self terms and split
+reduction, Euler update.  value = N^2 pair interactions per second (self pairs
+included, as the paper counts them).
+
+Extra legs on rank 0 (reported in the same line): the plain FP64 GPU path on the
+same system, the batched workload (16,384 clusters, N per cluster U{4..256}),
+and the CPU oracle on a bounded sample (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank steps its own replica (weak scaling, no collective on
+the data path); the elapsed time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RPY pair-interactions/s at N=65536 (FP32-comp vs FP64), batched steps/s"
+UNIT = "pair-interactions/s"
+N_MAIN = 65536
+PHI = 0.05
+DT = 0.01
+FLOPS_PER_PAIR = 34          # RPY pair term, FMA = 2 flops
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                p = [s.strip() for s in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = [nm for k, nm in enumerate(names) if any(r[5 + k] == "Active" for r in rows)]
+        loaded = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def _flush_l2(buf):
+    buf.add_(1)
+
+
+def _time_steps(step, nsteps, stream, flush_buf):
+    """Sum of CUDA-event durations of `nsteps` calls of step(), each preceded by an
+    L2 flush outside the events."""
+    import torch
+    total = 0.0
+    evs = []
+    for _ in range(nsteps):
+        _flush_l2(flush_buf)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        total += e0.elapsed_time(e1)
+    return total
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _main_inputs(n):
+    from paper_1205_6333_gb300 import inputs
+    x, L = inputs.cube_rsa(n, PHI, inputs.SEED_BASE + 2)
+    F = inputs.normal_forces(n, inputs.SEED_BASE + 1002)
+    return x.astype(np.float32).astype(np.float64), F.astype(np.float32).astype(np.float64), L
+
+
+def cpu_baseline(x, F, target_s=10.0):
+    """The FP64 oracle as it stands, on all host cores, on a bounded row sample of
+    the same system; pairs/s scaled from the sample."""
+    import oracle
+    n = x.shape[0]
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(123)
+    rows = rng.choice(n, 128, replace=False).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.mobility_rows(x, F, rows, "rpy", nthreads=cores)
+    t1 = time.perf_counter()
+    rate = len(rows) * n / max(t1 - t0, 1e-6)
+    nrows = int(min(n, max(128, target_s * rate / n)))
+    rows = rng.choice(n, nrows, replace=False).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.mobility_rows(x, F, rows, "rpy", nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": nrows * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d rows of the N=%d apply (RPY, FP64, ascending-j loop, OpenMP over rows); %.1f s"
+                      % (nrows, n, n, dt)}
+
+
+def _config(L, world):
+    return {"workload": "rpy_euler_step_N65536_phi0.05_cube_fp32c", "n": N_MAIN, "phi": PHI,
+            "box_side": L, "tensor": "rpy", "precision": "fp32 pair terms, compensated sums, fp64 state",
+            "step": "cells+mirror, all-pairs, fp64 near/self + reduction, Euler", "dt": DT,
+            "l2": "flushed (512 MiB write) before every timed step",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host cores, same metric/config."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    x, F, L = _main_inputs(N_MAIN)
+    cores = os.cpu_count() or 1
+    rows_per_step = 2048
+    rng = np.random.default_rng(7)
+    for _ in range(args.warmup):
+        r = rng.choice(N_MAIN, 64, replace=False).astype(np.int32)
+        oracle.mobility_rows(x, F, r, "rpy", nthreads=cores)
+    t = 0.0
+    for _ in range(args.steps):
+        r = rng.choice(N_MAIN, rows_per_step, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.mobility_rows(x, F, r, "rpy", nthreads=cores)
+        t += time.perf_counter() - t0
+    pairs = args.steps * rows_per_step * N_MAIN
+    val = pairs / t
+    sample = ("each step: %d seeded rows of the N=%d apply (RPY, FP64 oracle, %d threads)"
+              % (rows_per_step, N_MAIN, cores))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": _config(L, 1),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_1205_6333_gb300 as sd
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    x, F, L = _main_inputs(N_MAIN)
+    n = N_MAIN
+    s = sd.System(n, prec="fp32c", tensor="rpy", stream="torch", torch_allocator=True, device=dev)
+    s.set_positions(x)
+    s.set_forces(F)
+    step = lambda: s.step(DT, 1)   # noqa: E731
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time of K steps, kernel events for the roofline
+    s.profile(True)
+    l0 = s.launch_count()
+    _barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t_ms = _time_steps(step, args.steps, stream, flush)
+    torch.cuda.synchronize()
+    _barrier(world)
+    launches = s.launch_count() - l0
+    dense_ms, dense_n = s.profile_read(sd.SD_KERNEL_DENSE)
+    epi_ms, _ = s.profile_read(sd.SD_KERNEL_EPILOGUE)
+    cells_ms, _ = s.profile_read(sd.SD_KERNEL_CELLS)
+    s.profile(False)
+    t_ms = _max_over_ranks(t_ms, world)
+    ms_step = t_ms / args.steps
+    value = world * float(n) * n / (ms_step * 1e-3)
+
+    # ---- end to end through the public API with pinned host buffers
+    xh = torch.from_numpy(x).pin_memory()
+    outh = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    _barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_positions(xh)          # H2D of the step's input (synchronous call)
+        s.step(DT, 1)
+        s.get_positions(outh)        # D2H of the step's result
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = world * float(n) * n * args.steps / e2e_s
+
+    clocks = clk.summary()
+    peaks, peak_src = _peaks()
+    sms = props.multi_processor_count
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    dense_avg_ms = dense_ms / max(dense_n, 1)
+    achieved = FLOPS_PER_PAIR * float(n) * n / (dense_avg_ms * 1e-3) / 1e12
+    s.close()
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        extra = legs(args, x, F, stream, flush)
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(L, world),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "dense_kernel<RP, FP32C>",
+                     "flops_per_launch": FLOPS_PER_PAIR * float(n) * n,
+                     "avg_launch_ms": dense_avg_ms, "launches": dense_n,
+                     "peak_source": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz, %s)"
+                                    % (sms, FP32_LANES_PER_SM, peaks.get("sm_max_mhz", 2070.0), peak_src)},
+        "kernel_ms_per_step": {"dense": dense_ms / args.steps, "epilogue": epi_ms / args.steps,
+                               "cells": cells_ms / args.steps},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 24 * n},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def legs(args, x, F, stream, flush):
+    """FP64 path, batched workload and the CPU oracle baseline (rank 0 only)."""
+    import torch
+    import paper_1205_6333_gb300 as sd
+    from paper_1205_6333_gb300 import inputs
+    out = {}
+    n = x.shape[0]
+    # plain FP64 GPU path on the same system
+    s = sd.System(n, prec="fp64", stream="torch")
+    s.set_positions(x)
+    s.set_forces(F)
+    s.step(DT, 1)
+    torch.cuda.synchronize()
+    k = max(2, min(5, args.steps))
+    t = _time_steps(lambda: s.step(DT, 1), k, stream, flush)
+    s.close()
+    fp64_ms = t / k
+    out["fp64"] = {"value": float(n) * n / (fp64_ms * 1e-3), "unit": UNIT, "ms_per_step": fp64_ms, "steps": k}
+
+    # batched clusters (16,384 clusters, N ~ U{4..256}, phi = 0.05, forces N(0,1))
+    w = inputs.config_inputs(4)
+    off = w["offsets"]
+    sizes = np.diff(off).astype(np.int64)
+    pairs = float((sizes ** 2).sum())
+    b = sd.Batch(off, prec="fp32c", stream="torch", torch_allocator=True)
+    b.set_positions(w["x"])
+    b.set_forces(w["F"])
+    choice = b.autotune()
+    b.step(0.01, 3)
+    torch.cuda.synchronize()
+    kb = max(args.steps, 10)
+    b.profile(True)
+    tb = _time_steps(lambda: b.step(0.01, 1), kb, stream, flush)
+    bk_ms, bk_n = b.profile_read(sd.SD_KERNEL_BATCHED)
+    b.profile(False)
+    # steady state through the captured graph (16 steps per replay)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(0.01, 160)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g_ms = e0.elapsed_time(e1) / 160
+    b.close()
+    P = int(off[-1])
+    bytes_step = P * (24 + 16 + 24)
+    ms_b = tb / kb
+    out["batched"] = {
+        "steps_per_s": 1e3 / ms_b, "ms_per_step": ms_b, "graph_ms_per_step": g_ms,
+        "graph_steps_per_s": 1e3 / g_ms, "pairs_per_s": pairs / (ms_b * 1e-3),
+        "clusters": int(len(sizes)), "particles": P, "pairs_per_step": pairs,
+        "kernel_avg_ms": bk_ms / max(bk_n, 1),
+        "kernel_tflops": FLOPS_PER_PAIR * pairs / (bk_ms / max(bk_n, 1) * 1e-3) / 1e12,
+        "algorithmic_gbs": bytes_step / (bk_ms / max(bk_n, 1) * 1e-3) / 1e9,
+        "autotune_choice": int(choice), "steps": kb}
+    # the CPU oracle on a bounded sample
+    out["cpu_baseline"] = cpu_baseline(x, F, target_s=args.cpu_seconds)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="main leg only")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
