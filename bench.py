@@ -308,7 +308,7 @@ def run_ours(args):
         "config": _config(L, world),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": None,
-                     "kernel": "dense_kernel<RP, FP32C>",
+                     "kernel": "dense2_kernel<RP, FP32C> (packed f32x2)",
                      "flops_per_launch": FLOPS_PER_PAIR * float(n) * n,
                      "avg_launch_ms": dense_avg_ms, "launches": dense_n,
                      "peak_source": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz, %s)"

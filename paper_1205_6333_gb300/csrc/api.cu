@@ -133,8 +133,9 @@ static sd_status launch_check(cudaError_t e, const char *what) {
 static cudaError_t launch_step(sd_handle *h, cudaStream_t st, double dt, const double *x_in, double *x_out) {
     cudaError_t e = launch_build_cells(h, st, x_in, h->posm);
     if (e == cudaSuccess && !h->forces_const) e = launch_forces_rep(h, st, x_in);
+    if (e == cudaSuccess) e = launch_near(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos);
     if (e == cudaSuccess) e = launch_dense(h, st, h->posm, h->frcm, h->part);
-    if (e == cudaSuccess) e = launch_epilogue(h, st, OUT_EULER, x_in, h->posm, h->F64, h->frcm, nullptr, dt, x_out);
+    if (e == cudaSuccess) e = launch_epilogue(h, st, OUT_EULER, x_in, h->posm.aos, h->F64, h->frcm.aos, nullptr, dt, x_out);
     return e;
 }
 
@@ -271,17 +272,19 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     const size_t n3 = 3 * static_cast<size_t>(std::max(h->n, 1));
     const size_t np = static_cast<size_t>(std::max(h->npad, kPadTo));
     const size_t vb = v4size(h);
-    bool ok = dalloc_t(h, h->d_err, 1);
+    bool ok = dalloc_t(h, h->d_err, 1) && dalloc_t(h, h->d_flag, 1) && dalloc_t(h, h->near64, 2 * n3);
     for (int b = 0; b < 2 && ok; ++b) ok = dalloc_t(h, h->x64[b], n3);
-    h->posm = ok ? dalloc(h, np * vb) : nullptr;
-    ok = ok && h->posm;
     ok = ok && dalloc_t(h, h->fext64, n3) && dalloc_t(h, h->F64, n3) && dalloc_t(h, h->Fa64, n3) &&
          dalloc_t(h, h->Wa64, n3);
-    if (ok) {
-        h->frcm = dalloc(h, np * vb);
-        h->frcam = dalloc(h, np * vb);
-        h->wam = dalloc(h, np * vb);
-        ok = h->frcm && h->frcam && h->wam;
+    const bool soa = h->mode != MODE_FP64;
+    for (Mirror *m : {&h->posm, &h->frcm, &h->frcam, &h->wam}) {
+        if (!ok) break;
+        m->aos = dalloc(h, np * vb);
+        ok = m->aos != nullptr;
+        if (ok && soa && m != &h->wam) {
+            m->soa = static_cast<float *>(dalloc(h, 3 * np * sizeof(float)));
+            ok = m->soa != nullptr;
+        }
     }
     if (!ok) return fail(SD_ERR_OOM, "device allocation of particle buffers");
 
@@ -313,11 +316,12 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     // zero everything that padding or defaults rely on
     cudaStream_t st = h->stream;
     e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->posm, 0, np * vb, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, sizeof(int), st);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(h->x64[b], 0, n3 * sizeof(double), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->frcm, 0, np * vb, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->frcam, 0, np * vb, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->wam, 0, np * vb, st);
+    for (Mirror *m : {&h->posm, &h->frcm, &h->frcam, &h->wam}) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->aos, 0, np * vb, st);
+        if (e == cudaSuccess && m->soa) e = cudaMemsetAsync(m->soa, 0, 3 * np * sizeof(float), st);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fext64, 0, n3 * sizeof(double), st);
     if (e == cudaSuccess) e = launch_stage_forces(h, st, nullptr, SD_DTYPE_F64, 1, h->F64, h->frcm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -333,10 +337,13 @@ void sd_destroy(sd_handle *h) {
     drop_graphs(h);
     prof_destroy(h->prof);
     for (int b = 0; b < 2; ++b) dfree(h, h->x64[b]);
-    dfree(h, h->posm);
-    void *bufs[] = {h->fext64, h->F64, h->frcm, h->Fa64, h->frcam, h->Wa64, h->wam, h->part, h->part2,
+    for (Mirror *m : {&h->posm, &h->frcm, &h->frcam, &h->wam}) {
+        dfree(h, m->aos);
+        dfree(h, m->soa);
+    }
+    void *bufs[] = {h->fext64, h->F64, h->Fa64, h->Wa64, h->part, h->part2,
                     h->cl.cell, h->cl.key, h->cl.cnt, h->cl.fill, h->cl.start, h->cl.bsum, h->cl.sorted,
-                    h->ckpt, h->seg, h->lam, h->gFacc, h->d_err};
+                    h->ckpt, h->seg, h->lam, h->gFacc, h->near64, h->d_flag, h->d_err};
     for (void *p : bufs) dfree(h, p);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
@@ -438,10 +445,12 @@ sd_status sd_mobility_apply(sd_handle *h, const void *F, void *V, int dtype, int
     }
     sd_status s = launch_check(launch_stage_forces(h, h->stream, Fd, dtype, 0, h->Fa64, h->frcam), "stage F");
     if (s == SD_OK) s = ensure_cells(h);
+    if (s == SD_OK)
+        s = launch_check(launch_near(h, h->stream, h->x64[h->cur], h->posm.aos, h->Fa64, h->frcam.aos), "near pass");
     if (s == SD_OK) s = launch_check(launch_dense(h, h->stream, h->posm, h->frcam, h->part), "dense kernel");
     if (s == SD_OK)
         s = launch_check(launch_epilogue(h, h->stream, dtype == SD_DTYPE_F32 ? OUT_F32 : OUT_F64, h->x64[h->cur],
-                                         h->posm, h->Fa64, h->frcam, Vd, 0.0, nullptr),
+                                         h->posm.aos, h->Fa64, h->frcam.aos, Vd, 0.0, nullptr),
                          "epilogue");
     if (s != SD_OK) return s;
     if (!on_device) {
@@ -511,11 +520,11 @@ sd_status sd_mobility_vjp(sd_handle *h, const void *F, const void *W, void *gX, 
     if (s == SD_OK) s = launch_check(launch_stage_forces(h, h->stream, Wd, dtype, 0, h->Wa64, h->wam), "stage W");
     if (s == SD_OK) s = ensure_cells(h);
     if (s == SD_OK)
-        s = launch_check(launch_vjp_dense(h, h->stream, h->posm, h->frcam, h->wam, h->part, h->part2),
+        s = launch_check(launch_vjp_dense(h, h->stream, h->posm.aos, h->frcam.aos, h->wam.aos, h->part, h->part2),
                          "vjp kernel");
     if (s == SD_OK)
-        s = launch_check(launch_vjp_epilogue(h, h->stream, h->x64[h->cur], h->posm, h->Fa64, h->frcam,
-                                             h->Wa64, h->wam, dtype, gXd, gFd, 0.0, nullptr, nullptr),
+        s = launch_check(launch_vjp_epilogue(h, h->stream, h->x64[h->cur], h->posm.aos, h->Fa64, h->frcam.aos,
+                                             h->Wa64, h->wam.aos, dtype, gXd, gFd, 0.0, nullptr, nullptr),
                          "vjp epilogue");
     if (s != SD_OK) return s;
     if (!on_device) {
@@ -592,9 +601,9 @@ sd_status sd_adjoint(sd_handle *h, double dt, int64_t nsteps, int32_t ckpt_every
             ss = launch_check(launch_stage_forces(h, st, h->lam, SD_DTYPE_F64, 0, h->Wa64, h->wam), "stage lambda");
             if (ss == SD_OK) ss = launch_check(launch_build_cells(h, st, segx(k), h->posm), "cells");
             if (ss == SD_OK)
-                ss = launch_check(launch_vjp_dense(h, st, h->posm, h->frcm, h->wam, h->part, h->part2), "vjp");
+                ss = launch_check(launch_vjp_dense(h, st, h->posm.aos, h->frcm.aos, h->wam.aos, h->part, h->part2), "vjp");
             if (ss == SD_OK)
-                ss = launch_check(launch_vjp_epilogue(h, st, segx(k), h->posm, h->F64, h->frcm, h->Wa64, h->wam, -1,
+                ss = launch_check(launch_vjp_epilogue(h, st, segx(k), h->posm.aos, h->F64, h->frcm.aos, h->Wa64, h->wam.aos, -1,
                                                       nullptr, nullptr, dt, h->lam, h->gFacc),
                                   "vjp epilogue");
         }

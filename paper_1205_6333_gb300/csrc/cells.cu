@@ -15,29 +15,43 @@ namespace sd {
 
 // ---------------------------------------------------------------- staging
 
+// Entry i of a mirror: (x, y, z, 0) in the AoS array and, if present, the SoA copy.
 template <typename V4>
-__global__ void stage_pos_kernel(const double *__restrict__ x, V4 *__restrict__ m, int n, int *err) {
+__device__ __forceinline__ void put_mirror(V4 *aos, float *soa, int npad, int i, double x, double y, double z) {
+    V4 v;
+    v.x = x;
+    v.y = y;
+    v.z = z;
+    v.w = 0;
+    aos[i] = v;
+    if (soa) {
+        soa[i] = static_cast<float>(x);
+        soa[npad + i] = static_cast<float>(y);
+        soa[2 * static_cast<size_t>(npad) + i] = static_cast<float>(z);
+    }
+}
+
+template <typename V4>
+__global__ void stage_pos_kernel(const double *__restrict__ x, V4 *__restrict__ m, float *__restrict__ soa, int n,
+                                 int npad, int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
     if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicOr(err, DEV_ERR_NONFINITE);
     // mirror relative to particle 0: only differences enter the pair terms, and
     // small coordinates keep FP32 separations accurate
-    V4 v;
-    v.x = px - x[0];
-    v.y = py - x[1];
-    v.z = pz - x[2];
-    v.w = 0;
-    m[i] = v;
+    put_mirror(m, soa, npad, i, px - x[0], py - x[1], pz - x[2]);
 }
 
-cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, void *posm) {
+cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm) {
     if (h->n == 0) return cudaSuccess;
     const int nb = (h->n + 255) / 256;
     if (h->mode == MODE_FP64)
-        stage_pos_kernel<dbl4><<<nb, 256, 0, st>>>(x64, static_cast<dbl4 *>(posm), h->n, h->d_err);
+        stage_pos_kernel<dbl4><<<nb, 256, 0, st>>>(x64, static_cast<dbl4 *>(posm.aos), posm.soa, h->n, h->npad,
+                                                   h->d_err);
     else
-        stage_pos_kernel<float4><<<nb, 256, 0, st>>>(x64, static_cast<float4 *>(posm), h->n, h->d_err);
+        stage_pos_kernel<float4><<<nb, 256, 0, st>>>(x64, static_cast<float4 *>(posm.aos), posm.soa, h->n, h->npad,
+                                                     h->d_err);
     ++h->launches;
     return cudaGetLastError();
 }
@@ -45,8 +59,8 @@ cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, v
 // dst64 = src (+ fext + gravity when add_ext) and its mirror; src is n x 3 float or double.
 template <typename V4, typename Src>
 __global__ void stage_forces_kernel(const Src *__restrict__ src, const double *__restrict__ fext, double gx,
-                                    double gy, double gz, double *__restrict__ dst, V4 *__restrict__ m, int n,
-                                    int *err) {
+                                    double gy, double gz, double *__restrict__ dst, V4 *__restrict__ m,
+                                    float *__restrict__ soa, int n, int npad, int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double f[3];
@@ -60,40 +74,30 @@ __global__ void stage_forces_kernel(const Src *__restrict__ src, const double *_
     dst[3 * i] = f[0];
     dst[3 * i + 1] = f[1];
     dst[3 * i + 2] = f[2];
-    V4 v;
-    v.x = f[0];
-    v.y = f[1];
-    v.z = f[2];
-    v.w = 0;
-    m[i] = v;
+    put_mirror(m, soa, npad, i, f[0], f[1], f[2]);
+}
+
+template <typename V4, typename Src>
+static void stage_forces_launch(sd_handle *h, cudaStream_t st, const void *src, const double *fe, double *dst64,
+                                Mirror dstm) {
+    const int nb = (h->n + 255) / 256;
+    const double *g = h->cfg.gravity;
+    stage_forces_kernel<V4, Src><<<nb, 256, 0, st>>>(static_cast<const Src *>(src), fe, g[0], g[1], g[2], dst64,
+                                                     static_cast<V4 *>(dstm.aos), dstm.soa, h->n, h->npad, h->d_err);
 }
 
 // src_dtype: SD_DTYPE_F32 / SD_DTYPE_F64 (src may be NULL = zeros); add_ext: add
 // the handle's F_ext and gravity.
 cudaError_t launch_stage_forces(sd_handle *h, cudaStream_t st, const void *src, int src_dtype, int add_ext,
-                                double *dst64, void *dstm) {
+                                double *dst64, Mirror dstm) {
     if (h->n == 0) return cudaSuccess;
-    const int nb = (h->n + 255) / 256;
     const double *fe = add_ext ? h->fext64 : nullptr;
-    const double *g = h->cfg.gravity;
     if (h->mode == MODE_FP64) {
-        if (src_dtype == SD_DTYPE_F32)
-            stage_forces_kernel<dbl4, float><<<nb, 256, 0, st>>>(static_cast<const float *>(src), fe, g[0], g[1],
-                                                                 g[2], dst64, static_cast<dbl4 *>(dstm), h->n,
-                                                                 h->d_err);
-        else
-            stage_forces_kernel<dbl4, double><<<nb, 256, 0, st>>>(static_cast<const double *>(src), fe, g[0], g[1],
-                                                                  g[2], dst64, static_cast<dbl4 *>(dstm), h->n,
-                                                                  h->d_err);
+        if (src_dtype == SD_DTYPE_F32) stage_forces_launch<dbl4, float>(h, st, src, fe, dst64, dstm);
+        else stage_forces_launch<dbl4, double>(h, st, src, fe, dst64, dstm);
     } else {
-        if (src_dtype == SD_DTYPE_F32)
-            stage_forces_kernel<float4, float><<<nb, 256, 0, st>>>(static_cast<const float *>(src), fe, g[0], g[1],
-                                                                   g[2], dst64, static_cast<float4 *>(dstm), h->n,
-                                                                   h->d_err);
-        else
-            stage_forces_kernel<float4, double><<<nb, 256, 0, st>>>(static_cast<const double *>(src), fe, g[0],
-                                                                    g[1], g[2], dst64, static_cast<float4 *>(dstm),
-                                                                    h->n, h->d_err);
+        if (src_dtype == SD_DTYPE_F32) stage_forces_launch<float4, float>(h, st, src, fe, dst64, dstm);
+        else stage_forces_launch<float4, double>(h, st, src, fe, dst64, dstm);
     }
     ++h->launches;
     return cudaGetLastError();
@@ -111,17 +115,14 @@ __device__ __forceinline__ int cell_coord(double x, double inv_h) {
 // dense kernels' precision), so the mirror is a pure function of the FP64 state.
 template <typename V4>
 __global__ void cells_hash_kernel(const double *__restrict__ x, int n, double inv_h, int H, int4 *__restrict__ cell,
-                                  uint32_t *__restrict__ key, int *__restrict__ cnt, V4 *__restrict__ m, int *err) {
+                                  uint32_t *__restrict__ key, int *__restrict__ cnt, V4 *__restrict__ m,
+                                  float *__restrict__ soa, int npad, int *flag, int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (i == 0) *flag = 0;   // the near pass of these positions raises it again if needed
     const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
     if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicOr(err, DEV_ERR_NONFINITE);
-    V4 v;
-    v.x = px - x[0];
-    v.y = py - x[1];
-    v.z = pz - x[2];
-    v.w = 0;
-    m[i] = v;
+    put_mirror(m, soa, npad, i, px - x[0], py - x[1], pz - x[2]);
     const int cx = cell_coord(px, inv_h);
     const int cy = cell_coord(py, inv_h);
     const int cz = cell_coord(pz, inv_h);
@@ -232,7 +233,7 @@ __global__ void cells_sort_kernel(const int *__restrict__ start, int *__restrict
     }
 }
 
-cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, void *posm) {
+cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm) {
     CellList &c = h->cl;
     if (h->n == 0) return cudaSuccess;
     prof_begin(h, SD_KERNEL_CELLS, st);
@@ -242,10 +243,12 @@ cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64,
     const int nb = (h->n + 255) / 256;
     if (h->mode == MODE_FP64)
         cells_hash_kernel<dbl4><<<nb, 256, 0, st>>>(x64, h->n, c.inv_h, c.H, c.cell, c.key, c.cnt,
-                                                    static_cast<dbl4 *>(posm), h->d_err);
+                                                    static_cast<dbl4 *>(posm.aos), posm.soa, h->npad, h->d_flag,
+                                                    h->d_err);
     else
         cells_hash_kernel<float4><<<nb, 256, 0, st>>>(x64, h->n, c.inv_h, c.H, c.cell, c.key, c.cnt,
-                                                      static_cast<float4 *>(posm), h->d_err);
+                                                      static_cast<float4 *>(posm.aos), posm.soa, h->npad,
+                                                      h->d_flag, h->d_err);
     scan_blocks_kernel<<<c.nblk, kScanThreads, 0, st>>>(c.cnt, c.start, c.bsum, c.H);
     scan_top_kernel<<<1, kScanThreads, 0, st>>>(c.bsum, c.nblk, c.start, c.H);
     scan_add_kernel<<<(c.H + 255) / 256, 256, 0, st>>>(c.start, c.bsum, c.H);
@@ -262,8 +265,8 @@ cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64,
 // (U = eps (2a/r)^12, truncated at r_c, F = -grad U), in FP64; writes F64 and its mirror.
 template <typename V4>
 __global__ void forces_rep_kernel(const double *__restrict__ x, const double *__restrict__ fext, double gx, double gy,
-                                  double gz, double eps, double rc, double s12, CellList c, int n,
-                                  double *__restrict__ F, V4 *__restrict__ m, int *err) {
+                                  double gz, double eps, double rc, double s12, CellList c, int n, int npad,
+                                  double *__restrict__ F, V4 *__restrict__ m, float *__restrict__ soa, int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
@@ -290,12 +293,7 @@ __global__ void forces_rep_kernel(const double *__restrict__ x, const double *__
     F[3 * i] = f0;
     F[3 * i + 1] = f1;
     F[3 * i + 2] = f2;
-    V4 v;
-    v.x = f0;
-    v.y = f1;
-    v.z = f2;
-    v.w = 0;
-    m[i] = v;
+    put_mirror(m, soa, npad, i, f0, f1, f2);
 }
 
 cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64) {
@@ -306,11 +304,12 @@ cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64) 
     prof_begin(h, SD_KERNEL_FORCES, st);
     if (h->mode == MODE_FP64)
         forces_rep_kernel<dbl4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, h->rep_rc, s12,
-                                                    h->cl, h->n, h->F64, static_cast<dbl4 *>(h->frcm), h->d_err);
+                                                    h->cl, h->n, h->npad, h->F64, static_cast<dbl4 *>(h->frcm.aos),
+                                                    h->frcm.soa, h->d_err);
     else
         forces_rep_kernel<float4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, h->rep_rc,
-                                                      s12, h->cl, h->n, h->F64, static_cast<float4 *>(h->frcm),
-                                                      h->d_err);
+                                                      s12, h->cl, h->n, h->npad, h->F64,
+                                                      static_cast<float4 *>(h->frcm.aos), h->frcm.soa, h->d_err);
     prof_end(h, SD_KERNEL_FORCES, st);
     ++h->launches;
     return cudaGetLastError();

@@ -1,17 +1,22 @@
-// epilogue.cu -- per-particle completion of the mobility product and the Euler
-// update (Sec. 3.1, steps 1 and 3):
+// epilogue.cu -- the FP64 parts of the mobility product and the Euler update
+// (Sec. 3.1, steps 1 and 3), around the all-pairs kernel:
 //
-//   V_i = sum over the CTA slots of the dense partial sums (ascending slot order)
-//       + F_i - Tdense(0) F_i                        self term mu_ii = mu0 I (Sec. 2.2)
-//       + sum_{j: |r_ij| < r_near} [Texact(r_ij) F_j - Tdense(r_ij) F_j]
-//   v_i = mu0 V_i
+//   near pass (before the all-pairs kernel), per particle i:
+//     C_i = sum_{j: |r_ij| < r_near} [Texact(r_ij) F_j - Tdense(r_ij) F_j]
+//     for both variants of Tdense (r^2 clamped to (2a)^2, and unclamped), and a
+//     device flag raised when some pair is closer than r_safe (then the
+//     all-pairs kernel clamps every tile, else only the tiles holding self pairs);
+//   epilogue (after it):
+//     V_i = sum over the CTA slots of the dense partial sums (ascending slot order)
+//         + F_i - Tdense(0) F_i                  self term mu_ii = mu0 I (Sec. 2.2)
+//         + C_i                                  (the variant the kernel used)
+//     v_i = mu0 V_i;  output v, or x_{n+1} = x_n + dt v_n in FP64.
 //
-// Tdense is re-evaluated with the very same device function and inputs the dense
-// kernel used; Texact is the FP64 tensor in use (Rotne-Prager, Oseen, or the RPY
-// overlap form) at the FP64 separation.  The near-pair terms are the ones whose
+// Tdense is re-evaluated with the very same device function and inputs the
+// all-pairs kernel used; Texact is the FP64 tensor in use (Rotne-Prager, Oseen,
+// or the RPY overlap form) at the FP64 separation.  These are the pairs whose
 // FP32 evaluation suffers from cancellation in r_i - r_j (large coordinates,
-// small separations) or that the dense kernel clamped (r < 2a).  Output: the
-// velocities (apply), or x_{n+1} = x_n + dt v_n in FP64 (step).
+// small separations) or that the clamp altered (r < 2a).
 #include "neighbours.cuh"
 
 namespace sd {
@@ -27,6 +32,127 @@ struct EpiT<MODE_FP64> {
     using S = double;
 };
 
+template <int TDENSE, int MODE, bool CLAMP>
+__device__ __forceinline__ void dense_term(const typename EpiT<MODE>::V4 &pi, const typename EpiT<MODE>::V4 &pj,
+                                           const typename EpiT<MODE>::V4 &fj, const PairConst &c, double out[3]) {
+    using S = typename EpiT<MODE>::S;
+    S ax = S(0), ay = S(0), az = S(0);
+    if constexpr (MODE == MODE_FP64)
+        pair_f64<TDENSE>(pi.x, pi.y, pi.z, pj, fj, c, ax, ay, az);
+    else
+        pair_f32<TDENSE, CLAMP>(pi.x, pi.y, pi.z, pj, fj, c, ax, ay, az);
+    out[0] = static_cast<double>(ax);
+    out[1] = static_cast<double>(ay);
+    out[2] = static_cast<double>(az);
+}
+
+// ---------------------------------------------------------------- near pass
+
+struct NearArgs {
+    const double *x64;
+    const void *posm;
+    const double *F64;
+    const void *frcm;
+    CellList cl;
+    double rnear2, rsafe2;
+    PairConst pc;
+    int n;
+    double *near;   // [n][6]: clamped-variant correction (3), unclamped-variant correction (3)
+    int *flag;      // raised when some pair has r < r_safe
+    int *err;
+    int I, J;       // the all-pairs kernel's i-block and j-tile sizes
+};
+
+template <int TENSOR, int MODE>
+__global__ void __launch_bounds__(128) near_kernel(NearArgs a) {
+    using V4 = typename EpiT<MODE>::V4;
+    constexpr int TDENSE = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const V4 *pm = static_cast<const V4 *>(a.posm);
+    const V4 *fm = static_cast<const V4 *>(a.frcm);
+    const V4 pi = pm[i];
+    const double xi = a.x64[3 * i], yi = a.x64[3 * i + 1], zi = a.x64[3 * i + 2];
+    double cC[3] = {0.0, 0.0, 0.0}, cU[3] = {0.0, 0.0, 0.0};
+    bool coincident = false, close = false;
+    for_each_neighbour(a.cl, i, a.cl.cell[i], [&](int j) {
+        const double dx = xi - a.x64[3 * j], dy = yi - a.x64[3 * j + 1], dz = zi - a.x64[3 * j + 2];
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= a.rnear2) return;
+        if (r2 < a.rsafe2) close = true;
+        if (r2 == 0.0 && TENSOR != T_RPY) {
+            coincident = true;
+            return;
+        }
+        double A, B, dA, dB;
+        profile_exact<TENSOR>(r2, a.pc, A, B, dA, dB);
+        const double fx = a.F64[3 * j], fy = a.F64[3 * j + 1], fz = a.F64[3 * j + 2];
+        const double s = B * (dx * fx + dy * fy + dz * fz);
+        const double e[3] = {A * fx + s * dx, A * fy + s * dy, A * fz + s * dz};
+        double tc[3], tu[3];
+        dense_term<TDENSE, MODE, true>(pi, pm[j], fm[j], a.pc, tc);
+        // the unclamped variant still clamps the tiles that hold self pairs
+        const long long i0 = static_cast<long long>(i / a.I) * a.I, j0 = static_cast<long long>(j / a.J) * a.J;
+        const bool diag = (j0 < i0 + a.I) && (i0 < j0 + a.J);
+        if (MODE == MODE_FP64 || diag) {
+            for (int d = 0; d < 3; ++d) tu[d] = tc[d];
+        } else {
+            dense_term<TDENSE, MODE, false>(pi, pm[j], fm[j], a.pc, tu);
+        }
+        for (int d = 0; d < 3; ++d) {
+            cC[d] += e[d] - tc[d];
+            cU[d] += e[d] - tu[d];
+        }
+    });
+    if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
+    if (close) atomicOr(a.flag, 1);
+    double *o = a.near + 6 * static_cast<size_t>(i);
+    for (int d = 0; d < 3; ++d) {
+        o[d] = cC[d];
+        o[3 + d] = cU[d];
+    }
+}
+
+template <int TENSOR>
+static void near_launch_mode(int mode, int nb, cudaStream_t st, const NearArgs &a) {
+    switch (mode) {
+        case MODE_FP64: near_kernel<TENSOR, MODE_FP64><<<nb, 128, 0, st>>>(a); break;
+        default: near_kernel<TENSOR, MODE_FP32C><<<nb, 128, 0, st>>>(a); break;   // FP32 and FP32C share it
+    }
+}
+
+cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const void *posm, const double *F64,
+                        const void *frcm) {
+    if (h->n == 0) return cudaSuccess;
+    NearArgs a;
+    a.x64 = x64;
+    a.posm = posm;
+    a.F64 = F64;
+    a.frcm = frcm;
+    a.cl = h->cl;
+    a.rnear2 = h->r_near * h->r_near;
+    a.rsafe2 = kRSafe * kRSafe * h->pc.a * h->pc.a;
+    a.pc = h->pc;
+    a.n = h->n;
+    a.near = h->near64;
+    a.flag = h->d_flag;
+    a.err = h->d_err;
+    a.I = h->geom.I;
+    a.J = h->geom.J;
+    const int nb = (h->n + 127) / 128;
+    prof_begin(h, SD_KERNEL_EPILOGUE, st);
+    switch (h->tensor) {
+        case T_RPY: near_launch_mode<T_RPY>(h->mode, nb, st, a); break;
+        case T_RP: near_launch_mode<T_RP>(h->mode, nb, st, a); break;
+        default: near_launch_mode<T_OSEEN>(h->mode, nb, st, a); break;
+    }
+    prof_end(h, SD_KERNEL_EPILOGUE, st);
+    ++h->launches;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- epilogue
+
 struct EpiArgs {
     const double *part;
     int npad;
@@ -35,8 +161,8 @@ struct EpiArgs {
     const void *posm;
     const double *F64;
     const void *frcm;
-    CellList cl;
-    double rnear2;
+    const double *near;
+    const int *flag;
     PairConst pc;
     int n;
     void *vout;
@@ -45,24 +171,9 @@ struct EpiArgs {
     int *err;
 };
 
-template <int TDENSE, int MODE>
-__device__ __forceinline__ void dense_term(const typename EpiT<MODE>::V4 &pi, const typename EpiT<MODE>::V4 &pj,
-                                           const typename EpiT<MODE>::V4 &fj, const PairConst &c, double out[3]) {
-    using S = typename EpiT<MODE>::S;
-    S ax = S(0), ay = S(0), az = S(0);
-    if constexpr (MODE == MODE_FP64)
-        pair_f64<TDENSE>(pi.x, pi.y, pi.z, pj, fj, c, ax, ay, az);
-    else
-        pair_f32<TDENSE>(pi.x, pi.y, pi.z, pj, fj, c, ax, ay, az);
-    out[0] = static_cast<double>(ax);
-    out[1] = static_cast<double>(ay);
-    out[2] = static_cast<double>(az);
-}
-
-template <int TENSOR, int MODE, int OUT>
+template <int TDENSE, int MODE, int OUT>
 __global__ void __launch_bounds__(128) epilogue_kernel(EpiArgs a) {
     using V4 = typename EpiT<MODE>::V4;
-    constexpr int TDENSE = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const V4 *pm = static_cast<const V4 *>(a.posm);
@@ -84,35 +195,18 @@ __global__ void __launch_bounds__(128) epilogue_kernel(EpiArgs a) {
                 for (int d = 0; d < 3; ++d) V[d] += a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
         }
     }
-    const V4 pi = pm[i];
-    const double xi = a.x64[3 * i], yi = a.x64[3 * i + 1], zi = a.x64[3 * i + 2];
-    // self term: replace the clamped dense value by mu_ii / mu0 = I
+    // self term: the tile holding it was clamped; replace by mu_ii / mu0 = I
     {
+        const V4 pi = pm[i];
         double t[3];
-        dense_term<TDENSE, MODE>(pi, pi, fm[i], a.pc, t);
+        dense_term<TDENSE, MODE, true>(pi, pi, fm[i], a.pc, t);
         for (int d = 0; d < 3; ++d) V[d] += a.F64[3 * i + d] - t[d];
     }
-    // near pairs in FP64
-    bool coincident = false;
-    for_each_neighbour(a.cl, i, a.cl.cell[i], [&](int j) {
-        const double dx = xi - a.x64[3 * j], dy = yi - a.x64[3 * j + 1], dz = zi - a.x64[3 * j + 2];
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= a.rnear2) return;
-        if (r2 == 0.0 && TENSOR != T_RPY) {
-            coincident = true;
-            return;
-        }
-        double A, B, dA, dB;
-        profile_exact<TENSOR>(r2, a.pc, A, B, dA, dB);
-        const double fx = a.F64[3 * j], fy = a.F64[3 * j + 1], fz = a.F64[3 * j + 2];
-        const double s = B * (dx * fx + dy * fy + dz * fz);
-        double t[3];
-        dense_term<TDENSE, MODE>(pi, pm[j], fm[j], a.pc, t);
-        V[0] += (A * fx + s * dx) - t[0];
-        V[1] += (A * fy + s * dy) - t[1];
-        V[2] += (A * fz + s * dz) - t[2];
-    });
-    if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
+    // near pairs: the variant matching the kernel's clamping
+    {
+        const double *c = a.near + 6 * static_cast<size_t>(i) + ((*a.flag) ? 0 : 3);
+        for (int d = 0; d < 3; ++d) V[d] += c[d];
+    }
     const double m0 = a.pc.mu0;
     const double v0 = m0 * V[0], v1 = m0 * V[1], v2 = m0 * V[2];
     if constexpr (OUT == OUT_F32) {
@@ -126,6 +220,7 @@ __global__ void __launch_bounds__(128) epilogue_kernel(EpiArgs a) {
         o[3 * i + 1] = v1;
         o[3 * i + 2] = v2;
     } else {
+        const double xi = a.x64[3 * i], yi = a.x64[3 * i + 1], zi = a.x64[3 * i + 2];
         const double nx = xi + a.dt * v0, ny = yi + a.dt * v1, nz = zi + a.dt * v2;
         if (!isfinite(nx) || !isfinite(ny) || !isfinite(nz)) atomicOr(a.err, DEV_ERR_NONFINITE);
         a.x64n[3 * i] = nx;
@@ -134,21 +229,21 @@ __global__ void __launch_bounds__(128) epilogue_kernel(EpiArgs a) {
     }
 }
 
-template <int TENSOR, int MODE>
+template <int TDENSE, int MODE>
 static void epi_launch(int out, int nb, cudaStream_t st, const EpiArgs &a) {
     switch (out) {
-        case OUT_F32: epilogue_kernel<TENSOR, MODE, OUT_F32><<<nb, 128, 0, st>>>(a); break;
-        case OUT_F64: epilogue_kernel<TENSOR, MODE, OUT_F64><<<nb, 128, 0, st>>>(a); break;
-        default: epilogue_kernel<TENSOR, MODE, OUT_EULER><<<nb, 128, 0, st>>>(a); break;
+        case OUT_F32: epilogue_kernel<TDENSE, MODE, OUT_F32><<<nb, 128, 0, st>>>(a); break;
+        case OUT_F64: epilogue_kernel<TDENSE, MODE, OUT_F64><<<nb, 128, 0, st>>>(a); break;
+        default: epilogue_kernel<TDENSE, MODE, OUT_EULER><<<nb, 128, 0, st>>>(a); break;
     }
 }
 
-template <int TENSOR>
+template <int TDENSE>
 static void epi_launch_mode(int mode, int out, int nb, cudaStream_t st, const EpiArgs &a) {
     switch (mode) {
-        case MODE_FP32C: epi_launch<TENSOR, MODE_FP32C>(out, nb, st, a); break;
-        case MODE_FP64: epi_launch<TENSOR, MODE_FP64>(out, nb, st, a); break;
-        default: epi_launch<TENSOR, MODE_FP32>(out, nb, st, a); break;
+        case MODE_FP32C: epi_launch<TDENSE, MODE_FP32C>(out, nb, st, a); break;
+        case MODE_FP64: epi_launch<TDENSE, MODE_FP64>(out, nb, st, a); break;
+        default: epi_launch<TDENSE, MODE_FP32>(out, nb, st, a); break;
     }
 }
 
@@ -163,8 +258,8 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
     a.posm = posm;
     a.F64 = F64;
     a.frcm = frcm;
-    a.cl = h->cl;
-    a.rnear2 = h->r_near * h->r_near;
+    a.near = h->near64;
+    a.flag = h->d_flag;
     a.pc = h->pc;
     a.n = h->n;
     a.vout = vout;
@@ -173,11 +268,10 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
     a.err = h->d_err;
     const int nb = (h->n + 127) / 128;
     prof_begin(h, SD_KERNEL_EPILOGUE, st);
-    switch (h->tensor) {
-        case T_RPY: epi_launch_mode<T_RPY>(h->mode, out, nb, st, a); break;
-        case T_RP: epi_launch_mode<T_RP>(h->mode, out, nb, st, a); break;
-        default: epi_launch_mode<T_OSEEN>(h->mode, out, nb, st, a); break;
-    }
+    if (h->tensor == T_OSEEN)
+        epi_launch_mode<T_OSEEN>(h->mode, out, nb, st, a);
+    else
+        epi_launch_mode<T_RP>(h->mode, out, nb, st, a);
     prof_end(h, SD_KERNEL_EPILOGUE, st);
     ++h->launches;
     return cudaGetLastError();

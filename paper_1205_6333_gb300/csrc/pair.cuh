@@ -10,9 +10,10 @@
 // the epilogue, never per pair.
 //
 // The all-pairs ("dense") kernels evaluate the Rotne-Prager / Oseen branch for
-// every pair with r^2 clamped to >= (2a)^2 -- one FMNMX instead of a branch on the
-// self pair or on overlaps -- and the FP64 epilogue replaces the self term and
-// every pair closer than r_near by its exact value.  Every FP32 operation is an
+// every pair, with r^2 clamped to >= (2a)^2 (one FMNMX instead of a branch) in
+// the tiles that hold self pairs, and everywhere when some pair is closer than
+// r_safe; an FP64 pass replaces the self term and every pair closer than r_near
+// by its exact value.  Every FP32 operation is an
 // explicit round-to-nearest intrinsic, so the epilogue can re-evaluate exactly
 // the value a dense kernel used for a pair.
 #pragma once
@@ -35,15 +36,15 @@ struct PairConst {
 // ---------------------------------------------------------------- dense FP32
 
 // One pair of the dense sum, accumulated into (ax, ay, az): 22 FP32-pipe ops
-// (RP) or 20 (Oseen), one FMNMX, one MUFU.RSQ.
-template <int TENSOR>
+// (RP) or 20 (Oseen), one MUFU.RSQ, and with CLAMP one FMNMX.
+template <int TENSOR, bool CLAMP = true>
 __device__ __forceinline__ void pair_f32(float xi, float yi, float zi, float4 p, float4 f, const PairConst &c,
                                          float &ax, float &ay, float &az) {
     const float dx = __fsub_rn(xi, p.x);
     const float dy = __fsub_rn(yi, p.y);
     const float dz = __fsub_rn(zi, p.z);
     float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    r2 = fmaxf(r2, c.r2min_f);
+    if (CLAMP) r2 = fmaxf(r2, c.r2min_f);
     const float ri = rsqrt_sfu(r2);
     const float ri2 = __fmul_rn(ri, ri);
     float A, B;
@@ -60,6 +61,87 @@ __device__ __forceinline__ void pair_f32(float xi, float yi, float zi, float4 p,
     ax = __fmaf_rn(s, dx, __fmaf_rn(A, f.x, ax));
     ay = __fmaf_rn(s, dy, __fmaf_rn(A, f.y, ay));
     az = __fmaf_rn(s, dz, __fmaf_rn(A, f.z, az));
+}
+
+// ---------------------------------------------------------------- dense FP32, packed
+
+// Two FP32 lanes in one 64-bit register pair, operated on by the sm_100+ packed
+// instructions {add,sub,mul,fma}.rn.f32x2: one issued instruction, two IEEE
+// round-to-nearest results.  Each half is bit-identical to the scalar op.
+using f2 = unsigned long long;
+
+__device__ __forceinline__ f2 pk2(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(f2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Host-side (c, c) pair: the first element of mov.b64 {lo, hi} is the low word.
+inline f2 pk2_host(float c) {
+    unsigned int b;
+    __builtin_memcpy(&b, &c, sizeof(b));
+    return (static_cast<f2>(b) << 32) | b;
+}
+
+struct PairConst2 {
+    f2 c1, c3, m3c3;   // (c, c) pairs of the constants of PairConst
+    float r2min;
+};
+
+// Two pairs (i, j0) and (i, j1) at once: P* hold (x_j0, x_j1) etc., XI = (x_i, x_i).
+// Same operation sequence as pair_f32<TENSOR, CLAMP>, lane by lane.
+template <int TENSOR, bool CLAMP = true>
+__device__ __forceinline__ void pair_f32x2(f2 XI, f2 YI, f2 ZI, f2 PX, f2 PY, f2 PZ, f2 FX, f2 FY, f2 FZ,
+                                           const PairConst2 &c, f2 &AX, f2 &AY, f2 &AZ) {
+    const f2 dx = sub2(XI, PX);
+    const f2 dy = sub2(YI, PY);
+    const f2 dz = sub2(ZI, PZ);
+    const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    float ra, rb;
+    upk2(r2, ra, rb);
+    if (CLAMP) {
+        ra = fmaxf(ra, c.r2min);
+        rb = fmaxf(rb, c.r2min);
+    }
+    const f2 ri = pk2(rsqrt_sfu(ra), rsqrt_sfu(rb));
+    const f2 ri2 = mul2(ri, ri);
+    f2 A, B;
+    if (TENSOR == T_OSEEN) {
+        A = mul2(c.c1, ri);
+        B = mul2(A, ri2);
+    } else {
+        A = mul2(ri, fma2(c.c3, ri2, c.c1));
+        const f2 ri3 = mul2(ri, ri2);
+        B = mul2(ri3, fma2(c.m3c3, ri2, c.c1));
+    }
+    const f2 dF = fma2(dz, FZ, fma2(dy, FY, mul2(dx, FX)));
+    const f2 s = mul2(B, dF);
+    AX = fma2(s, dx, fma2(A, FX, AX));
+    AY = fma2(s, dy, fma2(A, FY, AY));
+    AZ = fma2(s, dz, fma2(A, FZ, AZ));
 }
 
 // ---------------------------------------------------------------- dense FP64

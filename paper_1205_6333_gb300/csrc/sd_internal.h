@@ -21,12 +21,23 @@ enum : int {
 enum { MODE_FP32C = 0, MODE_FP64 = 1, MODE_FP32 = 2 };
 enum { OUT_F32 = 0, OUT_F64 = 1, OUT_EULER = 2 };
 
-constexpr int kPadTo = 512;      // particle arrays are padded to a multiple of this
-constexpr int kNT = 128;         // threads per CTA of the dense kernels
-constexpr int kR32 = 4;          // i-particles per thread, FP32 dense kernel
+constexpr int kPadTo = 1024;     // particle arrays are padded to a multiple of this
+#ifndef SD_DENSE_THREADS
+#define SD_DENSE_THREADS 128
+#endif
+#ifndef SD_DENSE_R32
+#define SD_DENSE_R32 2
+#endif
+#ifndef SD_DENSE_JUNROLL
+#define SD_DENSE_JUNROLL 1
+#endif
+constexpr int kNT = SD_DENSE_THREADS;   // threads per CTA of the dense kernels
+constexpr int kR32 = SD_DENSE_R32;      // i-particles per thread, FP32 (packed) dense kernel
+constexpr int kJUnroll = SD_DENSE_JUNROLL;  // unroll of the packed kernel's 4-particle j step
 constexpr int kR64 = 2;          // i-particles per thread, FP64 dense kernel
 constexpr int kRV = 2;           // i-particles per thread, VJP dense kernel
 constexpr int kJmax = 256;       // largest j-tile
+constexpr double kRSafe = 1.0;   // pairs closer than kRSafe * a make the FP32 kernel clamp every tile
 constexpr long long kDefaultWatchdog = 1LL << 22;
 
 // Partition of the (i-block, j-tile) plane over a persistent grid: CTA b takes
@@ -70,6 +81,15 @@ __device__ __forceinline__ uint32_t cell_hash(int cx, int cy, int cz, int H) {
            static_cast<uint32_t>(H - 1);
 }
 
+// A mirror of an n x 3 FP64 array in the dense kernels' precision: `aos` holds
+// float4 / double4 [npad] (x, y, z, 0); for the FP32 modes `soa` additionally
+// holds the same values as three float arrays [3][npad] (x..., y..., z...), the
+// layout the packed FP32 kernel stages j-tiles from.  Padding entries are zero.
+struct Mirror {
+    void *aos = nullptr;
+    float *soa = nullptr;
+};
+
 struct Profiler {
     bool on = false;
     double ms[SD_KERNEL_COUNT] = {};
@@ -107,25 +127,27 @@ struct sd_handle {
     // double4 [npad], positions relative to particle 0 of the state, rewritten by
     // the cell-list build of every step (a pure function of the FP64 state)
     double *x64[2] = {nullptr, nullptr};
-    void *posm = nullptr;
+    sd::Mirror posm;
     int cur = 0;
     bool pos_set = false;
     bool cells_valid = false;             // cell list matches x64[cur]
 
     double *fext64 = nullptr;   // [n*3] per-particle external forces
     double *F64 = nullptr;      // [n*3] total force of the current step
-    void *frcm = nullptr;       // mirror of F64
+    sd::Mirror frcm;            // mirror of F64
     bool forces_const = true;   // no repulsion: F64 depends on nothing that changes
 
     // apply / vjp scratch
-    double *Fa64 = nullptr;  void *frcam = nullptr;
-    double *Wa64 = nullptr;  void *wam = nullptr;
+    double *Fa64 = nullptr;  sd::Mirror frcam;
+    double *Wa64 = nullptr;  sd::Mirror wam;
     double *part = nullptr;  size_t part_bytes = 0;   // dense partial sums
     double *part2 = nullptr; size_t part2_bytes = 0;  // second output of the VJP kernel
     sd::DenseGeom geom{}, geomv{};
     int dense_occ = 0, vjp_occ = 0;
 
     sd::CellList cl;
+    double *near64 = nullptr;   // [n][6] FP64 near-pair corrections (clamped / unclamped variant)
+    int *d_flag = nullptr;      // set by the near pass when some pair has r < kRSafe a
     int *d_err = nullptr;
 
     // graph cache for sd_step
@@ -166,15 +188,17 @@ void prof_end(sd_handle *h, int kind, cudaStream_t st);
 
 // ---- launchers (return cudaGetLastError of the launch)
 // cells.cu
-cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, void *posm);
+cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm);
 cudaError_t launch_stage_forces(sd_handle *h, cudaStream_t st, const void *src, int src_dtype, int add_ext,
-                                double *dst64, void *dstm);
-cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, void *posm);
+                                double *dst64, Mirror dstm);
+cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm);
 cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64);
 // dense.cu
 cudaError_t dense_setup(sd_handle *h);
-cudaError_t launch_dense(sd_handle *h, cudaStream_t st, const void *posm, const void *frcm, double *part);
+cudaError_t launch_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part);
 // epilogue.cu
+cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const void *posm, const double *F64,
+                        const void *frcm);
 cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double *x64, const void *posm,
                             const double *F64, const void *frcm, void *vout, double dt, double *x64n);
 // vjp.cu

@@ -166,3 +166,22 @@ def test_linearity_and_time_reversal_on_gpu():
         np.testing.assert_allclose(s.mobility_apply(-2.0 * F), -2.0 * v, rtol=1e-13, atol=1e-15)
         s.set_positions(-x)
         np.testing.assert_allclose(s.mobility_apply(-F), -v, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp32"])
+@pytest.mark.parametrize("tensor", ["rpy", "rp"])
+def test_overlaps_between_a_and_2a(prec, tensor):
+    """Overlaps only in a <= r < 2a: the all-pairs kernel skips the clamp outside
+    the tiles holding self pairs, and the near pass must undo exactly the
+    unclamped values (also for overlapping pairs that share a tile with a self pair)."""
+    n = 3000
+    x, _ = inputs.cube_rsa(n, 0.05, 17)
+    rng = np.random.default_rng(18)
+    for i, j in [(0, 1), (5, 700), (1024, 1025), (2047, 2600), (2999, 10)]:
+        d = rng.standard_normal(3)
+        x[j] = x[i] + d / np.linalg.norm(d) * rng.uniform(1.05, 1.95)
+    F = inputs.normal_forces(n, 19)
+    with sd.System(n, tensor=tensor, prec=prec) as s:
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+    assert rel_err(v, oracle.mobility_apply(x, F, tensor)) <= TOL[prec]
