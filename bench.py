@@ -268,6 +268,7 @@ def run_ours(args):
     launches = s.launch_count() - l0
     dense_ms, dense_n = s.profile_read(sd.SD_KERNEL_DENSE)
     epi_ms, _ = s.profile_read(sd.SD_KERNEL_EPILOGUE)
+    near_ms, _ = s.profile_read(sd.SD_KERNEL_NEAR)
     cells_ms, _ = s.profile_read(sd.SD_KERNEL_CELLS)
     s.profile(False)
     t_ms = _max_over_ranks(t_ms, world)
@@ -313,8 +314,8 @@ def run_ours(args):
                      "avg_launch_ms": dense_avg_ms, "launches": dense_n,
                      "peak_source": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz, %s)"
                                     % (sms, FP32_LANES_PER_SM, peaks.get("sm_max_mhz", 2070.0), peak_src)},
-        "kernel_ms_per_step": {"dense": dense_ms / args.steps, "epilogue": epi_ms / args.steps,
-                               "cells": cells_ms / args.steps},
+        "kernel_ms_per_step": {"dense": dense_ms / args.steps, "near": near_ms / args.steps,
+                               "epilogue": epi_ms / args.steps, "cells": cells_ms / args.steps},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 24 * n},
         "gpu_launches": int(launches),
         "clocks": clocks,

@@ -162,12 +162,13 @@ sd_status sd_batch_synchronize(sd_batch *b);
 /* Kernel families that can be timed with CUDA events on the handle's stream. */
 typedef enum {
     SD_KERNEL_DENSE = 0,     /* all-pairs sum (the hot loop, Sec. 3.1 step 3)  */
-    SD_KERNEL_EPILOGUE = 1,  /* split reduction + FP64 near/self terms + Euler */
+    SD_KERNEL_EPILOGUE = 1,  /* split reduction + self term + Euler update     */
     SD_KERNEL_CELLS = 2,     /* cell-list build                                */
     SD_KERNEL_FORCES = 3,    /* force assembly (Sec. 3.1 step 2)               */
     SD_KERNEL_BATCHED = 4,   /* batched persistent kernel                      */
     SD_KERNEL_VJP = 5,       /* adjoint all-pairs kernel                       */
-    SD_KERNEL_COUNT = 6
+    SD_KERNEL_NEAR = 6,      /* FP64 near-pair pass before the all-pairs sum   */
+    SD_KERNEL_COUNT = 7
 } sd_kernel;
 
 /* on = 1: record a CUDA event pair around every launch of each kernel family (steps

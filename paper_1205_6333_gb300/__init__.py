@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib as L
 from ._lib import (SD_TENSOR_RPY, SD_TENSOR_RP, SD_TENSOR_OSEEN, SD_PREC_FP32C, SD_PREC_FP64, SD_PREC_FP32,
                    SD_DTYPE_F32, SD_DTYPE_F64, SD_KERNEL_DENSE, SD_KERNEL_EPILOGUE, SD_KERNEL_CELLS,
-                   SD_KERNEL_FORCES, SD_KERNEL_BATCHED, SD_KERNEL_VJP, sd_config)
+                   SD_KERNEL_FORCES, SD_KERNEL_BATCHED, SD_KERNEL_VJP, SD_KERNEL_NEAR, sd_config)
 
 TENSORS = {"rpy": SD_TENSOR_RPY, "rp": SD_TENSOR_RP, "oseen": SD_TENSOR_OSEEN}
 PRECISIONS = {"fp32c": SD_PREC_FP32C, "fp64": SD_PREC_FP64, "fp32": SD_PREC_FP32}

@@ -25,7 +25,8 @@ STATUS_NAMES = ["SD_OK", "SD_ERR_ARG", "SD_ERR_CUDA", "SD_ERR_OOM", "SD_ERR_COIN
 SD_TENSOR_RPY, SD_TENSOR_RP, SD_TENSOR_OSEEN = 0, 1, 2
 SD_PREC_FP32C, SD_PREC_FP64, SD_PREC_FP32 = 0, 1, 2
 SD_DTYPE_F32, SD_DTYPE_F64 = 0, 1
-SD_KERNEL_DENSE, SD_KERNEL_EPILOGUE, SD_KERNEL_CELLS, SD_KERNEL_FORCES, SD_KERNEL_BATCHED, SD_KERNEL_VJP = range(6)
+SD_KERNEL_DENSE, SD_KERNEL_EPILOGUE, SD_KERNEL_CELLS, SD_KERNEL_FORCES, SD_KERNEL_BATCHED, SD_KERNEL_VJP, \
+    SD_KERNEL_NEAR = range(7)
 
 
 class sd_config(ctypes.Structure):

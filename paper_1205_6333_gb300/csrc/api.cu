@@ -323,6 +323,7 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
         if (e == cudaSuccess && m->soa) e = cudaMemsetAsync(m->soa, 0, 3 * np * sizeof(float), st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fext64, 0, n3 * sizeof(double), st);
+    if (e == cudaSuccess) e = launch_pad_mirror(h, st, h->posm);
     if (e == cudaSuccess) e = launch_stage_forces(h, st, nullptr, SD_DTYPE_F64, 1, h->F64, h->frcm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(SD_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));

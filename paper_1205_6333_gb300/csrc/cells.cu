@@ -103,6 +103,29 @@ cudaError_t launch_stage_forces(sd_handle *h, cudaStream_t st, const void *src, 
     return cudaGetLastError();
 }
 
+// Padding entries n..npad-1 of a position mirror: far from every particle
+// (1e18, 0, 0), so that with their zero padding force each pair term with them is
+// exactly zero even where the all-pairs kernel does not clamp r^2.
+template <typename V4>
+__global__ void pad_mirror_kernel(V4 *__restrict__ m, float *__restrict__ soa, int n, int npad) {
+    const int i = n + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    put_mirror(m, soa, npad, i, 1.0e18, 0.0, 0.0);
+}
+
+cudaError_t launch_pad_mirror(sd_handle *h, cudaStream_t st, Mirror m) {
+    const int npad = h->npad > 0 ? h->npad : kPadTo;
+    const int cnt = npad - h->n;
+    if (cnt <= 0) return cudaSuccess;
+    const int nb = (cnt + 255) / 256;
+    if (h->mode == MODE_FP64)
+        pad_mirror_kernel<dbl4><<<nb, 256, 0, st>>>(static_cast<dbl4 *>(m.aos), m.soa, h->n, npad);
+    else
+        pad_mirror_kernel<float4><<<nb, 256, 0, st>>>(static_cast<float4 *>(m.aos), m.soa, h->n, npad);
+    ++h->launches;
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- cell list
 
 __device__ __forceinline__ int cell_coord(double x, double inv_h) {
@@ -267,38 +290,47 @@ template <typename V4>
 __global__ void forces_rep_kernel(const double *__restrict__ x, const double *__restrict__ fext, double gx, double gy,
                                   double gz, double eps, double rc, double s12, CellList c, int n, int npad,
                                   double *__restrict__ F, V4 *__restrict__ m, float *__restrict__ soa, int *err) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
-    double f0 = fext[3 * i] + gx, f1 = fext[3 * i + 1] + gy, f2 = fext[3 * i + 2] + gz;
+    // kWalkLanes threads per particle, partial sums meet in a fixed shuffle tree
+    const long long gt = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int i = static_cast<int>(gt / kWalkLanes), sub = static_cast<int>(gt % kWalkLanes);
+    const bool active = i < n;
     const double rc2 = rc * rc;
-    bool coincident = false;
-    for_each_neighbour(c, i, c.cell[i], [&](int j) {
-        const double dx = xi - x[3 * j], dy = yi - x[3 * j + 1], dz = zi - x[3 * j + 2];
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= rc2) return;
-        if (r2 == 0.0) {
-            coincident = true;
-            return;
-        }
-        const double ir2 = 1.0 / r2;
-        const double ir6 = ir2 * ir2 * ir2;
-        const double coef = 12.0 * eps * s12 * ir6 * ir6 * ir2;
-        f0 += coef * dx;
-        f1 += coef * dy;
-        f2 += coef * dz;
-    });
+    double f[3] = {0.0, 0.0, 0.0};
+    bool coincident = false, found = false;
+    if (active) {
+        const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
+        for_each_neighbour_part(c, i, c.cell[i], sub, kWalkLanes, [&](int j) {
+            const double dx = xi - x[3 * j], dy = yi - x[3 * j + 1], dz = zi - x[3 * j + 2];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= rc2) return;
+            found = true;
+            if (r2 == 0.0) {
+                coincident = true;
+                return;
+            }
+            const double ir2 = 1.0 / r2;
+            const double ir6 = ir2 * ir2 * ir2;
+            const double coef = 12.0 * eps * s12 * ir6 * ir6 * ir2;
+            f[0] += coef * dx;
+            f[1] += coef * dy;
+            f[2] += coef * dz;
+        });
+    }
+    const int writer = walk_combine(f, found, sub);
+    coincident = walk_any(coincident);
+    if (!active || sub != writer) return;
+    const double f0 = f[0] + fext[3 * i] + gx, f1 = f[1] + fext[3 * i + 1] + gy, f2v = f[2] + fext[3 * i + 2] + gz;
     if (coincident) atomicOr(err, DEV_ERR_COINCIDENT);
-    if (!isfinite(f0) || !isfinite(f1) || !isfinite(f2)) atomicOr(err, DEV_ERR_NONFINITE);
+    if (!isfinite(f0) || !isfinite(f1) || !isfinite(f2v)) atomicOr(err, DEV_ERR_NONFINITE);
     F[3 * i] = f0;
     F[3 * i + 1] = f1;
-    F[3 * i + 2] = f2;
-    put_mirror(m, soa, npad, i, f0, f1, f2);
+    F[3 * i + 2] = f2v;
+    put_mirror(m, soa, npad, i, f0, f1, f2v);
 }
 
 cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64) {
     if (h->n == 0) return cudaSuccess;
-    const int nb = (h->n + 127) / 128;
+    const int nb = static_cast<int>((static_cast<long long>(h->n) * kWalkLanes + 127) / 128);
     const double *g = h->cfg.gravity;
     const double s12 = pow(2.0 * h->cfg.a, 12.0);
     prof_begin(h, SD_KERNEL_FORCES, st);

@@ -399,8 +399,11 @@ cudaError_t dense_setup(sd_handle *h) {
     }
     occ = std::max(occ, 1);
     const long long T = static_cast<long long>(g.nIB) * g.nJT;
+// The grid holds SD_DENSE_CTA_SCALE times as many CTAs as fit at once: the
+// hardware block scheduler then balances uneven per-SM progress (measured on
+// GB300: 58% -> 60% of the FP32 peak going from 1 to 8).
 #ifndef SD_DENSE_CTA_SCALE
-#define SD_DENSE_CTA_SCALE 1
+#define SD_DENSE_CTA_SCALE 8
 #endif
     const long long want = static_cast<long long>(h->num_sms) * occ * SD_DENSE_CTA_SCALE;
     g.chunk = (T + want - 1) / want;

@@ -55,6 +55,7 @@ struct NearArgs {
     const void *frcm;
     CellList cl;
     double rnear2, rsafe2;
+    float rscreen2;   // (1.01 r_near)^2: FP32 screen of candidates before the FP64 test
     PairConst pc;
     int n;
     double *near;   // [n][6]: clamped-variant correction (3), unclamped-variant correction (3)
@@ -63,54 +64,67 @@ struct NearArgs {
     int I, J;       // the all-pairs kernel's i-block and j-tile sizes
 };
 
+// kWalkLanes threads per particle, each walking a share of the 27 cells; the
+// partial sums meet in a fixed shuffle tree (deterministic).
 template <int TENSOR, int MODE>
 __global__ void __launch_bounds__(128) near_kernel(NearArgs a) {
     using V4 = typename EpiT<MODE>::V4;
     constexpr int TDENSE = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    const long long gt = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int i = static_cast<int>(gt / kWalkLanes), sub = static_cast<int>(gt % kWalkLanes);
+    const bool active = i < a.n;   // inactive lanes still join the shuffles
     const V4 *pm = static_cast<const V4 *>(a.posm);
     const V4 *fm = static_cast<const V4 *>(a.frcm);
-    const V4 pi = pm[i];
-    const double xi = a.x64[3 * i], yi = a.x64[3 * i + 1], zi = a.x64[3 * i + 2];
-    double cC[3] = {0.0, 0.0, 0.0}, cU[3] = {0.0, 0.0, 0.0};
-    bool coincident = false, close = false;
-    for_each_neighbour(a.cl, i, a.cl.cell[i], [&](int j) {
-        const double dx = xi - a.x64[3 * j], dy = yi - a.x64[3 * j + 1], dz = zi - a.x64[3 * j + 2];
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= a.rnear2) return;
-        if (r2 < a.rsafe2) close = true;
-        if (r2 == 0.0 && TENSOR != T_RPY) {
-            coincident = true;
-            return;
-        }
-        double A, B, dA, dB;
-        profile_exact<TENSOR>(r2, a.pc, A, B, dA, dB);
-        const double fx = a.F64[3 * j], fy = a.F64[3 * j + 1], fz = a.F64[3 * j + 2];
-        const double s = B * (dx * fx + dy * fy + dz * fz);
-        const double e[3] = {A * fx + s * dx, A * fy + s * dy, A * fz + s * dz};
-        double tc[3], tu[3];
-        dense_term<TDENSE, MODE, true>(pi, pm[j], fm[j], a.pc, tc);
-        // the unclamped variant still clamps the tiles that hold self pairs
-        const long long i0 = static_cast<long long>(i / a.I) * a.I, j0 = static_cast<long long>(j / a.J) * a.J;
-        const bool diag = (j0 < i0 + a.I) && (i0 < j0 + a.J);
-        if (MODE == MODE_FP64 || diag) {
-            for (int d = 0; d < 3; ++d) tu[d] = tc[d];
-        } else {
-            dense_term<TDENSE, MODE, false>(pi, pm[j], fm[j], a.pc, tu);
-        }
-        for (int d = 0; d < 3; ++d) {
-            cC[d] += e[d] - tc[d];
-            cU[d] += e[d] - tu[d];
-        }
-    });
+    double c6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // clamped variant, then unclamped variant
+    bool coincident = false, close = false, found = false;
+    if (active) {
+        const V4 pi = pm[i];
+        const double xi = a.x64[3 * i], yi = a.x64[3 * i + 1], zi = a.x64[3 * i + 2];
+        for_each_neighbour_part(a.cl, i, a.cl.cell[i], sub, kWalkLanes, [&](int j) {
+            // screen in the mirror's precision (with a margin far above its
+            // rounding error), then decide in FP64
+            const V4 pj = pm[j];
+            const float sx = static_cast<float>(pi.x - pj.x), sy = static_cast<float>(pi.y - pj.y),
+                        sz = static_cast<float>(pi.z - pj.z);
+            if (sx * sx + sy * sy + sz * sz > a.rscreen2) return;
+            const double dx = xi - a.x64[3 * j], dy = yi - a.x64[3 * j + 1], dz = zi - a.x64[3 * j + 2];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= a.rnear2) return;
+            found = true;
+            if (r2 < a.rsafe2) close = true;
+            if (r2 == 0.0 && TENSOR != T_RPY) {
+                coincident = true;
+                return;
+            }
+            double A, B, dA, dB;
+            profile_exact<TENSOR>(r2, a.pc, A, B, dA, dB);
+            const double fx = a.F64[3 * j], fy = a.F64[3 * j + 1], fz = a.F64[3 * j + 2];
+            const double s = B * (dx * fx + dy * fy + dz * fz);
+            const double e[3] = {A * fx + s * dx, A * fy + s * dy, A * fz + s * dz};
+            double tc[3], tu[3];
+            dense_term<TDENSE, MODE, true>(pi, pm[j], fm[j], a.pc, tc);
+            // the unclamped variant still clamps the tiles that hold self pairs
+            const long long i0 = static_cast<long long>(i / a.I) * a.I, j0 = static_cast<long long>(j / a.J) * a.J;
+            const bool diag = (j0 < i0 + a.I) && (i0 < j0 + a.J);
+            if (MODE == MODE_FP64 || diag) {
+                for (int d = 0; d < 3; ++d) tu[d] = tc[d];
+            } else {
+                dense_term<TDENSE, MODE, false>(pi, pm[j], fm[j], a.pc, tu);
+            }
+            for (int d = 0; d < 3; ++d) {
+                c6[d] += e[d] - tc[d];
+                c6[3 + d] += e[d] - tu[d];
+            }
+        });
+    }
+    const int writer = walk_combine(c6, found, sub);
+    coincident = walk_any(coincident);
+    close = walk_any(close);
+    if (!active || sub != writer) return;
     if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
     if (close) atomicOr(a.flag, 1);
     double *o = a.near + 6 * static_cast<size_t>(i);
-    for (int d = 0; d < 3; ++d) {
-        o[d] = cC[d];
-        o[3 + d] = cU[d];
-    }
+    for (int d = 0; d < 6; ++d) o[d] = c6[d];
 }
 
 template <int TENSOR>
@@ -132,6 +146,7 @@ cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const 
     a.cl = h->cl;
     a.rnear2 = h->r_near * h->r_near;
     a.rsafe2 = kRSafe * kRSafe * h->pc.a * h->pc.a;
+    a.rscreen2 = static_cast<float>(1.0201 * a.rnear2);
     a.pc = h->pc;
     a.n = h->n;
     a.near = h->near64;
@@ -139,14 +154,14 @@ cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const 
     a.err = h->d_err;
     a.I = h->geom.I;
     a.J = h->geom.J;
-    const int nb = (h->n + 127) / 128;
-    prof_begin(h, SD_KERNEL_EPILOGUE, st);
+    const int nb = static_cast<int>((static_cast<long long>(h->n) * kWalkLanes + 127) / 128);
+    prof_begin(h, SD_KERNEL_NEAR, st);
     switch (h->tensor) {
         case T_RPY: near_launch_mode<T_RPY>(h->mode, nb, st, a); break;
         case T_RP: near_launch_mode<T_RP>(h->mode, nb, st, a); break;
         default: near_launch_mode<T_OSEEN>(h->mode, nb, st, a); break;
     }
-    prof_end(h, SD_KERNEL_EPILOGUE, st);
+    prof_end(h, SD_KERNEL_NEAR, st);
     ++h->launches;
     return cudaGetLastError();
 }

@@ -24,4 +24,61 @@ __device__ __forceinline__ void for_each_neighbour(const CellList &c, int i, int
             }
 }
 
+// The same walk split over `step` cooperating threads: this thread visits the
+// neighbour cells first, first + step, ... of the 27 (same per-cell order).
+template <typename Fn>
+__device__ __forceinline__ void for_each_neighbour_part(const CellList &c, int i, int4 ci, int first, int step,
+                                                        Fn &&f) {
+    for (int k = first; k < 27; k += step) {
+        const int cx = ci.x + (k % 3) - 1, cy = ci.y + (k / 3) % 3 - 1, cz = ci.z + k / 9 - 1;
+        const uint32_t b = cell_hash(cx, cy, cz, c.H);
+        const int s1 = c.start[b + 1];
+        for (int s = c.start[b]; s < s1; ++s) {
+            const int j = c.sorted[s];
+            if (j == i) continue;
+            const int4 cj = c.cell[j];
+            if (cj.x != cx || cj.y != cy || cj.z != cz) continue;
+            f(j);
+        }
+    }
+}
+
+// Threads per particle in the neighbour-walking kernels (a power of two <= 32;
+// consecutive lanes of one warp), and the fixed-order sum over them.
+constexpr int kWalkLanes = 8;
+
+__device__ __forceinline__ double walk_sum(double v) {
+    for (int o = kWalkLanes / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Lanes of this thread's group whose flag `b` is set (bit k = sub-lane k).
+__device__ __forceinline__ unsigned walk_mask(bool b) {
+    const unsigned m = __ballot_sync(0xffffffffu, b);
+    const int lane = threadIdx.x & 31;
+    return (m >> (lane & ~(kWalkLanes - 1))) & ((1u << kWalkLanes) - 1u);
+}
+
+// Combine per-lane FP64 partial sums v[0..K) of a group.  Most groups have at
+// most one lane with a non-zero contribution (that lane's sums are the result,
+// no arithmetic); only when some group in the warp has two or more does the
+// warp run the fixed shuffle tree.  Returns the sub-lane that holds the result.
+template <int K>
+__device__ __forceinline__ int walk_combine(double (&v)[K], bool contributed, int sub) {
+    const unsigned gm = walk_mask(contributed);
+    const bool many = __popc(gm) > 1;
+    if (__any_sync(0xffffffffu, many)) {
+        for (int d = 0; d < K; ++d) v[d] = walk_sum(v[d]);
+        return 0;
+    }
+    (void)sub;
+    return gm ? __ffs(gm) - 1 : 0;
+}
+__device__ __forceinline__ bool walk_any(bool b) {
+    const unsigned m = __ballot_sync(0xffffffffu, b);
+    const int lane = threadIdx.x & 31;
+    const unsigned grp = ((1u << kWalkLanes) - 1u) << (lane & ~(kWalkLanes - 1));
+    return (m & grp) != 0u;
+}
+
 }  // namespace sd

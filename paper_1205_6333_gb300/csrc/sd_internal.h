@@ -193,6 +193,7 @@ cudaError_t launch_stage_forces(sd_handle *h, cudaStream_t st, const void *src, 
                                 double *dst64, Mirror dstm);
 cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm);
 cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64);
+cudaError_t launch_pad_mirror(sd_handle *h, cudaStream_t st, Mirror m);
 // dense.cu
 cudaError_t dense_setup(sd_handle *h);
 cudaError_t launch_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part);

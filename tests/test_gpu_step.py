@@ -116,6 +116,8 @@ def test_profiler_times_kernels():
         assert cnt == 3 and ms > 0
         ms_e, cnt_e = s.profile_read(sd.SD_KERNEL_EPILOGUE)
         assert cnt_e == 3 and ms_e > 0
+        ms_n, cnt_n = s.profile_read(sd.SD_KERNEL_NEAR)
+        assert cnt_n == 3 and ms_n > 0
         s.profile(False)
 
 
