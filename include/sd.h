@@ -157,6 +157,29 @@ sd_status sd_step_batched(sd_batch *b, double dt, int64_t nsteps);
 sd_status sd_batch_autotune(sd_batch *b, int32_t *choice);
 sd_status sd_batch_synchronize(sd_batch *b);
 
+/* Velocities V = mu(x) F for n particles, computed without allocating any GPU
+ * memory and without a handle.  The paper has no counterpart to this entry
+ * point; it exists for callers that must not allocate: code running while a
+ * stream is captured into a CUDA graph (cudaMalloc cannot be captured), plug-ins
+ * whose host gives them a fixed device-memory budget, and loops that cannot
+ * afford cudaMalloc's device synchronisation.
+ *   x, F, V : device pointers, n x 3 doubles (positions, forces, velocities out).
+ *   n       : 0 <= n <= 65536; larger n gives SD_ERR_ARG (the limit of the
+ *             fixed scratch array below).
+ *   a, eta  : radius and viscosity; tensor: sd_tensor.  Arithmetic: FP32 pair
+ *             terms with compensated accumulation, self term and overlapping
+ *             pairs exact, FP64 final sum (no FP64 near-pair pass).
+ *   stream  : cudaStream_t the kernels are queued on (asynchronous; no sync).
+ * Working memory is one static device array of about 14 MB, held by every GPU
+ * that loads the library until the process exits; its device address is looked
+ * up on the first call on each device, so make that first call before any stream
+ * capture begins.  All calls share the array, so calls whose kernels overlap on
+ * the GPU (different streams, or different host threads) race and give wrong
+ * results: order them on one stream.  Coincident distinct particles in RP or
+ * Oseen mode give NaN velocities (no error word is kept). */
+sd_status sd_mobility_apply_noalloc(const double *x, const double *F, double *V, int32_t n, double a, double eta,
+                                    int32_t tensor, void *stream);
+
 /* ---- instrumentation (used by benchmarks and tests) ---------------------- */
 
 /* Kernel families that can be timed with CUDA events on the handle's stream. */

@@ -128,6 +128,14 @@ def sd_batch_autotune(b) -> int:
     return c.value
 
 
+def sd_mobility_apply_noalloc(x_ptr, F_ptr, V_ptr, n, a=1.0, eta=1.0, tensor="rpy", stream=None):
+    """V = mu(x) F without any GPU allocation (device pointers only; see include/sd.h).
+    For callers that must not allocate, e.g. while a CUDA graph is being captured."""
+    t = TENSORS[tensor] if isinstance(tensor, str) else int(tensor)
+    _check(lib().sd_mobility_apply_noalloc(x_ptr, F_ptr, V_ptr, int(n), float(a), float(eta), t, stream),
+           "sd_mobility_apply_noalloc")
+
+
 def sd_last_error() -> str:
     return lib().sd_last_error().decode()
 

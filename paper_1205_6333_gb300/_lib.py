@@ -77,6 +77,8 @@ PROTOTYPES = {
     "sd_launch_count": (c_int64, [c_void_p]),
     "sd_batch_launch_count": (c_int64, [c_void_p]),
     "sd_set_watchdog": (c_int32, [c_void_p, c_int64]),
+    "sd_mobility_apply_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_double, c_int32,
+                                            c_void_p]),
     "sd_last_error": (c_char_p, []),
     "sd_version": (c_char_p, []),
 }
