@@ -308,7 +308,8 @@ __global__ void forces_rep_kernel(const double *__restrict__ x, const double *__
                 coincident = true;
                 return;
             }
-            const double ir2 = 1.0 / r2;
+            const double ri = rsqrt_nr64(r2);   // no FP64 division (scarce FP64 throughput)
+            const double ir2 = ri * ri;
             const double ir6 = ir2 * ir2 * ir2;
             const double coef = 12.0 * eps * s12 * ir6 * ir6 * ir2;
             f[0] += coef * dx;

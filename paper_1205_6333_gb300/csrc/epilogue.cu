@@ -101,19 +101,24 @@ __global__ void __launch_bounds__(128) near_kernel(NearArgs a) {
             const double fx = a.F64[3 * j], fy = a.F64[3 * j + 1], fz = a.F64[3 * j + 2];
             const double s = B * (dx * fx + dy * fy + dz * fz);
             const double e[3] = {A * fx + s * dx, A * fy + s * dy, A * fz + s * dz};
-            double tc[3], tu[3];
+            double tc[3];
             dense_term<TDENSE, MODE, true>(pi, pm[j], fm[j], a.pc, tc);
-            // the unclamped variant still clamps the tiles that hold self pairs
-            const long long i0 = static_cast<long long>(i / a.I) * a.I, j0 = static_cast<long long>(j / a.J) * a.J;
-            const bool diag = (j0 < i0 + a.I) && (i0 < j0 + a.J);
-            if (MODE == MODE_FP64 || diag) {
-                for (int d = 0; d < 3; ++d) tu[d] = tc[d];
-            } else {
-                dense_term<TDENSE, MODE, false>(pi, pm[j], fm[j], a.pc, tu);
-            }
-            for (int d = 0; d < 3; ++d) {
-                c6[d] += e[d] - tc[d];
-                c6[3 + d] += e[d] - tu[d];
+            for (int d = 0; d < 3; ++d) c6[d] += e[d] - tc[d];
+            // The unclamped variant differs only where the clamp was active, i.e.
+            // the pair's FP32 r^2 < (2a)^2, and outside the tiles holding self pairs
+            // (clamped in both variants); c6[3..5] collects that difference.
+            if constexpr (MODE != MODE_FP64) {
+                const float ux = __fsub_rn(pi.x, pm[j].x), uy = __fsub_rn(pi.y, pm[j].y),
+                            uz = __fsub_rn(pi.z, pm[j].z);
+                const float r2f = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
+                const long long i0 = static_cast<long long>(i / a.I) * a.I,
+                                j0 = static_cast<long long>(j / a.J) * a.J;
+                const bool diag = (j0 < i0 + a.I) && (i0 < j0 + a.J);
+                if (r2f < a.pc.r2min_f && !diag) {
+                    double tu[3];
+                    dense_term<TDENSE, MODE, false>(pi, pm[j], fm[j], a.pc, tu);
+                    for (int d = 0; d < 3; ++d) c6[3 + d] += tc[d] - tu[d];
+                }
             }
         });
     }
@@ -124,7 +129,10 @@ __global__ void __launch_bounds__(128) near_kernel(NearArgs a) {
     if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
     if (close) atomicOr(a.flag, 1);
     double *o = a.near + 6 * static_cast<size_t>(i);
-    for (int d = 0; d < 6; ++d) o[d] = c6[d];
+    for (int d = 0; d < 3; ++d) {
+        o[d] = c6[d];                 // correction when every tile is clamped
+        o[3 + d] = c6[d] + c6[3 + d]; // correction when only self-pair tiles are
+    }
 }
 
 template <int TENSOR>

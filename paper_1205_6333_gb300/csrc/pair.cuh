@@ -179,19 +179,24 @@ __device__ __forceinline__ void pair_f64(double xi, double yi, double zi, dbl4 p
 template <int TENSOR>
 __device__ __forceinline__ void profile_exact(double r2, const PairConst &c, double &A, double &B, double &dA,
                                               double &dB) {
+    // 1/r from the SFU seed and two Newton steps (rsqrt_nr64): FP64 division and
+    // square-root sequences are avoided because FP64 throughput is scarce on GB300
     if (TENSOR == T_RPY && r2 < c.two_a * c.two_a) {
-        const double r = sqrt(r2);
-        A = 1.0 - 9.0 * r / (32.0 * c.a);
         if (r2 > 0.0) {
-            B = 3.0 / (32.0 * c.a * r);
-            dA = -9.0 / (32.0 * c.a * r);
-            dB = -3.0 / (32.0 * c.a * r * r2);
+            const double ri = rsqrt_nr64(r2);
+            const double r = r2 * ri;
+            const double k = 1.0 / (32.0 * c.a);   // constant, folded per launch
+            A = 1.0 - 9.0 * k * r;
+            B = 3.0 * k * ri;
+            dA = -9.0 * k * ri;
+            dB = -3.0 * k * ri * ri * ri;
         } else {
+            A = 1.0;
             B = dA = dB = 0.0;  // the terms they multiply carry a factor r
         }
         return;
     }
-    const double ri = 1.0 / sqrt(r2);
+    const double ri = rsqrt_nr64(r2);
     const double ri2 = ri * ri;
     const double ri3 = ri * ri2;
     const double ri5 = ri3 * ri2;

@@ -88,3 +88,31 @@ def test_adjoint_rejects_repulsion():
         with pytest.raises(sd.SDError) as ei:
             s.adjoint(0.01, 2, 1, np.ones((8, 3)))
         assert ei.value.status_name == "SD_ERR_UNSUPPORTED"
+
+
+def test_torch_autograd_functions():
+    """torch.autograd through the C ABI: the apply's VJP and the Euler trajectory's
+    adjoint match the oracle."""
+    import torch
+    from paper_1205_6333_gb300.autograd import euler_trajectory, mobility_apply
+    x0, target = _adjoint_case()
+    n = x0.shape[0]
+    with sd.System(n, prec="fp64", gravity=(0.0, 0.0, -1.0)) as s:
+        x = torch.tensor(x0, device="cuda", requires_grad=True)
+        F = torch.tensor(inputs.normal_forces(n, 71), device="cuda", requires_grad=True)
+        W = inputs.normal_forces(n, 72)
+        v = mobility_apply(s, x, F)
+        (v * torch.tensor(W, device="cuda")).sum().backward()
+        rx, rF = oracle.vjp(x0, F.detach().cpu().numpy(), W, "rpy")
+        assert rel_err(x.grad.cpu().numpy(), rx) <= 1e-10
+        assert rel_err(F.grad.cpu().numpy(), rF) <= 1e-10
+
+        x = torch.tensor(x0, device="cuda", requires_grad=True)
+        fe = torch.zeros((n, 3), dtype=torch.float64, device="cuda", requires_grad=True)
+        xT = euler_trajectory(s, x, fe, 0.01, 200, 25)
+        loss = ((xT - torch.tensor(target, device="cuda")) ** 2).sum()
+        loss.backward()
+        xr = oracle.euler(x0, 200, 0.01, np.zeros_like(x0), (0.0, 0.0, -1.0))
+        gx0, gF = oracle.adjoint(x0, np.zeros_like(x0), 2.0 * (xr - target), 200, 0.01, (0.0, 0.0, -1.0))
+        assert rel_err(x.grad.cpu().numpy(), gx0) <= 1e-9
+        assert rel_err(fe.grad.cpu().numpy(), gF) <= 1e-9
