@@ -324,14 +324,31 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
-def legs(args, x, F, stream, flush):
+def run_leg(args):
+    """One extra leg alone (used for profiling it): prints its JSON object."""
+    import torch
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    x, F, _ = _main_inputs(N_MAIN)
+    print(json.dumps(legs(args, x, F, stream, flush, only=args.leg)), flush=True)
+
+
+def legs(args, x, F, stream, flush, only=None):
     """FP64 path, batched workload and the CPU oracle baseline (rank 0 only)."""
+    out = {}
+    if only in (None, "fp64"):
+        out.update(_leg_fp64(args, x, F, stream, flush))
+    if only in (None, "batched"):
+        out.update(_leg_batched(args, stream, flush))
+    if only is None:
+        out["cpu_baseline"] = cpu_baseline(x, F, target_s=args.cpu_seconds)
+    return out
+
+
+def _leg_fp64(args, x, F, stream, flush):
     import torch
     import paper_1205_6333_gb300 as sd
-    from paper_1205_6333_gb300 import inputs
-    out = {}
     n = x.shape[0]
-    # plain FP64 GPU path on the same system
     s = sd.System(n, prec="fp64", stream="torch")
     s.set_positions(x)
     s.set_forces(F)
@@ -341,9 +358,14 @@ def legs(args, x, F, stream, flush):
     t = _time_steps(lambda: s.step(DT, 1), k, stream, flush)
     s.close()
     fp64_ms = t / k
-    out["fp64"] = {"value": float(n) * n / (fp64_ms * 1e-3), "unit": UNIT, "ms_per_step": fp64_ms, "steps": k}
+    return {"fp64": {"value": float(n) * n / (fp64_ms * 1e-3), "unit": UNIT, "ms_per_step": fp64_ms, "steps": k}}
 
-    # batched clusters (16,384 clusters, N ~ U{4..256}, phi = 0.05, forces N(0,1))
+
+def _leg_batched(args, stream, flush):
+    """Batched clusters (16,384 clusters, N ~ U{4..256}, phi = 0.05, forces N(0,1))."""
+    import torch
+    import paper_1205_6333_gb300 as sd
+    from paper_1205_6333_gb300 import inputs
     w = inputs.config_inputs(4)
     off = w["offsets"]
     sizes = np.diff(off).astype(np.int64)
@@ -371,17 +393,14 @@ def legs(args, x, F, stream, flush):
     P = int(off[-1])
     bytes_step = P * (24 + 16 + 24)
     ms_b = tb / kb
-    out["batched"] = {
+    return {"batched": {
         "steps_per_s": 1e3 / ms_b, "ms_per_step": ms_b, "graph_ms_per_step": g_ms,
         "graph_steps_per_s": 1e3 / g_ms, "pairs_per_s": pairs / (ms_b * 1e-3),
         "clusters": int(len(sizes)), "particles": P, "pairs_per_step": pairs,
         "kernel_avg_ms": bk_ms / max(bk_n, 1),
         "kernel_tflops": FLOPS_PER_PAIR * pairs / (bk_ms / max(bk_n, 1) * 1e-3) / 1e12,
         "algorithmic_gbs": bytes_step / (bk_ms / max(bk_n, 1) * 1e-3) / 1e9,
-        "autotune_choice": int(choice), "steps": kb}
-    # the CPU oracle on a bounded sample
-    out["cpu_baseline"] = cpu_baseline(x, F, target_s=args.cpu_seconds)
-    return out
+        "autotune_choice": int(choice), "steps": kb}}
 
 
 def main():
@@ -391,13 +410,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="main leg only")
+    ap.add_argument("--leg", default="all", choices=["all", "main", "fp64", "batched"],
+                    help="run one leg alone and print its numbers (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.leg in ("fp64", "batched"):
+        run_leg(args)
     else:
+        if args.leg == "main":
+            args.quick = True
         run_ours(args)
 
 

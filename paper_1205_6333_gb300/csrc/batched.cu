@@ -24,6 +24,7 @@
 #include <cmath>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "sd_internal.h"
@@ -245,16 +246,223 @@ __device__ __forceinline__ void cluster_compute(const BatchArgs &a, int o, int n
     (void)anchor;
 }
 
+// FP32C path.  Shared layout of one staged particle: (x, x, y, y, z, z, Fx, Fx,
+// Fy, Fy, Fz, Fz) -- every source value duplicated, so that three 128-bit loads
+// give the six packed operands (v, v) that pair two targets (slots k0, k1 of the
+// lane) against the same source in one f32x2 instruction.
+constexpr int kDup = 12;
+constexpr int kOvlCap = 16;   // overlapping pairs a lane can list per cluster
+
+template <int TENSOR, int RP>
+__device__ __forceinline__ void cluster_packed(const BatchArgs &a, int o, int n, const float *s_dup, float *s_acc,
+                                               int *s_ovl, int lane) {
+    constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
+    constexpr int R = 2 * RP;   // target slots per lane, i = lane + 32 k
+    PairConst2 c2;
+    c2.c1 = pk2(a.pc.c1_f, a.pc.c1_f);
+    c2.c3 = pk2(a.pc.c3_f, a.pc.c3_f);
+    c2.m3c3 = pk2(a.pc.m3c3_f, a.pc.m3c3_f);
+    c2.r2min = a.pc.r2min_f;
+    const float r2min = a.pc.r2min_f;
+    float xs[R], ys[R], zs[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        // slots beyond n sit far from everything (their results are discarded)
+        const int i = lane + 32 * k;
+        const bool real = i < n;
+        xs[k] = real ? s_dup[i * kDup] : -1.0e15f;
+        ys[k] = real ? s_dup[i * kDup + 2] : 0.0f;
+        zs[k] = real ? s_dup[i * kDup + 4] : 0.0f;
+        for (int d = 0; d < 6; ++d) s_acc[(k * 6 + d) * 32 + lane] = 0.0f;
+    }
+    f2 XI[RP], YI[RP], ZI[RP], AX[RP], AY[RP], AZ[RP];
+#pragma unroll
+    for (int q = 0; q < RP; ++q) {
+        XI[q] = pk2(xs[2 * q], xs[2 * q + 1]);
+        YI[q] = pk2(ys[2 * q], ys[2 * q + 1]);
+        ZI[q] = pk2(zs[2 * q], zs[2 * q + 1]);
+        AX[q] = AY[q] = AZ[q] = 0ull;
+    }
+    // every pair the loop clamps (r < 2a, never the self pair) is listed as
+    // (slot << 16 | source) in this lane's column of s_ovl; novl counts them all
+    int novl = 0;
+    auto note = [&](int k, int j) {
+        if (novl < kOvlCap) s_ovl[novl * 32 + lane] = (k << 16) | j;
+        ++novl;
+    };
+    const uint32_t base = smem_addr(s_dup);
+    const int nchunk = (n + 31) >> 5;
+    for (int jb = 0; jb < nchunk; ++jb) {
+        // m = 0: the source is particle 32 jb + lane, i.e. slot jb meets itself --
+        // skip that one pair, evaluate the others in scalar form
+        {
+            const int j = 32 * jb + lane;
+            const float4 pj = make_float4(s_dup[j * kDup], s_dup[j * kDup + 2], s_dup[j * kDup + 4], 0.0f);
+            const float4 fj = make_float4(s_dup[j * kDup + 6], s_dup[j * kDup + 8], s_dup[j * kDup + 10], 0.0f);
+#pragma unroll
+            for (int q = 0; q < RP; ++q) {
+                float t[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = 2 * q + h;
+                    if (k == jb) continue;
+                    const float dx = __fsub_rn(xs[k], pj.x), dy = __fsub_rn(ys[k], pj.y), dz = __fsub_rn(zs[k], pj.z);
+                    if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) note(k, j);
+                    pair_f32<TD, true>(xs[k], ys[k], zs[k], pj, fj, a.pc, t[h][0], t[h][1], t[h][2]);
+                }
+                AX[q] = add2(AX[q], pk2(t[0][0], t[1][0]));
+                AY[q] = add2(AY[q], pk2(t[0][1], t[1][1]));
+                AZ[q] = add2(AZ[q], pk2(t[0][2], t[1][2]));
+            }
+        }
+        // m = 1..31: lane-rotated sources, two targets per packed instruction, in
+        // groups of G; after each group one warp vote on the group's minimum r^2,
+        // and only if some lane met a source closer than 2a are that group's
+        // sources rescanned and the overlapping pairs listed (rare)
+        auto group = [&](int m0, auto G) {
+            constexpr int NG = decltype(G)::value;
+            float mg[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) mg[k] = 1.0e30f;
+#pragma unroll
+            for (int mm = 0; mm < NG; ++mm) {
+                const int j = 32 * jb + ((lane + m0 + mm) & 31);
+                const uint32_t pa = base + static_cast<uint32_t>(j * kDup * 4);
+                f2 PX, PY, PZ, FX, FY, FZ;
+                asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(PX), "=l"(PY) : "r"(pa));
+                asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(PZ), "=l"(FX) : "r"(pa + 16));
+                asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(FY), "=l"(FZ) : "r"(pa + 32));
+#pragma unroll
+                for (int q = 0; q < RP; ++q) {
+                    float ra, rb;
+                    pair_f32x2_t<TD, true, true>(XI[q], YI[q], ZI[q], PX, PY, PZ, FX, FY, FZ, c2, AX[q], AY[q],
+                                                 AZ[q], ra, rb);
+                    mg[2 * q] = fminf(mg[2 * q], ra);
+                    mg[2 * q + 1] = fminf(mg[2 * q + 1], rb);
+                }
+            }
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < R; ++k) any |= mg[k] < r2min;
+            if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    if (!(mg[k] < r2min)) continue;
+                    for (int mm = 0; mm < NG; ++mm) {
+                        const int j = 32 * jb + ((lane + m0 + mm) & 31);
+                        const float dx = __fsub_rn(xs[k], s_dup[j * kDup]), dy = __fsub_rn(ys[k], s_dup[j * kDup + 2]),
+                                    dz = __fsub_rn(zs[k], s_dup[j * kDup + 4]);
+                        if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) note(k, j);
+                    }
+                }
+            }
+        };
+        for (int m0 = 1; m0 < 29; m0 += 4) group(m0, std::integral_constant<int, 4>{});
+        group(29, std::integral_constant<int, 3>{});
+        // every 4 chunks (128 sources) and at the end: fold both lanes of every
+        // packed accumulator into its slot's (hi, lo)
+        if (((jb + 1) & 3) != 0 && jb + 1 != nchunk) continue;
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+            const f2 acc[3] = {AX[q], AY[q], AZ[q]};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                float v0, v1;
+                upk2(acc[d], v0, v1);
+                float *q0 = s_acc + (2 * q * 6) * 32 + lane;
+                float *q1 = s_acc + ((2 * q + 1) * 6) * 32 + lane;
+                float h0 = q0[d * 32], l0 = q0[(3 + d) * 32], h1 = q1[d * 32], l1 = q1[(3 + d) * 32];
+                fold2(h0, l0, v0);
+                fold2(h1, l1, v1);
+                q0[d * 32] = h0;
+                q0[(3 + d) * 32] = l0;
+                q1[d * 32] = h1;
+                q1[(3 + d) * 32] = l1;
+            }
+            AX[q] = AY[q] = AZ[q] = 0ull;
+        }
+    }
+    // per slot: compensated sum with the self term mu_ii = mu0 I joined as
+    // (hi + F) + lo; then the clamped terms of the listed overlapping pairs are
+    // swapped for exact ones; the velocity and dt v stay in FP32 (FP64 throughput
+    // is scarce on GB300), only x += dt v is FP64
+    float V[R][3];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int i = lane + 32 * k;
+        const int ic = i < n ? i : 0;
+        const float *qa = s_acc + (k * 6) * 32 + lane;
+        for (int d = 0; d < 3; ++d) {
+            float h, e;
+            two_sum(qa[d * 32], s_dup[ic * kDup + 6 + 2 * d], h, e);
+            V[k][d] = __fadd_rn(h, __fadd_rn(e, qa[(3 + d) * 32]));
+        }
+    }
+    bool coincident = false;
+    auto fix = [&](int k, int j) {
+        const float4 pi = make_float4(xs[k], ys[k], zs[k], 0.0f);
+        const float4 pj = make_float4(s_dup[j * kDup], s_dup[j * kDup + 2], s_dup[j * kDup + 4], 0.0f);
+        const float4 fj = make_float4(s_dup[j * kDup + 6], s_dup[j * kDup + 8], s_dup[j * kDup + 10], 0.0f);
+        const float dx = __fsub_rn(pi.x, pj.x), dy = __fsub_rn(pi.y, pj.y), dz = __fsub_rn(pi.z, pj.z);
+        float cx = 0.f, cy = 0.f, cz = 0.f, ex, ey, ez;
+        pair_f32<TD, true>(pi.x, pi.y, pi.z, pj, fj, a.pc, cx, cy, cz);
+        exact_pair<TENSOR, float>(dx, dy, dz, fj.x, fj.y, fj.z, a.pc, ex, ey, ez, coincident);
+        const float c[3] = {__fsub_rn(ex, cx), __fsub_rn(ey, cy), __fsub_rn(ez, cz)};
+#pragma unroll
+        for (int kk = 0; kk < R; ++kk)
+            if (kk == k)
+                for (int d = 0; d < 3; ++d) V[kk][d] = __fadd_rn(V[kk][d], c[d]);
+    };
+    if (novl <= kOvlCap) {
+        for (int e = 0; e < novl; ++e) {
+            const int code = s_ovl[e * 32 + lane];
+            const int k = code >> 16, j = code & 0xffff;
+            if (k < R && j < n) fix(k, j);   // every counted entry was written by this cluster
+        }
+    } else {
+        // list overflow (more than kOvlCap overlapping pairs on this lane): scan
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int i = lane + 32 * k;
+            if (i >= n) continue;
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                const float dx = __fsub_rn(xs[k], s_dup[j * kDup]), dy = __fsub_rn(ys[k], s_dup[j * kDup + 2]),
+                            dz = __fsub_rn(zs[k], s_dup[j * kDup + 4]);
+                if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) fix(k, j);
+            }
+        }
+    }
+    const float m0dt = static_cast<float>(a.pc.mu0 * a.dt);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int i = lane + 32 * k;
+        if (i >= n) continue;
+        const size_t g = static_cast<size_t>(o + i);
+        const double nx = a.x64[3 * g] + static_cast<double>(__fmul_rn(m0dt, V[k][0]));
+        const double ny = a.x64[3 * g + 1] + static_cast<double>(__fmul_rn(m0dt, V[k][1]));
+        const double nz = a.x64[3 * g + 2] + static_cast<double>(__fmul_rn(m0dt, V[k][2]));
+        if (!isfinite(nx) || !isfinite(ny) || !isfinite(nz)) atomicOr(a.err, DEV_ERR_NONFINITE);
+        a.x64[3 * g] = nx;
+        a.x64[3 * g + 1] = ny;
+        a.x64[3 * g + 2] = nz;
+    }
+    if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
+}
+
+template <int MODE>
+__host__ __device__ constexpr size_t warp_stage_size() {
+    return MODE == MODE_FP64 ? 2 * kMaxCluster * sizeof(dbl4)
+                             : (kMaxCluster * kDup + kMaxR * 6 * 32 + kOvlCap * 32) * sizeof(float);
+}
+
 template <int TENSOR, int MODE>
 __global__ void batched_kernel(BatchArgs a) {
     using V4 = typename BT<MODE>::V4;
-    constexpr int stage_bytes = 2 * kMaxCluster * sizeof(V4) + (MODE == MODE_FP32C ? kMaxR * 6 * 32 * 4 : 0);
+    constexpr size_t stage_bytes = warp_stage_size<MODE>();
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned char *mine = smem + static_cast<size_t>(wid) * stage_bytes;
-    V4 *s_pos = reinterpret_cast<V4 *>(mine);
-    V4 *s_frc = s_pos + kMaxCluster;
-    float *s_acc = reinterpret_cast<float *>(s_frc + kMaxCluster);
     const V4 *frcm = static_cast<const V4 *>(a.frcm);
     for (;;) {
         unsigned long long t = 0;
@@ -271,45 +479,78 @@ __global__ void batched_kernel(BatchArgs a) {
         }
         const double3 anchor = make_double3(a.x64[3 * o], a.x64[3 * o + 1], a.x64[3 * o + 2]);
         const int R = (n + 31) >> 5;
-        for (int p = lane; p < 32 * R; p += 32) {
-            V4 q, f;
-            if (p < n) {
-                const size_t g = static_cast<size_t>(o + p);
-                q.x = a.x64[3 * g] - anchor.x;
-                q.y = a.x64[3 * g + 1] - anchor.y;
-                q.z = a.x64[3 * g + 2] - anchor.z;
-                f = frcm[g];
-            } else {
-                // padding: far away (and far from the unused i-slots at -1e15), zero force
-                q.x = 1.0e15;
-                q.y = 0;
-                q.z = 0;
-                f.x = f.y = f.z = 0;
+        if constexpr (MODE == MODE_FP64) {
+            V4 *s_pos = reinterpret_cast<V4 *>(mine);
+            V4 *s_frc = s_pos + kMaxCluster;
+            for (int p = lane; p < 32 * R; p += 32) {
+                V4 q, f;
+                if (p < n) {
+                    const size_t g = static_cast<size_t>(o + p);
+                    q.x = a.x64[3 * g] - anchor.x;
+                    q.y = a.x64[3 * g + 1] - anchor.y;
+                    q.z = a.x64[3 * g + 2] - anchor.z;
+                    f = frcm[g];
+                } else {
+                    // padding: far away (and far from the unused i-slots at -1e15), zero force
+                    q.x = 1.0e15;
+                    q.y = 0;
+                    q.z = 0;
+                    f.x = f.y = f.z = 0;
+                }
+                q.w = 0;
+                f.w = 0;
+                s_pos[p] = q;
+                s_frc[p] = f;
             }
-            q.w = 0;
-            f.w = 0;
-            s_pos[p] = q;
-            s_frc[p] = f;
-        }
-        __syncwarp();
-        switch (R) {
+            __syncwarp();
+            switch (R) {
 #define SD_BR(RR) \
-    case RR: cluster_compute<TENSOR, MODE, RR>(a, o, n, anchor, s_pos, s_frc, s_acc, lane); break
-            SD_BR(1); SD_BR(2); SD_BR(3); SD_BR(4); SD_BR(5); SD_BR(6); SD_BR(7); SD_BR(8);
+    case RR: cluster_compute<TENSOR, MODE, RR>(a, o, n, anchor, s_pos, s_frc, nullptr, lane); break
+                SD_BR(1); SD_BR(2); SD_BR(3); SD_BR(4); SD_BR(5); SD_BR(6); SD_BR(7); SD_BR(8);
 #undef SD_BR
-            default: break;
+                default: break;
+            }
+        } else {
+            float *s_dup = reinterpret_cast<float *>(mine);
+            float *s_acc = s_dup + kMaxCluster * kDup;
+            int *s_ovl = reinterpret_cast<int *>(s_acc + kMaxR * 6 * 32);
+            const int RP = (R + 1) >> 1;
+            for (int p = lane; p < 64 * RP; p += 32) {
+                float v[6];
+                if (p < n) {
+                    const size_t g = static_cast<size_t>(o + p);
+                    const V4 f = frcm[g];
+                    v[0] = static_cast<float>(a.x64[3 * g] - anchor.x);
+                    v[1] = static_cast<float>(a.x64[3 * g + 1] - anchor.y);
+                    v[2] = static_cast<float>(a.x64[3 * g + 2] - anchor.z);
+                    v[3] = f.x;
+                    v[4] = f.y;
+                    v[5] = f.z;
+                } else {
+                    // padding: far away (and far from the unused target slots at -1e15), zero force
+                    v[0] = 1.0e15f;
+                    v[1] = v[2] = v[3] = v[4] = v[5] = 0.0f;
+                }
+                float4 *d = reinterpret_cast<float4 *>(s_dup + p * kDup);
+                d[0] = make_float4(v[0], v[0], v[1], v[1]);
+                d[1] = make_float4(v[2], v[2], v[3], v[3]);
+                d[2] = make_float4(v[4], v[4], v[5], v[5]);
+            }
+            __syncwarp();
+            switch (RP) {
+                case 1: cluster_packed<TENSOR, 1>(a, o, n, s_dup, s_acc, s_ovl, lane); break;
+                case 2: cluster_packed<TENSOR, 2>(a, o, n, s_dup, s_acc, s_ovl, lane); break;
+                case 3: cluster_packed<TENSOR, 3>(a, o, n, s_dup, s_acc, s_ovl, lane); break;
+                case 4: cluster_packed<TENSOR, 4>(a, o, n, s_dup, s_acc, s_ovl, lane); break;
+                default: break;
+            }
         }
         __syncwarp();
     }
 }
 
-template <int MODE>
-static size_t warp_stage_bytes() {
-    return 2 * kMaxCluster * sizeof(typename BT<MODE>::V4) + (MODE == MODE_FP32C ? kMaxR * 6 * 32 * 4 : 0);
-}
-
 static size_t stage_bytes(int mode) {
-    return mode == MODE_FP64 ? warp_stage_bytes<MODE_FP64>() : warp_stage_bytes<MODE_FP32C>();
+    return mode == MODE_FP64 ? warp_stage_size<MODE_FP64>() : warp_stage_size<MODE_FP32C>();
 }
 
 static void *batched_fn(int tensor, int mode) {
@@ -555,7 +796,7 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
     const size_t sb = stage_bytes(b->mode);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(8 * sb)) != cudaSuccess)
         return fail(SD_ERR_CUDA, "shared-memory opt-in for the batched kernel");
-    for (int w : {4, 8, 2}) {
+    for (int w : {4, 8}) {
         const size_t smem = w * sb;
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * w, smem) != cudaSuccess) {

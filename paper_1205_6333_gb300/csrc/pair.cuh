@@ -111,17 +111,24 @@ struct PairConst2 {
     float r2min;
 };
 
-// Two pairs (i, j0) and (i, j1) at once: P* hold (x_j0, x_j1) etc., XI = (x_i, x_i).
-// Same operation sequence as pair_f32<TENSOR, CLAMP>, lane by lane.
-template <int TENSOR, bool CLAMP = true>
-__device__ __forceinline__ void pair_f32x2(f2 XI, f2 YI, f2 ZI, f2 PX, f2 PY, f2 PZ, f2 FX, f2 FY, f2 FZ,
-                                           const PairConst2 &c, f2 &AX, f2 &AY, f2 &AZ) {
+// Two pairs at once, lane by lane the operation sequence of pair_f32<TENSOR, CLAMP>:
+// either (i, j0), (i, j1) with P* = (x_j0, x_j1) and XI = (x_i, x_i), or
+// (i0, j), (i1, j) with XI = (x_i0, x_i1) and P* = (x_j, x_j).  With TRACK, mn0
+// and mn1 receive the two unclamped r^2.
+template <int TENSOR, bool CLAMP, bool TRACK>
+__device__ __forceinline__ void pair_f32x2_t(f2 XI, f2 YI, f2 ZI, f2 PX, f2 PY, f2 PZ, f2 FX, f2 FY, f2 FZ,
+                                             const PairConst2 &c, f2 &AX, f2 &AY, f2 &AZ, float &mn0,
+                                             float &mn1) {
     const f2 dx = sub2(XI, PX);
     const f2 dy = sub2(YI, PY);
     const f2 dz = sub2(ZI, PZ);
     const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
     float ra, rb;
     upk2(r2, ra, rb);
+    if (TRACK) {
+        mn0 = ra;
+        mn1 = rb;
+    }
     if (CLAMP) {
         ra = fmaxf(ra, c.r2min);
         rb = fmaxf(rb, c.r2min);
@@ -142,6 +149,13 @@ __device__ __forceinline__ void pair_f32x2(f2 XI, f2 YI, f2 ZI, f2 PX, f2 PY, f2
     AX = fma2(s, dx, fma2(A, FX, AX));
     AY = fma2(s, dy, fma2(A, FY, AY));
     AZ = fma2(s, dz, fma2(A, FZ, AZ));
+}
+
+template <int TENSOR, bool CLAMP = true>
+__device__ __forceinline__ void pair_f32x2(f2 XI, f2 YI, f2 ZI, f2 PX, f2 PY, f2 PZ, f2 FX, f2 FY, f2 FZ,
+                                           const PairConst2 &c, f2 &AX, f2 &AY, f2 &AZ) {
+    float unused0 = 0.0f, unused1 = 0.0f;
+    pair_f32x2_t<TENSOR, CLAMP, false>(XI, YI, ZI, PX, PY, PZ, FX, FY, FZ, c, AX, AY, AZ, unused0, unused1);
 }
 
 // ---------------------------------------------------------------- dense FP64
