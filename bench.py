@@ -161,6 +161,28 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+KERNEL_SOURCES = ["dense.cu", "pair.cuh", "ptx.cuh", "sd_internal.h"]
+DENSE_PROFILE = os.path.join(ROOT, "profiles", "dense2_kernel_N65536_fp32c.md")
+
+
+def _dense_traffic():
+    """DRAM bytes per launch of the all-pairs kernel from the committed ncu summary,
+    or None when the kernel sources changed since those counters were taken."""
+    import hashlib
+    import re
+    try:
+        txt = open(DENSE_PROFILE).read()
+        want = re.search(r"kernel_sources_sha256_16 = ([0-9a-f]+)", txt).group(1)
+        val = int(re.search(r"traffic_bytes_per_launch = ([0-9]+)", txt).group(1))
+    except (OSError, AttributeError):
+        return None
+    hsh = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1205_6333_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return val if hsh.hexdigest()[:16] == want else None
+
+
 def _main_inputs(n):
     from paper_1205_6333_gb300 import inputs
     x, L = inputs.cube_rsa(n, PHI, inputs.SEED_BASE + 2)
@@ -308,7 +330,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(L, world),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak, "traffic": _dense_traffic(),
                      "kernel": "dense2_kernel<RP, FP32C> (packed f32x2)",
                      "flops_per_launch": FLOPS_PER_PAIR * float(n) * n,
                      "avg_launch_ms": dense_avg_ms, "launches": dense_n,
