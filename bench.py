@@ -362,6 +362,8 @@ def legs(args, x, F, stream, flush, only=None):
         out.update(_leg_fp64(args, x, F, stream, flush))
     if only in (None, "batched"):
         out.update(_leg_batched(args, stream, flush))
+    if only in (None, "oseen"):
+        out.update(_leg_oseen(args, x, F, stream, flush))
     if only is None:
         out["cpu_baseline"] = cpu_baseline(x, F, target_s=args.cpu_seconds)
     return out
@@ -381,6 +383,180 @@ def _leg_fp64(args, x, F, stream, flush):
     s.close()
     fp64_ms = t / k
     return {"fp64": {"value": float(n) * n / (fp64_ms * 1e-3), "unit": UNIT, "ms_per_step": fp64_ms, "steps": k}}
+
+
+def _dense_ms(s, k, stream, flush, step):
+    """Mean event time of the all-pairs kernel over k steps (profiler on)."""
+    import paper_1205_6333_gb300 as sd
+    s.profile(True)
+    _time_steps(step, k, stream, flush)
+    ms, cnt = s.profile_read(sd.SD_KERNEL_DENSE)
+    s.profile(False)
+    return ms / max(cnt, 1)
+
+
+def _leg_oseen(args, x, F, stream, flush):
+    """The paper's Oseen-only variant (Sec. 3.3: 13% faster than Rotne-Prager on C2050)."""
+    import paper_1205_6333_gb300 as sd
+    n = x.shape[0]
+    out = {}
+    for tensor in ("rpy", "oseen"):
+        s = sd.System(n, tensor=tensor, stream="torch", torch_allocator=True)
+        s.set_positions(x)
+        s.set_forces(F)
+        s.step(DT, 3)
+        out[tensor] = _dense_ms(s, max(5, min(args.steps, 20)), stream, flush, lambda: s.step(DT, 1))
+        s.close()
+    return {"oseen": {"dense_ms_rpy": out["rpy"], "dense_ms_oseen": out["oseen"],
+                      "oseen_speedup": out["rpy"] / out["oseen"],
+                      "flops_per_pair": {"rpy": 34, "oseen": 30}}}
+
+
+def leg_sweep(args):
+    """N = 2^10 .. 2^18 at phi = 0.05: FP32C and FP64 step times, the all-pairs kernel's
+    fraction of the FP32 peak, and the FP32C / FP64 velocity error against the oracle
+    on sampled rows."""
+    import torch
+    import oracle
+    import paper_1205_6333_gb300 as sd
+    from paper_1205_6333_gb300 import inputs
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * _peaks()[0].get("sm_max_mhz", 2070.0) * 1e6
+    rows_out = []
+    for e in range(10, 19):
+        n = 1 << e
+        x, L = inputs.cube_rsa(n, PHI, inputs.SEED_BASE + 2)
+        F = inputs.normal_forces(n, inputs.SEED_BASE + 1002)
+        x = x.astype(np.float32).astype(np.float64)
+        F = F.astype(np.float32).astype(np.float64)
+        rows = np.random.default_rng(e).choice(n, min(n, 256), replace=False).astype(np.int32)
+        ref = oracle.mobility_rows(x, F, rows, "rpy", nthreads=os.cpu_count())
+        rec = {"n": n, "box_side": L}
+        for prec in ("fp32c", "fp64"):
+            s = sd.System(n, prec=prec, stream="torch", torch_allocator=True)
+            s.set_positions(x)
+            v = s.mobility_apply(F)
+            den = np.linalg.norm(ref, axis=1).max()
+            rec["err_" + prec] = float(np.linalg.norm(v[rows] - ref, axis=1).max() / den)
+            s.set_forces(F)
+            s.step(DT, 2)
+            k = 10 if prec == "fp32c" else (3 if n <= 65536 else 2)
+            t = _time_steps(lambda: s.step(DT, 1), k, stream, flush) / k
+            rec["step_ms_" + prec] = t
+            rec["pairs_per_s_" + prec] = float(n) * n / (t * 1e-3)
+            if prec == "fp32c":
+                dms = _dense_ms(s, 5, stream, flush, lambda: s.step(DT, 1))
+                rec["dense_ms"] = dms
+                rec["frac_fp32_peak"] = FLOPS_PER_PAIR * float(n) * n / (dms * 1e-3) / peak
+            s.close()
+        rec["fp64_over_fp32c_time"] = rec["step_ms_fp64"] / rec["step_ms_fp32c"]
+        rows_out.append(rec)
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+    return {"sweep": rows_out}
+
+
+def leg_drift(args):
+    """Workload 3: N = 16,384, phi = 0.10, gravity + eps (2a/r)^12 repulsion cut at
+    2.5a, Euler dt = 1e-3.  FP32C trajectory drift against the FP64 GPU path at 10^2,
+    10^3, 10^4 steps, oracle parity at 10^2 steps, FP32C steps/s."""
+    import torch
+    import oracle
+    import paper_1205_6333_gb300 as sd
+    from paper_1205_6333_gb300 import inputs
+    w = inputs.config_inputs(3)
+    x0 = w["x"]
+    n = x0.shape[0]
+    kw = dict(gravity=(0.0, 0.0, -1.0), rep_eps=1.0, rep_rc=2.5, stream="torch", torch_allocator=True)
+    s32 = sd.System(n, prec="fp32c", **kw)
+    s64 = sd.System(n, prec="fp64", **kw)
+    for s in (s32, s64):
+        s.set_positions(x0)
+    out = {"n": n, "checkpoints": []}
+    done = 0
+    t32 = 0.0
+    for target in (100, 1000, 10000):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s32.step(1e-3, target - done)
+        e1.record()
+        torch.cuda.synchronize()
+        t32 += e0.elapsed_time(e1)
+        s64.step(1e-3, target - done)
+        done = target
+        a, b = s32.get_positions(), s64.get_positions()
+        disp = np.abs(b - x0).max()
+        rec = {"step": target, "max_abs_diff": float(np.abs(a - b).max()),
+               "rel_to_max_displacement": float(np.abs(a - b).max() / disp), "max_displacement": float(disp)}
+        if target == 100:
+            ref = oracle.euler(x0, 100, 1e-3, gravity=(0.0, 0.0, -1.0), rep_eps=1.0, rep_rc=2.5,
+                               nthreads=os.cpu_count())
+            dref = np.abs(ref - x0).max()
+            rec["oracle_rel_err_fp32c"] = float(np.abs(a - ref).max() / dref)
+            rec["oracle_rel_err_fp64"] = float(np.abs(b - ref).max() / dref)
+        out["checkpoints"].append(rec)
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+    out["fp32c_steps_per_s"] = 1e3 * done / t32
+    return {"drift": out}
+
+
+def leg_adjoint(args, n_fd=16):
+    """Workload 5: N = 4,096, phi = 0.05, gravity, dt = 0.01, 1000 Euler steps,
+    L = sum |x_i(T) - x_i*|^2, checkpoints every 50 steps.  Central finite differences
+    (h = 1e-4) of the FP64 GPU path on n_fd seeded components of x0 and of F, the
+    FP32C-forward gradient against the FP64 one, and the backward/forward time ratio."""
+    import torch
+    import paper_1205_6333_gb300 as sd
+    from paper_1205_6333_gb300 import inputs
+    w = inputs.config_inputs(5)
+    x0, target = w["x"], w["target"]
+    n = x0.shape[0]
+    nsteps, dt, K, h = 1000, 0.01, 50, 1e-4
+    fe = np.zeros_like(x0)
+    res = {}
+    grads = {}
+    for prec in ("fp64", "fp32c"):
+        s = sd.System(n, prec=prec, gravity=(0.0, 0.0, -1.0), stream="torch", torch_allocator=True)
+        s.set_positions(x0)
+        s.set_forces(fe)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(dt, nsteps)
+        xT = s.get_positions()
+        tf = time.perf_counter() - t0
+        s.set_positions(x0)
+        t0 = time.perf_counter()
+        gx0, gF = s.adjoint(dt, nsteps, K, 2.0 * (xT - target))
+        tb = time.perf_counter() - t0
+        grads[prec] = (gx0, gF)
+        res[prec] = {"forward_s": tf, "backward_s": tb, "backward_over_forward": tb / tf}
+        if prec == "fp64":
+            def loss(x, f):
+                s.set_positions(x)
+                s.set_forces(f)
+                s.step(dt, nsteps)
+                return float(((s.get_positions() - target) ** 2).sum())
+            rng = np.random.default_rng(inputs.SEED_BASE + 55)
+            errs_x, errs_f = [], []
+            for comp in rng.choice(3 * n, n_fd, replace=False):
+                i, d = divmod(int(comp), 3)
+                e = np.zeros_like(x0)
+                e[i, d] = h
+                fdx = (loss(x0 + e, fe) - loss(x0 - e, fe)) / (2 * h)
+                fdf = (loss(x0, fe + e) - loss(x0, fe - e)) / (2 * h)
+                # relative to the component, floored at 1e-3 of the gradient's scale
+                errs_x.append(abs(gx0[i, d] - fdx) / max(abs(fdx), 1e-3 * np.abs(gx0).max()))
+                errs_f.append(abs(gF[i, d] - fdf) / max(abs(fdf), 1e-3 * np.abs(gF).max()))
+            res["fd_components"] = n_fd
+            res["fd_max_rel_err_x0"] = float(max(errs_x))
+            res["fd_max_rel_err_F"] = float(max(errs_f))
+        s.close()
+    for k, nm in ((0, "x0"), (1, "F")):
+        a, b = grads["fp32c"][k], grads["fp64"][k]
+        res["fp32c_vs_fp64_rel_err_" + nm] = float(np.abs(a - b).max() / np.abs(b).max())
+    return {"adjoint": res}
 
 
 def _leg_batched(args, stream, flush):
@@ -432,7 +608,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="main leg only")
-    ap.add_argument("--leg", default="all", choices=["all", "main", "fp64", "batched"],
+    ap.add_argument("--leg", default="all", choices=["all", "main", "fp64", "batched", "oseen", "sweep", "drift",
+                                                     "adjoint"],
                     help="run one leg alone and print its numbers (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
@@ -440,8 +617,14 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    elif args.leg in ("fp64", "batched"):
+    elif args.leg in ("fp64", "batched", "oseen"):
         run_leg(args)
+    elif args.leg == "sweep":
+        print(json.dumps(leg_sweep(args)), flush=True)
+    elif args.leg == "drift":
+        print(json.dumps(leg_drift(args)), flush=True)
+    elif args.leg == "adjoint":
+        print(json.dumps(leg_adjoint(args)), flush=True)
     else:
         if args.leg == "main":
             args.quick = True
