@@ -53,8 +53,13 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB)
+        # SD_ORACLE_LIB: load another build of sd_oracle.c (the mutation tests plant
+        # mistakes in a copy and check that the pins catch them)
+        path = os.environ.get("SD_ORACLE_LIB")
+        if not path:
+            build()
+            path = _LIB
+        lib = ctypes.CDLL(path)
         D, I, P, L = ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64
         lib.sdo_mu0.restype = D
         lib.sdo_mu0.argtypes = [D, D]

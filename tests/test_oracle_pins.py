@@ -329,6 +329,19 @@ def test_repulsion_is_minus_gradient_of_energy(orc):
     g = np.array([0.1, -0.2, -1.0])
     fe = rng.standard_normal((n, 3))
     np.testing.assert_allclose(orc.forces(x, fe, g, 0.0), fe + g, rtol=1e-15)
+    # the potential is truncated at r_c: a pair just inside feels -dU/dr of its own
+    # energy (Newton's third law holds), a pair just outside feels nothing
+    for r, inside in [(0.99 * rc, True), (1.01 * rc, False)]:
+        y = np.array([[0.3, -0.2, 0.1], [0.3 + r, -0.2, 0.1]])
+        F2 = orc.forces(y, gravity=(0, 0, 0), rep_eps=eps, rep_rc=rc, a=a)
+        if inside:
+            h = 1e-7
+            fd = -(eps * (2 * a / (r + h)) ** 12 - eps * (2 * a / (r - h)) ** 12) / (2 * h)
+            assert F2[1, 0] == pytest.approx(fd, rel=1e-6)
+            np.testing.assert_allclose(F2[0], -F2[1], rtol=1e-15)
+            assert F2[1, 1] == 0.0 and F2[1, 2] == 0.0
+        else:
+            np.testing.assert_array_equal(F2, 0.0)
 
 
 def test_euler_step_is_forward_euler(orc):
