@@ -162,16 +162,19 @@ def _peaks():
 
 
 KERNEL_SOURCES = ["dense.cu", "pair.cuh", "ptx.cuh", "sd_internal.h"]
-DENSE_PROFILE = os.path.join(ROOT, "profiles", "dense2_kernel_N65536_fp32c.md")
+DENSE_PROFILES = {"directed": os.path.join(ROOT, "profiles", "dense2_kernel_N65536_fp32c.md"),
+                  "symmetric": os.path.join(ROOT, "profiles", "dense_sym_kernel_N65536_fp32c.md")}
+DENSE_NAMES = {"directed": "dense2_kernel<RP, FP32C> (packed f32x2, every ordered pair)",
+               "symmetric": "dense_sym_kernel<RP, FP32C> (packed f32x2, each unordered pair once)"}
 
 
-def _dense_traffic():
+def _dense_traffic(kind):
     """DRAM bytes per launch of the all-pairs kernel from the committed ncu summary,
     or None when the kernel sources changed since those counters were taken."""
     import hashlib
     import re
     try:
-        txt = open(DENSE_PROFILE).read()
+        txt = open(DENSE_PROFILES[kind]).read()
         want = re.search(r"kernel_sources_sha256_16 = ([0-9a-f]+)", txt).group(1)
         val = int(re.search(r"traffic_bytes_per_launch = ([0-9]+)", txt).group(1))
     except (OSError, AttributeError):
@@ -288,6 +291,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     _barrier(world)
     launches = s.launch_count() - l0
+    dense_kind = s.dense_kernel()
     dense_ms, dense_n = s.profile_read(sd.SD_KERNEL_DENSE)
     epi_ms, _ = s.profile_read(sd.SD_KERNEL_EPILOGUE)
     near_ms, _ = s.profile_read(sd.SD_KERNEL_NEAR)
@@ -330,9 +334,11 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(L, world),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": _dense_traffic(),
-                     "kernel": "dense2_kernel<RP, FP32C> (packed f32x2)",
+                     "frac": achieved / fp32_peak, "traffic": _dense_traffic(dense_kind),
+                     "kernel": DENSE_NAMES[dense_kind],
                      "flops_per_launch": FLOPS_PER_PAIR * float(n) * n,
+                     "flops_definition": "34 per ordered pair (i, j) of the sum, N^2 per launch, whichever "
+                                         "kernel visits them",
                      "avg_launch_ms": dense_avg_ms, "launches": dense_n,
                      "peak_source": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz, %s)"
                                     % (sms, FP32_LANES_PER_SM, peaks.get("sm_max_mhz", 2070.0), peak_src)},

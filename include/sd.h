@@ -66,6 +66,18 @@ typedef enum { SD_PREC_FP32C = 0, SD_PREC_FP64 = 1, SD_PREC_FP32 = 2 } sd_precis
 
 typedef enum { SD_DTYPE_F32 = 0, SD_DTYPE_F64 = 1 } sd_dtype;
 
+/* How the FP32 all-pairs kernel visits the pairs (FP32C and FP32 only; FP64 is
+ * always DIRECTED).
+ *   DIRECTED : every ordered pair (i, j) separately, as in Sec. 3.2.
+ *   SYMMETRIC: every unordered pair once, its term used for both particles
+ *              (mu_ij = mu_ji, Sec. 2.2).  Each direction's FP32 term is the same
+ *              as DIRECTED's; only the order of the sums differs.  Needs
+ *              ceil(n/1024)*1024 / 256 = nb blocks and nb (nb + 1) / 2 * 3 KB of
+ *              device memory for the source-side partial sums.
+ *   AUTO     : SYMMETRIC once the nb (nb + 1) / 2 block pairs fill the GPU,
+ *              else DIRECTED. */
+typedef enum { SD_DENSE_AUTO = 0, SD_DENSE_DIRECTED = 1, SD_DENSE_SYMMETRIC = 2 } sd_dense_kernel;
+
 typedef struct sd_config {
     int32_t n;               /* particles; 0 <= n <= 2^24                                  */
     double a;                /* sphere radius, > 0                                          */
@@ -85,6 +97,7 @@ typedef struct sd_config {
     void *(*alloc)(size_t bytes, void *ctx);   /* optional device allocator              */
     void (*free)(void *ptr, void *ctx);        /* its matching free                      */
     void *alloc_ctx;
+    int32_t dense_kernel;    /* sd_dense_kernel; SYMMETRIC with FP64 gives SD_ERR_UNSUPPORTED */
 } sd_config;
 
 typedef struct sd_handle sd_handle;
@@ -204,6 +217,9 @@ sd_status sd_batch_profile_read(sd_batch *b, int kernel, double *ms, int64_t *la
 /* Number of kernel launches this handle has issued so far (graph replays count
  * every kernel node). */
 int64_t sd_launch_count(const sd_handle *h);
+/* The all-pairs kernel the handle runs: SD_DENSE_DIRECTED or SD_DENSE_SYMMETRIC
+ * (AUTO resolved at sd_create); SD_DENSE_AUTO for a NULL handle or n = 0. */
+int32_t sd_dense_kernel_used(const sd_handle *h);
 int64_t sd_batch_launch_count(const sd_batch *b);
 /* Iteration limit of every bounded device-side wait (default 1 << 22). */
 sd_status sd_set_watchdog(sd_handle *h, int64_t iterations);

@@ -25,6 +25,7 @@ from ._lib import (SD_TENSOR_RPY, SD_TENSOR_RP, SD_TENSOR_OSEEN, SD_PREC_FP32C, 
 
 TENSORS = {"rpy": SD_TENSOR_RPY, "rp": SD_TENSOR_RP, "oseen": SD_TENSOR_OSEEN}
 PRECISIONS = {"fp32c": SD_PREC_FP32C, "fp64": SD_PREC_FP64, "fp32": SD_PREC_FP32}
+DENSE_KERNELS = {"auto": L.SD_DENSE_AUTO, "directed": L.SD_DENSE_DIRECTED, "symmetric": L.SD_DENSE_SYMMETRIC}
 
 
 class SDError(RuntimeError):
@@ -201,8 +202,9 @@ def _torch_allocator(device: int):
 
 
 def _make_config(n=0, a=1.0, eta=1.0, tensor="rpy", prec="fp32c", r_near=None, rep_eps=0.0, rep_rc=None,
-                 gravity=(0.0, 0.0, 0.0), device=0, stream=None, torch_allocator=False):
+                 gravity=(0.0, 0.0, 0.0), device=0, stream=None, torch_allocator=False, dense="auto"):
     cfg = sd_config_init()
+    cfg.dense_kernel = DENSE_KERNELS[dense] if isinstance(dense, str) else int(dense)
     cfg.n = int(n)
     cfg.a = float(a)
     cfg.eta = float(eta)
@@ -235,9 +237,9 @@ class System:
     memory, CUDA torch tensors device memory."""
 
     def __init__(self, n, a=1.0, eta=1.0, tensor="rpy", prec="fp32c", r_near=None, rep_eps=0.0, rep_rc=None,
-                 gravity=(0.0, 0.0, 0.0), device=0, stream=None, torch_allocator=False):
+                 gravity=(0.0, 0.0, 0.0), device=0, stream=None, torch_allocator=False, dense="auto"):
         self.cfg, self._keep = _make_config(n, a, eta, tensor, prec, r_near, rep_eps, rep_rc, gravity, device,
-                                            stream, torch_allocator)
+                                            stream, torch_allocator, dense)
         self.n = int(n)
         self.h = sd_create(self.cfg)
 
@@ -313,6 +315,11 @@ class System:
 
     def launch_count(self) -> int:
         return int(lib().sd_launch_count(self.h))
+
+    def dense_kernel(self) -> str:
+        """'directed' or 'symmetric': the all-pairs kernel this system runs."""
+        k = int(lib().sd_dense_kernel_used(self.h))
+        return {v: k2 for k2, v in DENSE_KERNELS.items()}[k]
 
     def set_watchdog(self, iterations):
         _check(lib().sd_set_watchdog(self.h, int(iterations)), "sd_set_watchdog")

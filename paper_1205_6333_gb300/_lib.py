@@ -25,6 +25,7 @@ STATUS_NAMES = ["SD_OK", "SD_ERR_ARG", "SD_ERR_CUDA", "SD_ERR_OOM", "SD_ERR_COIN
 SD_TENSOR_RPY, SD_TENSOR_RP, SD_TENSOR_OSEEN = 0, 1, 2
 SD_PREC_FP32C, SD_PREC_FP64, SD_PREC_FP32 = 0, 1, 2
 SD_DTYPE_F32, SD_DTYPE_F64 = 0, 1
+SD_DENSE_AUTO, SD_DENSE_DIRECTED, SD_DENSE_SYMMETRIC = 0, 1, 2
 SD_KERNEL_DENSE, SD_KERNEL_EPILOGUE, SD_KERNEL_CELLS, SD_KERNEL_FORCES, SD_KERNEL_BATCHED, SD_KERNEL_VJP, \
     SD_KERNEL_NEAR = range(7)
 
@@ -46,6 +47,7 @@ class sd_config(ctypes.Structure):
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_ctx", c_void_p),
+        ("dense_kernel", c_int32),
     ]
 
 
@@ -75,6 +77,7 @@ PROTOTYPES = {
     "sd_profile_read": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "sd_batch_profile_read": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "sd_launch_count": (c_int64, [c_void_p]),
+    "sd_dense_kernel_used": (c_int32, [c_void_p]),
     "sd_batch_launch_count": (c_int64, [c_void_p]),
     "sd_set_watchdog": (c_int32, [c_void_p, c_int64]),
     "sd_mobility_apply_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_double, c_int32,

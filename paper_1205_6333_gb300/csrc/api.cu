@@ -210,6 +210,9 @@ static sd_status validate_common(const sd_config *cfg) {
             return set_error(SD_ERR_UNSUPPORTED, "periodic boxes (nearest image) are not implemented in this build");
         if (!std::isfinite(cfg->gravity[d])) return set_error(SD_ERR_ARG, "gravity must be finite");
     }
+    if (cfg->dense_kernel < 0 || cfg->dense_kernel > 2) return set_error(SD_ERR_ARG, "unknown dense kernel");
+    if (cfg->dense_kernel == SD_DENSE_SYMMETRIC && cfg->prec == SD_PREC_FP64)
+        return set_error(SD_ERR_UNSUPPORTED, "the symmetric all-pairs kernel is FP32 only");
     if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
         return set_error(SD_ERR_ARG, "alloc and free callbacks must be given together");
     return SD_OK;
@@ -311,6 +314,11 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
         h->part = static_cast<double *>(dalloc(h, h->part_bytes));
         h->part2 = static_cast<double *>(dalloc(h, h->part2_bytes));
         if (!h->part || !h->part2) return fail(SD_ERR_OOM, "device allocation of partial sums");
+        if (h->geom.sym) {
+            h->jpart_bytes = static_cast<size_t>(h->geom.nT) * 3 * kSymB * sizeof(float);
+            h->jpart = static_cast<float *>(dalloc(h, h->jpart_bytes));
+            if (!h->jpart) return fail(SD_ERR_OOM, "device allocation of source-side partial sums");
+        }
     }
 
     // zero everything that padding or defaults rely on
@@ -342,7 +350,7 @@ void sd_destroy(sd_handle *h) {
         dfree(h, m->aos);
         dfree(h, m->soa);
     }
-    void *bufs[] = {h->fext64, h->F64, h->Fa64, h->Wa64, h->part, h->part2,
+    void *bufs[] = {h->fext64, h->F64, h->Fa64, h->Wa64, h->part, h->part2, h->jpart,
                     h->cl.cell, h->cl.key, h->cl.cnt, h->cl.fill, h->cl.start, h->cl.bsum, h->cl.sorted,
                     h->ckpt, h->seg, h->lam, h->gFacc, h->near64, h->d_flag, h->d_err};
     for (void *p : bufs) dfree(h, p);
@@ -650,6 +658,10 @@ sd_status sd_profile_read(sd_handle *h, int kernel, double *ms, int64_t *launche
 }
 
 int64_t sd_launch_count(const sd_handle *h) { return h ? h->launches : 0; }
+int32_t sd_dense_kernel_used(const sd_handle *h) {
+    if (!h || h->n == 0) return SD_DENSE_AUTO;
+    return h->geom.sym ? SD_DENSE_SYMMETRIC : SD_DENSE_DIRECTED;
+}
 
 sd_status sd_set_watchdog(sd_handle *h, int64_t iterations) {
     if (!h || iterations < 1) return set_error(SD_ERR_ARG, "bad handle or iteration limit");

@@ -352,6 +352,236 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
     }
 }
 
+// ---------------------------------------------------------------- FP32, symmetric
+
+// The FP32 all-pairs kernel using mu_ij = mu_ji (Sec. 2.2).  The paper's GPU
+// kernel evaluates every pair twice, once per thread of each particle (Sec. 3.2):
+// on its hardware, handing a result to another thread cost global-memory traffic.
+// Here the hand-off stays on chip:
+//   * the particles are cut into blocks of kSymB = 256; a tile is an unordered
+//     pair of blocks (ib <= jb), laid out row-major over the upper triangle and
+//     partitioned over the persistent grid like the directed kernel's plane;
+//   * off-diagonal tiles: each warp holds 64 targets of block ib (2 per lane,
+//     duplicated into both halves of a packed register) and walks block jb in
+//     groups of 64 sources = 32 packets of two.  At step m lane l takes packet
+//     (l + m) mod 32, so the 32 lanes read 32 different packets (conflict-free
+//     64-bit shared loads) and each packet's running source-side sum (3 packed
+//     registers) moves one lane down per step with a shuffle; after 32 steps
+//     lane l holds packet l, having met all 64 targets of the warp.  The four
+//     warps' source sums are added in fixed order and written, in FP32, to the
+//     tile's own slot of `jpart`; the epilogue adds a block's column of slots in
+//     FP64 in ascending ib;
+//   * diagonal tiles (ib == jb) hold the self pairs: they run the directed step
+//     (tile_pairs, clamped) and write no source-side sums;
+//   * target-side sums are kept and written exactly as in dense2_kernel (TwoSum
+//     fold per tile, one slot per CTA and row).
+// Per directed pair this spends 16 FP32-pipe operations instead of 22 (RP), at
+// the price of one shuffle of 6 words and six 64-bit shared loads per 8 pairs.
+// A pair in an off-diagonal tile is clamped iff the near pass raised the flag,
+// exactly as in dense2_kernel, and each direction's FP32 term is bit-identical to
+// dense2_kernel's; only the order of the sums differs.
+template <int TENSOR, bool CLAMP>
+__device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, const f2 (&XI)[2], const f2 (&YI)[2],
+                                         const f2 (&ZI)[2], const f2 (&GX)[2], const f2 (&GY)[2], const f2 (&GZ)[2],
+                                         const PairConst2 &c, f2 (&AX)[2], f2 (&AY)[2], f2 (&AZ)[2],
+                                         float *__restrict__ jw) {
+    constexpr int B = kSymB;
+    constexpr int S = B / 2;   // packets per array
+    const int nxt = (lane + 1) & 31;
+#pragma unroll 1
+    for (int g = 0; g < B / 64; ++g) {
+        const f2 *gp = sp + g * 32;
+        f2 JX = 0ull, JY = 0ull, JZ = 0ull;
+#pragma unroll 4
+        for (int m = 0; m < 32; ++m) {
+            const int p = (lane + m) & 31;
+            const f2 PX = gp[p], PY = gp[S + p], PZ = gp[2 * S + p];
+            const f2 FX = gp[3 * S + p], FY = gp[4 * S + p], FZ = gp[5 * S + p];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                pair_sym_f32x2<TENSOR, CLAMP>(XI[k], YI[k], ZI[k], GX[k], GY[k], GZ[k], PX, PY, PZ, FX, FY, FZ, c,
+                                              AX[k], AY[k], AZ[k], JX, JY, JZ);
+            JX = __shfl_sync(0xffffffffu, JX, nxt);
+            JY = __shfl_sync(0xffffffffu, JY, nxt);
+            JZ = __shfl_sync(0xffffffffu, JZ, nxt);
+        }
+        // lane holds packet `lane` of group g: sources 64 g + 2 lane (+1)
+        f2 *jd = reinterpret_cast<f2 *>(jw) + g * 32 + lane;
+        jd[0] = JX;
+        jd[S] = JY;
+        jd[2 * S] = JZ;
+    }
+}
+
+template <int TENSOR, bool COMP>
+__global__ void __launch_bounds__(kSymNT) dense_sym_kernel(const float *__restrict__ pos,
+                                                           const float *__restrict__ frc, double *__restrict__ part,
+                                                           float *__restrict__ jpart, int npad, DenseGeom g,
+                                                           PairConst2 c, const int *__restrict__ flag,
+                                                           int *__restrict__ err, long long wd) {
+    constexpr int R = 2, NT = kSymNT, B = kSymB, NW = NT / 32;
+    static_assert(B == NT * R, "a block is two targets per thread");
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+    float *s_tile = reinterpret_cast<float *>(smem);   // [2 stages][6 arrays][B]
+    float *s_acc = s_tile + 12 * B;                     // [R][6][NT]: hx hy hz lx ly lz
+    float *s_jacc = s_acc + R * 6 * NT;                 // [NW][3][B] source-side sums per warp
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nb = g.nIB;
+    const long long t0 = static_cast<long long>(blockIdx.x) * g.chunk;
+    const long long t1 = (t0 + g.chunk < g.nT) ? t0 + g.chunk : g.nT;
+    if (t0 >= t1) return;
+    constexpr uint32_t arr_bytes = B * sizeof(float);
+
+    // (ib, jb) of tile t0: row ib starts at ib nb - ib (ib - 1) / 2
+    int ib0;
+    {
+        const double q = 2.0 * nb + 1.0;
+        ib0 = static_cast<int>(0.5 * (q - sqrt(q * q - 8.0 * static_cast<double>(t0))));
+        ib0 = ib0 < 0 ? 0 : (ib0 > nb - 1 ? nb - 1 : ib0);
+        while (ib0 > 0 && geom_rowstart(g, ib0) > t0) --ib0;
+        while (ib0 + 1 < nb && geom_rowstart(g, ib0 + 1) <= t0) ++ib0;
+    }
+    const int jb0 = ib0 + static_cast<int>(t0 - geom_rowstart(g, ib0));
+
+    int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0;  // bookkeeping of thread 0 only
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    int qi = ib0, qj = jb0;   // next tile to stage (thread 0)
+    auto issue = [&](int stg) {
+        float *dst = s_tile + stg * 6 * B;
+        const size_t j0 = static_cast<size_t>(qj) * B;
+        mbar_arrive_expect_tx(&bars[stg], 6 * arr_bytes);
+        for (int a = 0; a < 3; ++a) {
+            bulk_g2s(dst + a * B, pos + a * static_cast<size_t>(npad) + j0, arr_bytes, &bars[stg]);
+            bulk_g2s(dst + (3 + a) * B, frc + a * static_cast<size_t>(npad) + j0, arr_bytes, &bars[stg]);
+        }
+        if (stg == 0) ++issued0; else ++issued1;
+        if (++qj == nb) { ++qi; qj = qi; }
+    };
+    if (tid == 0)
+        for (int q = 0; q < 2 && t0 + q < t1; ++q) issue(q);
+
+    f2 XI[R], YI[R], ZI[R], GX[R], GY[R], GZ[R], AX[R], AY[R], AZ[R];
+    int cur_ib = -1;
+    bool aborted = false;
+    const bool clamp_all = *flag != 0;
+
+    auto flush = [&](int ib) {
+        const int slot = static_cast<int>(blockIdx.x) - geom_first(g, ib);
+        double *dst = part + static_cast<size_t>(slot) * 3 * npad;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const size_t i = static_cast<size_t>(ib) * B + tid + k * NT;
+            const f2 acc[3] = {AX[k], AY[k], AZ[k]};
+            for (int d = 0; d < 3; ++d) {
+                double v;
+                if constexpr (COMP) {
+                    const float *qa = s_acc + (k * 6) * NT + tid;
+                    v = static_cast<double>(qa[d * NT]) + static_cast<double>(qa[(3 + d) * NT]);
+                } else {
+                    float lo, hi;
+                    upk2(acc[d], lo, hi);
+                    v = static_cast<double>(__fadd_rn(lo, hi));
+                }
+                dst[d * static_cast<size_t>(npad) + i] = v;
+            }
+        }
+    };
+
+    int ib = ib0, jb = jb0;
+    for (long long t = t0; t < t1; ++t) {
+        if (ib != cur_ib) {
+            if (cur_ib >= 0) flush(cur_ib);
+            cur_ib = ib;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const size_t i = static_cast<size_t>(ib) * B + tid + k * NT;
+                const float x = pos[i], y = pos[npad + i], z = pos[2 * static_cast<size_t>(npad) + i];
+                const float fx = frc[i], fy = frc[npad + i], fz = frc[2 * static_cast<size_t>(npad) + i];
+                XI[k] = pk2(x, x);
+                YI[k] = pk2(y, y);
+                ZI[k] = pk2(z, z);
+                GX[k] = pk2(fx, fx);
+                GY[k] = pk2(fy, fy);
+                GZ[k] = pk2(fz, fz);
+                AX[k] = AY[k] = AZ[k] = 0ull;
+                if constexpr (COMP)
+                    for (int d = 0; d < 6; ++d) s_acc[(k * 6 + d) * NT + tid] = 0.0f;
+            }
+        }
+        const int q = static_cast<int>(t - t0);
+        const int st = q & 1;
+        if (!aborted) {
+            if (mbar_wait_bounded(&bars[st], (q >> 1) & 1, wd)) {
+                if (tid == 0) { if (st == 0) ++waited0; else ++waited1; }
+            } else {
+                atomicOr(err, DEV_ERR_TIMEOUT);
+                s_abort = 1;
+            }
+        }
+        const bool diag = ib == jb;
+        if (diag) {
+            const uint32_t base = smem_addr(s_tile + st * 6 * B);
+            tile_pairs<TENSOR, true, R>(base, B * sizeof(float), B, XI, YI, ZI, c, AX, AY, AZ);
+        } else {
+            const f2 *sp = reinterpret_cast<const f2 *>(s_tile + st * 6 * B);
+            float *jw = s_jacc + warp * 3 * B;
+            if (clamp_all)
+                sym_tile<TENSOR, true>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
+            else
+                sym_tile<TENSOR, false>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
+        }
+        if constexpr (COMP) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                float *qa = s_acc + (k * 6) * NT + tid;
+                const f2 acc[3] = {AX[k], AY[k], AZ[k]};
+                for (int d = 0; d < 3; ++d) {
+                    float lo, hi2;
+                    upk2(acc[d], lo, hi2);
+                    float h = qa[d * NT], l = qa[(3 + d) * NT];
+                    fold2(h, l, lo);
+                    fold2(h, l, hi2);
+                    qa[d * NT] = h;
+                    qa[(3 + d) * NT] = l;
+                }
+                AX[k] = AY[k] = AZ[k] = 0ull;
+            }
+        }
+        __syncthreads();  // stage st consumed; every warp's source sums are in s_jacc
+        if (!diag) {
+            float *dst = jpart + static_cast<size_t>(t) * 3 * B;
+            for (int e = tid; e < 3 * B; e += NT) {
+                float v = s_jacc[e];
+#pragma unroll
+                for (int w = 1; w < NW; ++w) v = __fadd_rn(v, s_jacc[w * 3 * B + e]);
+                dst[e] = v;
+            }
+            __syncthreads();  // s_jacc free for the next tile
+        }
+        aborted = s_abort != 0;
+        if (tid == 0 && !aborted && t + 2 < t1) issue(st);
+        if (++jb == nb) { ++ib; jb = ib; }
+    }
+    flush(cur_ib);
+    if (tid == 0) {
+        // After a time-out, wait (bounded) for copies still in flight into this CTA's
+        // shared memory before the CTA exits.
+        for (int k = waited0; k < issued0; ++k)
+            if (!mbar_wait_bounded(&bars[0], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+        for (int k = waited1; k < issued1; ++k)
+            if (!mbar_wait_bounded(&bars[1], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+    }
+}
+
 // ---------------------------------------------------------------- dispatch
 
 static void *pick_dense(int tensor, int mode) {
@@ -369,11 +599,27 @@ static void *pick_dense(int tensor, int mode) {
     }
 }
 
+static void *pick_sym(int tensor, int mode) {
+    const bool oseen = tensor == T_OSEEN, comp = mode == MODE_FP32C;
+    if (oseen)
+        return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, true>)
+                    : reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, false>);
+    return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_RP, true>)
+                : reinterpret_cast<void *>(&dense_sym_kernel<T_RP, false>);
+}
+
 // Dynamic shared memory of the dense kernel of this mode for tile J.
 static size_t dense_smem(int mode, int J) {
     if (mode == MODE_FP64) return 4 * static_cast<size_t>(J) * sizeof(dbl4);
     return 12 * static_cast<size_t>(J) * sizeof(float) + static_cast<size_t>(kR32) * 6 * kNT * sizeof(float);
 }
+static constexpr size_t kSymSmem = (12 * kSymB + 2 * 6 * kSymNT + (kSymNT / 32) * 3 * kSymB) * sizeof(float);
+
+// The symmetric kernel replaces the directed FP32 kernel once the triangle holds at
+// least this many tiles per resident CTA (below, its 256-particle blocks leave SMs idle).
+#ifndef SD_DENSE_SYM_MIN_TILES
+#define SD_DENSE_SYM_MIN_TILES 2
+#endif
 
 // Choose the tile J and the persistent grid for h->npad, and size the partials.
 cudaError_t dense_setup(sd_handle *h) {
@@ -409,6 +655,32 @@ cudaError_t dense_setup(sd_handle *h) {
     g.chunk = (T + want - 1) / want;
     if (g.chunk < 1) g.chunk = 1;
     g.grid = static_cast<int>((T + g.chunk - 1) / g.chunk);
+    g.nT = T;
+    g.sym = 0;
+    const int want_sym = h->cfg.dense_kernel;
+    if (h->mode != MODE_FP64 && h->npad % kSymB == 0 && want_sym != SD_DENSE_DIRECTED) {
+        void *sfn = pick_sym(h->tensor, h->mode);
+        cudaError_t e = cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(kSymSmem));
+        if (e != cudaSuccess) return e;
+        int socc = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, sfn, kSymNT, kSymSmem);
+        if (e != cudaSuccess) return e;
+        socc = std::max(socc, 1);
+        DenseGeom s{};
+        s.sym = 1;
+        s.I = s.J = kSymB;
+        s.nIB = s.nJT = h->npad / kSymB;
+        s.nT = static_cast<long long>(s.nIB) * (s.nIB + 1) / 2;
+        if (want_sym == SD_DENSE_SYMMETRIC ||
+            s.nT >= static_cast<long long>(SD_DENSE_SYM_MIN_TILES) * h->num_sms * socc) {
+            const long long swant = static_cast<long long>(h->num_sms) * socc * SD_DENSE_CTA_SCALE;
+            s.chunk = std::max(1LL, (s.nT + swant - 1) / swant);
+            s.grid = static_cast<int>((s.nT + s.chunk - 1) / s.chunk);
+            g = s;
+            occ = socc;
+        }
+    }
     int ms = 0;
     for (int ib = 0; ib < g.nIB; ++ib) ms = std::max(ms, geom_last(g, ib) - geom_first(g, ib) + 1);
     g.maxSlots = ms;
@@ -437,6 +709,20 @@ cudaError_t launch_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm
         c2.m3c3 = pk2_host(h->pc.m3c3_f);
         c2.r2min = h->pc.r2min_f;
         const bool comp = h->mode == MODE_FP32C;
+        if (g.sym) {
+#define SD_DS(TT, CC)                                                                                      \
+    dense_sym_kernel<TT, CC><<<g.grid, kSymNT, kSymSmem, st>>>(posm.soa, frcm.soa, part, h->jpart, h->npad, g, c2, \
+                                                               h->d_flag, h->d_err, h->watchdog)
+            if (oseen) {
+                if (comp) SD_DS(T_OSEEN, true); else SD_DS(T_OSEEN, false);
+            } else {
+                if (comp) SD_DS(T_RP, true); else SD_DS(T_RP, false);
+            }
+#undef SD_DS
+            prof_end(h, SD_KERNEL_DENSE, st);
+            ++h->launches;
+            return cudaGetLastError();
+        }
 #define SD_D2(TT, CC) \
     dense2_kernel<TT, CC><<<g.grid, kNT, smem, st>>>(posm.soa, frcm.soa, part, h->npad, g, c2, h->d_flag, h->d_err, \
                                                      h->watchdog)

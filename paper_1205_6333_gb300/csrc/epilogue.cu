@@ -7,7 +7,9 @@
 //     device flag raised when some pair is closer than r_safe (then the
 //     all-pairs kernel clamps every tile, else only the tiles holding self pairs);
 //   epilogue (after it):
-//     V_i = sum over the CTA slots of the dense partial sums (ascending slot order)
+//     V_i = sum over the CTA slots of the dense partial sums (and, after the
+//           symmetric kernel, over the source-side slots of the particle's block
+//           column), in a fixed order
 //         + F_i - Tdense(0) F_i                  self term mu_ii = mu0 I (Sec. 2.2)
 //         + C_i                                  (the variant the kernel used)
 //     v_i = mu0 V_i;  output v, or x_{n+1} = x_n + dt v_n in FP64.
@@ -178,6 +180,7 @@ cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const 
 
 struct EpiArgs {
     const double *part;
+    const float *jpart;   // source-side sums of the symmetric kernel (g.sym)
     int npad;
     DenseGeom g;
     const double *x64;
@@ -194,28 +197,81 @@ struct EpiArgs {
     int *err;
 };
 
+// Each CTA finishes 32 consecutive particles.  Warp w of the kEpiWarps adds the
+// slots s = w, w + kEpiWarps, ... of the dense partial sums (and, after the
+// symmetric kernel, the source-side tiles r = w, w + kEpiWarps, ... of the
+// particle's block column); lane l reads particle 32 b + l, so every warp load is
+// one coalesced 128-byte row.  Warp 0 adds the warps' results in ascending w
+// (fixed order: deterministic) and applies the FP64 terms.
+constexpr int kEpiWarps = 8;
+
 template <int TDENSE, int MODE, int OUT>
-__global__ void __launch_bounds__(128) epilogue_kernel(EpiArgs a) {
+__global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
     using V4 = typename EpiT<MODE>::V4;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    __shared__ double s_v[kEpiWarps][3][32];
+    __shared__ float s_h[kEpiWarps][3][32], s_l[kEpiWarps][3][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const bool active = i < a.n;
+
+    // This warp's share of the dense sum: the CTA slots of the particle's i-block,
+    // then (symmetric kernel) the source-side slots of the tiles (r, ib), r < ib.
+    // The column holds up to N/256 FP32 values per component: it is summed with
+    // TwoSum in FP32 (hi, lo), because FP64 issues at 1/64 the FP32 rate on GB300.
+    {
+        double v[3] = {0.0, 0.0, 0.0};
+        float hi[3] = {0.0f, 0.0f, 0.0f}, lo[3] = {0.0f, 0.0f, 0.0f};
+        if (active) {
+            const int ib = i / a.g.I;
+            const int ns = geom_last(a.g, ib) - geom_first(a.g, ib) + 1;
+            const int nc = a.g.sym ? ib : 0;
+            const int o = i - ib * a.g.I;
+            const int J = a.g.J;
+            const size_t cs = 3 * static_cast<size_t>(J);
+            if constexpr (MODE == MODE_FP32) {
+                for (int s = w; s < ns; s += kEpiWarps)
+                    for (int d = 0; d < 3; ++d)
+                        hi[d] = __fadd_rn(hi[d],
+                                          static_cast<float>(a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i]));
+                for (int r = w; r < nc; r += kEpiWarps) {
+                    const float *src = a.jpart + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
+                    for (int d = 0; d < 3; ++d) hi[d] = __fadd_rn(hi[d], src[d * J]);
+                }
+            } else {
+                for (int s = w; s < ns; s += kEpiWarps)
+                    for (int d = 0; d < 3; ++d) v[d] += a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+#pragma unroll 2
+                for (int r = w; r < nc; r += kEpiWarps) {
+                    const float *src = a.jpart + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
+                    for (int d = 0; d < 3; ++d) fold2(hi[d], lo[d], src[d * J]);
+                }
+            }
+        }
+        for (int d = 0; d < 3; ++d) {
+            s_v[w][d][lane] = v[d];
+            s_h[w][d][lane] = hi[d];
+            s_l[w][d][lane] = lo[d];
+        }
+    }
+    __syncthreads();
+    if (w != 0 || !active) return;
     const V4 *pm = static_cast<const V4 *>(a.posm);
     const V4 *fm = static_cast<const V4 *>(a.frcm);
-
-    // dense sum over the CTA slots of this particle's i-block, in slot order
-    double V[3] = {0.0, 0.0, 0.0};
-    {
-        const int ib = i / a.g.I;
-        const int ns = geom_last(a.g, ib) - geom_first(a.g, ib) + 1;
+    double V[3];
+    for (int d = 0; d < 3; ++d) {
         if constexpr (MODE == MODE_FP32) {
-            float vf[3] = {0.0f, 0.0f, 0.0f};
-            for (int s = 0; s < ns; ++s)
-                for (int d = 0; d < 3; ++d)
-                    vf[d] = __fadd_rn(vf[d], static_cast<float>(a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i]));
-            for (int d = 0; d < 3; ++d) V[d] = vf[d];
+            float f = s_h[0][d][lane];
+            for (int q = 1; q < kEpiWarps; ++q) f = __fadd_rn(f, s_h[q][d][lane]);
+            V[d] = f;
         } else {
-            for (int s = 0; s < ns; ++s)
-                for (int d = 0; d < 3; ++d) V[d] += a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+            double v = s_v[0][d][lane];
+            float h = s_h[0][d][lane], l = s_l[0][d][lane];
+            for (int q = 1; q < kEpiWarps; ++q) {
+                v += s_v[q][d][lane];
+                fold2(h, l, s_h[q][d][lane]);
+                l = __fadd_rn(l, s_l[q][d][lane]);
+            }
+            V[d] = v + (static_cast<double>(h) + static_cast<double>(l));
         }
     }
     // self term: the tile holding it was clamped; replace by mu_ii / mu0 = I
@@ -255,9 +311,9 @@ __global__ void __launch_bounds__(128) epilogue_kernel(EpiArgs a) {
 template <int TDENSE, int MODE>
 static void epi_launch(int out, int nb, cudaStream_t st, const EpiArgs &a) {
     switch (out) {
-        case OUT_F32: epilogue_kernel<TDENSE, MODE, OUT_F32><<<nb, 128, 0, st>>>(a); break;
-        case OUT_F64: epilogue_kernel<TDENSE, MODE, OUT_F64><<<nb, 128, 0, st>>>(a); break;
-        default: epilogue_kernel<TDENSE, MODE, OUT_EULER><<<nb, 128, 0, st>>>(a); break;
+        case OUT_F32: epilogue_kernel<TDENSE, MODE, OUT_F32><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
+        case OUT_F64: epilogue_kernel<TDENSE, MODE, OUT_F64><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
+        default: epilogue_kernel<TDENSE, MODE, OUT_EULER><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
     }
 }
 
@@ -275,6 +331,7 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
     if (h->n == 0) return cudaSuccess;
     EpiArgs a;
     a.part = h->part;
+    a.jpart = h->jpart;
     a.npad = h->npad;
     a.g = h->geom;
     a.x64 = x64;
@@ -289,7 +346,7 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
     a.dt = dt;
     a.x64n = x64n;
     a.err = h->d_err;
-    const int nb = (h->n + 127) / 128;
+    const int nb = (h->n + 31) / 32;
     prof_begin(h, SD_KERNEL_EPILOGUE, st);
     if (h->tensor == T_OSEEN)
         epi_launch_mode<T_OSEEN>(h->mode, out, nb, st, a);

@@ -158,6 +158,50 @@ __device__ __forceinline__ void pair_f32x2(f2 XI, f2 YI, f2 ZI, f2 PX, f2 PY, f2
     pair_f32x2_t<TENSOR, CLAMP, false>(XI, YI, ZI, PX, PY, PZ, FX, FY, FZ, c, AX, AY, AZ, unused0, unused1);
 }
 
+// The pairs (i, j0), (i, j1) used in both directions (mu_ij = mu_ji, Sec. 2.2):
+// XI = (x_i, x_i), GX = (F_i, F_i), P* = (x_j0, x_j1), F* = (F_j0, F_j1).
+//   AX += mu(r_i - r_j) F_j      (the target's sum, lanes j0 / j1)
+//   JX += mu(r_j - r_i) F_i      (the sources' sums, lanes j0 / j1)
+// r_j - r_i = -(r_i - r_j) exactly, T is even in r and round-to-nearest is odd, so
+// each lane's J term is bit-identical to pair_f32x2_t evaluated for (j, i); A and B
+// are shared.  32 packed FP32-pipe instructions for four pair terms (RP).
+template <int TENSOR, bool CLAMP>
+__device__ __forceinline__ void pair_sym_f32x2(f2 XI, f2 YI, f2 ZI, f2 GX, f2 GY, f2 GZ, f2 PX, f2 PY, f2 PZ,
+                                               f2 FX, f2 FY, f2 FZ, const PairConst2 &c, f2 &AX, f2 &AY,
+                                               f2 &AZ, f2 &JX, f2 &JY, f2 &JZ) {
+    const f2 dx = sub2(XI, PX);
+    const f2 dy = sub2(YI, PY);
+    const f2 dz = sub2(ZI, PZ);
+    const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    float ra, rb;
+    upk2(r2, ra, rb);
+    if (CLAMP) {
+        ra = fmaxf(ra, c.r2min);
+        rb = fmaxf(rb, c.r2min);
+    }
+    const f2 ri = pk2(rsqrt_sfu(ra), rsqrt_sfu(rb));
+    const f2 ri2 = mul2(ri, ri);
+    f2 A, B;
+    if (TENSOR == T_OSEEN) {
+        A = mul2(c.c1, ri);
+        B = mul2(A, ri2);
+    } else {
+        A = mul2(ri, fma2(c.c3, ri2, c.c1));
+        const f2 ri3 = mul2(ri, ri2);
+        B = mul2(ri3, fma2(c.m3c3, ri2, c.c1));
+    }
+    const f2 dF = fma2(dz, FZ, fma2(dy, FY, mul2(dx, FX)));
+    const f2 s = mul2(B, dF);
+    AX = fma2(s, dx, fma2(A, FX, AX));
+    AY = fma2(s, dy, fma2(A, FY, AY));
+    AZ = fma2(s, dz, fma2(A, FZ, AZ));
+    const f2 dG = fma2(dz, GZ, fma2(dy, GY, mul2(dx, GX)));
+    const f2 u = mul2(B, dG);
+    JX = fma2(u, dx, fma2(A, GX, JX));
+    JY = fma2(u, dy, fma2(A, GY, JY));
+    JZ = fma2(u, dz, fma2(A, GZ, JZ));
+}
+
 // ---------------------------------------------------------------- dense FP64
 
 template <int TENSOR>

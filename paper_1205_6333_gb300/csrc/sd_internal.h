@@ -39,11 +39,15 @@ constexpr int kRV = 2;           // i-particles per thread, VJP dense kernel
 constexpr int kJmax = 256;       // largest j-tile
 constexpr double kRSafe = 1.0;   // pairs closer than kRSafe * a make the FP32 kernel clamp every tile
 constexpr long long kDefaultWatchdog = 1LL << 22;
+constexpr int kSymNT = 128;      // threads per CTA of the symmetric FP32 kernel
+constexpr int kSymB = 256;       // particles per block (2 per thread) = sources per tile
 
 // Partition of the (i-block, j-tile) plane over a persistent grid: CTA b takes
 // the row-major tile range [b*chunk, min((b+1)*chunk, nIB*nJT)).  The CTAs that
 // touch i-block ib are first(ib) .. last(ib); each writes its partial sum for ib
 // into slot (b - first(ib)), and the epilogue adds slots in ascending order.
+// With sym != 0 (the symmetric FP32 kernel, I == J) only the tiles ib <= jb of
+// the plane exist, still row-major: row ib holds jb = ib .. nJT-1.
 struct DenseGeom {
     int I;          // i-particles per CTA (threads x R)
     int J;          // j-particles per tile
@@ -51,13 +55,20 @@ struct DenseGeom {
     long long chunk;
     int grid;
     int maxSlots;
+    int sym;        // upper triangle of the plane (mu_ij = mu_ji used once per pair)
+    long long nT;   // tiles
 };
 
+// First tile of row ib.
+__host__ __device__ inline long long geom_rowstart(const DenseGeom &g, int ib) {
+    const long long b = ib;
+    return g.sym ? b * g.nJT - b * (b - 1) / 2 : b * g.nJT;
+}
 __host__ __device__ inline int geom_first(const DenseGeom &g, int ib) {
-    return static_cast<int>((static_cast<long long>(ib) * g.nJT) / g.chunk);
+    return static_cast<int>(geom_rowstart(g, ib) / g.chunk);
 }
 __host__ __device__ inline int geom_last(const DenseGeom &g, int ib) {
-    return static_cast<int>((static_cast<long long>(ib + 1) * g.nJT - 1) / g.chunk);
+    return static_cast<int>((geom_rowstart(g, ib + 1) - 1) / g.chunk);
 }
 
 // Hashed cell list over FP64 positions (unbounded domains): cells of side h,
@@ -142,6 +153,7 @@ struct sd_handle {
     double *Wa64 = nullptr;  sd::Mirror wam;
     double *part = nullptr;  size_t part_bytes = 0;   // dense partial sums
     double *part2 = nullptr; size_t part2_bytes = 0;  // second output of the VJP kernel
+    float *jpart = nullptr;  size_t jpart_bytes = 0;   // symmetric kernel: source-side sums [tile][3][kSymB]
     sd::DenseGeom geom{}, geomv{};
     int dense_occ = 0, vjp_occ = 0;
 
