@@ -380,6 +380,14 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
 // A pair in an off-diagonal tile is clamped iff the near pass raised the flag,
 // exactly as in dense2_kernel, and each direction's FP32 term is bit-identical to
 // dense2_kernel's; only the order of the sums differs.
+#ifndef SD_SYM_UNROLL
+#define SD_SYM_UNROLL 4
+#endif
+#ifndef SD_SYM_MINB
+#define SD_SYM_MINB 1
+#endif
+constexpr int kSymUnroll = SD_SYM_UNROLL;
+
 template <int TENSOR, bool CLAMP>
 __device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, const f2 (&XI)[2], const f2 (&YI)[2],
                                          const f2 (&ZI)[2], const f2 (&GX)[2], const f2 (&GY)[2], const f2 (&GZ)[2],
@@ -392,7 +400,7 @@ __device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, co
     for (int g = 0; g < B / 64; ++g) {
         const f2 *gp = sp + g * 32;
         f2 JX = 0ull, JY = 0ull, JZ = 0ull;
-#pragma unroll 4
+#pragma unroll kSymUnroll
         for (int m = 0; m < 32; ++m) {
             const int p = (lane + m) & 31;
             const f2 PX = gp[p], PY = gp[S + p], PZ = gp[2 * S + p];
@@ -414,7 +422,7 @@ __device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, co
 }
 
 template <int TENSOR, bool COMP>
-__global__ void __launch_bounds__(kSymNT) dense_sym_kernel(const float *__restrict__ pos,
+__global__ void __launch_bounds__(kSymNT, SD_SYM_MINB) dense_sym_kernel(const float *__restrict__ pos,
                                                            const float *__restrict__ frc, double *__restrict__ part,
                                                            float *__restrict__ jpart, int npad, DenseGeom g,
                                                            PairConst2 c, const int *__restrict__ flag,

@@ -65,6 +65,10 @@ __device__ __forceinline__ void pair_f32(float xi, float yi, float zi, float4 p,
 
 // ---------------------------------------------------------------- dense FP32, packed
 
+#ifndef SD_SYM_RCP
+#define SD_SYM_RCP 0
+#endif
+
 // Two FP32 lanes in one 64-bit register pair, operated on by the sm_100+ packed
 // instructions {add,sub,mul,fma}.rn.f32x2: one issued instruction, two IEEE
 // round-to-nearest results.  Each half is bit-identical to the scalar op.
@@ -180,7 +184,11 @@ __device__ __forceinline__ void pair_sym_f32x2(f2 XI, f2 YI, f2 ZI, f2 GX, f2 GY
         rb = fmaxf(rb, c.r2min);
     }
     const f2 ri = pk2(rsqrt_sfu(ra), rsqrt_sfu(rb));
+#if SD_SYM_RCP
+    const f2 ri2 = pk2(rcp_sfu(ra), rcp_sfu(rb));
+#else
     const f2 ri2 = mul2(ri, ri);
+#endif
     f2 A, B;
     if (TENSOR == T_OSEEN) {
         A = mul2(c.c1, ri);

@@ -66,6 +66,11 @@ __device__ __forceinline__ float rsqrt_sfu(float x) {
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float rcp_sfu(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // FP64 reciprocal square root: SFU seed refined by two Newton-Raphson steps
 // y <- y (3 - x y^2) / 2 (quadratic convergence: 2^-22 -> 2^-44 -> below 2^-53).
