@@ -454,8 +454,18 @@ def leg_sweep(args):
             rec["pairs_per_s_" + prec] = float(n) * n / (t * 1e-3)
             if prec == "fp32c":
                 dms = _dense_ms(s, 5, stream, flush, lambda: s.step(DT, 1))
+                rec["dense_kernel"] = s.dense_kernel()
                 rec["dense_ms"] = dms
                 rec["frac_fp32_peak"] = FLOPS_PER_PAIR * float(n) * n / (dms * 1e-3) / peak
+            s.close()
+        # both all-pairs kernels forced, for the automatic choice between them
+        for dense in ("directed", "symmetric"):
+            s = sd.System(n, prec="fp32c", stream="torch", torch_allocator=True, dense=dense)
+            s.set_positions(x)
+            s.set_forces(F)
+            s.step(DT, 2)
+            rec["step_ms_" + dense] = _time_steps(lambda: s.step(DT, 1), 10, stream, flush) / 10
+            rec["dense_ms_" + dense] = _dense_ms(s, 5, stream, flush, lambda: s.step(DT, 1))
             s.close()
         rec["fp64_over_fp32c_time"] = rec["step_ms_fp64"] / rec["step_ms_fp32c"]
         rows_out.append(rec)

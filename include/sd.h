@@ -74,8 +74,9 @@ typedef enum { SD_DTYPE_F32 = 0, SD_DTYPE_F64 = 1 } sd_dtype;
  *              as DIRECTED's; only the order of the sums differs.  Needs
  *              ceil(n/1024)*1024 / 256 = nb blocks and nb (nb + 1) / 2 * 3 KB of
  *              device memory for the source-side partial sums.
- *   AUTO     : SYMMETRIC once the nb (nb + 1) / 2 block pairs fill the GPU,
- *              else DIRECTED. */
+ *   AUTO     : SYMMETRIC once there is at least one block pair per two SMs
+ *              (nb (nb + 1) / 2 >= SMs / 2; n > 2048 on a 152-SM GB300), else
+ *              DIRECTED. */
 typedef enum { SD_DENSE_AUTO = 0, SD_DENSE_DIRECTED = 1, SD_DENSE_SYMMETRIC = 2 } sd_dense_kernel;
 
 typedef struct sd_config {

@@ -275,7 +275,11 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     const size_t n3 = 3 * static_cast<size_t>(std::max(h->n, 1));
     const size_t np = static_cast<size_t>(std::max(h->npad, kPadTo));
     const size_t vb = v4size(h);
-    bool ok = dalloc_t(h, h->d_err, 1) && dalloc_t(h, h->d_flag, 1) && dalloc_t(h, h->near64, 2 * n3);
+    h->near_cap = static_cast<int>(std::min<long long>(static_cast<long long>(kNearPerParticle) * h->n + 1024,
+                                                        1LL << 30));
+    bool ok = dalloc_t(h, h->d_err, 1) && dalloc_t(h, h->d_flag, 1) && dalloc_t(h, h->near64, 2 * n3) &&
+              dalloc_t(h, h->near_ent, h->near_cap) && dalloc_t(h, h->near_out, 6 * static_cast<size_t>(h->near_cap)) &&
+              dalloc_t(h, h->near_n, 1) && dalloc_t(h, h->near_off, n3 / 3 + 1) && dalloc_t(h, h->near_cnt, n3 / 3 + 1);
     for (int b = 0; b < 2 && ok; ++b) ok = dalloc_t(h, h->x64[b], n3);
     ok = ok && dalloc_t(h, h->fext64, n3) && dalloc_t(h, h->F64, n3) && dalloc_t(h, h->Fa64, n3) &&
          dalloc_t(h, h->Wa64, n3);
@@ -352,7 +356,8 @@ void sd_destroy(sd_handle *h) {
     }
     void *bufs[] = {h->fext64, h->F64, h->Fa64, h->Wa64, h->part, h->part2, h->jpart,
                     h->cl.cell, h->cl.key, h->cl.cnt, h->cl.fill, h->cl.start, h->cl.bsum, h->cl.sorted,
-                    h->ckpt, h->seg, h->lam, h->gFacc, h->near64, h->d_flag, h->d_err};
+                    h->ckpt, h->seg, h->lam, h->gFacc, h->near64, h->d_flag, h->d_err,
+                    h->near_ent, h->near_out, h->near_n, h->near_off, h->near_cnt};
     for (void *p : bufs) dfree(h, p);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;

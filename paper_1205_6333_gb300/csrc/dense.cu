@@ -624,9 +624,11 @@ static size_t dense_smem(int mode, int J) {
 static constexpr size_t kSymSmem = (12 * kSymB + 2 * 6 * kSymNT + (kSymNT / 32) * 3 * kSymB) * sizeof(float);
 
 // The symmetric kernel replaces the directed FP32 kernel once the triangle holds at
-// least this many tiles per resident CTA (below, its 256-particle blocks leave SMs idle).
-#ifndef SD_DENSE_SYM_MIN_TILES
-#define SD_DENSE_SYM_MIN_TILES 2
+// least one tile per SD_DENSE_SYM_SMS_PER_TILE SMs.  Measured on GB300 (step time,
+// N = 2^k at volume fraction 0.05): directed faster at N <= 2048 (36 tiles),
+// symmetric faster from N = 4096 (136 tiles) on.
+#ifndef SD_DENSE_SYM_SMS_PER_TILE
+#define SD_DENSE_SYM_SMS_PER_TILE 2
 #endif
 
 // Choose the tile J and the persistent grid for h->npad, and size the partials.
@@ -680,8 +682,7 @@ cudaError_t dense_setup(sd_handle *h) {
         s.I = s.J = kSymB;
         s.nIB = s.nJT = h->npad / kSymB;
         s.nT = static_cast<long long>(s.nIB) * (s.nIB + 1) / 2;
-        if (want_sym == SD_DENSE_SYMMETRIC ||
-            s.nT >= static_cast<long long>(SD_DENSE_SYM_MIN_TILES) * h->num_sms * socc) {
+        if (want_sym == SD_DENSE_SYMMETRIC || s.nT * SD_DENSE_SYM_SMS_PER_TILE >= h->num_sms) {
             const long long swant = static_cast<long long>(h->num_sms) * socc * SD_DENSE_CTA_SCALE;
             s.chunk = std::max(1LL, (s.nT + swant - 1) / swant);
             s.grid = static_cast<int>((s.nT + s.chunk - 1) / s.chunk);

@@ -19,6 +19,7 @@
 // or the RPY overlap form) at the FP64 separation.  These are the pairs whose
 // FP32 evaluation suffers from cancellation in r_i - r_j (large coordinates,
 // small separations) or that the clamp altered (r < 2a).
+#include <algorithm>
 #include "neighbours.cuh"
 
 namespace sd {
@@ -64,27 +65,66 @@ struct NearArgs {
     int *flag;      // raised when some pair has r < r_safe
     int *err;
     int I, J;       // the all-pairs kernel's i-block and j-tile sizes
+    // compacted candidate list (near_collect_kernel -> near_pair_kernel -> epilogue)
+    int2 *ent;        // [cap] (i, j), or (-1, -1) for a slot that holds no pair
+    double *ent_out;  // [cap][6] the pair's two correction variants, as `near`
+    unsigned long long *ent_n;   // entries claimed (zeroed before the collect kernel)
+    int *noff, *ncnt; // per particle: first entry and count; ncnt = -1: correction is in near[i]
+    int cap;
 };
 
-// kWalkLanes threads per particle, each walking a share of the 27 cells; the
-// partial sums meet in a fixed shuffle tree (deterministic).
+// The correction of one near pair (FP64 r^2 < r_near^2), added to c6: the exact
+// FP64 term minus the all-pairs kernel's FP32 term with r^2 clamped (c6[0..2]),
+// and the further difference when that kernel did not clamp (c6[3..5]).
 template <int TENSOR, int MODE>
-__global__ void __launch_bounds__(128) near_kernel(NearArgs a) {
+__device__ __forceinline__ void near_pair_term(const NearArgs &a, int i, int j, double dx, double dy, double dz,
+                                               double r2, double (&c6)[6], bool &coincident) {
     using V4 = typename EpiT<MODE>::V4;
     constexpr int TDENSE = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
-    const long long gt = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int i = static_cast<int>(gt / kWalkLanes), sub = static_cast<int>(gt % kWalkLanes);
-    const bool active = i < a.n;   // inactive lanes still join the shuffles
     const V4 *pm = static_cast<const V4 *>(a.posm);
     const V4 *fm = static_cast<const V4 *>(a.frcm);
-    double c6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // clamped variant, then unclamped variant
+    if (r2 == 0.0 && TENSOR != T_RPY) {
+        coincident = true;
+        return;
+    }
+    double A, B, dA, dB;
+    profile_exact<TENSOR>(r2, a.pc, A, B, dA, dB);
+    const double fx = a.F64[3 * j], fy = a.F64[3 * j + 1], fz = a.F64[3 * j + 2];
+    const double s = B * (dx * fx + dy * fy + dz * fz);
+    const double e[3] = {A * fx + s * dx, A * fy + s * dy, A * fz + s * dz};
+    const V4 pi = pm[i], pj = pm[j];
+    double tc[3];
+    dense_term<TDENSE, MODE, true>(pi, pj, fm[j], a.pc, tc);
+    for (int d = 0; d < 3; ++d) c6[d] += e[d] - tc[d];
+    // The unclamped variant differs only where the clamp was active, i.e. the
+    // pair's FP32 r^2 < (2a)^2, and outside the tiles holding self pairs (clamped
+    // in both variants); c6[3..5] collects that difference.
+    if constexpr (MODE != MODE_FP64) {
+        const float ux = __fsub_rn(pi.x, pj.x), uy = __fsub_rn(pi.y, pj.y), uz = __fsub_rn(pi.z, pj.z);
+        const float r2f = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
+        const long long i0 = static_cast<long long>(i / a.I) * a.I, j0 = static_cast<long long>(j / a.J) * a.J;
+        const bool diag = (j0 < i0 + a.I) && (i0 < j0 + a.J);
+        if (r2f < a.pc.r2min_f && !diag) {
+            double tu[3];
+            dense_term<TDENSE, MODE, false>(pi, pj, fm[j], a.pc, tu);
+            for (int d = 0; d < 3; ++d) c6[3 + d] += tc[d] - tu[d];
+        }
+    }
+}
+
+// In-place correction of particle i by its kWalkLanes lanes (used when the
+// candidate list has no room): the walk, the FP64 test and the term per lane,
+// then the fixed shuffle tree.  Warp-collective.
+template <int TENSOR, int MODE>
+__device__ void near_direct(const NearArgs &a, int i, int sub, bool active) {
+    using V4 = typename EpiT<MODE>::V4;
+    const V4 *pm = static_cast<const V4 *>(a.posm);
+    double c6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     bool coincident = false, close = false, found = false;
     if (active) {
         const V4 pi = pm[i];
         const double xi = a.x64[3 * i], yi = a.x64[3 * i + 1], zi = a.x64[3 * i + 2];
         for_each_neighbour_part(a.cl, i, a.cl.cell[i], sub, kWalkLanes, [&](int j) {
-            // screen in the mirror's precision (with a margin far above its
-            // rounding error), then decide in FP64
             const V4 pj = pm[j];
             const float sx = static_cast<float>(pi.x - pj.x), sy = static_cast<float>(pi.y - pj.y),
                         sz = static_cast<float>(pi.z - pj.z);
@@ -94,34 +134,7 @@ __global__ void __launch_bounds__(128) near_kernel(NearArgs a) {
             if (r2 >= a.rnear2) return;
             found = true;
             if (r2 < a.rsafe2) close = true;
-            if (r2 == 0.0 && TENSOR != T_RPY) {
-                coincident = true;
-                return;
-            }
-            double A, B, dA, dB;
-            profile_exact<TENSOR>(r2, a.pc, A, B, dA, dB);
-            const double fx = a.F64[3 * j], fy = a.F64[3 * j + 1], fz = a.F64[3 * j + 2];
-            const double s = B * (dx * fx + dy * fy + dz * fz);
-            const double e[3] = {A * fx + s * dx, A * fy + s * dy, A * fz + s * dz};
-            double tc[3];
-            dense_term<TDENSE, MODE, true>(pi, pm[j], fm[j], a.pc, tc);
-            for (int d = 0; d < 3; ++d) c6[d] += e[d] - tc[d];
-            // The unclamped variant differs only where the clamp was active, i.e.
-            // the pair's FP32 r^2 < (2a)^2, and outside the tiles holding self pairs
-            // (clamped in both variants); c6[3..5] collects that difference.
-            if constexpr (MODE != MODE_FP64) {
-                const float ux = __fsub_rn(pi.x, pm[j].x), uy = __fsub_rn(pi.y, pm[j].y),
-                            uz = __fsub_rn(pi.z, pm[j].z);
-                const float r2f = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
-                const long long i0 = static_cast<long long>(i / a.I) * a.I,
-                                j0 = static_cast<long long>(j / a.J) * a.J;
-                const bool diag = (j0 < i0 + a.I) && (i0 < j0 + a.J);
-                if (r2f < a.pc.r2min_f && !diag) {
-                    double tu[3];
-                    dense_term<TDENSE, MODE, false>(pi, pm[j], fm[j], a.pc, tu);
-                    for (int d = 0; d < 3; ++d) c6[3 + d] += tc[d] - tu[d];
-                }
-            }
+            near_pair_term<TENSOR, MODE>(a, i, j, dx, dy, dz, r2, c6, coincident);
         });
     }
     const int writer = walk_combine(c6, found, sub);
@@ -137,11 +150,140 @@ __global__ void __launch_bounds__(128) near_kernel(NearArgs a) {
     }
 }
 
+// Step 1 of the near pass: kWalkLanes lanes per particle walk the 27 cells and keep
+// the neighbours that pass an FP32 screen on the mirror.  The candidates go to a
+// list in (particle, lane, walk) order: a warp-wide prefix sum places each lane's
+// run, one atomicAdd per CTA claims the CTA's range.  The FP64 arithmetic is left
+// to near_pair_kernel, where every lane of a warp has a pair (here only ~1 lane
+// in 20 would).
+constexpr int kNearRegs = 4;   // candidates a lane keeps in registers; more -> second walk
+
+template <int TENSOR, int MODE>
+__global__ void __launch_bounds__(128) near_collect_kernel(NearArgs a) {
+    using V4 = typename EpiT<MODE>::V4;
+    __shared__ int s_w[4];
+    __shared__ long long s_base;
+    __shared__ int s_tot;
+    const V4 *pm = static_cast<const V4 *>(a.posm);
+    const long long gt = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int i = static_cast<int>(gt / kWalkLanes), sub = static_cast<int>(gt % kWalkLanes);
+    const bool active = i < a.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int cnt = 0, j0 = -1, j1 = -1, j2 = -1, j3 = -1;
+    auto screen = [&](const V4 &pi, int j) {
+        const V4 pj = pm[j];
+        const float sx = static_cast<float>(pi.x - pj.x), sy = static_cast<float>(pi.y - pj.y),
+                    sz = static_cast<float>(pi.z - pj.z);
+        return sx * sx + sy * sy + sz * sz <= a.rscreen2;
+    };
+    if (active) {
+        const V4 pi = pm[i];
+        for_each_neighbour_part(a.cl, i, a.cl.cell[i], sub, kWalkLanes, [&](int j) {
+            if (!screen(pi, j)) return;
+            if (cnt == 0) j0 = j;
+            else if (cnt == 1) j1 = j;
+            else if (cnt == 2) j2 = j;
+            else if (cnt == 3) j3 = j;
+            ++cnt;
+        });
+    }
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - cnt;
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < 4; ++w) {
+            const int t = s_w[w];
+            s_w[w] = run;
+            run += t;
+        }
+        s_tot = run;
+        s_base = run ? static_cast<long long>(atomicAdd(a.ent_n, static_cast<unsigned long long>(run))) : 0;
+    }
+    __syncthreads();
+    const long long base = s_base;
+    const int tot = s_tot;
+    const bool fits = base + tot <= a.cap;
+    // this lane's first entry (only used when the CTA's range fits below the capacity)
+    const int first = fits ? static_cast<int>(base) + s_w[warp] + excl : 0;
+    const int pfirst = __shfl_sync(0xffffffffu, first, lane & ~(kWalkLanes - 1));
+    int pcnt = cnt;
+    for (int o = kWalkLanes / 2; o >= 1; o >>= 1) pcnt += __shfl_xor_sync(0xffffffffu, pcnt, o);
+    if (fits) {
+        if (active) {
+            const int js[kNearRegs] = {j0, j1, j2, j3};
+#pragma unroll
+            for (int k = 0; k < kNearRegs; ++k)
+                if (k < cnt) a.ent[first + k] = make_int2(i, js[k]);
+            if (cnt > kNearRegs) {   // rare: walk again for the candidates beyond the registers
+                const V4 pi = pm[i];
+                int k = 0;
+                for_each_neighbour_part(a.cl, i, a.cl.cell[i], sub, kWalkLanes, [&](int j) {
+                    if (!screen(pi, j)) return;
+                    if (k >= kNearRegs && k < cnt) a.ent[first + k] = make_int2(i, j);
+                    ++k;
+                });
+            }
+            if (sub == 0) {
+                a.noff[i] = pfirst;
+                a.ncnt[i] = pcnt;
+            }
+        }
+    } else {
+        // The list is full: mark this CTA's claimed slots below the capacity as
+        // empty and correct its particles in place.
+        for (long long e = base + threadIdx.x; e < base + tot && e < a.cap; e += blockDim.x)
+            a.ent[e] = make_int2(-1, -1);
+        if (active && sub == 0) a.ncnt[i] = -1;
+        near_direct<TENSOR, MODE>(a, i, sub, active);
+    }
+}
+
+// Step 2: one thread per listed pair: the FP64 test r < r_near, the flags, and the
+// two correction variants of the pair, written to its entry.
+template <int TENSOR, int MODE>
+__global__ void __launch_bounds__(128) near_pair_kernel(NearArgs a) {
+    const int total = static_cast<int>(min(*a.ent_n, static_cast<unsigned long long>(a.cap)));
+    bool coincident = false, close = false;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int2 p = a.ent[e];
+        double c6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (p.x >= 0) {
+            const int i = p.x, j = p.y;
+            const double dx = a.x64[3 * i] - a.x64[3 * j], dy = a.x64[3 * i + 1] - a.x64[3 * j + 1],
+                         dz = a.x64[3 * i + 2] - a.x64[3 * j + 2];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < a.rnear2) {
+                if (r2 < a.rsafe2) close = true;
+                near_pair_term<TENSOR, MODE>(a, i, j, dx, dy, dz, r2, c6, coincident);
+            }
+        }
+        double *o = a.ent_out + 6 * static_cast<size_t>(e);
+        for (int d = 0; d < 3; ++d) {
+            o[d] = c6[d];
+            o[3 + d] = c6[d] + c6[3 + d];
+        }
+    }
+    if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
+    if (close) atomicOr(a.flag, 1);
+}
+
+template <int TENSOR, int MODE>
+static void near_launch2(int nb, int np, cudaStream_t st, const NearArgs &a) {
+    near_collect_kernel<TENSOR, MODE><<<nb, 128, 0, st>>>(a);
+    near_pair_kernel<TENSOR, MODE><<<np, 128, 0, st>>>(a);
+}
+
 template <int TENSOR>
-static void near_launch_mode(int mode, int nb, cudaStream_t st, const NearArgs &a) {
+static void near_launch_mode(int mode, int nb, int np, cudaStream_t st, const NearArgs &a) {
     switch (mode) {
-        case MODE_FP64: near_kernel<TENSOR, MODE_FP64><<<nb, 128, 0, st>>>(a); break;
-        default: near_kernel<TENSOR, MODE_FP32C><<<nb, 128, 0, st>>>(a); break;   // FP32 and FP32C share it
+        case MODE_FP64: near_launch2<TENSOR, MODE_FP64>(nb, np, st, a); break;
+        default: near_launch2<TENSOR, MODE_FP32C>(nb, np, st, a); break;   // FP32 and FP32C share it
     }
 }
 
@@ -164,21 +306,33 @@ cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const 
     a.err = h->d_err;
     a.I = h->geom.I;
     a.J = h->geom.J;
+    a.ent = h->near_ent;
+    a.ent_out = h->near_out;
+    a.ent_n = h->near_n;
+    a.noff = h->near_off;
+    a.ncnt = h->near_cnt;
+    a.cap = h->near_cap;
     const int nb = static_cast<int>((static_cast<long long>(h->n) * kWalkLanes + 127) / 128);
+    const int np = static_cast<int>(std::min<long long>((static_cast<long long>(a.cap) + 127) / 128,
+                                                        8LL * h->num_sms));
     prof_begin(h, SD_KERNEL_NEAR, st);
+    cudaError_t e = cudaMemsetAsync(a.ent_n, 0, sizeof(*a.ent_n), st);
+    if (e != cudaSuccess) return e;
     switch (h->tensor) {
-        case T_RPY: near_launch_mode<T_RPY>(h->mode, nb, st, a); break;
-        case T_RP: near_launch_mode<T_RP>(h->mode, nb, st, a); break;
-        default: near_launch_mode<T_OSEEN>(h->mode, nb, st, a); break;
+        case T_RPY: near_launch_mode<T_RPY>(h->mode, nb, np, st, a); break;
+        case T_RP: near_launch_mode<T_RP>(h->mode, nb, np, st, a); break;
+        default: near_launch_mode<T_OSEEN>(h->mode, nb, np, st, a); break;
     }
     prof_end(h, SD_KERNEL_NEAR, st);
-    ++h->launches;
+    h->launches += 2;
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- epilogue
 
 struct EpiArgs {
+    const double *ent_out;   // near-pass list results, per particle noff/ncnt
+    const int *noff, *ncnt;
     const double *part;
     const float *jpart;   // source-side sums of the symmetric kernel (g.sym)
     int npad;
@@ -203,7 +357,14 @@ struct EpiArgs {
 // particle's block column); lane l reads particle 32 b + l, so every warp load is
 // one coalesced 128-byte row.  Warp 0 adds the warps' results in ascending w
 // (fixed order: deterministic) and applies the FP64 terms.
-constexpr int kEpiWarps = 8;
+#ifndef SD_EPI_WARPS
+#define SD_EPI_WARPS 8
+#endif
+#ifndef SD_EPI_UNROLL
+#define SD_EPI_UNROLL 2
+#endif
+constexpr int kEpiWarps = SD_EPI_WARPS;
+constexpr int kEpiUnroll = SD_EPI_UNROLL;
 
 template <int TDENSE, int MODE, int OUT>
 __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
@@ -240,7 +401,7 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
             } else {
                 for (int s = w; s < ns; s += kEpiWarps)
                     for (int d = 0; d < 3; ++d) v[d] += a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
-#pragma unroll 2
+#pragma unroll kEpiUnroll
                 for (int r = w; r < nc; r += kEpiWarps) {
                     const float *src = a.jpart + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
                     for (int d = 0; d < 3; ++d) fold2(hi[d], lo[d], src[d * J]);
@@ -281,10 +442,19 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
         dense_term<TDENSE, MODE, true>(pi, pi, fm[i], a.pc, t);
         for (int d = 0; d < 3; ++d) V[d] += a.F64[3 * i + d] - t[d];
     }
-    // near pairs: the variant matching the kernel's clamping
+    // near pairs: the variant matching the kernel's clamping, from the particle's
+    // entries of the candidate list in list order (or from its in-place result)
     {
-        const double *c = a.near + 6 * static_cast<size_t>(i) + ((*a.flag) ? 0 : 3);
-        for (int d = 0; d < 3; ++d) V[d] += c[d];
+        const int var = (*a.flag) ? 0 : 3;
+        const int cnt = a.ncnt[i];
+        if (cnt < 0) {
+            const double *c = a.near + 6 * static_cast<size_t>(i) + var;
+            for (int d = 0; d < 3; ++d) V[d] += c[d];
+        } else {
+            const double *c = a.ent_out + 6 * static_cast<size_t>(a.noff[i]) + var;
+            for (int k = 0; k < cnt; ++k, c += 6)
+                for (int d = 0; d < 3; ++d) V[d] += c[d];
+        }
     }
     const double m0 = a.pc.mu0;
     const double v0 = m0 * V[0], v1 = m0 * V[1], v2 = m0 * V[2];
@@ -330,6 +500,9 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
                             const double *F64, const void *frcm, void *vout, double dt, double *x64n) {
     if (h->n == 0) return cudaSuccess;
     EpiArgs a;
+    a.ent_out = h->near_out;
+    a.noff = h->near_off;
+    a.ncnt = h->near_cnt;
     a.part = h->part;
     a.jpart = h->jpart;
     a.npad = h->npad;

@@ -39,6 +39,7 @@ constexpr int kRV = 2;           // i-particles per thread, VJP dense kernel
 constexpr int kJmax = 256;       // largest j-tile
 constexpr double kRSafe = 1.0;   // pairs closer than kRSafe * a make the FP32 kernel clamp every tile
 constexpr long long kDefaultWatchdog = 1LL << 22;
+constexpr int kNearPerParticle = 8;   // near-pass list capacity per particle (overflow: in-place path)
 constexpr int kSymNT = 128;      // threads per CTA of the symmetric FP32 kernel
 constexpr int kSymB = 256;       // particles per block (2 per thread) = sources per tile
 
@@ -159,6 +160,11 @@ struct sd_handle {
 
     sd::CellList cl;
     double *near64 = nullptr;   // [n][6] FP64 near-pair corrections (clamped / unclamped variant)
+    int2 *near_ent = nullptr;   // [near_cap] candidate pairs of the near pass
+    double *near_out = nullptr; // [near_cap][6] their corrections
+    unsigned long long *near_n = nullptr;   // entries claimed this pass
+    int *near_off = nullptr, *near_cnt = nullptr;   // [n] each particle's run of entries
+    int near_cap = 0;
     int *d_flag = nullptr;      // set by the near pass when some pair has r < kRSafe a
     int *d_err = nullptr;
 

@@ -185,3 +185,31 @@ def test_overlaps_between_a_and_2a(prec, tensor):
         s.set_positions(x)
         v = s.mobility_apply(F)
     assert rel_err(v, oracle.mobility_apply(x, F, tensor)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_near_list_overflow_falls_back(prec):
+    """A crowded, heavily overlapping cluster (~130 candidates per particle) overflows
+    the near pass's candidate list (8 per particle): the CTAs without room correct
+    their particles in place, the others through the list; both must agree with
+    the oracle."""
+    n = 2000
+    x = np.random.default_rng(inputs.SEED_BASE + 40).uniform(0.0, 10.0, (n, 3))
+    F = inputs.normal_forces(n, inputs.SEED_BASE + 41)
+    with sd.System(n, prec=prec) as s:
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+    ref = oracle.mobility_apply(x, F, "rpy", nthreads=8)
+    assert rel_err(v, ref) <= TOL[prec]
+
+
+def test_near_list_dense_packing():
+    """Volume fraction 0.3 (about 5 near pairs per particle): the list holds them all."""
+    n = 3000
+    x, _ = inputs.cube_rsa(n, 0.3, inputs.SEED_BASE + 42)
+    F = inputs.normal_forces(n, inputs.SEED_BASE + 43)
+    ref = oracle.mobility_apply(x, F, "rpy", nthreads=8)
+    for prec in ["fp32c", "fp64"]:
+        with sd.System(n, prec=prec) as s:
+            s.set_positions(x)
+            assert rel_err(s.mobility_apply(F), ref) <= TOL[prec], prec

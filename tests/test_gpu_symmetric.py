@@ -86,6 +86,8 @@ def test_auto_choice_and_fp64_rejection():
         assert s.dense_kernel() == "symmetric"
     with sd.System(1024) as s:
         assert s.dense_kernel() == "directed"
+    with sd.System(8192) as s:
+        assert s.dense_kernel() == "symmetric"
     with sd.System(65536, prec="fp64") as s:
         assert s.dense_kernel() == "directed"
     with pytest.raises(sd.SDError) as ei:
