@@ -151,24 +151,25 @@ __device__ void near_direct(const NearArgs &a, int i, int sub, bool active) {
 }
 
 // Step 1 of the near pass: kWalkLanes lanes per particle walk the 27 cells and keep
-// the neighbours that pass an FP32 screen on the mirror.  The candidates go to a
-// list in (particle, lane, walk) order: a warp-wide prefix sum places each lane's
-// run, one atomicAdd per CTA claims the CTA's range.  The FP64 arithmetic is left
-// to near_pair_kernel, where every lane of a warp has a pair (here only ~1 lane
-// in 20 would).
+// the neighbours that pass an FP32 screen on the mirror.  Particles are taken in
+// cell-list order, so the groups of a warp are spatial neighbours and share the
+// cells they read.  The candidates go to a list in (particle, lane, walk) order: a
+// warp-wide prefix sum places each lane's run, one atomicAdd per warp claims the
+// warp's range (where the warps' ranges land does not matter: each particle's run
+// is contiguous and read in order).  The FP64 arithmetic is left to
+// near_pair_kernel, where every lane of a warp has a pair (here only ~1 lane in 20
+// would).
 constexpr int kNearRegs = 4;   // candidates a lane keeps in registers; more -> second walk
 
 template <int TENSOR, int MODE>
 __global__ void __launch_bounds__(128) near_collect_kernel(NearArgs a) {
     using V4 = typename EpiT<MODE>::V4;
-    __shared__ int s_w[4];
-    __shared__ long long s_base;
-    __shared__ int s_tot;
     const V4 *pm = static_cast<const V4 *>(a.posm);
     const long long gt = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int i = static_cast<int>(gt / kWalkLanes), sub = static_cast<int>(gt % kWalkLanes);
-    const bool active = i < a.n;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = static_cast<int>(gt / kWalkLanes), sub = static_cast<int>(gt % kWalkLanes);
+    const bool active = q < a.n;
+    const int i = active ? a.cl.sorted[q] : 0;
+    const int lane = threadIdx.x & 31;
     int cnt = 0, j0 = -1, j1 = -1, j2 = -1, j3 = -1;
     auto screen = [&](const V4 &pi, int j) {
         const V4 pj = pm[j];
@@ -193,24 +194,13 @@ __global__ void __launch_bounds__(128) near_collect_kernel(NearArgs a) {
         if (lane >= o) incl += t;
     }
     const int excl = incl - cnt;
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int w = 0; w < 4; ++w) {
-            const int t = s_w[w];
-            s_w[w] = run;
-            run += t;
-        }
-        s_tot = run;
-        s_base = run ? static_cast<long long>(atomicAdd(a.ent_n, static_cast<unsigned long long>(run))) : 0;
-    }
-    __syncthreads();
-    const long long base = s_base;
-    const int tot = s_tot;
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    long long base = 0;
+    if (lane == 0 && tot > 0) base = static_cast<long long>(atomicAdd(a.ent_n, static_cast<unsigned long long>(tot)));
+    base = __shfl_sync(0xffffffffu, base, 0);
     const bool fits = base + tot <= a.cap;
-    // this lane's first entry (only used when the CTA's range fits below the capacity)
-    const int first = fits ? static_cast<int>(base) + s_w[warp] + excl : 0;
+    // this lane's first entry (only used when the warp's range fits below the capacity)
+    const int first = fits ? static_cast<int>(base) + excl : 0;
     const int pfirst = __shfl_sync(0xffffffffu, first, lane & ~(kWalkLanes - 1));
     int pcnt = cnt;
     for (int o = kWalkLanes / 2; o >= 1; o >>= 1) pcnt += __shfl_xor_sync(0xffffffffu, pcnt, o);
@@ -235,10 +225,9 @@ __global__ void __launch_bounds__(128) near_collect_kernel(NearArgs a) {
             }
         }
     } else {
-        // The list is full: mark this CTA's claimed slots below the capacity as
+        // The list is full: mark this warp's claimed slots below the capacity as
         // empty and correct its particles in place.
-        for (long long e = base + threadIdx.x; e < base + tot && e < a.cap; e += blockDim.x)
-            a.ent[e] = make_int2(-1, -1);
+        for (long long e = base + lane; e < base + tot && e < a.cap; e += 32) a.ent[e] = make_int2(-1, -1);
         if (active && sub == 0) a.ncnt[i] = -1;
         near_direct<TENSOR, MODE>(a, i, sub, active);
     }
@@ -372,7 +361,9 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
     __shared__ double s_v[kEpiWarps][3][32];
     __shared__ float s_h[kEpiWarps][3][32], s_l[kEpiWarps][3][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int i = blockIdx.x * 32 + lane;
+    // CTAs in reverse particle order: the last blocks have the longest source-side
+    // columns, so they start first instead of forming the tail
+    const int i = (gridDim.x - 1 - blockIdx.x) * 32 + lane;
     const bool active = i < a.n;
 
     // This warp's share of the dense sum: the CTA slots of the particle's i-block,
