@@ -15,6 +15,7 @@ Every function is the paper's definition written out:
 * ``mobility_rows``       -- the same sum for selected rows i
 * ``assemble``            -- the 3N x 3N matrix mu (second formulation, tests only)
 * ``forces``              -- F_ext + gravity + truncated (2a/r)^12 repulsion (Sec. 3.1, step 2)
+* ``lubrication``         -- -sum_j zeta^sing_ij (v_i - v_j), cut at r = 3a (Sec. 2.3 Eq. lubrication)
 * ``euler``               -- x <- x + dt M(x) F(x)                     (Sec. 3.1, steps 1-3)
 * ``vjp``                 -- (dv/dx)^T w and M w, closed-form derivative of T
 * ``adjoint``             -- reverse sweep through Euler steps
@@ -68,7 +69,8 @@ def _load():
         lib.sdo_mobility_rows.argtypes = [I, D, D, P, I, P, P, I, P, P, I]
         lib.sdo_assemble.argtypes = [I, D, D, P, I, P, P]
         lib.sdo_forces.argtypes = [D, P, I, P, P, P, D, D, P]
-        lib.sdo_euler.argtypes = [I, D, D, P, I, P, P, P, D, D, D, L, L, P, I]
+        lib.sdo_euler.argtypes = [I, D, D, P, I, P, P, P, D, D, I, D, L, L, P, I]
+        lib.sdo_lubrication.argtypes = [D, D, P, I, P, P, P]
         lib.sdo_vjp.argtypes = [I, D, D, P, I, P, P, P, P, P, I]
         lib.sdo_adjoint.argtypes = [I, D, D, P, I, P, P, P, D, L, P, P, P, I]
         lib.sdo_has_openmp.restype = I
@@ -163,9 +165,20 @@ def forces(x, fext=None, gravity=(0.0, 0.0, 0.0), rep_eps=0.0, rep_rc=2.5, a=1.0
     return F
 
 
+def lubrication(x, v, a=1.0, eta=1.0, box=None) -> np.ndarray:
+    """The lubrication friction forces -sum_j zeta_ij (v_i - v_j) of Sec. 2.3 / 3.1 step 2."""
+    x, v = _d(x).reshape(-1, 3), _d(v).reshape(-1, 3)
+    F = np.zeros_like(x)
+    b = _box(box)
+    _check(_load().sdo_lubrication(float(a), float(eta), _p(b), x.shape[0], _p(x), _p(v), _p(F)))
+    return F
+
+
 def euler(x0, nsteps, dt, fext=None, gravity=(0.0, 0.0, 0.0), rep_eps=0.0, rep_rc=2.5, tensor="rpy",
-          a=1.0, eta=1.0, box=None, every=0, nthreads=None):
-    """Returns x after nsteps, and the positions after every `every`-th step if every > 0."""
+          a=1.0, eta=1.0, box=None, every=0, nthreads=None, lubrication=False):
+    """Returns x after nsteps, and the positions after every `every`-th step if every > 0.
+    With lubrication=True each step's forces include the lubrication friction of
+    close pairs computed from the previous step's velocities (zero at the start)."""
     x = _d(x0).reshape(-1, 3).copy()
     n = x.shape[0]
     fe = None if fext is None else _d(fext).reshape(n, 3)
@@ -175,8 +188,8 @@ def euler(x0, nsteps, dt, fext=None, gravity=(0.0, 0.0, 0.0), rep_eps=0.0, rep_r
         traj = np.zeros((int(nsteps) // int(every), n, 3))
     b = _box(box)
     _check(_load().sdo_euler(_t(tensor), float(a), float(eta), _p(b), n, _p(x), _p(fe), _p(g), float(rep_eps),
-                             float(rep_rc), float(dt), int(nsteps), int(every or 0), _p(traj),
-                             _threads(nthreads)))
+                             float(rep_rc), int(bool(lubrication)), float(dt), int(nsteps), int(every or 0),
+                             _p(traj), _threads(nthreads)))
     return (x, traj) if traj is not None else x
 
 

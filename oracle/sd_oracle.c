@@ -21,7 +21,9 @@
  *   - mobility sum v_i = sum_j mu_ij F_j, one ascending-j loop per i,
  *     self term mu0 F_i (Sec. 2.2 Eq. rotneMobility; Sec. 3.2 Algorithm 1)
  *   - explicit Euler r_i <- r_i + dt v_i (Sec. 3.1, step 1); forces F_ext plus
- *     a truncated soft repulsion U = eps (2a/r)^12 for r < r_c (Sec. 3.1, step 2)
+ *     a truncated soft repulsion U = eps (2a/r)^12 for r < r_c (Sec. 3.1, step 2),
+ *     optionally minus the singular lubrication friction of pairs closer than 3a
+ *     with the previous step's velocities (Sec. 2.3 Eq. lubrication; Sec. 3.1)
  *   - adjoint of the Euler recursion with the closed-form derivative of the
  *     pair tensor (derived from Eq. rotneMobility; not in the paper).
  *
@@ -196,21 +198,61 @@ int sdo_forces(double a, const double *box, int n, const double *x, const double
     return SDO_OK;
 }
 
+/* Singular lubrication friction of close pairs, Sec. 2.3 Eq. lubrication, in the
+ * form Sec. 3.1 step 2 uses it:
+ *   F_i -= sum_{j: 0 < s_ij < 1} zeta_ij (v_i - v_j),   s_ij = r_ij / a - 2,
+ *   mu0 zeta_ij = (1/(4s) - (9/40) ln s) e e^T - (1/6) ln s (I - e e^T),  e = r_ij / r_ij,
+ * truncated at s = 1 (r = 3a) as the paper does; pairs with s <= 0 (overlapping
+ * spheres, where the expansion has no value) contribute nothing.  v holds the
+ * velocities of the previous step.  The result is ADDED to F. */
+int sdo_lubrication(double a, double eta, const double *box, int n, const double *x, const double *v, double *F) {
+    const double mu0 = sdo_mu0(a, eta);
+    for (int i = 0; i < n; ++i) {
+        double f[3] = {0.0, 0.0, 0.0};
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
+            sdo_min_image(box, r);
+            const double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            const double sg = rn / a - 2.0;
+            if (!(sg > 0.0 && sg < 1.0)) continue;
+            const double e[3] = {r[0] / rn, r[1] / rn, r[2] / rn};
+            const double vij[3] = {v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1], v[3 * i + 2] - v[3 * j + 2]};
+            const double normal = 1.0 / (4.0 * sg) - (9.0 / 40.0) * log(sg);
+            const double tangential = -(1.0 / 6.0) * log(sg);
+            for (int al = 0; al < 3; ++al) {
+                double zv = 0.0;
+                for (int be = 0; be < 3; ++be) {
+                    const double I = (al == be) ? 1.0 : 0.0;
+                    const double ee = e[al] * e[be];
+                    zv += (normal * ee + tangential * (I - ee)) * vij[be];
+                }
+                f[al] -= zv / mu0;
+            }
+        }
+        for (int d = 0; d < 3; ++d) F[3 * i + d] += f[d];
+    }
+    return SDO_OK;
+}
+
 /* Explicit Euler, Sec. 3.1 steps 1-3 in the standard order
- *   F_n = F(x_n);  v_n = M(x_n) F_n;  x_{n+1} = x_n + dt v_n.
- * x is updated in place.  If traj != NULL, x after every `every`-th step is
- * appended (traj holds (nsteps/every) * n * 3 doubles). */
+ *   F_n = F(x_n) [- lubrication with v_{n-1}];  v_n = M(x_n) F_n;  x_{n+1} = x_n + dt v_n.
+ * x is updated in place.  With lub != 0 the forces of each step carry the
+ * lubrication friction computed from the previous step's velocities (zero before
+ * the first step).  If traj != NULL, x after every `every`-th step is appended
+ * (traj holds (nsteps/every) * n * 3 doubles). */
 int sdo_euler(int tensor, double a, double eta, const double *box, int n, double *x,
-              const double *fext, const double g[3], double rep_eps, double rep_rc,
+              const double *fext, const double g[3], double rep_eps, double rep_rc, int lub,
               double dt, int64_t nsteps, int64_t every, double *traj, int nthreads) {
     double *F = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
-    double *v = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double *v = (double *)calloc(3 * (size_t)(n > 0 ? n : 1), sizeof(double));
     if (!F || !v) { free(F); free(v); return SDO_ERR_ARG; }
     int st = SDO_OK;
     int64_t out = 0;
     for (int64_t s = 0; s < nsteps && st == SDO_OK; ++s) {
         st = sdo_forces(a, box, n, x, fext, g, rep_eps, rep_rc, F);
         if (st != SDO_OK) break;
+        if (lub) sdo_lubrication(a, eta, box, n, x, v, F);
         st = sdo_mobility_apply(tensor, a, eta, box, n, x, F, v, nthreads);
         if (st != SDO_OK) break;
         for (int k = 0; k < 3 * n; ++k) x[k] += dt * v[k];

@@ -74,6 +74,19 @@ MUTANTS = [
     ("adjoint_wrong_state", "const double *xs = traj + (size_t)s * m;\n        st = sdo_vjp",
      "const double *xs = traj + (size_t)(s + 1) * m;\n        st = sdo_vjp"),
     ("adjoint_gravity_dropped", "F[k] = (fext ? fext[k] : 0.0) + g[k % 3];", "F[k] = (fext ? fext[k] : 0.0);"),
+    # lubrication (Sec. 2.3) and its use in the Euler step
+    ("lub_reynolds_coef", "1.0 / (4.0 * sg)", "1.0 / (2.0 * sg)"),
+    ("lub_normal_log_coef", "(9.0 / 40.0) * log(sg)", "(9.0 / 20.0) * log(sg)"),
+    ("lub_tangential_coef", "-(1.0 / 6.0) * log(sg)", "-(1.0 / 3.0) * log(sg)"),
+    ("lub_tangential_dropped", "(normal * ee + tangential * (I - ee))", "(normal * ee)"),
+    ("lub_projector_swapped", "(normal * ee + tangential * (I - ee))", "(normal * (I - ee) + tangential * ee)"),
+    ("lub_sign", "f[al] -= zv / mu0;", "f[al] += zv / mu0;"),
+    ("lub_times_mu0", "f[al] -= zv / mu0;", "f[al] -= zv * mu0;"),
+    ("lub_cutoff", "sg > 0.0 && sg < 1.0", "sg > 0.0 && sg < 2.0"),
+    ("lub_overlap_kept", "sg > 0.0 && sg < 1.0", "sg > -1.0 && sg < 1.0"),
+    ("lub_own_velocity_only", "v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1], v[3 * i + 2] - v[3 * j + 2]",
+     "v[3 * i], v[3 * i + 1], v[3 * i + 2]"),
+    ("euler_lub_not_applied", "if (lub) sdo_lubrication(a, eta, box, n, x, v, F);", ""),
 ]
 
 

@@ -450,3 +450,83 @@ def test_adjoint_matches_central_differences(orc):
             e[i, d] = h
             assert gx0[i, d] == pytest.approx((loss(x0 + e, fe) - loss(x0 - e, fe)) / (2 * h), rel=1e-6, abs=1e-9)
             assert gF[i, d] == pytest.approx((loss(x0, fe + e) - loss(x0, fe - e)) / (2 * h), rel=1e-6, abs=1e-9)
+
+
+# ---------------------------------------------------------------- lubrication (Sec. 2.3)
+
+def _pair_along(e, r):
+    e = np.asarray(e, float) / np.linalg.norm(e)
+    return np.array([[0.2, -0.4, 0.3], [0.2, -0.4, 0.3] + r * e]), e
+
+
+def test_lubrication_squeeze_film_limit(orc):
+    """Head-on approach of two equal spheres: as the gap h -> 0 the friction force
+    tends to Reynolds' squeeze-film result 6 pi eta a*^2 U / h with the reduced radius
+    a* = a/2, independent of the expansion the oracle evaluates; the next term is
+    O(s log s) relative."""
+    a, eta, U = 1.3, 0.7, 0.37
+    for s in [1e-3, 1e-4, 1e-5]:
+        x, e = _pair_along([0.3, 1.0, -0.5], (2.0 + s) * a)
+        v = np.array([0.5 * U * e, -0.5 * U * e])      # closing speed U
+        F = orc.lubrication(x, v, a, eta)
+        reynolds = 6 * math.pi * eta * (a / 2) ** 2 * U / (s * a)
+        assert F[0] @ e == pytest.approx(-reynolds, rel=1.0 * s * abs(math.log(s)) + 1e-12)
+        np.testing.assert_allclose(F[0] - (F[0] @ e) * e, 0.0, atol=1e-12 * reynolds)   # no sideways force
+
+
+def test_lubrication_matches_jeffrey_onishi_coefficients(orc):
+    """The two singular resistance functions of equal spheres as Jeffrey & Onishi (1984)
+    tabulate them (the source the paper cites): X11A = 1/(4 xi) + (9/40) ln(1/xi) for
+    motion along the line of centres and Y11A = (1/6) ln(1/xi) across it, in units of
+    6 pi eta a, xi = the gap over a."""
+    a, eta = 1.0, 1.0
+    mu0 = orc.mu0(a, eta)
+    for s in [0.02, 0.3, 0.9]:
+        x, e = _pair_along([1.0, 0.2, 0.1], (2.0 + s) * a)
+        t = np.cross(e, [0.0, 0.0, 1.0])
+        t /= np.linalg.norm(t)
+        Fn = orc.lubrication(x, np.array([e, 0 * e]), a, eta)[0]
+        Ft = orc.lubrication(x, np.array([t, 0 * t]), a, eta)[0]
+        assert -mu0 * (Fn @ e) == pytest.approx(1 / (4 * s) + 9 / 40 * math.log(1 / s), rel=1e-13)
+        assert -mu0 * (Ft @ t) == pytest.approx(1 / 6 * math.log(1 / s), rel=1e-13)
+        assert abs(Ft @ e) < 1e-13 and abs(Fn @ t) < 1e-13
+
+
+def test_lubrication_invariants(orc):
+    """Galilean invariance, momentum conservation, dissipation, rotation covariance and
+    the truncation window 0 < s < 1 (2a < r < 3a)."""
+    rng = np.random.default_rng(21)
+    n = 40
+    x = _nonoverlap(rng, n, 9.0)                       # many pairs inside 3a
+    v = rng.standard_normal((n, 3))
+    F = orc.lubrication(x, v)
+    assert np.abs(F).max() > 0
+    np.testing.assert_allclose(orc.lubrication(x, np.tile(v[0], (n, 1))), 0.0, atol=1e-12)
+    np.testing.assert_allclose(F.sum(axis=0), 0.0, atol=1e-10 * np.abs(F).max())
+    assert float((v * F).sum()) < 0.0
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    np.testing.assert_allclose(orc.lubrication(x @ Q.T, v @ Q.T), F @ Q.T, atol=1e-10 * np.abs(F).max())
+    for r, inside in [(2.0, False), (1.5, False), (2.0 + 1e-9, True), (3.0 - 1e-9, True), (3.0, False), (3.5, False)]:
+        xx, e = _pair_along([0.0, 0.0, 1.0], r)
+        Fp = orc.lubrication(xx, np.array([e, -e]))
+        if inside:
+            assert np.all(np.isfinite(Fp)) and np.abs(Fp).max() > 0, r
+        else:
+            np.testing.assert_array_equal(Fp, 0.0)
+
+
+def test_euler_lubrication_uses_previous_velocities(orc):
+    """Sec. 3.1: the first step has no friction (no previous velocity); step n adds the
+    friction of the velocities of step n-1 to the forces."""
+    rng = np.random.default_rng(22)
+    n, dt = 12, 0.05
+    x0 = _nonoverlap(rng, n, 6.0)
+    fe = rng.standard_normal((n, 3))
+    g = np.array([0.0, 0.0, -1.0])
+    x1 = orc.euler(x0, 1, dt, fe, g, lubrication=True)
+    np.testing.assert_array_equal(x1, orc.euler(x0, 1, dt, fe, g))
+    v0 = orc.mobility_apply(x0, fe + g)
+    F1 = fe + g + orc.lubrication(x1, v0)
+    x2 = x1 + dt * orc.mobility_apply(x1, F1)
+    np.testing.assert_allclose(orc.euler(x0, 2, dt, fe, g, lubrication=True), x2, rtol=1e-14, atol=1e-14)
+    assert np.abs(x2 - orc.euler(x0, 2, dt, fe, g)).max() > 1e-6   # the friction acted
