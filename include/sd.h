@@ -99,6 +99,13 @@ typedef struct sd_config {
     void (*free)(void *ptr, void *ctx);        /* its matching free                      */
     void *alloc_ctx;
     int32_t dense_kernel;    /* sd_dense_kernel; SYMMETRIC with FP64 gives SD_ERR_UNSUPPORTED */
+    int32_t lubrication;     /* 1: sd_step adds to each particle's force the singular lubrication
+                                friction of the pairs with 2a < r < 3a (Sec. 2.3 Eq. lubrication,
+                                truncated at s = r/a - 2 = 1), -sum_j zeta_ij (v_i - v_j), with the
+                                velocities of the previous step (Sec. 3.1 step 2; zero before the
+                                first step and after sd_set_positions).  Overlapping pairs (s <= 0)
+                                get no term.  FP64.  Not with sd_adjoint or sd_batch_create
+                                (SD_ERR_UNSUPPORTED). */
 } sd_config;
 
 typedef struct sd_handle sd_handle;

@@ -48,6 +48,7 @@ class sd_config(ctypes.Structure):
         ("free", FREE_FN),
         ("alloc_ctx", c_void_p),
         ("dense_kernel", c_int32),
+        ("lubrication", c_int32),
     ]
 
 

@@ -244,7 +244,8 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     h->al.ctx = cfg->alloc_ctx;
     h->r_near = r_near;
     h->rep_rc = rep_rc;
-    h->forces_const = (cfg->rep_eps == 0.0);
+    h->lub = cfg->lubrication != 0;
+    h->forces_const = (cfg->rep_eps == 0.0) && !h->lub;
 
     PairConst &pc = h->pc;
     pc.a = a;
@@ -281,6 +282,7 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
               dalloc_t(h, h->near_ent, h->near_cap) && dalloc_t(h, h->near_out, 6 * static_cast<size_t>(h->near_cap)) &&
               dalloc_t(h, h->near_n, 1) && dalloc_t(h, h->near_off, n3 / 3 + 1) && dalloc_t(h, h->near_cnt, n3 / 3 + 1);
     for (int b = 0; b < 2 && ok; ++b) ok = dalloc_t(h, h->x64[b], n3);
+    if (ok && h->lub) ok = dalloc_t(h, h->vlag, n3);
     ok = ok && dalloc_t(h, h->fext64, n3) && dalloc_t(h, h->F64, n3) && dalloc_t(h, h->Fa64, n3) &&
          dalloc_t(h, h->Wa64, n3);
     const bool soa = h->mode != MODE_FP64;
@@ -297,7 +299,7 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
 
     // cell list
     CellList &c = h->cl;
-    c.h = std::max(r_near, h->forces_const ? 0.0 : rep_rc);
+    c.h = std::max(r_near, std::max(cfg->rep_eps != 0.0 ? rep_rc : 0.0, h->lub ? 3.0 * a : 0.0));
     c.inv_h = 1.0 / c.h;
     int H = 1024;
     while (H < 2 * h->n) H <<= 1;
@@ -335,6 +337,7 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
         if (e == cudaSuccess && m->soa) e = cudaMemsetAsync(m->soa, 0, 3 * np * sizeof(float), st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fext64, 0, n3 * sizeof(double), st);
+    if (e == cudaSuccess && h->vlag) e = cudaMemsetAsync(h->vlag, 0, n3 * sizeof(double), st);
     if (e == cudaSuccess) e = launch_pad_mirror(h, st, h->posm);
     if (e == cudaSuccess) e = launch_stage_forces(h, st, nullptr, SD_DTYPE_F64, 1, h->F64, h->frcm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -357,7 +360,7 @@ void sd_destroy(sd_handle *h) {
     void *bufs[] = {h->fext64, h->F64, h->Fa64, h->Wa64, h->part, h->part2, h->jpart,
                     h->cl.cell, h->cl.key, h->cl.cnt, h->cl.fill, h->cl.start, h->cl.bsum, h->cl.sorted,
                     h->ckpt, h->seg, h->lam, h->gFacc, h->near64, h->d_flag, h->d_err,
-                    h->near_ent, h->near_out, h->near_n, h->near_off, h->near_cnt};
+                    h->near_ent, h->near_out, h->near_n, h->near_off, h->near_cnt, h->vlag};
     for (void *p : bufs) dfree(h, p);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
@@ -376,6 +379,8 @@ sd_status sd_set_positions(sd_handle *h, const double *xyz, int on_device) {
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
         sd_status s = launch_check(launch_stage_pos(h, h->stream, h->x64[h->cur], h->posm), "stage positions");
         if (s != SD_OK) return s;
+        // new positions: the previous step's velocities no longer apply (lubrication)
+        if (h->vlag) SD_CUDA(cudaMemsetAsync(h->vlag, 0, 3 * sizeof(double) * h->n, h->stream));
     }
     h->pos_set = true;
     h->cells_valid = false;
@@ -554,7 +559,8 @@ sd_status sd_adjoint(sd_handle *h, double dt, int64_t nsteps, int32_t ckpt_every
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (nsteps < 0 || ckpt_every < 1 || !std::isfinite(dt)) return set_error(SD_ERR_ARG, "nsteps, ckpt_every or dt");
     if (h->n > 0 && (!gxT || !gx0 || !gF)) return set_error(SD_ERR_ARG, "null argument");
-    if (!h->forces_const) return set_error(SD_ERR_UNSUPPORTED, "adjoint with soft repulsion is not implemented");
+    if (!h->forces_const)
+        return set_error(SD_ERR_UNSUPPORTED, "adjoint with soft repulsion or lubrication is not implemented");
     if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
     if (h->n == 0) return SD_OK;
     cudaSetDevice(h->device);

@@ -718,6 +718,7 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
     }
     if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
         return set_error(SD_ERR_ARG, "alloc and free callbacks must be given together");
+    if (cfg->lubrication != 0) return set_error(SD_ERR_UNSUPPORTED, "lubrication is not implemented for batches");
     if (nclusters > 0 && offsets[0] != 0) return set_error(SD_ERR_ARG, "offsets[0] must be 0");
     int maxn = 0;
     for (int c = 0; c < nclusters; ++c) {

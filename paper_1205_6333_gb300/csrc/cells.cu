@@ -285,16 +285,25 @@ cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64,
 // ---------------------------------------------------------------- forces (Sec. 3.1, step 2)
 
 // F_i = F_ext,i + g + sum_{j: r_ij < r_c} 12 eps (2a)^12 r^-14 (r_i - r_j)
-// (U = eps (2a/r)^12, truncated at r_c, F = -grad U), in FP64; writes F64 and its mirror.
+// (U = eps (2a/r)^12, truncated at r_c, F = -grad U; Sec. 3.1 step 2), and with
+// lubrication (vlag != nullptr) the singular friction of Sec. 2.3 Eq. lubrication,
+//   F_i -= (1/mu0) sum_{j: 0 < s < 1} [(1/(4s) - (9/40) ln s) e e^T - (1/6) ln s (I - e e^T)] (v_i - v_j),
+// s = r/a - 2, e = r_ij / r, with the previous step's velocities vlag (Sec. 3.1:
+// the forces are corrected for lubrication before the velocity update).  FP64;
+// writes F64 and its mirror.
 template <typename V4>
 __global__ void forces_rep_kernel(const double *__restrict__ x, const double *__restrict__ fext, double gx, double gy,
-                                  double gz, double eps, double rc, double s12, CellList c, int n, int npad,
-                                  double *__restrict__ F, V4 *__restrict__ m, float *__restrict__ soa, int *err) {
+                                  double gz, double eps, double rc, double s12, const double *__restrict__ vlag,
+                                  double inv_a, double inv_mu0, CellList c, int n, int npad, double *__restrict__ F,
+                                  V4 *__restrict__ m, float *__restrict__ soa, int *err) {
     // kWalkLanes threads per particle, partial sums meet in a fixed shuffle tree
     const long long gt = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int i = static_cast<int>(gt / kWalkLanes), sub = static_cast<int>(gt % kWalkLanes);
     const bool active = i < n;
-    const double rc2 = rc * rc;
+    const bool rep = eps != 0.0, lub = vlag != nullptr;
+    const double rc2 = rep ? rc * rc : 0.0;
+    const double rl2 = lub ? 9.0 / (inv_a * inv_a) : 0.0;   // (3a)^2
+    const double rmax2 = rc2 > rl2 ? rc2 : rl2;
     double f[3] = {0.0, 0.0, 0.0};
     bool coincident = false, found = false;
     if (active) {
@@ -302,19 +311,37 @@ __global__ void forces_rep_kernel(const double *__restrict__ x, const double *__
         for_each_neighbour_part(c, i, c.cell[i], sub, kWalkLanes, [&](int j) {
             const double dx = xi - x[3 * j], dy = yi - x[3 * j + 1], dz = zi - x[3 * j + 2];
             const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 >= rc2) return;
+            if (r2 >= rmax2) return;
             found = true;
             if (r2 == 0.0) {
-                coincident = true;
+                if (rep) coincident = true;   // s = -2: no lubrication term
                 return;
             }
             const double ri = rsqrt_nr64(r2);   // no FP64 division (scarce FP64 throughput)
-            const double ir2 = ri * ri;
-            const double ir6 = ir2 * ir2 * ir2;
-            const double coef = 12.0 * eps * s12 * ir6 * ir6 * ir2;
-            f[0] += coef * dx;
-            f[1] += coef * dy;
-            f[2] += coef * dz;
+            if (r2 < rc2) {
+                const double ir2 = ri * ri;
+                const double ir6 = ir2 * ir2 * ir2;
+                const double coef = 12.0 * eps * s12 * ir6 * ir6 * ir2;
+                f[0] += coef * dx;
+                f[1] += coef * dy;
+                f[2] += coef * dz;
+            }
+            if (lub) {
+                const double sg = r2 * ri * inv_a - 2.0;
+                if (sg > 0.0 && sg < 1.0) {
+                    const double ls = log(sg);
+                    const double zn = 0.25 / sg - 0.225 * ls, zt = -ls / 6.0;
+                    const double ex = dx * ri, ey = dy * ri, ez = dz * ri;
+                    const double wx = vlag[3 * i] - vlag[3 * j], wy = vlag[3 * i + 1] - vlag[3 * j + 1],
+                                 wz = vlag[3 * i + 2] - vlag[3 * j + 2];
+                    const double en = ex * wx + ey * wy + ez * wz;
+                    // zeta w = zn (e.w) e + zt (w - (e.w) e)
+                    const double kn = (zn - zt) * en;
+                    f[0] -= inv_mu0 * (kn * ex + zt * wx);
+                    f[1] -= inv_mu0 * (kn * ey + zt * wy);
+                    f[2] -= inv_mu0 * (kn * ez + zt * wz);
+                }
+            }
         });
     }
     const int writer = walk_combine(f, found, sub);
@@ -335,13 +362,15 @@ cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64) 
     const double *g = h->cfg.gravity;
     const double s12 = pow(2.0 * h->cfg.a, 12.0);
     prof_begin(h, SD_KERNEL_FORCES, st);
+    const double *vlag = h->lub ? h->vlag : nullptr;
+    const double inv_a = 1.0 / h->pc.a, inv_mu0 = 1.0 / h->pc.mu0;
     if (h->mode == MODE_FP64)
         forces_rep_kernel<dbl4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, h->rep_rc, s12,
-                                                    h->cl, h->n, h->npad, h->F64, static_cast<dbl4 *>(h->frcm.aos),
-                                                    h->frcm.soa, h->d_err);
+                                                    vlag, inv_a, inv_mu0, h->cl, h->n, h->npad, h->F64,
+                                                    static_cast<dbl4 *>(h->frcm.aos), h->frcm.soa, h->d_err);
     else
         forces_rep_kernel<float4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, h->rep_rc,
-                                                      s12, h->cl, h->n, h->npad, h->F64,
+                                                      s12, vlag, inv_a, inv_mu0, h->cl, h->n, h->npad, h->F64,
                                                       static_cast<float4 *>(h->frcm.aos), h->frcm.soa, h->d_err);
     prof_end(h, SD_KERNEL_FORCES, st);
     ++h->launches;

@@ -337,6 +337,7 @@ struct EpiArgs {
     void *vout;
     double dt;
     double *x64n;
+    double *vlag;   // OUT_EULER with lubrication: this step's FP64 velocities, for the next step's forces
     int *err;
 };
 
@@ -462,6 +463,11 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
     } else {
         const double xi = a.x64[3 * i], yi = a.x64[3 * i + 1], zi = a.x64[3 * i + 2];
         const double nx = xi + a.dt * v0, ny = yi + a.dt * v1, nz = zi + a.dt * v2;
+        if (a.vlag) {
+            a.vlag[3 * i] = v0;
+            a.vlag[3 * i + 1] = v1;
+            a.vlag[3 * i + 2] = v2;
+        }
         if (!isfinite(nx) || !isfinite(ny) || !isfinite(nz)) atomicOr(a.err, DEV_ERR_NONFINITE);
         a.x64n[3 * i] = nx;
         a.x64n[3 * i + 1] = ny;
@@ -509,6 +515,7 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
     a.vout = vout;
     a.dt = dt;
     a.x64n = x64n;
+    a.vlag = (out == OUT_EULER && h->lub) ? h->vlag : nullptr;
     a.err = h->d_err;
     const int nb = (h->n + 31) / 32;
     prof_begin(h, SD_KERNEL_EPILOGUE, st);

@@ -147,7 +147,9 @@ struct sd_handle {
     double *fext64 = nullptr;   // [n*3] per-particle external forces
     double *F64 = nullptr;      // [n*3] total force of the current step
     sd::Mirror frcm;            // mirror of F64
-    bool forces_const = true;   // no repulsion: F64 depends on nothing that changes
+    bool forces_const = true;   // no repulsion, no lubrication: F64 depends on nothing that changes
+    bool lub = false;           // lubrication friction (Sec. 2.3) in the forces of sd_step
+    double *vlag = nullptr;     // [n*3] velocities of the previous step (lubrication), zeroed by set_positions
 
     // apply / vjp scratch
     double *Fa64 = nullptr;  sd::Mirror frcam;
