@@ -518,6 +518,60 @@ def leg_drift(args):
     return {"drift": out}
 
 
+def leg_lubrication(args):
+    """Lubrication (Sec. 2.3, lagged velocities of Sec. 3.1): N = 32^3 = 32,768 spheres on
+    a jittered simple-cubic lattice of spacing 2.9a (phi = 0.17, every nearest-neighbour
+    gap inside the friction window), forces N(0,1), dt = 0.02, 40 steps (the lagged
+    friction is stable there; under gravity the cluster's collective shear closes gaps
+    until it is not).  FP32C steps/s with and without the friction, the FP64
+    neighbour-pass time per step, and the FP32C-vs-FP64 trajectory difference."""
+    import torch
+    import paper_1205_6333_gb300 as sd
+    from paper_1205_6333_gb300 import inputs
+    m, spacing, steps = 32, 2.9, 40
+    rng = np.random.default_rng(inputs.SEED_BASE + 70)
+    g = np.arange(m) * spacing
+    x0 = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    x0 = x0 + rng.uniform(-0.05, 0.05, x0.shape)
+    n = x0.shape[0]
+    fe = inputs.normal_forces(n, inputs.SEED_BASE + 71)
+    stream = torch.cuda.current_stream()
+    out = {"n": n, "lattice_spacing_a": spacing, "dt": 0.02}
+    pos = {}
+    for lub in (False, True):
+        for prec in ("fp32c", "fp64"):
+            s = sd.System(n, prec=prec, lubrication=lub, stream="torch", torch_allocator=True)
+            s.set_positions(x0)
+            s.set_forces(fe)
+            if prec == "fp32c":
+                s.step(0.02, 3)
+                s.set_positions(x0)
+                s.profile(True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.step(0.02, steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                fms, fcnt = s.profile_read(sd.SD_KERNEL_FORCES)
+                s.profile(False)
+                key = "lub" if lub else "plain"
+                out["steps_per_s_" + key] = 1e3 / ms
+                out["forces_ms_per_step_" + key] = fms / steps
+            else:
+                s.step(0.02, steps)
+            pos[(lub, prec)] = s.get_positions()
+            s.close()
+    a, b = pos[(True, "fp32c")], pos[(True, "fp64")]
+    disp = np.linalg.norm(b - x0, axis=1).max()
+    out["steps"] = steps
+    out["fp32c_vs_fp64_rel_to_displacement"] = float(np.linalg.norm(a - b, axis=1).max() / disp)
+    out["lub_effect_rel_to_displacement"] = float(np.linalg.norm(pos[(False, "fp64")] - b, axis=1).max() / disp)
+    print(json.dumps(out), file=sys.stderr, flush=True)
+    return {"lubrication": out}
+
+
 def leg_adjoint(args, n_fd=16):
     """Workload 5: N = 4,096, phi = 0.05, gravity, dt = 0.01, 1000 Euler steps,
     L = sum |x_i(T) - x_i*|^2, checkpoints every 50 steps.  Central finite differences
@@ -625,7 +679,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="main leg only")
     ap.add_argument("--leg", default="all", choices=["all", "main", "fp64", "batched", "oseen", "sweep", "drift",
-                                                     "adjoint"],
+                                                     "adjoint", "lubrication"],
                     help="run one leg alone and print its numbers (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
@@ -641,6 +695,8 @@ def main():
         print(json.dumps(leg_drift(args)), flush=True)
     elif args.leg == "adjoint":
         print(json.dumps(leg_adjoint(args)), flush=True)
+    elif args.leg == "lubrication":
+        print(json.dumps(leg_lubrication(args)), flush=True)
     else:
         if args.leg == "main":
             args.quick = True
