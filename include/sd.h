@@ -85,9 +85,12 @@ typedef struct sd_config {
     double eta;              /* viscosity, > 0                                              */
     int32_t tensor;          /* sd_tensor                                                   */
     int32_t prec;            /* sd_precision                                                */
-    double box[3];           /* 0 = unbounded (default); > 0 = periodic, nearest image only
-                                (Sec. 3.1 footnote).  This build returns SD_ERR_UNSUPPORTED
-                                for a periodic box.                                         */
+    double box[3];           /* per dimension: 0 = unbounded (default); L > 0 = periodic with
+                                side L, each pair interacting through its nearest image only
+                                (Sec. 3.1 footnote).  L must be >= 3 max(r_near, rep_rc when
+                                rep_eps != 0, 3a with lubrication) (SD_ERR_ARG).  Positions
+                                are integrated unwrapped; sd_get_positions returns them so.
+                                Batches return SD_ERR_UNSUPPORTED for a periodic box.        */
     double r_near;           /* pairs closer than r_near get their term in FP64; 0 = 2.5a;
                                 must be >= 2.2a                                             */
     double rep_eps;          /* soft repulsion U = rep_eps (2a/r)^12 for r < rep_rc; 0 = off */

@@ -203,9 +203,12 @@ def _torch_allocator(device: int):
 
 def _make_config(n=0, a=1.0, eta=1.0, tensor="rpy", prec="fp32c", r_near=None, rep_eps=0.0, rep_rc=None,
                  gravity=(0.0, 0.0, 0.0), device=0, stream=None, torch_allocator=False, dense="auto",
-                 lubrication=False):
+                 lubrication=False, box=None):
     cfg = sd_config_init()
     cfg.lubrication = int(bool(lubrication))
+    if box is not None:
+        for d in range(3):
+            cfg.box[d] = float(box[d])
     cfg.dense_kernel = DENSE_KERNELS[dense] if isinstance(dense, str) else int(dense)
     cfg.n = int(n)
     cfg.a = float(a)
@@ -240,9 +243,9 @@ class System:
 
     def __init__(self, n, a=1.0, eta=1.0, tensor="rpy", prec="fp32c", r_near=None, rep_eps=0.0, rep_rc=None,
                  gravity=(0.0, 0.0, 0.0), device=0, stream=None, torch_allocator=False, dense="auto",
-                 lubrication=False):
+                 lubrication=False, box=None):
         self.cfg, self._keep = _make_config(n, a, eta, tensor, prec, r_near, rep_eps, rep_rc, gravity, device,
-                                            stream, torch_allocator, dense, lubrication)
+                                            stream, torch_allocator, dense, lubrication, box)
         self.n = int(n)
         self.h = sd_create(self.cfg)
 

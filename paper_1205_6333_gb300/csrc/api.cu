@@ -206,8 +206,6 @@ static sd_status validate_common(const sd_config *cfg) {
     if (cfg->prec < 0 || cfg->prec > 2) return set_error(SD_ERR_ARG, "unknown precision");
     for (int d = 0; d < 3; ++d) {
         if (cfg->box[d] < 0.0 || !std::isfinite(cfg->box[d])) return set_error(SD_ERR_ARG, "box must be >= 0");
-        if (cfg->box[d] > 0.0)
-            return set_error(SD_ERR_UNSUPPORTED, "periodic boxes (nearest image) are not implemented in this build");
         if (!std::isfinite(cfg->gravity[d])) return set_error(SD_ERR_ARG, "gravity must be finite");
     }
     if (cfg->dense_kernel < 0 || cfg->dense_kernel > 2) return set_error(SD_ERR_ARG, "unknown dense kernel");
@@ -229,6 +227,13 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     if (!(r_near >= 2.2 * a) || !std::isfinite(r_near)) return set_error(SD_ERR_ARG, "r_near must be >= 2.2 a");
     const double rep_rc = cfg->rep_rc > 0.0 ? cfg->rep_rc : 2.5 * a;
     if (!std::isfinite(cfg->rep_eps) || !std::isfinite(rep_rc)) return set_error(SD_ERR_ARG, "repulsion parameters");
+    // cell side: every FP64 neighbour pass (near pairs, repulsion, lubrication) within one cell
+    const double cell_h = std::max(r_near, std::max(cfg->rep_eps != 0.0 ? rep_rc : 0.0,
+                                                    cfg->lubrication != 0 ? 3.0 * a : 0.0));
+    for (int d = 0; d < 3; ++d)
+        if (cfg->box[d] > 0.0 && cfg->box[d] < 3.0 * cell_h)
+            return set_error(SD_ERR_ARG, "a periodic box side must be at least 3 max(r_near, rep_rc, 3a if "
+                                         "lubrication)");
 
     sd_handle *h = new (std::nothrow) sd_handle();
     if (!h) return set_error(SD_ERR_OOM, "host allocation");
@@ -259,6 +264,16 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     pc.c1_f = static_cast<float>(pc.c1_d);
     pc.c3_f = static_cast<float>(pc.c3_d);
     pc.m3c3_f = static_cast<float>(pc.m3c3_d);
+    // periodic box, nearest image only (Sec. 3.1 footnote)
+    pc.periodic = 0;
+    for (int d = 0; d < 3; ++d) {
+        const double L = cfg->box[d];
+        pc.Ld[d] = L;
+        pc.invLd[d] = L > 0.0 ? 1.0 / L : 0.0;
+        pc.Lf[d] = static_cast<float>(pc.Ld[d]);
+        pc.invLf[d] = static_cast<float>(pc.invLd[d]);
+        if (L > 0.0) pc.periodic = 1;
+    }
 
     auto fail = [&](sd_status st, const std::string &m) {
         sd_destroy(h);
@@ -299,8 +314,14 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
 
     // cell list
     CellList &c = h->cl;
-    c.h = std::max(r_near, std::max(cfg->rep_eps != 0.0 ? rep_rc : 0.0, h->lub ? 3.0 * a : 0.0));
+    c.h = cell_h;
     c.inv_h = 1.0 / c.h;
+    for (int d = 0; d < 3; ++d) {
+        c.box.L[d] = pc.Ld[d];
+        c.box.invL[d] = pc.invLd[d];
+        c.nc[d] = pc.Ld[d] > 0.0 ? static_cast<int>(std::floor(pc.Ld[d] / c.h)) : 0;   // >= 3, checked above
+    }
+    c.box.periodic = pc.periodic;
     int H = 1024;
     while (H < 2 * h->n) H <<= 1;
     c.H = H;

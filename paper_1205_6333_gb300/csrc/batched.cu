@@ -258,7 +258,7 @@ __device__ __forceinline__ void cluster_packed(const BatchArgs &a, int o, int n,
                                                int *s_ovl, int lane) {
     constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
     constexpr int R = 2 * RP;   // target slots per lane, i = lane + 32 k
-    PairConst2 c2;
+    PairConst2 c2{};
     c2.c1 = pk2(a.pc.c1_f, a.pc.c1_f);
     c2.c3 = pk2(a.pc.c3_f, a.pc.c3_f);
     c2.m3c3 = pk2(a.pc.m3c3_f, a.pc.m3c3_f);

@@ -31,16 +31,29 @@ __device__ __forceinline__ void put_mirror(V4 *aos, float *soa, int npad, int i,
     }
 }
 
+// u wrapped into [0, L) in a periodic dimension (L > 0), unchanged otherwise.
+__device__ __forceinline__ double wrap_box(double u, double L, double invL) {
+    return L > 0.0 ? u - L * floor(u * invL) : u;
+}
+
+// Mirror entry of a position: relative to particle 0 (only differences enter the
+// pair terms, and small coordinates keep FP32 separations accurate), wrapped into
+// the box in periodic dimensions (the pair terms take the nearest image).
+template <typename V4>
+__device__ __forceinline__ void put_pos_mirror(V4 *m, float *soa, int npad, int i, const double *x, const Box &b) {
+    const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+    put_mirror(m, soa, npad, i, wrap_box(px - x[0], b.L[0], b.invL[0]), wrap_box(py - x[1], b.L[1], b.invL[1]),
+               wrap_box(pz - x[2], b.L[2], b.invL[2]));
+}
+
 template <typename V4>
 __global__ void stage_pos_kernel(const double *__restrict__ x, V4 *__restrict__ m, float *__restrict__ soa, int n,
-                                 int npad, int *err) {
+                                 int npad, Box b, int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
     if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicOr(err, DEV_ERR_NONFINITE);
-    // mirror relative to particle 0: only differences enter the pair terms, and
-    // small coordinates keep FP32 separations accurate
-    put_mirror(m, soa, npad, i, px - x[0], py - x[1], pz - x[2]);
+    put_pos_mirror(m, soa, npad, i, x, b);
 }
 
 cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm) {
@@ -48,10 +61,10 @@ cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, M
     const int nb = (h->n + 255) / 256;
     if (h->mode == MODE_FP64)
         stage_pos_kernel<dbl4><<<nb, 256, 0, st>>>(x64, static_cast<dbl4 *>(posm.aos), posm.soa, h->n, h->npad,
-                                                   h->d_err);
+                                                   h->cl.box, h->d_err);
     else
         stage_pos_kernel<float4><<<nb, 256, 0, st>>>(x64, static_cast<float4 *>(posm.aos), posm.soa, h->n, h->npad,
-                                                     h->d_err);
+                                                     h->cl.box, h->d_err);
     ++h->launches;
     return cudaGetLastError();
 }
@@ -134,21 +147,31 @@ __device__ __forceinline__ int cell_coord(double x, double inv_h) {
     return static_cast<int>(c);
 }
 
+// Cell coordinate in dimension d: nc[d] cells over [0, L) of the wrapped coordinate
+// in a periodic dimension, cells of side h otherwise.
+__device__ __forceinline__ int cell_coord_d(const CellList &c, int d, double x) {
+    const int nc = c.nc[d];
+    if (nc <= 0) return cell_coord(x, c.inv_h);
+    const int k = static_cast<int>(floor(wrap_box(x, c.box.L[d], c.box.invL[d]) * c.box.invL[d] * nc));
+    return k < 0 ? 0 : (k >= nc ? nc - 1 : k);
+}
+
 // Bins particle i and writes its mirror (position relative to particle 0, in the
 // dense kernels' precision), so the mirror is a pure function of the FP64 state.
 template <typename V4>
-__global__ void cells_hash_kernel(const double *__restrict__ x, int n, double inv_h, int H, int4 *__restrict__ cell,
+__global__ void cells_hash_kernel(const double *__restrict__ x, int n, CellList c, int4 *__restrict__ cell,
                                   uint32_t *__restrict__ key, int *__restrict__ cnt, V4 *__restrict__ m,
                                   float *__restrict__ soa, int npad, int *flag, int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (i == 0) *flag = 0;   // the near pass of these positions raises it again if needed
+    const int H = c.H;
     const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
     if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicOr(err, DEV_ERR_NONFINITE);
-    put_mirror(m, soa, npad, i, px - x[0], py - x[1], pz - x[2]);
-    const int cx = cell_coord(px, inv_h);
-    const int cy = cell_coord(py, inv_h);
-    const int cz = cell_coord(pz, inv_h);
+    put_pos_mirror(m, soa, npad, i, x, c.box);
+    const int cx = cell_coord_d(c, 0, px);
+    const int cy = cell_coord_d(c, 1, py);
+    const int cz = cell_coord_d(c, 2, pz);
     cell[i] = make_int4(cx, cy, cz, 0);
     const uint32_t k = cell_hash(cx, cy, cz, H);
     key[i] = k;
@@ -265,11 +288,11 @@ cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64,
     if (e != cudaSuccess) return e;
     const int nb = (h->n + 255) / 256;
     if (h->mode == MODE_FP64)
-        cells_hash_kernel<dbl4><<<nb, 256, 0, st>>>(x64, h->n, c.inv_h, c.H, c.cell, c.key, c.cnt,
+        cells_hash_kernel<dbl4><<<nb, 256, 0, st>>>(x64, h->n, c, c.cell, c.key, c.cnt,
                                                     static_cast<dbl4 *>(posm.aos), posm.soa, h->npad, h->d_flag,
                                                     h->d_err);
     else
-        cells_hash_kernel<float4><<<nb, 256, 0, st>>>(x64, h->n, c.inv_h, c.H, c.cell, c.key, c.cnt,
+        cells_hash_kernel<float4><<<nb, 256, 0, st>>>(x64, h->n, c, c.cell, c.key, c.cnt,
                                                       static_cast<float4 *>(posm.aos), posm.soa, h->npad,
                                                       h->d_flag, h->d_err);
     scan_blocks_kernel<<<c.nblk, kScanThreads, 0, st>>>(c.cnt, c.start, c.bsum, c.H);
@@ -309,7 +332,8 @@ __global__ void forces_rep_kernel(const double *__restrict__ x, const double *__
     if (active) {
         const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
         for_each_neighbour_part(c, i, c.cell[i], sub, kWalkLanes, [&](int j) {
-            const double dx = xi - x[3 * j], dy = yi - x[3 * j + 1], dz = zi - x[3 * j + 2];
+            double dx = xi - x[3 * j], dy = yi - x[3 * j + 1], dz = zi - x[3 * j + 2];
+            box_image(c.box, dx, dy, dz);
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= rmax2) return;
             found = true;

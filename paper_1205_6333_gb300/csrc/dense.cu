@@ -41,19 +41,19 @@ struct DenseT<MODE_FP64> {
     static constexpr int R = kR64;
 };
 
-template <int TENSOR, int MODE>
+template <int TENSOR, int MODE, bool PER>
 __device__ __forceinline__ void dense_pair(typename DenseT<MODE>::S xi, typename DenseT<MODE>::S yi,
                                            typename DenseT<MODE>::S zi, const typename DenseT<MODE>::V4 &p,
                                            const typename DenseT<MODE>::V4 &f, const PairConst &c,
                                            typename DenseT<MODE>::S &ax, typename DenseT<MODE>::S &ay,
                                            typename DenseT<MODE>::S &az) {
     if constexpr (MODE == MODE_FP64)
-        pair_f64<TENSOR>(xi, yi, zi, p, f, c, ax, ay, az);
+        pair_f64<TENSOR, PER>(xi, yi, zi, p, f, c, ax, ay, az);
     else
-        pair_f32<TENSOR>(xi, yi, zi, p, f, c, ax, ay, az);
+        pair_f32<TENSOR, true, PER>(xi, yi, zi, p, f, c, ax, ay, az);
 }
 
-template <int TENSOR, int MODE>
+template <int TENSOR, int MODE, bool PER>
 __global__ void __launch_bounds__(kNT) dense_kernel(const typename DenseT<MODE>::V4 *__restrict__ pos,
                                                     const typename DenseT<MODE>::V4 *__restrict__ frc,
                                                     double *__restrict__ part, int npad, DenseGeom g, PairConst c,
@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(kNT) dense_kernel(const typename DenseT<MODE>:
             const V4 p = P[jj];
             const V4 f = Fq[jj];
 #pragma unroll
-            for (int k = 0; k < R; ++k) dense_pair<TENSOR, MODE>(xi[k], yi[k], zi[k], p, f, c, ax[k], ay[k], az[k]);
+            for (int k = 0; k < R; ++k)
+                dense_pair<TENSOR, MODE, PER>(xi[k], yi[k], zi[k], p, f, c, ax[k], ay[k], az[k]);
         }
         if constexpr (MODE == MODE_FP32C) {
 #pragma unroll
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(kNT) dense_kernel(const typename DenseT<MODE>:
 // plain FP32 running sum per lane instead (ablation).
 // One staged j-tile against the thread's R targets: 4 j's (two packed pairs) per
 // step, six 128-bit shared loads per step.
-template <int TENSOR, bool CLAMP, int R>
+template <int TENSOR, bool CLAMP, int R, bool PER>
 __device__ __forceinline__ void tile_pairs(uint32_t base, uint32_t astride, int J, const f2 (&XI)[R],
                                            const f2 (&YI)[R], const f2 (&ZI)[R], const PairConst2 &c, f2 (&AX)[R],
                                            f2 (&AY)[R], f2 (&AZ)[R]) {
@@ -211,12 +212,12 @@ __device__ __forceinline__ void tile_pairs(uint32_t base, uint32_t astride, int 
         for (int h2 = 0; h2 < 2; ++h2)
 #pragma unroll
             for (int k = 0; k < R; ++k)
-                pair_f32x2<TENSOR, CLAMP>(XI[k], YI[k], ZI[k], P[0][h2], P[1][h2], P[2][h2], P[3][h2], P[4][h2],
-                                          P[5][h2], c, AX[k], AY[k], AZ[k]);
+                pair_f32x2<TENSOR, CLAMP, PER>(XI[k], YI[k], ZI[k], P[0][h2], P[1][h2], P[2][h2], P[3][h2],
+                                               P[4][h2], P[5][h2], c, AX[k], AY[k], AZ[k]);
     }
 }
 
-template <int TENSOR, bool COMP>
+template <int TENSOR, bool COMP, bool PER>
 __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ pos, const float *__restrict__ frc,
                                                      double *__restrict__ part, int npad, DenseGeom g, PairConst2 c,
                                                      const int *__restrict__ flag, int *__restrict__ err,
@@ -317,9 +318,9 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
         const long long i0 = static_cast<long long>(ib) * g.I, j0 = (t % g.nJT) * static_cast<long long>(g.J);
         const bool diag = (j0 < i0 + g.I) && (i0 < j0 + g.J);
         if (clamp_all || diag)
-            tile_pairs<TENSOR, true, R>(base, astride, g.J, XI, YI, ZI, c, AX, AY, AZ);
+            tile_pairs<TENSOR, true, R, PER>(base, astride, g.J, XI, YI, ZI, c, AX, AY, AZ);
         else
-            tile_pairs<TENSOR, false, R>(base, astride, g.J, XI, YI, ZI, c, AX, AY, AZ);
+            tile_pairs<TENSOR, false, R, PER>(base, astride, g.J, XI, YI, ZI, c, AX, AY, AZ);
         if constexpr (COMP) {
 #pragma unroll
             for (int k = 0; k < R; ++k) {
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
 #endif
 constexpr int kSymUnroll = SD_SYM_UNROLL;
 
-template <int TENSOR, bool CLAMP>
+template <int TENSOR, bool CLAMP, bool PER>
 __device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, const f2 (&XI)[2], const f2 (&YI)[2],
                                          const f2 (&ZI)[2], const f2 (&GX)[2], const f2 (&GY)[2], const f2 (&GZ)[2],
                                          const PairConst2 &c, f2 (&AX)[2], f2 (&AY)[2], f2 (&AZ)[2],
@@ -407,8 +408,8 @@ __device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, co
             const f2 FX = gp[3 * S + p], FY = gp[4 * S + p], FZ = gp[5 * S + p];
 #pragma unroll
             for (int k = 0; k < 2; ++k)
-                pair_sym_f32x2<TENSOR, CLAMP>(XI[k], YI[k], ZI[k], GX[k], GY[k], GZ[k], PX, PY, PZ, FX, FY, FZ, c,
-                                              AX[k], AY[k], AZ[k], JX, JY, JZ);
+                pair_sym_f32x2<TENSOR, CLAMP, PER>(XI[k], YI[k], ZI[k], GX[k], GY[k], GZ[k], PX, PY, PZ, FX, FY,
+                                                   FZ, c, AX[k], AY[k], AZ[k], JX, JY, JZ);
             JX = __shfl_sync(0xffffffffu, JX, nxt);
             JY = __shfl_sync(0xffffffffu, JY, nxt);
             JZ = __shfl_sync(0xffffffffu, JZ, nxt);
@@ -421,7 +422,7 @@ __device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, co
     }
 }
 
-template <int TENSOR, bool COMP>
+template <int TENSOR, bool COMP, bool PER>
 __global__ void __launch_bounds__(kSymNT, SD_SYM_MINB) dense_sym_kernel(const float *__restrict__ pos,
                                                            const float *__restrict__ frc, double *__restrict__ part,
                                                            float *__restrict__ jpart, int npad, DenseGeom g,
@@ -538,14 +539,14 @@ __global__ void __launch_bounds__(kSymNT, SD_SYM_MINB) dense_sym_kernel(const fl
         const bool diag = ib == jb;
         if (diag) {
             const uint32_t base = smem_addr(s_tile + st * 6 * B);
-            tile_pairs<TENSOR, true, R>(base, B * sizeof(float), B, XI, YI, ZI, c, AX, AY, AZ);
+            tile_pairs<TENSOR, true, R, PER>(base, B * sizeof(float), B, XI, YI, ZI, c, AX, AY, AZ);
         } else {
             const f2 *sp = reinterpret_cast<const f2 *>(s_tile + st * 6 * B);
             float *jw = s_jacc + warp * 3 * B;
             if (clamp_all)
-                sym_tile<TENSOR, true>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
+                sym_tile<TENSOR, true, PER>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
             else
-                sym_tile<TENSOR, false>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
+                sym_tile<TENSOR, false, PER>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
         }
         if constexpr (COMP) {
 #pragma unroll
@@ -592,28 +593,36 @@ __global__ void __launch_bounds__(kSymNT, SD_SYM_MINB) dense_sym_kernel(const fl
 
 // ---------------------------------------------------------------- dispatch
 
-static void *pick_dense(int tensor, int mode) {
+template <bool PER>
+static void *pick_dense_t(int tensor, int mode) {
     const bool oseen = tensor == T_OSEEN;
     switch (mode) {
         case MODE_FP32C:
-            return oseen ? reinterpret_cast<void *>(&dense2_kernel<T_OSEEN, true>)
-                         : reinterpret_cast<void *>(&dense2_kernel<T_RP, true>);
+            return oseen ? reinterpret_cast<void *>(&dense2_kernel<T_OSEEN, true, PER>)
+                         : reinterpret_cast<void *>(&dense2_kernel<T_RP, true, PER>);
         case MODE_FP64:
-            return oseen ? reinterpret_cast<void *>(&dense_kernel<T_OSEEN, MODE_FP64>)
-                         : reinterpret_cast<void *>(&dense_kernel<T_RP, MODE_FP64>);
+            return oseen ? reinterpret_cast<void *>(&dense_kernel<T_OSEEN, MODE_FP64, PER>)
+                         : reinterpret_cast<void *>(&dense_kernel<T_RP, MODE_FP64, PER>);
         default:
-            return oseen ? reinterpret_cast<void *>(&dense2_kernel<T_OSEEN, false>)
-                         : reinterpret_cast<void *>(&dense2_kernel<T_RP, false>);
+            return oseen ? reinterpret_cast<void *>(&dense2_kernel<T_OSEEN, false, PER>)
+                         : reinterpret_cast<void *>(&dense2_kernel<T_RP, false, PER>);
     }
 }
+static void *pick_dense(int tensor, int mode, bool per) {
+    return per ? pick_dense_t<true>(tensor, mode) : pick_dense_t<false>(tensor, mode);
+}
 
-static void *pick_sym(int tensor, int mode) {
+template <bool PER>
+static void *pick_sym_t(int tensor, int mode) {
     const bool oseen = tensor == T_OSEEN, comp = mode == MODE_FP32C;
     if (oseen)
-        return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, true>)
-                    : reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, false>);
-    return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_RP, true>)
-                : reinterpret_cast<void *>(&dense_sym_kernel<T_RP, false>);
+        return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, true, PER>)
+                    : reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, false, PER>);
+    return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_RP, true, PER>)
+                : reinterpret_cast<void *>(&dense_sym_kernel<T_RP, false, PER>);
+}
+static void *pick_sym(int tensor, int mode, bool per) {
+    return per ? pick_sym_t<true>(tensor, mode) : pick_sym_t<false>(tensor, mode);
 }
 
 // Dynamic shared memory of the dense kernel of this mode for tile J.
@@ -637,7 +646,7 @@ cudaError_t dense_setup(sd_handle *h) {
     DenseGeom g{};
     g.I = kNT * R;
     g.nIB = h->npad / g.I;
-    void *fn = pick_dense(h->tensor, h->mode);
+    void *fn = pick_dense(h->tensor, h->mode, h->pc.periodic != 0);
     const int Jcand[3] = {kJmax, 128, 64};
     int occ = 0;
     for (int ci = 0; ci < 3; ++ci) {
@@ -669,7 +678,7 @@ cudaError_t dense_setup(sd_handle *h) {
     g.sym = 0;
     const int want_sym = h->cfg.dense_kernel;
     if (h->mode != MODE_FP64 && h->npad % kSymB == 0 && want_sym != SD_DENSE_DIRECTED) {
-        void *sfn = pick_sym(h->tensor, h->mode);
+        void *sfn = pick_sym(h->tensor, h->mode, h->pc.periodic != 0);
         cudaError_t e = cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(kSymSmem));
         if (e != cudaSuccess) return e;
@@ -698,50 +707,60 @@ cudaError_t dense_setup(sd_handle *h) {
     return cudaSuccess;
 }
 
-cudaError_t launch_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part) {
+template <bool PER>
+static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part) {
     const DenseGeom &g = h->geom;
     const size_t smem = dense_smem(h->mode, g.J);
     const bool oseen = h->tensor == T_OSEEN;
-    prof_begin(h, SD_KERNEL_DENSE, st);
     if (h->mode == MODE_FP64) {
         const dbl4 *p = static_cast<const dbl4 *>(posm.aos), *f = static_cast<const dbl4 *>(frcm.aos);
         if (oseen)
-            dense_kernel<T_OSEEN, MODE_FP64><<<g.grid, kNT, smem, st>>>(p, f, part, h->npad, g, h->pc, h->d_err,
-                                                                         h->watchdog);
+            dense_kernel<T_OSEEN, MODE_FP64, PER><<<g.grid, kNT, smem, st>>>(p, f, part, h->npad, g, h->pc,
+                                                                              h->d_err, h->watchdog);
         else
-            dense_kernel<T_RP, MODE_FP64><<<g.grid, kNT, smem, st>>>(p, f, part, h->npad, g, h->pc, h->d_err,
-                                                                      h->watchdog);
-    } else {
-        PairConst2 c2;
-        c2.c1 = pk2_host(h->pc.c1_f);
-        c2.c3 = pk2_host(h->pc.c3_f);
-        c2.m3c3 = pk2_host(h->pc.m3c3_f);
-        c2.r2min = h->pc.r2min_f;
-        const bool comp = h->mode == MODE_FP32C;
-        if (g.sym) {
-#define SD_DS(TT, CC)                                                                                      \
-    dense_sym_kernel<TT, CC><<<g.grid, kSymNT, kSymSmem, st>>>(posm.soa, frcm.soa, part, h->jpart, h->npad, g, c2, \
-                                                               h->d_flag, h->d_err, h->watchdog)
-            if (oseen) {
-                if (comp) SD_DS(T_OSEEN, true); else SD_DS(T_OSEEN, false);
-            } else {
-                if (comp) SD_DS(T_RP, true); else SD_DS(T_RP, false);
-            }
-#undef SD_DS
-            prof_end(h, SD_KERNEL_DENSE, st);
-            ++h->launches;
-            return cudaGetLastError();
-        }
-#define SD_D2(TT, CC) \
-    dense2_kernel<TT, CC><<<g.grid, kNT, smem, st>>>(posm.soa, frcm.soa, part, h->npad, g, c2, h->d_flag, h->d_err, \
-                                                     h->watchdog)
-        if (oseen) {
-            if (comp) SD_D2(T_OSEEN, true); else SD_D2(T_OSEEN, false);
-        } else {
-            if (comp) SD_D2(T_RP, true); else SD_D2(T_RP, false);
-        }
-#undef SD_D2
+            dense_kernel<T_RP, MODE_FP64, PER><<<g.grid, kNT, smem, st>>>(p, f, part, h->npad, g, h->pc, h->d_err,
+                                                                           h->watchdog);
+        return;
     }
+    PairConst2 c2{};
+    c2.c1 = pk2_host(h->pc.c1_f);
+    c2.c3 = pk2_host(h->pc.c3_f);
+    c2.m3c3 = pk2_host(h->pc.m3c3_f);
+    c2.r2min = h->pc.r2min_f;
+    for (int d = 0; d < 3; ++d) {
+        c2.negL[d] = pk2_host(-h->pc.Lf[d]);
+        c2.invL[d] = pk2_host(h->pc.invLf[d]);
+    }
+    const bool comp = h->mode == MODE_FP32C;
+    if (g.sym) {
+#define SD_DS(TT, CC)                                                                                          \
+    dense_sym_kernel<TT, CC, PER><<<g.grid, kSymNT, kSymSmem, st>>>(posm.soa, frcm.soa, part, h->jpart, h->npad, g, \
+                                                                    c2, h->d_flag, h->d_err, h->watchdog)
+        if (oseen) {
+            if (comp) SD_DS(T_OSEEN, true); else SD_DS(T_OSEEN, false);
+        } else {
+            if (comp) SD_DS(T_RP, true); else SD_DS(T_RP, false);
+        }
+#undef SD_DS
+        return;
+    }
+#define SD_D2(TT, CC)                                                                                          \
+    dense2_kernel<TT, CC, PER><<<g.grid, kNT, smem, st>>>(posm.soa, frcm.soa, part, h->npad, g, c2, h->d_flag, \
+                                                          h->d_err, h->watchdog)
+    if (oseen) {
+        if (comp) SD_D2(T_OSEEN, true); else SD_D2(T_OSEEN, false);
+    } else {
+        if (comp) SD_D2(T_RP, true); else SD_D2(T_RP, false);
+    }
+#undef SD_D2
+}
+
+cudaError_t launch_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part) {
+    prof_begin(h, SD_KERNEL_DENSE, st);
+    if (h->pc.periodic)
+        launch_dense_t<true>(h, st, posm, frcm, part);
+    else
+        launch_dense_t<false>(h, st, posm, frcm, part);
     prof_end(h, SD_KERNEL_DENSE, st);
     ++h->launches;
     return cudaGetLastError();

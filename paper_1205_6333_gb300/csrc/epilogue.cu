@@ -20,6 +20,7 @@
 // FP32 evaluation suffers from cancellation in r_i - r_j (large coordinates,
 // small separations) or that the clamp altered (r < 2a).
 #include <algorithm>
+#include <type_traits>
 #include "neighbours.cuh"
 
 namespace sd {
@@ -35,18 +36,47 @@ struct EpiT<MODE_FP64> {
     using S = double;
 };
 
-template <int TDENSE, int MODE, bool CLAMP>
+template <int TDENSE, int MODE, bool CLAMP, bool PER = false>
 __device__ __forceinline__ void dense_term(const typename EpiT<MODE>::V4 &pi, const typename EpiT<MODE>::V4 &pj,
                                            const typename EpiT<MODE>::V4 &fj, const PairConst &c, double out[3]) {
     using S = typename EpiT<MODE>::S;
     S ax = S(0), ay = S(0), az = S(0);
     if constexpr (MODE == MODE_FP64)
-        pair_f64<TDENSE>(pi.x, pi.y, pi.z, pj, fj, c, ax, ay, az);
+        pair_f64<TDENSE, PER>(pi.x, pi.y, pi.z, pj, fj, c, ax, ay, az);
     else
-        pair_f32<TDENSE, CLAMP>(pi.x, pi.y, pi.z, pj, fj, c, ax, ay, az);
+        pair_f32<TDENSE, CLAMP, PER>(pi.x, pi.y, pi.z, pj, fj, c, ax, ay, az);
     out[0] = static_cast<double>(ax);
     out[1] = static_cast<double>(ay);
     out[2] = static_cast<double>(az);
+}
+
+// The all-pairs kernels' term of the pair (i, j), nearest image in a periodic box.
+template <int TDENSE, int MODE, bool CLAMP>
+__device__ __forceinline__ void dense_term_box(const typename EpiT<MODE>::V4 &pi, const typename EpiT<MODE>::V4 &pj,
+                                               const typename EpiT<MODE>::V4 &fj, const PairConst &c,
+                                               double out[3]) {
+    if (c.periodic)
+        dense_term<TDENSE, MODE, CLAMP, true>(pi, pj, fj, c, out);
+    else
+        dense_term<TDENSE, MODE, CLAMP, false>(pi, pj, fj, c, out);
+}
+
+// Mirror separation (nearest image in a periodic box) rounded to FP32, for the
+// near pass's screen.
+template <typename V4>
+__device__ __forceinline__ float screen_r2(const V4 &pi, const V4 &pj, const PairConst &c) {
+    float s[3];
+    const double di[3] = {pi.x, pi.y, pi.z}, dj[3] = {pj.x, pj.y, pj.z};
+    for (int d = 0; d < 3; ++d) {
+        if constexpr (std::is_same<V4, float4>::value) {
+            const float u = __fsub_rn(static_cast<float>(di[d]), static_cast<float>(dj[d]));
+            s[d] = c.periodic ? min_image_f32(u, c.Lf[d], c.invLf[d]) : u;
+        } else {
+            const double u = di[d] - dj[d];
+            s[d] = static_cast<float>(c.periodic ? min_image_f64(u, c.Ld[d], c.invLd[d]) : u);
+        }
+    }
+    return s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
 }
 
 // ---------------------------------------------------------------- near pass
@@ -94,19 +124,24 @@ __device__ __forceinline__ void near_pair_term(const NearArgs &a, int i, int j, 
     const double e[3] = {A * fx + s * dx, A * fy + s * dy, A * fz + s * dz};
     const V4 pi = pm[i], pj = pm[j];
     double tc[3];
-    dense_term<TDENSE, MODE, true>(pi, pj, fm[j], a.pc, tc);
+    dense_term_box<TDENSE, MODE, true>(pi, pj, fm[j], a.pc, tc);
     for (int d = 0; d < 3; ++d) c6[d] += e[d] - tc[d];
     // The unclamped variant differs only where the clamp was active, i.e. the
     // pair's FP32 r^2 < (2a)^2, and outside the tiles holding self pairs (clamped
     // in both variants); c6[3..5] collects that difference.
     if constexpr (MODE != MODE_FP64) {
-        const float ux = __fsub_rn(pi.x, pj.x), uy = __fsub_rn(pi.y, pj.y), uz = __fsub_rn(pi.z, pj.z);
+        float ux = __fsub_rn(pi.x, pj.x), uy = __fsub_rn(pi.y, pj.y), uz = __fsub_rn(pi.z, pj.z);
+        if (a.pc.periodic) {
+            ux = min_image_f32(ux, a.pc.Lf[0], a.pc.invLf[0]);
+            uy = min_image_f32(uy, a.pc.Lf[1], a.pc.invLf[1]);
+            uz = min_image_f32(uz, a.pc.Lf[2], a.pc.invLf[2]);
+        }
         const float r2f = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
         const long long i0 = static_cast<long long>(i / a.I) * a.I, j0 = static_cast<long long>(j / a.J) * a.J;
         const bool diag = (j0 < i0 + a.I) && (i0 < j0 + a.J);
         if (r2f < a.pc.r2min_f && !diag) {
             double tu[3];
-            dense_term<TDENSE, MODE, false>(pi, pj, fm[j], a.pc, tu);
+            dense_term_box<TDENSE, MODE, false>(pi, pj, fm[j], a.pc, tu);
             for (int d = 0; d < 3; ++d) c6[3 + d] += tc[d] - tu[d];
         }
     }
@@ -125,11 +160,9 @@ __device__ void near_direct(const NearArgs &a, int i, int sub, bool active) {
         const V4 pi = pm[i];
         const double xi = a.x64[3 * i], yi = a.x64[3 * i + 1], zi = a.x64[3 * i + 2];
         for_each_neighbour_part(a.cl, i, a.cl.cell[i], sub, kWalkLanes, [&](int j) {
-            const V4 pj = pm[j];
-            const float sx = static_cast<float>(pi.x - pj.x), sy = static_cast<float>(pi.y - pj.y),
-                        sz = static_cast<float>(pi.z - pj.z);
-            if (sx * sx + sy * sy + sz * sz > a.rscreen2) return;
-            const double dx = xi - a.x64[3 * j], dy = yi - a.x64[3 * j + 1], dz = zi - a.x64[3 * j + 2];
+            if (screen_r2(pi, pm[j], a.pc) > a.rscreen2) return;
+            double dx = xi - a.x64[3 * j], dy = yi - a.x64[3 * j + 1], dz = zi - a.x64[3 * j + 2];
+            box_image(a.cl.box, dx, dy, dz);
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= a.rnear2) return;
             found = true;
@@ -171,12 +204,7 @@ __global__ void __launch_bounds__(128) near_collect_kernel(NearArgs a) {
     const int i = active ? a.cl.sorted[q] : 0;
     const int lane = threadIdx.x & 31;
     int cnt = 0, j0 = -1, j1 = -1, j2 = -1, j3 = -1;
-    auto screen = [&](const V4 &pi, int j) {
-        const V4 pj = pm[j];
-        const float sx = static_cast<float>(pi.x - pj.x), sy = static_cast<float>(pi.y - pj.y),
-                    sz = static_cast<float>(pi.z - pj.z);
-        return sx * sx + sy * sy + sz * sz <= a.rscreen2;
-    };
+    auto screen = [&](const V4 &pi, int j) { return screen_r2(pi, pm[j], a.pc) <= a.rscreen2; };
     if (active) {
         const V4 pi = pm[i];
         for_each_neighbour_part(a.cl, i, a.cl.cell[i], sub, kWalkLanes, [&](int j) {
@@ -244,8 +272,9 @@ __global__ void __launch_bounds__(128) near_pair_kernel(NearArgs a) {
         double c6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (p.x >= 0) {
             const int i = p.x, j = p.y;
-            const double dx = a.x64[3 * i] - a.x64[3 * j], dy = a.x64[3 * i + 1] - a.x64[3 * j + 1],
-                         dz = a.x64[3 * i + 2] - a.x64[3 * j + 2];
+            double dx = a.x64[3 * i] - a.x64[3 * j], dy = a.x64[3 * i + 1] - a.x64[3 * j + 1],
+                   dz = a.x64[3 * i + 2] - a.x64[3 * j + 2];
+            box_image(a.cl.box, dx, dy, dz);
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < a.rnear2) {
                 if (r2 < a.rsafe2) close = true;

@@ -6,12 +6,19 @@ namespace sd {
 
 // Calls f(j) for every particle j != i whose cell is one of the 27 cells around
 // cell ci, in fixed order (cells by offset, bucket entries by index).
+// A neighbour cell coordinate: wrapped in a periodic dimension (nc > 0).
+__device__ __forceinline__ int cell_wrap(int c, int nc) {
+    if (nc <= 0) return c;
+    return c < 0 ? c + nc : (c >= nc ? c - nc : c);
+}
+
 template <typename Fn>
 __device__ __forceinline__ void for_each_neighbour(const CellList &c, int i, int4 ci, Fn &&f) {
     for (int oz = -1; oz <= 1; ++oz)
         for (int oy = -1; oy <= 1; ++oy)
             for (int ox = -1; ox <= 1; ++ox) {
-                const int cx = ci.x + ox, cy = ci.y + oy, cz = ci.z + oz;
+                const int cx = cell_wrap(ci.x + ox, c.nc[0]), cy = cell_wrap(ci.y + oy, c.nc[1]),
+                          cz = cell_wrap(ci.z + oz, c.nc[2]);
                 const uint32_t b = cell_hash(cx, cy, cz, c.H);
                 const int s1 = c.start[b + 1];
                 for (int s = c.start[b]; s < s1; ++s) {
@@ -30,7 +37,8 @@ template <typename Fn>
 __device__ __forceinline__ void for_each_neighbour_part(const CellList &c, int i, int4 ci, int first, int step,
                                                         Fn &&f) {
     for (int k = first; k < 27; k += step) {
-        const int cx = ci.x + (k % 3) - 1, cy = ci.y + (k / 3) % 3 - 1, cz = ci.z + k / 9 - 1;
+        const int cx = cell_wrap(ci.x + (k % 3) - 1, c.nc[0]), cy = cell_wrap(ci.y + (k / 3) % 3 - 1, c.nc[1]),
+                  cz = cell_wrap(ci.z + k / 9 - 1, c.nc[2]);
         const uint32_t b = cell_hash(cx, cy, cz, c.H);
         const int s1 = c.start[b + 1];
         for (int s = c.start[b]; s < s1; ++s) {
@@ -41,6 +49,14 @@ __device__ __forceinline__ void for_each_neighbour_part(const CellList &c, int i
             f(j);
         }
     }
+}
+
+// Nearest-image FP64 separation r_i - r_j (identity in unbounded dimensions).
+__device__ __forceinline__ void box_image(const Box &b, double &dx, double &dy, double &dz) {
+    if (!b.periodic) return;
+    dx = min_image_f64(dx, b.L[0], b.invL[0]);
+    dy = min_image_f64(dy, b.L[1], b.invL[1]);
+    dz = min_image_f64(dz, b.L[2], b.invL[2]);
 }
 
 // Threads per particle in the neighbour-walking kernels (a power of two <= 32;

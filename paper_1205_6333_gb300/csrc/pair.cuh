@@ -31,18 +31,41 @@ struct PairConst {
     float r2min_f, c1_f, c3_f, m3c3_f;   // (2a)^2, 3a/4, a^3/2, -3a^3/2
     double r2min_d, c1_d, c3_d, m3c3_d;
     double a, two_a, mu0;
+    // periodic box, nearest image only (Sec. 3.1 footnote): side L_d, 1/L_d; both 0
+    // in a dimension without periodicity (the minimum image is then the identity)
+    float Lf[3], invLf[3];
+    double Ld[3], invLd[3];
+    int periodic;
 };
+
+// Nearest image of a separation d in a dimension of period L (1/L = invL):
+// d - L rint(d / L), with rint(t) = (t + 1.5 2^23) - 1.5 2^23, exact round-to-even
+// for |t| < 2^22 (FP32; 2^51 for FP64).  The result is odd in d, bit for bit, so
+// the image of r_j - r_i is the negated image of r_i - r_j; with invL = 0 it is d.
+__device__ __forceinline__ float min_image_f32(float d, float L, float invL) {
+    const float n = __fsub_rn(__fadd_rn(__fmul_rn(d, invL), 12582912.0f), 12582912.0f);
+    return __fmaf_rn(-L, n, d);
+}
+__device__ __forceinline__ double min_image_f64(double d, double L, double invL) {
+    const double n = __dsub_rn(__dadd_rn(__dmul_rn(d, invL), 6755399441055744.0), 6755399441055744.0);
+    return __fma_rn(-L, n, d);
+}
 
 // ---------------------------------------------------------------- dense FP32
 
 // One pair of the dense sum, accumulated into (ax, ay, az): 22 FP32-pipe ops
 // (RP) or 20 (Oseen), one MUFU.RSQ, and with CLAMP one FMNMX.
-template <int TENSOR, bool CLAMP = true>
+template <int TENSOR, bool CLAMP = true, bool PER = false>
 __device__ __forceinline__ void pair_f32(float xi, float yi, float zi, float4 p, float4 f, const PairConst &c,
                                          float &ax, float &ay, float &az) {
-    const float dx = __fsub_rn(xi, p.x);
-    const float dy = __fsub_rn(yi, p.y);
-    const float dz = __fsub_rn(zi, p.z);
+    float dx = __fsub_rn(xi, p.x);
+    float dy = __fsub_rn(yi, p.y);
+    float dz = __fsub_rn(zi, p.z);
+    if (PER) {
+        dx = min_image_f32(dx, c.Lf[0], c.invLf[0]);
+        dy = min_image_f32(dy, c.Lf[1], c.invLf[1]);
+        dz = min_image_f32(dz, c.Lf[2], c.invLf[2]);
+    }
     float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     if (CLAMP) r2 = fmaxf(r2, c.r2min_f);
     const float ri = rsqrt_sfu(r2);
@@ -113,19 +136,31 @@ inline f2 pk2_host(float c) {
 struct PairConst2 {
     f2 c1, c3, m3c3;   // (c, c) pairs of the constants of PairConst
     float r2min;
+    f2 negL[3], invL[3];   // (-L, -L), (1/L, 1/L) per dimension (zeros: not periodic)
 };
+
+__device__ __forceinline__ f2 min_image2(f2 d, f2 negL, f2 invL) {
+    const f2 magic = 0x4B4000004B400000ull;   // (1.5 2^23, 1.5 2^23)
+    const f2 n = sub2(add2(mul2(d, invL), magic), magic);
+    return fma2(negL, n, d);
+}
 
 // Two pairs at once, lane by lane the operation sequence of pair_f32<TENSOR, CLAMP>:
 // either (i, j0), (i, j1) with P* = (x_j0, x_j1) and XI = (x_i, x_i), or
 // (i0, j), (i1, j) with XI = (x_i0, x_i1) and P* = (x_j, x_j).  With TRACK, mn0
 // and mn1 receive the two unclamped r^2.
-template <int TENSOR, bool CLAMP, bool TRACK>
+template <int TENSOR, bool CLAMP, bool TRACK, bool PER = false>
 __device__ __forceinline__ void pair_f32x2_t(f2 XI, f2 YI, f2 ZI, f2 PX, f2 PY, f2 PZ, f2 FX, f2 FY, f2 FZ,
                                              const PairConst2 &c, f2 &AX, f2 &AY, f2 &AZ, float &mn0,
                                              float &mn1) {
-    const f2 dx = sub2(XI, PX);
-    const f2 dy = sub2(YI, PY);
-    const f2 dz = sub2(ZI, PZ);
+    f2 dx = sub2(XI, PX);
+    f2 dy = sub2(YI, PY);
+    f2 dz = sub2(ZI, PZ);
+    if (PER) {
+        dx = min_image2(dx, c.negL[0], c.invL[0]);
+        dy = min_image2(dy, c.negL[1], c.invL[1]);
+        dz = min_image2(dz, c.negL[2], c.invL[2]);
+    }
     const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
     float ra, rb;
     upk2(r2, ra, rb);
@@ -155,11 +190,11 @@ __device__ __forceinline__ void pair_f32x2_t(f2 XI, f2 YI, f2 ZI, f2 PX, f2 PY, 
     AZ = fma2(s, dz, fma2(A, FZ, AZ));
 }
 
-template <int TENSOR, bool CLAMP = true>
+template <int TENSOR, bool CLAMP = true, bool PER = false>
 __device__ __forceinline__ void pair_f32x2(f2 XI, f2 YI, f2 ZI, f2 PX, f2 PY, f2 PZ, f2 FX, f2 FY, f2 FZ,
                                            const PairConst2 &c, f2 &AX, f2 &AY, f2 &AZ) {
     float unused0 = 0.0f, unused1 = 0.0f;
-    pair_f32x2_t<TENSOR, CLAMP, false>(XI, YI, ZI, PX, PY, PZ, FX, FY, FZ, c, AX, AY, AZ, unused0, unused1);
+    pair_f32x2_t<TENSOR, CLAMP, false, PER>(XI, YI, ZI, PX, PY, PZ, FX, FY, FZ, c, AX, AY, AZ, unused0, unused1);
 }
 
 // The pairs (i, j0), (i, j1) used in both directions (mu_ij = mu_ji, Sec. 2.2):
@@ -169,13 +204,18 @@ __device__ __forceinline__ void pair_f32x2(f2 XI, f2 YI, f2 ZI, f2 PX, f2 PY, f2
 // r_j - r_i = -(r_i - r_j) exactly, T is even in r and round-to-nearest is odd, so
 // each lane's J term is bit-identical to pair_f32x2_t evaluated for (j, i); A and B
 // are shared.  32 packed FP32-pipe instructions for four pair terms (RP).
-template <int TENSOR, bool CLAMP>
+template <int TENSOR, bool CLAMP, bool PER = false>
 __device__ __forceinline__ void pair_sym_f32x2(f2 XI, f2 YI, f2 ZI, f2 GX, f2 GY, f2 GZ, f2 PX, f2 PY, f2 PZ,
                                                f2 FX, f2 FY, f2 FZ, const PairConst2 &c, f2 &AX, f2 &AY,
                                                f2 &AZ, f2 &JX, f2 &JY, f2 &JZ) {
-    const f2 dx = sub2(XI, PX);
-    const f2 dy = sub2(YI, PY);
-    const f2 dz = sub2(ZI, PZ);
+    f2 dx = sub2(XI, PX);
+    f2 dy = sub2(YI, PY);
+    f2 dz = sub2(ZI, PZ);
+    if (PER) {
+        dx = min_image2(dx, c.negL[0], c.invL[0]);
+        dy = min_image2(dy, c.negL[1], c.invL[1]);
+        dz = min_image2(dz, c.negL[2], c.invL[2]);
+    }
     const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
     float ra, rb;
     upk2(r2, ra, rb);
@@ -212,12 +252,17 @@ __device__ __forceinline__ void pair_sym_f32x2(f2 XI, f2 YI, f2 ZI, f2 GX, f2 GY
 
 // ---------------------------------------------------------------- dense FP64
 
-template <int TENSOR>
+template <int TENSOR, bool PER = false>
 __device__ __forceinline__ void pair_f64(double xi, double yi, double zi, dbl4 p, dbl4 f, const PairConst &c,
                                          double &ax, double &ay, double &az) {
-    const double dx = __dsub_rn(xi, p.x);
-    const double dy = __dsub_rn(yi, p.y);
-    const double dz = __dsub_rn(zi, p.z);
+    double dx = __dsub_rn(xi, p.x);
+    double dy = __dsub_rn(yi, p.y);
+    double dz = __dsub_rn(zi, p.z);
+    if (PER) {
+        dx = min_image_f64(dx, c.Ld[0], c.invLd[0]);
+        dy = min_image_f64(dy, c.Ld[1], c.invLd[1]);
+        dz = min_image_f64(dz, c.Ld[2], c.invLd[2]);
+    }
     double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
     r2 = fmax(r2, c.r2min_d);
     const double ri = rsqrt_nr64(r2);
@@ -286,12 +331,17 @@ __device__ __forceinline__ void profile_exact(double r2, const PairConst &c, dou
 //   g += (dA U + dB Q) r + B [Wi (Fj.r) + Fj (Wi.r) + Wj (Fi.r) + Fi (Wj.r)]
 // with U = Wi.Fj + Wj.Fi and Q = (Wi.r)(Fj.r) + (Wj.r)(Fi.r)  -- the gradient of
 // Wi.T(r)Fj + Wj.T(r)Fi with respect to x_i.  FP32, r^2 clamped like pair_f32.
-template <int TENSOR>
+template <int TENSOR, bool PER = false>
 __device__ __forceinline__ void vjp_pair_f32(float xi, float yi, float zi, float3 Fi, float3 Wi, float4 p, float4 f,
                                              float4 w, const PairConst &c, float3 &m, float3 &g) {
-    const float dx = __fsub_rn(xi, p.x);
-    const float dy = __fsub_rn(yi, p.y);
-    const float dz = __fsub_rn(zi, p.z);
+    float dx = __fsub_rn(xi, p.x);
+    float dy = __fsub_rn(yi, p.y);
+    float dz = __fsub_rn(zi, p.z);
+    if (PER) {
+        dx = min_image_f32(dx, c.Lf[0], c.invLf[0]);
+        dy = min_image_f32(dy, c.Lf[1], c.invLf[1]);
+        dz = min_image_f32(dz, c.Lf[2], c.invLf[2]);
+    }
     float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     r2 = fmaxf(r2, c.r2min_f);
     const float ri = rsqrt_sfu(r2);
@@ -328,12 +378,17 @@ __device__ __forceinline__ void vjp_pair_f32(float xi, float yi, float zi, float
 }
 
 // The same pair in FP64 with the clamp (what the FP64 dense VJP kernel adds).
-template <int TENSOR>
+template <int TENSOR, bool PER = false>
 __device__ __forceinline__ void vjp_pair_f64(double xi, double yi, double zi, double3 Fi, double3 Wi, dbl4 p,
                                              dbl4 f, dbl4 w, const PairConst &c, double3 &m, double3 &g) {
-    const double dx = __dsub_rn(xi, p.x);
-    const double dy = __dsub_rn(yi, p.y);
-    const double dz = __dsub_rn(zi, p.z);
+    double dx = __dsub_rn(xi, p.x);
+    double dy = __dsub_rn(yi, p.y);
+    double dz = __dsub_rn(zi, p.z);
+    if (PER) {
+        dx = min_image_f64(dx, c.Ld[0], c.invLd[0]);
+        dy = min_image_f64(dy, c.Ld[1], c.invLd[1]);
+        dz = min_image_f64(dz, c.Ld[2], c.invLd[2]);
+    }
     double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
     r2 = fmax(r2, c.r2min_d);
     const double ri = rsqrt_nr64(r2);

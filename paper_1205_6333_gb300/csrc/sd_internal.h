@@ -72,10 +72,22 @@ __host__ __device__ inline int geom_last(const DenseGeom &g, int ib) {
     return static_cast<int>((geom_rowstart(g, ib + 1) - 1) / g.chunk);
 }
 
-// Hashed cell list over FP64 positions (unbounded domains): cells of side h,
-// H buckets (power of two), particles sorted by bucket, each bucket ascending.
+// Periodic box, nearest image only (Sec. 3.1 footnote): side L[d] and 1/L[d] in
+// each periodic dimension, 0 and 0 in the others.
+struct Box {
+    double L[3] = {0.0, 0.0, 0.0};
+    double invL[3] = {0.0, 0.0, 0.0};
+    int periodic = 0;
+};
+
+// Hashed cell list over FP64 positions: cells of side h in unbounded dimensions
+// (no bounding box needed), nc[d] >= 3 cells of side L[d] / nc[d] >= h in a
+// periodic one (coordinates wrapped into [0, L)); H buckets (power of two),
+// particles sorted by bucket, each bucket ascending.
 struct CellList {
     double h = 0.0, inv_h = 0.0;
+    Box box;
+    int nc[3] = {0, 0, 0};          // cells per periodic dimension (0: unbounded)
     int H = 0;
     int nblk = 0;          // scan blocks
     int4 *cell = nullptr;  // [n] integer cell coordinates (w unused)

@@ -28,7 +28,7 @@ struct VjpT<MODE_FP64> {
     using S = double;
 };
 
-template <int TENSOR, int MODE>
+template <int TENSOR, int MODE, bool PER>
 __device__ __forceinline__ void vjp_term(typename VjpT<MODE>::S xi, typename VjpT<MODE>::S yi,
                                          typename VjpT<MODE>::S zi, const typename VjpT<MODE>::V3 &Fi,
                                          const typename VjpT<MODE>::V3 &Wi, const typename VjpT<MODE>::V4 &p,
@@ -36,12 +36,12 @@ __device__ __forceinline__ void vjp_term(typename VjpT<MODE>::S xi, typename Vjp
                                          const PairConst &c, typename VjpT<MODE>::V3 &m,
                                          typename VjpT<MODE>::V3 &g) {
     if constexpr (MODE == MODE_FP64)
-        vjp_pair_f64<TENSOR>(xi, yi, zi, Fi, Wi, p, f, w, c, m, g);
+        vjp_pair_f64<TENSOR, PER>(xi, yi, zi, Fi, Wi, p, f, w, c, m, g);
     else
-        vjp_pair_f32<TENSOR>(xi, yi, zi, Fi, Wi, p, f, w, c, m, g);
+        vjp_pair_f32<TENSOR, PER>(xi, yi, zi, Fi, Wi, p, f, w, c, m, g);
 }
 
-template <int TENSOR, int MODE>
+template <int TENSOR, int MODE, bool PER>
 __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 *__restrict__ pos,
                                                   const typename VjpT<MODE>::V4 *__restrict__ frc,
                                                   const typename VjpT<MODE>::V4 *__restrict__ wv,
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 
         for (int jj = 0; jj < g.J; ++jj) {
             const V4 p = P[jj], f = Fq[jj], w = Wq[jj];
 #pragma unroll
-            for (int k = 0; k < R; ++k) vjp_term<TENSOR, MODE>(xi[k], yi[k], zi[k], Fi[k], Wi[k], p, f, w, c, m[k], gg[k]);
+            for (int k = 0; k < R; ++k) vjp_term<TENSOR, MODE, PER>(xi[k], yi[k], zi[k], Fi[k], Wi[k], p, f, w, c, m[k], gg[k]);
         }
         if constexpr (COMP) {
 #pragma unroll
@@ -180,14 +180,15 @@ __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 
 static size_t v4b(int mode) { return mode == MODE_FP64 ? sizeof(dbl4) : sizeof(float4); }
 
 template <int TT, int MM>
-static void *vjp_fn() {
-    return reinterpret_cast<void *>(&vjp_kernel<TT, MM>);
+static void *vjp_fn(bool per) {
+    return per ? reinterpret_cast<void *>(&vjp_kernel<TT, MM, true>)
+               : reinterpret_cast<void *>(&vjp_kernel<TT, MM, false>);
 }
 
-static void *pick_vjp(int tensor, int mode) {
+static void *pick_vjp(int tensor, int mode, bool per) {
     const int dt = (tensor == T_OSEEN) ? T_OSEEN : T_RP;
-    if (mode == MODE_FP64) return dt == T_OSEEN ? vjp_fn<T_OSEEN, MODE_FP64>() : vjp_fn<T_RP, MODE_FP64>();
-    return dt == T_OSEEN ? vjp_fn<T_OSEEN, MODE_FP32C>() : vjp_fn<T_RP, MODE_FP32C>();
+    if (mode == MODE_FP64) return dt == T_OSEEN ? vjp_fn<T_OSEEN, MODE_FP64>(per) : vjp_fn<T_RP, MODE_FP64>(per);
+    return dt == T_OSEEN ? vjp_fn<T_OSEEN, MODE_FP32C>(per) : vjp_fn<T_RP, MODE_FP32C>(per);
 }
 
 cudaError_t vjp_setup(sd_handle *h) {
@@ -195,7 +196,7 @@ cudaError_t vjp_setup(sd_handle *h) {
     g.I = kNT * kRV;
     g.nIB = h->npad / g.I;
     const int mode = (h->mode == MODE_FP64) ? MODE_FP64 : MODE_FP32C;
-    void *fn = pick_vjp(h->tensor, mode);
+    void *fn = pick_vjp(h->tensor, mode, h->pc.periodic != 0);
     int occ = 0;
     const int Jc[3] = {kJmax, 128, 64};
     for (int ci = 0; ci < 3; ++ci) {
@@ -230,15 +231,20 @@ cudaError_t launch_vjp_dense(sd_handle *h, cudaStream_t st, const void *posm, co
     const size_t smem = 6 * static_cast<size_t>(g.J) * v4b(f64 ? MODE_FP64 : MODE_FP32C);
     const bool oseen = h->tensor == T_OSEEN;
     prof_begin(h, SD_KERNEL_VJP, st);
-#define SD_VJP_LAUNCH(TT, MM)                                                                                 \
-    vjp_kernel<TT, MM><<<g.grid, kNT, smem, st>>>(                                                            \
+#define SD_VJP_LAUNCH(TT, MM, PP)                                                                             \
+    vjp_kernel<TT, MM, PP><<<g.grid, kNT, smem, st>>>(                                                        \
         static_cast<const typename VjpT<MM>::V4 *>(posm), static_cast<const typename VjpT<MM>::V4 *>(frcm),   \
         static_cast<const typename VjpT<MM>::V4 *>(wm), partM, partG, h->npad, g, h->pc, h->d_err, h->watchdog)
+#define SD_VJP_PER(TT, MM)                                                                                    \
+    do {                                                                                                      \
+        if (h->pc.periodic) SD_VJP_LAUNCH(TT, MM, true); else SD_VJP_LAUNCH(TT, MM, false);                  \
+    } while (0)
     if (f64) {
-        if (oseen) SD_VJP_LAUNCH(T_OSEEN, MODE_FP64); else SD_VJP_LAUNCH(T_RP, MODE_FP64);
+        if (oseen) SD_VJP_PER(T_OSEEN, MODE_FP64); else SD_VJP_PER(T_RP, MODE_FP64);
     } else {
-        if (oseen) SD_VJP_LAUNCH(T_OSEEN, MODE_FP32C); else SD_VJP_LAUNCH(T_RP, MODE_FP32C);
+        if (oseen) SD_VJP_PER(T_OSEEN, MODE_FP32C); else SD_VJP_PER(T_RP, MODE_FP32C);
     }
+#undef SD_VJP_PER
 #undef SD_VJP_LAUNCH
     prof_end(h, SD_KERNEL_VJP, st);
     ++h->launches;
@@ -298,7 +304,10 @@ __global__ void __launch_bounds__(128) vjp_epilogue_kernel(VjpEpiArgs a) {
         V3 m, g;
         m.x = m.y = m.z = S(0);
         g.x = g.y = g.z = S(0);
-        vjp_term<TD, MODE>(pi.x, pi.y, pi.z, Fi, Wi, pj, fj, wj, a.pc, m, g);
+        if (a.pc.periodic)
+            vjp_term<TD, MODE, true>(pi.x, pi.y, pi.z, Fi, Wi, pj, fj, wj, a.pc, m, g);
+        else
+            vjp_term<TD, MODE, false>(pi.x, pi.y, pi.z, Fi, Wi, pj, fj, wj, a.pc, m, g);
         tm[0] = m.x; tm[1] = m.y; tm[2] = m.z;
         tg[0] = g.x; tg[1] = g.y; tg[2] = g.z;
     };
@@ -315,7 +324,8 @@ __global__ void __launch_bounds__(128) vjp_epilogue_kernel(VjpEpiArgs a) {
     const double Wx = a.W64[3 * i], Wy = a.W64[3 * i + 1], Wz = a.W64[3 * i + 2];
     bool coincident = false;
     for_each_neighbour(a.cl, i, a.cl.cell[i], [&](int j) {
-        const double dx = xi - a.x64[3 * j], dy = yi - a.x64[3 * j + 1], dz = zi - a.x64[3 * j + 2];
+        double dx = xi - a.x64[3 * j], dy = yi - a.x64[3 * j + 1], dz = zi - a.x64[3 * j + 2];
+        box_image(a.cl.box, dx, dy, dz);
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= a.rnear2) return;
         if (r2 == 0.0 && TENSOR != T_RPY) {

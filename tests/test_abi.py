@@ -78,12 +78,22 @@ def test_create_rejects_bad_config_on_host(sd, field, value, status):
     assert sd.sd_last_error()
 
 
-def test_periodic_box_is_reported_unsupported(sd):
+def test_periodic_box_validation(sd):
+    """A periodic side shorter than three cell-list cells is an argument error (checked
+    before any device work); batches have no periodic mode."""
+    for box, lub in [((7.4, 0.0, 0.0), 0), ((20.0, 20.0, 8.9), 1)]:   # 3 x 2.5a, 3 x 3a
+        cfg = sd.sd_config_init()
+        cfg.n = 10
+        cfg.lubrication = lub
+        for d in range(3):
+            cfg.box[d] = box[d]
+        with pytest.raises(sd.SDError) as ei:
+            sd.sd_create(cfg)
+        assert ei.value.status_name == "SD_ERR_ARG"
     cfg = sd.sd_config_init()
-    cfg.n = 10
-    cfg.box[0] = 20.0
+    cfg.box[2] = 20.0
     with pytest.raises(sd.SDError) as ei:
-        sd.sd_create(cfg)
+        sd.sd_batch_create(cfg, [0, 4])
     assert ei.value.status_name == "SD_ERR_UNSUPPORTED"
 
 

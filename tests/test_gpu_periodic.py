@@ -1,0 +1,126 @@
+"""Periodic box, nearest image only (Sec. 3.1 footnote), against the FP64 oracle
+through the C ABI: mobility apply (both all-pairs kernels), Euler steps with
+repulsion and lubrication, and the VJP."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1205_6333_gb300 as sd
+from paper_1205_6333_gb300 import inputs
+from helpers import TOL, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _periodic_system(n, phi, seed, overlaps=4, min_side=10.0):
+    """Cube packing of side L (>= min_side); particles shifted by whole periods so
+    the state is unwrapped; a few pairs overlapping across the faces of the box."""
+    x, L = inputs.cube_rsa(n, phi, seed)
+    L = max(L, min_side)
+    rng = np.random.default_rng(seed + 11)
+    x = x + L * rng.integers(-2, 3, x.shape)          # unwrapped images of the same configuration
+    for k in range(min(overlaps, n // 2)):
+        i, j = 2 * k, 2 * k + 1
+        d = rng.standard_normal(3)
+        base = np.array([0.05, rng.uniform(0, L), L - 0.05])   # at the faces x = 0 and z = L
+        x[i] = base + L * rng.integers(-1, 2, 3)
+        x[j] = base + d / np.linalg.norm(d) * rng.uniform(0.3, 1.9) + L * rng.integers(-1, 2, 3)
+    return x, L
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64", "fp32"])
+@pytest.mark.parametrize("tensor", ["rpy", "rp", "oseen"])
+@pytest.mark.parametrize("n", [1, 2, 33, 513, 1500, 4133])
+def test_periodic_apply_matches_oracle(prec, tensor, n):
+    x, L = _periodic_system(n, 0.05, 500 + n)
+    F = inputs.normal_forces(n, 600 + n)
+    box = (L, L, L)
+    with sd.System(n, tensor=tensor, prec=prec, box=box) as s:
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+    ref = oracle.mobility_apply(x, F, tensor, box=box, nthreads=8)
+    assert rel_err(v, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("dense", ["directed", "symmetric"])
+@pytest.mark.parametrize("box", [(1, 1, 0), (0, 0, 1), (1, 0.7, 1.3)])
+def test_periodic_slabs_and_boxes(dense, box):
+    """Periodic in some dimensions only, unequal sides; both all-pairs kernels."""
+    n = 3000
+    x, L = _periodic_system(n, 0.05, 700)
+    b = tuple(L * f for f in box)
+    F = inputs.normal_forces(n, 701)
+    with sd.System(n, box=b, dense=dense) as s:
+        assert s.dense_kernel() == dense
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+    ref = oracle.mobility_apply(x, F, "rpy", box=b, nthreads=8)
+    assert rel_err(v, ref) <= TOL["fp32c"]
+
+
+def test_periodic_images_are_equivalent():
+    """Moving particles by whole periods does not change the velocities (the state is
+    kept unwrapped; only the nearest image interacts)."""
+    n = 2048
+    x, L = _periodic_system(n, 0.08, 710, overlaps=0)
+    F = inputs.normal_forces(n, 711)
+    shift = L * np.random.default_rng(712).integers(-3, 4, x.shape)
+    with sd.System(n, prec="fp64", box=(L, L, L)) as s:
+        s.set_positions(x)
+        v1 = s.mobility_apply(F)
+        s.set_positions(x + shift)
+        v2 = s.mobility_apply(F)
+    assert rel_err(v2, v1) <= 1e-13
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32c", 2e-6)])
+def test_periodic_steps_match_oracle(prec, tol):
+    """Gravity + soft repulsion in a periodic box, 20 Euler steps (workload-3 physics)."""
+    n = 2500
+    x0, L = inputs.cube_rsa(n, 0.10, 720)
+    box = (L, L, L)
+    g = (0.0, 0.0, -1.0)
+    fe = inputs.normal_forces(n, 721)
+    ref = oracle.euler(x0, 20, 0.01, fe, g, rep_eps=1.0, rep_rc=2.5, box=box, nthreads=8)
+    with sd.System(n, prec=prec, gravity=g, rep_eps=1.0, rep_rc=2.5, box=box) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(0.01, 20)
+        xT = s.get_positions()
+    disp = np.linalg.norm(ref - x0, axis=1).max()
+    assert np.linalg.norm(xT - ref, axis=1).max() <= tol * disp
+
+
+def test_periodic_lubrication_lattice():
+    """A jittered lattice filling a periodic box (every sphere has 6 neighbours inside
+    the friction window, across the faces too): 10 steps with lubrication."""
+    m, spacing = 8, 2.8
+    g1 = np.arange(m) * spacing
+    x0 = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3)
+    x0 = x0 + np.random.default_rng(730).uniform(-0.05, 0.05, x0.shape)
+    n, L = x0.shape[0], m * spacing
+    box = (L, L, L)
+    fe = inputs.normal_forces(n, 731)
+    ref = oracle.euler(x0, 10, 0.02, fe, box=box, lubrication=True, nthreads=8)
+    with sd.System(n, prec="fp64", box=box, lubrication=True) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(0.02, 10)
+        xT = s.get_positions()
+    disp = np.linalg.norm(ref - x0, axis=1).max()
+    assert np.linalg.norm(xT - ref, axis=1).max() <= 1e-10 * disp
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32c", 1e-5)])
+def test_periodic_vjp_matches_oracle(prec, tol):
+    n = 700
+    x, L = _periodic_system(n, 0.05, 740)
+    box = (L, L, L)
+    F = inputs.normal_forces(n, 741)
+    W = inputs.normal_forces(n, 742)
+    with sd.System(n, prec=prec, box=box) as s:
+        s.set_positions(x)
+        gx, gF = s.vjp(F, W)
+    rx, rF = oracle.vjp(x, F, W, "rpy", box=box, nthreads=8)
+    assert rel_err(gF, rF) <= tol
+    assert rel_err(gx, rx) <= 10 * tol
