@@ -9,6 +9,8 @@
 // so unbounded domains need no bounding box.  Build = count, exclusive scan,
 // scatter, and an insertion sort of each bucket by particle index (makes every
 // neighbour walk, hence every FP64 near-pair sum, independent of atomics order).
+#include <type_traits>
+
 #include "neighbours.cuh"
 
 namespace sd {
@@ -351,10 +353,20 @@ __global__ void forces_rep_kernel(const double *__restrict__ x, const double *__
                 f[2] += coef * dz;
             }
             if (lub) {
+                // the gap s in FP64 (it cancels: r/a - 2); the coefficients in the
+                // working precision of the pair terms (FP32 in the FP32 modes)
                 const double sg = r2 * ri * inv_a - 2.0;
                 if (sg > 0.0 && sg < 1.0) {
-                    const double ls = log(sg);
-                    const double zn = 0.25 / sg - 0.225 * ls, zt = -ls / 6.0;
+                    double zn, zt;
+                    if constexpr (std::is_same<V4, float4>::value) {
+                        const float sf = static_cast<float>(sg), ls = logf(sf);
+                        zn = __fsub_rn(__fdiv_rn(0.25f, sf), __fmul_rn(0.225f, ls));
+                        zt = __fmul_rn(ls, -1.0f / 6.0f);
+                    } else {
+                        const double ls = log(sg);
+                        zn = 0.25 / sg - 0.225 * ls;
+                        zt = -ls / 6.0;
+                    }
                     const double ex = dx * ri, ey = dy * ri, ez = dz * ri;
                     const double wx = vlag[3 * i] - vlag[3 * j], wy = vlag[3 * i + 1] - vlag[3 * j + 1],
                                  wz = vlag[3 * i + 2] - vlag[3 * j + 2];

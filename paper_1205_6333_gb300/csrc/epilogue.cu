@@ -94,7 +94,7 @@ struct NearArgs {
     double *near;   // [n][6]: clamped-variant correction (3), unclamped-variant correction (3)
     int *flag;      // raised when some pair has r < r_safe
     int *err;
-    int I, J;       // the all-pairs kernel's i-block and j-tile sizes
+    DenseGeom g;    // the all-pairs kernel's tiling (which tiles clamp r^2)
     // compacted candidate list (near_collect_kernel -> near_pair_kernel -> epilogue)
     int2 *ent;        // [cap] (i, j), or (-1, -1) for a slot that holds no pair
     double *ent_out;  // [cap][6] the pair's two correction variants, as `near`
@@ -137,9 +137,9 @@ __device__ __forceinline__ void near_pair_term(const NearArgs &a, int i, int j, 
             uz = min_image_f32(uz, a.pc.Lf[2], a.pc.invLf[2]);
         }
         const float r2f = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
-        const long long i0 = static_cast<long long>(i / a.I) * a.I, j0 = static_cast<long long>(j / a.J) * a.J;
-        const bool diag = (j0 < i0 + a.I) && (i0 < j0 + a.J);
-        if (r2f < a.pc.r2min_f && !diag) {
+        const long long i0 = static_cast<long long>(i / a.g.I) * a.g.I, j0 = static_cast<long long>(j / a.g.J) * a.g.J;
+        const bool diag = (j0 < i0 + a.g.I) && (i0 < j0 + a.g.J);
+        if (r2f < a.pc.r2min_f && !diag && !geom_pad_tile(a.g, i0, j0)) {
             double tu[3];
             dense_term_box<TDENSE, MODE, false>(pi, pj, fm[j], a.pc, tu);
             for (int d = 0; d < 3; ++d) c6[3 + d] += tc[d] - tu[d];
@@ -322,8 +322,7 @@ cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const 
     a.near = h->near64;
     a.flag = h->d_flag;
     a.err = h->d_err;
-    a.I = h->geom.I;
-    a.J = h->geom.J;
+    a.g = h->geom;
     a.ent = h->near_ent;
     a.ent_out = h->near_out;
     a.ent_n = h->near_n;

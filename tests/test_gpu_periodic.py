@@ -82,6 +82,7 @@ def test_periodic_steps_match_oracle(prec, tol):
     moves that pair's term by O(1e-3) of the velocity for one step."""
     n = 2500
     x0, L = inputs.cube_rsa(n, 0.10, 720)
+    L = L + 2.5          # the packing is non-overlapping across the faces as well
     box = (L, L, L)
     g = (0.0, 0.0, -1.0)
     fe = inputs.normal_forces(n, 721)
