@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -572,6 +573,60 @@ def leg_lubrication(args):
     return {"lubrication": out}
 
 
+def leg_fcc(args):
+    """The paper's runtime benchmark (Sec. 3.3): a sedimenting fcc lattice at number
+    density 0.1/a^3 in a periodic cube (nearest image only), the same force (0, 0, -1) on
+    every sphere, Euler dt = 0.001 tau_s, 100 steps; N = 4 m^3 from 108 to 202,612.
+    Device time per step (CUDA events around the 100 steps, replayed from the captured
+    graphs) in FP32C with and without lubrication, and in FP64 up to N = 32,000; the N
+    where the time per step turns from flat (launch- and latency-bound) to quadratic."""
+    import torch
+    import paper_1205_6333_gb300 as sd
+    from paper_1205_6333_gb300 import inputs
+    stream = torch.cuda.current_stream()
+    tau_s = 6.0 * math.pi            # a / (mu0 F) with a = eta = F = 1
+    dt = 0.001 * tau_s
+    rows = []
+
+    def time_steps(s, k):
+        s.step(dt, 16)               # warm-up, graphs captured
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(dt, k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    for m in (3, 4, 5, 6, 8, 10, 13, 16, 20, 25, 32, 37):
+        x, L = inputs.fcc_lattice(m)
+        n = x.shape[0]
+        rec = {"n": n, "box_side": L}
+        for key, prec, lub, k in (("fp32c", "fp32c", False, 100), ("fp32c_lub", "fp32c", True, 100),
+                                  ("fp64", "fp64", False, 10 if n > 8192 else 100)):
+            if prec == "fp64" and n > 32000:
+                continue
+            s = sd.System(n, prec=prec, gravity=(0.0, 0.0, -1.0), box=(L, L, L), lubrication=lub,
+                          stream="torch", torch_allocator=True)
+            s.set_positions(x)
+            rec["ms_per_step_" + key] = time_steps(s, k)
+            if key == "fp32c":
+                rec["dense_kernel"] = s.dense_kernel()
+            s.close()
+        rec["pairs_per_s_fp32c"] = float(n) * n / (rec["ms_per_step_fp32c"] * 1e-3)
+        rows.append(rec)
+        print(json.dumps(rec), file=sys.stderr, flush=True)
+    # crossover: t(N) = t0 + c N^2 with t0 the small-N floor and c from the largest N
+    t0 = min(r["ms_per_step_fp32c"] for r in rows)
+    big = rows[-1]
+    c = (big["ms_per_step_fp32c"] - t0) / float(big["n"]) ** 2
+    out = {"rows": rows, "flat_ms_per_step": t0, "ms_per_pair_large_n": c,
+           "crossover_n": math.sqrt(t0 / c),
+           "paper_context": "Tesla C2050: linear in N up to about 2,000 particles, quadratic above; 5.7 ms per "
+                            "step at N = 4,150 with lubrication (Sec. 3.3)"}
+    return {"fcc": out}
+
+
 def leg_adjoint(args, n_fd=16):
     """Workload 5: N = 4,096, phi = 0.05, gravity, dt = 0.01, 1000 Euler steps,
     L = sum |x_i(T) - x_i*|^2, checkpoints every 50 steps.  Central finite differences
@@ -679,7 +734,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="main leg only")
     ap.add_argument("--leg", default="all", choices=["all", "main", "fp64", "batched", "oseen", "sweep", "drift",
-                                                     "adjoint", "lubrication"],
+                                                     "adjoint", "lubrication", "fcc"],
                     help="run one leg alone and print its numbers (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
@@ -697,6 +752,8 @@ def main():
         print(json.dumps(leg_adjoint(args)), flush=True)
     elif args.leg == "lubrication":
         print(json.dumps(leg_lubrication(args)), flush=True)
+    elif args.leg == "fcc":
+        print(json.dumps(leg_fcc(args)), flush=True)
     else:
         if args.leg == "main":
             args.quick = True

@@ -39,7 +39,7 @@ constexpr int kRV = 2;           // i-particles per thread, VJP dense kernel
 constexpr int kJmax = 256;       // largest j-tile
 constexpr double kRSafe = 1.0;   // pairs closer than kRSafe * a make the FP32 kernel clamp every tile
 constexpr long long kDefaultWatchdog = 1LL << 22;
-constexpr int kNearPerParticle = 8;   // near-pass list capacity per particle (overflow: in-place path)
+constexpr int kNearPerParticle = 16;  // near-pass list capacity per particle (overflow: in-place path)
 constexpr int kSymNT = 128;      // threads per CTA of the symmetric FP32 kernel
 constexpr int kSymB = 256;       // particles per block (2 per thread) = sources per tile
 
