@@ -588,8 +588,9 @@ def leg_fcc(args):
     dt = 0.001 * tau_s
     rows = []
 
-    def time_steps(s, k):
+    def time_steps(s, x, k):
         s.step(dt, 16)               # warm-up, graphs captured
+        s.set_positions(x)           # fresh start (with lubrication: no previous velocities)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -602,14 +603,21 @@ def leg_fcc(args):
         x, L = inputs.fcc_lattice(m)
         n = x.shape[0]
         rec = {"n": n, "box_side": L}
-        for key, prec, lub, k in (("fp32c", "fp32c", False, 100), ("fp32c_lub", "fp32c", True, 100),
+        # With lubrication only 5 steps: on this lattice (gap s = 0.42, 12 neighbours) the
+        # lagged friction has spectral radius mu zeta > 1, so rounding noise in the
+        # relative velocities grows ~3x per step; 5 steps stay at rounding level.
+        for key, prec, lub, k in (("fp32c", "fp32c", False, 100), ("fp32c_lub", "fp32c", True, 5),
                                   ("fp64", "fp64", False, 10 if n > 8192 else 100)):
             if prec == "fp64" and n > 32000:
                 continue
             s = sd.System(n, prec=prec, gravity=(0.0, 0.0, -1.0), box=(L, L, L), lubrication=lub,
                           stream="torch", torch_allocator=True)
             s.set_positions(x)
-            rec["ms_per_step_" + key] = time_steps(s, k)
+            rec["ms_per_step_" + key] = time_steps(s, x, k)
+            xT = s.get_positions()
+            d = xT - x
+            # uniform sedimentation of a perfect periodic lattice: every sphere moves alike
+            rec["spread_" + key] = float(np.abs(d - d.mean(axis=0)).max() / max(np.abs(d).max(), 1e-300))
             if key == "fp32c":
                 rec["dense_kernel"] = s.dense_kernel()
             s.close()

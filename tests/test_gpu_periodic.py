@@ -129,3 +129,21 @@ def test_periodic_vjp_matches_oracle(prec, tol):
     rx, rF = oracle.vjp(x, F, W, "rpy", box=box, nthreads=8)
     assert rel_err(gF, rF) <= tol
     assert rel_err(gx, rx) <= 10 * tol
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_periodic_fcc_lattice_near_pairs(prec):
+    """The paper's benchmark geometry (Sec. 3.3): an fcc lattice at number density
+    0.1/a^3 in a periodic cube, every sphere with 12 neighbours at 2.42a < r_near
+    (the near pass's list holds them all); jittered so that no pair sits at an exact
+    half-period tie."""
+    x, L = inputs.fcc_lattice(5)
+    x = x + np.random.default_rng(750).uniform(-0.05, 0.05, x.shape)
+    n = x.shape[0]
+    box = (L, L, L)
+    F = inputs.normal_forces(n, 751)
+    with sd.System(n, prec=prec, box=box) as s:
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+    ref = oracle.mobility_apply(x, F, "rpy", box=box, nthreads=8)
+    assert periodic_rel_err(v, ref, x, F, box) <= TOL[prec]
