@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
         // near pass found a pair closer than r_safe (then everywhere)
         const long long i0 = static_cast<long long>(ib) * g.I, j0 = (t % g.nJT) * static_cast<long long>(g.J);
         const bool diag = (j0 < i0 + g.I) && (i0 < j0 + g.J);
-        if (clamp_all || diag || geom_pad_tile(g, i0, j0))
+        if (clamp_all || diag || (PER && geom_pad_tile(g, c.n, i0, j0)))
             tile_pairs<TENSOR, true, R, PER>(base, astride, g.J, XI, YI, ZI, c, AX, AY, AZ);
         else
             tile_pairs<TENSOR, false, R, PER>(base, astride, g.J, XI, YI, ZI, c, AX, AY, AZ);
@@ -543,7 +543,8 @@ __global__ void __launch_bounds__(kSymNT, SD_SYM_MINB) dense_sym_kernel(const fl
         } else {
             const f2 *sp = reinterpret_cast<const f2 *>(s_tile + st * 6 * B);
             float *jw = s_jacc + warp * 3 * B;
-            if (clamp_all || geom_pad_tile(g, static_cast<long long>(ib) * B, static_cast<long long>(jb) * B))
+            const bool pad = PER && geom_pad_tile(g, c.n, static_cast<long long>(ib) * B, static_cast<long long>(jb) * B);
+            if (clamp_all || pad)
                 sym_tile<TENSOR, true, PER>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
             else
                 sym_tile<TENSOR, false, PER>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
@@ -676,8 +677,6 @@ cudaError_t dense_setup(sd_handle *h) {
     g.grid = static_cast<int>((T + g.chunk - 1) / g.chunk);
     g.nT = T;
     g.sym = 0;
-    g.n = h->n;
-    g.pad_clamp = h->pc.periodic;
     const int want_sym = h->cfg.dense_kernel;
     if (h->mode != MODE_FP64 && h->npad % kSymB == 0 && want_sym != SD_DENSE_DIRECTED) {
         void *sfn = pick_sym(h->tensor, h->mode, h->pc.periodic != 0);
@@ -690,8 +689,6 @@ cudaError_t dense_setup(sd_handle *h) {
         socc = std::max(socc, 1);
         DenseGeom s{};
         s.sym = 1;
-        s.n = h->n;
-        s.pad_clamp = h->pc.periodic;
         s.I = s.J = kSymB;
         s.nIB = s.nJT = h->npad / kSymB;
         s.nT = static_cast<long long>(s.nIB) * (s.nIB + 1) / 2;
@@ -735,6 +732,7 @@ static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror fr
         c2.negL[d] = pk2_host(-h->pc.Lf[d]);
         c2.invL[d] = pk2_host(h->pc.invLf[d]);
     }
+    c2.n = h->n;
     const bool comp = h->mode == MODE_FP32C;
     if (g.sym) {
 #define SD_DS(TT, CC)                                                                                          \

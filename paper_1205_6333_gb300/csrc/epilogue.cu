@@ -139,7 +139,7 @@ __device__ __forceinline__ void near_pair_term(const NearArgs &a, int i, int j, 
         const float r2f = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
         const long long i0 = static_cast<long long>(i / a.g.I) * a.g.I, j0 = static_cast<long long>(j / a.g.J) * a.g.J;
         const bool diag = (j0 < i0 + a.g.I) && (i0 < j0 + a.g.J);
-        if (r2f < a.pc.r2min_f && !diag && !geom_pad_tile(a.g, i0, j0)) {
+        if (r2f < a.pc.r2min_f && !diag && !(a.pc.periodic && geom_pad_tile(a.g, a.n, i0, j0))) {
             double tu[3];
             dense_term_box<TDENSE, MODE, false>(pi, pj, fm[j], a.pc, tu);
             for (int d = 0; d < 3; ++d) c6[3 + d] += tc[d] - tu[d];

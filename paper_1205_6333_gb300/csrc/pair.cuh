@@ -137,6 +137,7 @@ struct PairConst2 {
     f2 c1, c3, m3c3;   // (c, c) pairs of the constants of PairConst
     float r2min;
     f2 negL[3], invL[3];   // (-L, -L), (1/L, 1/L) per dimension (zeros: not periodic)
+    int n;                 // particles (periodic kernels: tiles reaching index n clamp)
 };
 
 __device__ __forceinline__ f2 min_image2(f2 d, f2 negL, f2 invL) {

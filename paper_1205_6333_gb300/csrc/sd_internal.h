@@ -58,15 +58,15 @@ struct DenseGeom {
     int maxSlots;
     int sym;        // upper triangle of the plane (mu_ij = mu_ji used once per pair)
     long long nT;   // tiles
-    int n;          // particles; indices n .. npad-1 are padding
-    int pad_clamp;  // periodic box: padding has no far-away position under the nearest
-                    // image, so tiles whose i- or j-range reaches index n clamp r^2
 };
 
-// Does the tile of i-range [i0, i0 + I) and j-range [j0, j0 + J) clamp r^2 because
-// it holds padding (periodic box only)?
-__host__ __device__ inline bool geom_pad_tile(const DenseGeom &g, long long i0, long long j0) {
-    return g.pad_clamp && (i0 + g.I > g.n || j0 + g.J > g.n);
+// In a periodic box the padding entries n .. npad-1 have no far-away position under
+// the nearest image, so a tile whose i- or j-range reaches index n clamps r^2 (its
+// padding terms stay exactly zero).  (The particle count travels with the pair
+// constants, not in DenseGeom: a larger DenseGeom cost the symmetric kernel six
+// registers.)
+__host__ __device__ inline bool geom_pad_tile(const DenseGeom &g, int n, long long i0, long long j0) {
+    return i0 + g.I > n || j0 + g.J > n;
 }
 
 // First tile of row ib.

@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 
         for (int jj = 0; jj < g.J; ++jj) {
             const V4 p = P[jj], f = Fq[jj], w = Wq[jj];
 #pragma unroll
-            for (int k = 0; k < R; ++k) vjp_term<TENSOR, MODE, PER>(xi[k], yi[k], zi[k], Fi[k], Wi[k], p, f, w, c, m[k], gg[k]);
+            for (int k = 0; k < R; ++k)
+                vjp_term<TENSOR, MODE, PER>(xi[k], yi[k], zi[k], Fi[k], Wi[k], p, f, w, c, m[k], gg[k]);
         }
         if constexpr (COMP) {
 #pragma unroll
