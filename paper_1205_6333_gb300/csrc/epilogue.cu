@@ -63,20 +63,24 @@ __device__ __forceinline__ void dense_term_box(const typename EpiT<MODE>::V4 &pi
 
 // Mirror separation (nearest image in a periodic box) rounded to FP32, for the
 // near pass's screen.
-template <typename V4>
-__device__ __forceinline__ float screen_r2(const V4 &pi, const V4 &pj, const PairConst &c) {
-    float s[3];
-    const double di[3] = {pi.x, pi.y, pi.z}, dj[3] = {pj.x, pj.y, pj.z};
-    for (int d = 0; d < 3; ++d) {
-        if constexpr (std::is_same<V4, float4>::value) {
-            const float u = __fsub_rn(static_cast<float>(di[d]), static_cast<float>(dj[d]));
-            s[d] = c.periodic ? min_image_f32(u, c.Lf[d], c.invLf[d]) : u;
-        } else {
-            const double u = di[d] - dj[d];
-            s[d] = static_cast<float>(c.periodic ? min_image_f64(u, c.Ld[d], c.invLd[d]) : u);
-        }
+__device__ __forceinline__ float screen_r2(const float4 &pi, const float4 &pj, const PairConst &c) {
+    float sx = __fsub_rn(pi.x, pj.x), sy = __fsub_rn(pi.y, pj.y), sz = __fsub_rn(pi.z, pj.z);
+    if (c.periodic) {
+        sx = min_image_f32(sx, c.Lf[0], c.invLf[0]);
+        sy = min_image_f32(sy, c.Lf[1], c.invLf[1]);
+        sz = min_image_f32(sz, c.Lf[2], c.invLf[2]);
     }
-    return s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
+    return sx * sx + sy * sy + sz * sz;
+}
+__device__ __forceinline__ float screen_r2(const dbl4 &pi, const dbl4 &pj, const PairConst &c) {
+    double ux = pi.x - pj.x, uy = pi.y - pj.y, uz = pi.z - pj.z;
+    if (c.periodic) {
+        ux = min_image_f64(ux, c.Ld[0], c.invLd[0]);
+        uy = min_image_f64(uy, c.Ld[1], c.invLd[1]);
+        uz = min_image_f64(uz, c.Ld[2], c.invLd[2]);
+    }
+    const float sx = static_cast<float>(ux), sy = static_cast<float>(uy), sz = static_cast<float>(uz);
+    return sx * sx + sy * sy + sz * sz;
 }
 
 // ---------------------------------------------------------------- near pass
