@@ -143,6 +143,25 @@ sd_status sd_mobility_apply(sd_handle *h, const void *F, void *V, int dtype, int
  * (asynchronous; errors surface at the next synchronising call).  nsteps >= 0. */
 sd_status sd_step(sd_handle *h, double dt, int64_t nsteps);
 
+/* Row shards of the two calls above, for splitting one system over devices by
+ * target rows (each device holds all n positions and forces and computes the
+ * velocities of its own rows; the sum over j stays whole, Sec. 3.1 step 3).
+ *   sd_mobility_apply_rows: rows row0 .. row1-1 of V = mu(x) F; F holds all n
+ *     forces, V holds (row1 - row0) x 3 values.
+ *   sd_step_rows: one Euler step in which only rows row0 .. row1-1 advance; the
+ *     other rows keep their positions (the caller replaces them with the other
+ *     shards' results, e.g. by an all-gather and sd_set_positions).  Eager, no graph.
+ * Each row is bit-identical to the same row of sd_mobility_apply / sd_step(h, dt, 1):
+ * the shard runs exactly the CTAs of the full launch that cover its rows, with the
+ * same tiles.  Needs the directed all-pairs kernel (cfg.dense_kernel =
+ * SD_DENSE_DIRECTED, or FP64): SD_ERR_UNSUPPORTED with the symmetric one, whose
+ * source-side sums cross rows; sd_step_rows also with lubrication (the previous
+ * velocities of other shards' rows are not known).  0 <= row0 <= row1 <= n, else
+ * SD_ERR_ARG. */
+sd_status sd_mobility_apply_rows(sd_handle *h, const void *F, void *V, int dtype, int on_device, int32_t row0,
+                                 int32_t row1);
+sd_status sd_step_rows(sd_handle *h, double dt, int32_t row0, int32_t row1);
+
 /* Synchronise the handle's stream and report deferred device-side errors. */
 sd_status sd_synchronize(sd_handle *h);
 

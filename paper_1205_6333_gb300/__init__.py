@@ -82,6 +82,15 @@ def sd_step(h, dt, nsteps):
     _check(lib().sd_step(h, float(dt), int(nsteps)), "sd_step")
 
 
+def sd_mobility_apply_rows(h, F_ptr, V_ptr, dtype, on_device, row0, row1):
+    _check(lib().sd_mobility_apply_rows(h, F_ptr, V_ptr, int(dtype), int(on_device), int(row0), int(row1)),
+           "sd_mobility_apply_rows")
+
+
+def sd_step_rows(h, dt, row0, row1):
+    _check(lib().sd_step_rows(h, float(dt), int(row0), int(row1)), "sd_step_rows")
+
+
 def sd_synchronize(h):
     _check(lib().sd_synchronize(h), "sd_synchronize")
 
@@ -290,6 +299,18 @@ class System:
 
     def step(self, dt, nsteps=1):
         sd_step(self.h, dt, nsteps)
+
+    def mobility_apply_rows(self, F, row0, row1):
+        """Rows row0 .. row1-1 of mu(x) F (F: all n forces); a shard of mobility_apply."""
+        dt = _dtype_of(F)
+        pf, dev, _kf = _as_arg(F, dt)
+        pv, _, V = _out_like(F, int(row1) - int(row0), dt)
+        sd_mobility_apply_rows(self.h, pf, pv, SD_DTYPE_F32 if dt == np.float32 else SD_DTYPE_F64, dev, row0, row1)
+        return V
+
+    def step_rows(self, dt, row0, row1):
+        """One Euler step in which only rows row0 .. row1-1 advance."""
+        sd_step_rows(self.h, dt, row0, row1)
 
     def synchronize(self):
         sd_synchronize(self.h)

@@ -79,6 +79,8 @@ PROTOTYPES = {
     "sd_batch_profile_read": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "sd_launch_count": (c_int64, [c_void_p]),
     "sd_dense_kernel_used": (c_int32, [c_void_p]),
+    "sd_mobility_apply_rows": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32]),
+    "sd_step_rows": (c_int32, [c_void_p, c_double, c_int32, c_int32]),
     "sd_batch_launch_count": (c_int64, [c_void_p]),
     "sd_set_watchdog": (c_int32, [c_void_p, c_int64]),
     "sd_mobility_apply_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_double, c_int32,

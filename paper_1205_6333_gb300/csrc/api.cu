@@ -464,39 +464,96 @@ static sd_status ensure_cells(sd_handle *h) {
     return s;
 }
 
-sd_status sd_mobility_apply(sd_handle *h, const void *F, void *V, int dtype, int on_device) {
+// The tile window of the rows [row0, row1): whole i-blocks of the directed kernel.
+static TileWin row_window(const sd_handle *h, int row0, int row1) {
+    const DenseGeom &g = h->geom;
+    TileWin w;
+    w.lo = static_cast<long long>(row0 / g.I) * g.nJT;
+    w.hi = static_cast<long long>((row1 + g.I - 1) / g.I) * g.nJT;
+    return w;
+}
+
+// v for rows [row0, row1) (all rows: the whole product, either all-pairs kernel).
+static sd_status apply_rows(sd_handle *h, const void *F, void *V, int dtype, int on_device, int row0, int row1) {
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (dtype != SD_DTYPE_F32 && dtype != SD_DTYPE_F64) return set_error(SD_ERR_ARG, "dtype must be F32 or F64");
-    if (h->n > 0 && (!F || !V)) return set_error(SD_ERR_ARG, "F or V is NULL");
+    if (row0 < 0 || row1 < row0 || row1 > h->n) return set_error(SD_ERR_ARG, "rows must satisfy 0 <= row0 <= row1 <= n");
+    const bool all = row0 == 0 && row1 == h->n;
+    if (!all && h->geom.sym)
+        return set_error(SD_ERR_UNSUPPORTED, "row shards need the directed all-pairs kernel (SD_DENSE_DIRECTED)");
+    if (h->n > 0 && (!F || (!V && row1 > row0))) return set_error(SD_ERR_ARG, "F or V is NULL");
     if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
-    if (h->n == 0) return SD_OK;
+    if (h->n == 0 || row0 == row1) return SD_OK;
     cudaSetDevice(h->device);
     const size_t es = dtype == SD_DTYPE_F32 ? sizeof(float) : sizeof(double);
-    const size_t bytes = 3 * es * h->n;
+    const size_t bytes_in = 3 * es * h->n, bytes_out = 3 * es * static_cast<size_t>(row1 - row0);
     const void *Fd = F;
     void *Vd = V;
     if (!on_device) {
         void *in = nullptr, *out = nullptr;
         sd_status s = host_io(h, in, out);
         if (s != SD_OK) return s;
-        SD_CUDA(cudaMemcpyAsync(in, F, bytes, cudaMemcpyHostToDevice, h->stream));
+        SD_CUDA(cudaMemcpyAsync(in, F, bytes_in, cudaMemcpyHostToDevice, h->stream));
         Fd = in;
         Vd = out;
     }
+    const TileWin w = row_window(h, row0, row1);
     sd_status s = launch_check(launch_stage_forces(h, h->stream, Fd, dtype, 0, h->Fa64, h->frcam), "stage F");
     if (s == SD_OK) s = ensure_cells(h);
     if (s == SD_OK)
         s = launch_check(launch_near(h, h->stream, h->x64[h->cur], h->posm.aos, h->Fa64, h->frcam.aos), "near pass");
-    if (s == SD_OK) s = launch_check(launch_dense(h, h->stream, h->posm, h->frcam, h->part), "dense kernel");
+    if (s == SD_OK)
+        s = launch_check(launch_dense(h, h->stream, h->posm, h->frcam, h->part, all ? nullptr : &w), "dense kernel");
     if (s == SD_OK)
         s = launch_check(launch_epilogue(h, h->stream, dtype == SD_DTYPE_F32 ? OUT_F32 : OUT_F64, h->x64[h->cur],
-                                         h->posm.aos, h->Fa64, h->frcam.aos, Vd, 0.0, nullptr),
+                                         h->posm.aos, h->Fa64, h->frcam.aos, Vd, 0.0, nullptr, row0, row1),
                          "epilogue");
     if (s != SD_OK) return s;
     if (!on_device) {
-        SD_CUDA(cudaMemcpyAsync(V, Vd, bytes, cudaMemcpyDeviceToHost, h->stream));
+        SD_CUDA(cudaMemcpyAsync(V, Vd, bytes_out, cudaMemcpyDeviceToHost, h->stream));
         return sync_check(h);
     }
+    return SD_OK;
+}
+
+sd_status sd_mobility_apply(sd_handle *h, const void *F, void *V, int dtype, int on_device) {
+    return apply_rows(h, F, V, dtype, on_device, 0, h ? h->n : 0);
+}
+
+sd_status sd_mobility_apply_rows(sd_handle *h, const void *F, void *V, int dtype, int on_device, int32_t row0,
+                                 int32_t row1) {
+    return apply_rows(h, F, V, dtype, on_device, row0, row1);
+}
+
+sd_status sd_step_rows(sd_handle *h, double dt, int32_t row0, int32_t row1) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    if (!std::isfinite(dt)) return set_error(SD_ERR_ARG, "dt must be finite");
+    if (row0 < 0 || row1 < row0 || row1 > h->n) return set_error(SD_ERR_ARG, "rows must satisfy 0 <= row0 <= row1 <= n");
+    if (h->geom.sym && !(row0 == 0 && row1 == h->n))
+        return set_error(SD_ERR_UNSUPPORTED, "row shards need the directed all-pairs kernel (SD_DENSE_DIRECTED)");
+    if (h->lub) return set_error(SD_ERR_UNSUPPORTED, "sharded steps with lubrication are not implemented");
+    if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
+    if (h->n == 0) return SD_OK;
+    cudaSetDevice(h->device);
+    cudaStream_t st = h->stream;
+    const double *x_in = h->x64[h->cur];
+    double *x_out = h->x64[1 - h->cur];
+    const TileWin w = row_window(h, row0, row1);
+    cudaError_t e = launch_build_cells(h, st, x_in, h->posm);
+    if (e == cudaSuccess && !h->forces_const) e = launch_forces_rep(h, st, x_in);
+    if (e == cudaSuccess) e = launch_near(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos);
+    if (e == cudaSuccess) e = launch_dense(h, st, h->posm, h->frcm, h->part, &w);
+    if (e == cudaSuccess)
+        e = launch_epilogue(h, st, OUT_EULER, x_in, h->posm.aos, h->F64, h->frcm.aos, nullptr, dt, x_out, row0, row1);
+    // the rows of other shards keep their positions
+    const size_t rb = 3 * sizeof(double);
+    if (e == cudaSuccess && row0 > 0) e = cudaMemcpyAsync(x_out, x_in, rb * row0, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && row1 < h->n)
+        e = cudaMemcpyAsync(x_out + 3 * static_cast<size_t>(row1), x_in + 3 * static_cast<size_t>(row1),
+                            rb * (h->n - row1), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e, "sharded step");
+    h->cur = 1 - h->cur;
+    h->cells_valid = false;
     return SD_OK;
 }
 

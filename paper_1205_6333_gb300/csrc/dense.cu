@@ -57,7 +57,7 @@ template <int TENSOR, int MODE, bool PER>
 __global__ void __launch_bounds__(kNT) dense_kernel(const typename DenseT<MODE>::V4 *__restrict__ pos,
                                                     const typename DenseT<MODE>::V4 *__restrict__ frc,
                                                     double *__restrict__ part, int npad, DenseGeom g, PairConst c,
-                                                    int *__restrict__ err, long long wd) {
+                                                    int *__restrict__ err, long long wd, TileWin w) {
     using V4 = typename DenseT<MODE>::V4;
     using S = typename DenseT<MODE>::S;
     constexpr int R = DenseT<MODE>::R;
@@ -69,8 +69,11 @@ __global__ void __launch_bounds__(kNT) dense_kernel(const typename DenseT<MODE>:
 
     const int tid = threadIdx.x;
     const long long T = static_cast<long long>(g.nIB) * g.nJT;
-    const long long t0 = static_cast<long long>(blockIdx.x) * g.chunk;
-    const long long t1 = (t0 + g.chunk < T) ? t0 + g.chunk : T;
+    const int cta = static_cast<int>(blockIdx.x) + w.b0;   // index in the full launch
+    const long long tb = static_cast<long long>(cta) * g.chunk;
+    const long long thi = (w.hi >= 0 && w.hi < T) ? w.hi : T;
+    const long long t0 = tb > w.lo ? tb : w.lo;
+    const long long t1 = (tb + g.chunk < thi) ? tb + g.chunk : thi;
     if (t0 >= t1) return;  // uniform over the CTA
     const uint32_t tile_bytes = static_cast<uint32_t>(g.J * sizeof(V4));
 
@@ -98,7 +101,7 @@ __global__ void __launch_bounds__(kNT) dense_kernel(const typename DenseT<MODE>:
     bool aborted = false;
 
     auto flush = [&](int ib) {
-        const int slot = static_cast<int>(blockIdx.x) - geom_first(g, ib);
+        const int slot = cta - geom_first(g, ib);
         double *dst = part + static_cast<size_t>(slot) * 3 * npad;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
@@ -221,7 +224,7 @@ template <int TENSOR, bool COMP, bool PER>
 __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ pos, const float *__restrict__ frc,
                                                      double *__restrict__ part, int npad, DenseGeom g, PairConst2 c,
                                                      const int *__restrict__ flag, int *__restrict__ err,
-                                                     long long wd) {
+                                                     long long wd, TileWin w) {
     constexpr int R = kR32;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -231,8 +234,11 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
 
     const int tid = threadIdx.x;
     const long long T = static_cast<long long>(g.nIB) * g.nJT;
-    const long long t0 = static_cast<long long>(blockIdx.x) * g.chunk;
-    const long long t1 = (t0 + g.chunk < T) ? t0 + g.chunk : T;
+    const int cta = static_cast<int>(blockIdx.x) + w.b0;   // index in the full launch
+    const long long tb = static_cast<long long>(cta) * g.chunk;
+    const long long thi = (w.hi >= 0 && w.hi < T) ? w.hi : T;
+    const long long t0 = tb > w.lo ? tb : w.lo;
+    const long long t1 = (tb + g.chunk < thi) ? tb + g.chunk : thi;
     if (t0 >= t1) return;
     const uint32_t arr_bytes = static_cast<uint32_t>(g.J * sizeof(float));
 
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
     const bool clamp_all = *flag != 0;
 
     auto flush = [&](int ib) {
-        const int slot = static_cast<int>(blockIdx.x) - geom_first(g, ib);
+        const int slot = cta - geom_first(g, ib);
         double *dst = part + static_cast<size_t>(slot) * 3 * npad;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
@@ -709,18 +715,19 @@ cudaError_t dense_setup(sd_handle *h) {
 }
 
 template <bool PER>
-static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part) {
+static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part, const TileWin &w,
+                           int grid) {
     const DenseGeom &g = h->geom;
     const size_t smem = dense_smem(h->mode, g.J);
     const bool oseen = h->tensor == T_OSEEN;
     if (h->mode == MODE_FP64) {
         const dbl4 *p = static_cast<const dbl4 *>(posm.aos), *f = static_cast<const dbl4 *>(frcm.aos);
         if (oseen)
-            dense_kernel<T_OSEEN, MODE_FP64, PER><<<g.grid, kNT, smem, st>>>(p, f, part, h->npad, g, h->pc,
-                                                                              h->d_err, h->watchdog);
+            dense_kernel<T_OSEEN, MODE_FP64, PER><<<grid, kNT, smem, st>>>(p, f, part, h->npad, g, h->pc,
+                                                                            h->d_err, h->watchdog, w);
         else
-            dense_kernel<T_RP, MODE_FP64, PER><<<g.grid, kNT, smem, st>>>(p, f, part, h->npad, g, h->pc, h->d_err,
-                                                                           h->watchdog);
+            dense_kernel<T_RP, MODE_FP64, PER><<<grid, kNT, smem, st>>>(p, f, part, h->npad, g, h->pc, h->d_err,
+                                                                         h->watchdog, w);
         return;
     }
     PairConst2 c2{};
@@ -747,8 +754,8 @@ static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror fr
         return;
     }
 #define SD_D2(TT, CC)                                                                                          \
-    dense2_kernel<TT, CC, PER><<<g.grid, kNT, smem, st>>>(posm.soa, frcm.soa, part, h->npad, g, c2, h->d_flag, \
-                                                          h->d_err, h->watchdog)
+    dense2_kernel<TT, CC, PER><<<grid, kNT, smem, st>>>(posm.soa, frcm.soa, part, h->npad, g, c2, h->d_flag, \
+                                                        h->d_err, h->watchdog, w)
     if (oseen) {
         if (comp) SD_D2(T_OSEEN, true); else SD_D2(T_OSEEN, false);
     } else {
@@ -757,12 +764,25 @@ static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror fr
 #undef SD_D2
 }
 
-cudaError_t launch_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part) {
+cudaError_t launch_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part,
+                         const TileWin *win) {
+    const DenseGeom &g = h->geom;
+    TileWin w{};
+    int grid = g.grid;
+    if (win) {   // a shard of whole i-blocks (directed kernels only): the CTAs of the full launch touching it
+        if (g.sym) return cudaErrorInvalidValue;
+        w = *win;
+        const long long T = static_cast<long long>(g.nIB) * g.nJT;
+        const long long hi = (w.hi >= 0 && w.hi < T) ? w.hi : T;
+        if (w.lo >= hi) return cudaSuccess;
+        w.b0 = static_cast<int>(w.lo / g.chunk);
+        grid = static_cast<int>((hi - 1) / g.chunk) - w.b0 + 1;
+    }
     prof_begin(h, SD_KERNEL_DENSE, st);
     if (h->pc.periodic)
-        launch_dense_t<true>(h, st, posm, frcm, part);
+        launch_dense_t<true>(h, st, posm, frcm, part, w, grid);
     else
-        launch_dense_t<false>(h, st, posm, frcm, part);
+        launch_dense_t<false>(h, st, posm, frcm, part, w, grid);
     prof_end(h, SD_KERNEL_DENSE, st);
     ++h->launches;
     return cudaGetLastError();

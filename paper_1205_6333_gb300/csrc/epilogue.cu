@@ -371,6 +371,7 @@ struct EpiArgs {
     double *x64n;
     double *vlag;   // OUT_EULER with lubrication: this step's FP64 velocities, for the next step's forces
     int *err;
+    int row0, row1; // rows written (a shard); vout holds rows row0 .. row1-1
 };
 
 // Each CTA finishes 32 consecutive particles.  Warp w of the kEpiWarps adds the
@@ -396,8 +397,8 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // CTAs in reverse particle order: the last blocks have the longest source-side
     // columns, so they start first instead of forming the tail
-    const int i = (gridDim.x - 1 - blockIdx.x) * 32 + lane;
-    const bool active = i < a.n;
+    const int i = a.row0 + (gridDim.x - 1 - blockIdx.x) * 32 + lane;
+    const bool active = i < a.row1;
 
     // This warp's share of the dense sum: the CTA slots of the particle's i-block,
     // then (symmetric kernel) the source-side slots of the tiles (r, ib), r < ib.
@@ -483,15 +484,15 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
     const double m0 = a.pc.mu0;
     const double v0 = m0 * V[0], v1 = m0 * V[1], v2 = m0 * V[2];
     if constexpr (OUT == OUT_F32) {
-        float *o = static_cast<float *>(a.vout);
-        o[3 * i] = static_cast<float>(v0);
-        o[3 * i + 1] = static_cast<float>(v1);
-        o[3 * i + 2] = static_cast<float>(v2);
+        float *o = static_cast<float *>(a.vout) + 3 * static_cast<size_t>(i - a.row0);
+        o[0] = static_cast<float>(v0);
+        o[1] = static_cast<float>(v1);
+        o[2] = static_cast<float>(v2);
     } else if constexpr (OUT == OUT_F64) {
-        double *o = static_cast<double *>(a.vout);
-        o[3 * i] = v0;
-        o[3 * i + 1] = v1;
-        o[3 * i + 2] = v2;
+        double *o = static_cast<double *>(a.vout) + 3 * static_cast<size_t>(i - a.row0);
+        o[0] = v0;
+        o[1] = v1;
+        o[2] = v2;
     } else {
         const double xi = a.x64[3 * i], yi = a.x64[3 * i + 1], zi = a.x64[3 * i + 2];
         const double nx = xi + a.dt * v0, ny = yi + a.dt * v1, nz = zi + a.dt * v2;
@@ -526,8 +527,12 @@ static void epi_launch_mode(int mode, int out, int nb, cudaStream_t st, const Ep
 }
 
 cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double *x64, const void *posm,
-                            const double *F64, const void *frcm, void *vout, double dt, double *x64n) {
+                            const double *F64, const void *frcm, void *vout, double dt, double *x64n, int row0,
+                            int row1) {
     if (h->n == 0) return cudaSuccess;
+    if (row1 < 0 || row1 > h->n) row1 = h->n;
+    if (row0 < 0) row0 = 0;
+    if (row0 >= row1) return cudaSuccess;
     EpiArgs a;
     a.ent_out = h->near_out;
     a.noff = h->near_off;
@@ -549,7 +554,9 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
     a.x64n = x64n;
     a.vlag = (out == OUT_EULER && h->lub) ? h->vlag : nullptr;
     a.err = h->d_err;
-    const int nb = (h->n + 31) / 32;
+    a.row0 = row0;
+    a.row1 = row1;
+    const int nb = (row1 - row0 + 31) / 32;
     prof_begin(h, SD_KERNEL_EPILOGUE, st);
     if (h->tensor == T_OSEEN)
         epi_launch_mode<T_OSEEN>(h->mode, out, nb, st, a);

@@ -60,6 +60,15 @@ struct DenseGeom {
     long long nT;   // tiles
 };
 
+// A window on the directed kernels' persistent grid, for a shard of rows: the CTAs
+// b0 .. b0 + grid - 1 of the full launch, restricted to the tiles [lo, hi) (whole
+// i-blocks).  Every CTA computes the same partial sums for the rows it keeps as in
+// the full launch, so a shard's rows are bit-identical to the unsharded result.
+struct TileWin {
+    long long lo = 0, hi = -1;   // hi < 0: every tile
+    int b0 = 0;
+};
+
 // In a periodic box the padding entries n .. npad-1 have no far-away position under
 // the nearest image, so a tile whose i- or j-range reaches index n clamps r^2 (its
 // padding terms stay exactly zero).  (The particle count travels with the pair
@@ -237,12 +246,14 @@ cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64);
 cudaError_t launch_pad_mirror(sd_handle *h, cudaStream_t st, Mirror m);
 // dense.cu
 cudaError_t dense_setup(sd_handle *h);
-cudaError_t launch_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part);
+cudaError_t launch_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part,
+                         const TileWin *win = nullptr);
 // epilogue.cu
 cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const void *posm, const double *F64,
                         const void *frcm);
 cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double *x64, const void *posm,
-                            const double *F64, const void *frcm, void *vout, double dt, double *x64n);
+                            const double *F64, const void *frcm, void *vout, double dt, double *x64n, int row0 = 0,
+                            int row1 = -1);
 // vjp.cu
 cudaError_t vjp_setup(sd_handle *h);
 cudaError_t launch_vjp_dense(sd_handle *h, cudaStream_t st, const void *posm, const void *frcm, const void *wm,
