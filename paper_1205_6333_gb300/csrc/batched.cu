@@ -25,6 +25,7 @@
 #include <new>
 #include <string>
 #include <type_traits>
+#include <tuple>
 #include <vector>
 
 #include "sd_internal.h"
@@ -49,7 +50,11 @@ struct sd_batch {
     sd::Allocator al;
     sd::PairConst pc{};
     int32_t *d_off = nullptr, *d_order = nullptr;
-    double *x64 = nullptr, *F64 = nullptr, *fext64 = nullptr;
+    // largest-first layout of the FP32C block kernel (see batched_blocks_kernel)
+    int32_t *qperm = nullptr, *qcl = nullptr, *cbeg = nullptr, *cend = nullptr, *canchor = nullptr;
+    double *x64[2] = {nullptr, nullptr};   // position ping-pong: step reads x64[cur], writes the other
+    int cur = 0;
+    double *F64 = nullptr, *fext64 = nullptr;
     void *frcm = nullptr;
     unsigned long long *ctr = nullptr;
     int *d_err = nullptr;
@@ -58,7 +63,7 @@ struct sd_batch {
     int choice = -1;
     cudaGraphExec_t gexec = nullptr;
     double g_dt = 0.0;
-    int g_choice = -1;
+    int g_choice = -1, g_cur = -1;
     int64_t launches = 0;
     sd::Profiler prof;
     long long watchdog = sd::kDefaultWatchdog;
@@ -79,7 +84,10 @@ struct BT<MODE_FP64> {
 
 struct BatchArgs {
     const int32_t *off, *order;
-    double *x64;
+    const int32_t *qperm, *qcl, *cbeg, *cend, *canchor;
+    int P, nblk;
+    const double *x64;   // positions of this step
+    double *x64n;        // positions after it
     const double *F64;
     const void *frcm;
     unsigned long long *ctr;
@@ -238,231 +246,23 @@ __device__ __forceinline__ void cluster_compute(const BatchArgs &a, int o, int n
         const double vz = m0 * (V2 + a.F64[3 * g + 2]);
         const double nx = a.x64[3 * g] + dt * vx, ny = a.x64[3 * g + 1] + dt * vy, nz = a.x64[3 * g + 2] + dt * vz;
         if (!isfinite(nx) || !isfinite(ny) || !isfinite(nz)) atomicOr(a.err, DEV_ERR_NONFINITE);
-        a.x64[3 * g] = nx;
-        a.x64[3 * g + 1] = ny;
-        a.x64[3 * g + 2] = nz;
+        a.x64n[3 * g] = nx;
+        a.x64n[3 * g + 1] = ny;
+        a.x64n[3 * g + 2] = nz;
     }
     if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
     (void)anchor;
 }
 
-// FP32C path.  Shared layout of one staged particle: (x, x, y, y, z, z, Fx, Fx,
-// Fy, Fy, Fz, Fz) -- every source value duplicated, so that three 128-bit loads
-// give the six packed operands (v, v) that pair two targets (slots k0, k1 of the
-// lane) against the same source in one f32x2 instruction.
-constexpr int kDup = 12;
-constexpr int kOvlCap = 16;   // overlapping pairs a lane can list per cluster
+// FP64 path: one warp per cluster, scalar FP64 pairs.
+constexpr size_t kWarpStage = 2 * kMaxCluster * sizeof(dbl4);
 
-template <int TENSOR, int RP>
-__device__ __forceinline__ void cluster_packed(const BatchArgs &a, int o, int n, const float *s_dup, float *s_acc,
-                                               int *s_ovl, int lane) {
-    constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
-    constexpr int R = 2 * RP;   // target slots per lane, i = lane + 32 k
-    PairConst2 c2{};
-    c2.c1 = pk2(a.pc.c1_f, a.pc.c1_f);
-    c2.c3 = pk2(a.pc.c3_f, a.pc.c3_f);
-    c2.m3c3 = pk2(a.pc.m3c3_f, a.pc.m3c3_f);
-    c2.r2min = a.pc.r2min_f;
-    const float r2min = a.pc.r2min_f;
-    float xs[R], ys[R], zs[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        // slots beyond n sit far from everything (their results are discarded)
-        const int i = lane + 32 * k;
-        const bool real = i < n;
-        xs[k] = real ? s_dup[i * kDup] : -1.0e15f;
-        ys[k] = real ? s_dup[i * kDup + 2] : 0.0f;
-        zs[k] = real ? s_dup[i * kDup + 4] : 0.0f;
-        for (int d = 0; d < 6; ++d) s_acc[(k * 6 + d) * 32 + lane] = 0.0f;
-    }
-    f2 XI[RP], YI[RP], ZI[RP], AX[RP], AY[RP], AZ[RP];
-#pragma unroll
-    for (int q = 0; q < RP; ++q) {
-        XI[q] = pk2(xs[2 * q], xs[2 * q + 1]);
-        YI[q] = pk2(ys[2 * q], ys[2 * q + 1]);
-        ZI[q] = pk2(zs[2 * q], zs[2 * q + 1]);
-        AX[q] = AY[q] = AZ[q] = 0ull;
-    }
-    // every pair the loop clamps (r < 2a, never the self pair) is listed as
-    // (slot << 16 | source) in this lane's column of s_ovl; novl counts them all
-    int novl = 0;
-    auto note = [&](int k, int j) {
-        if (novl < kOvlCap) s_ovl[novl * 32 + lane] = (k << 16) | j;
-        ++novl;
-    };
-    const uint32_t base = smem_addr(s_dup);
-    const int nchunk = (n + 31) >> 5;
-    for (int jb = 0; jb < nchunk; ++jb) {
-        // m = 0: the source is particle 32 jb + lane, i.e. slot jb meets itself --
-        // skip that one pair, evaluate the others in scalar form
-        {
-            const int j = 32 * jb + lane;
-            const float4 pj = make_float4(s_dup[j * kDup], s_dup[j * kDup + 2], s_dup[j * kDup + 4], 0.0f);
-            const float4 fj = make_float4(s_dup[j * kDup + 6], s_dup[j * kDup + 8], s_dup[j * kDup + 10], 0.0f);
-#pragma unroll
-            for (int q = 0; q < RP; ++q) {
-                float t[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int k = 2 * q + h;
-                    if (k == jb) continue;
-                    const float dx = __fsub_rn(xs[k], pj.x), dy = __fsub_rn(ys[k], pj.y), dz = __fsub_rn(zs[k], pj.z);
-                    if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) note(k, j);
-                    pair_f32<TD, true>(xs[k], ys[k], zs[k], pj, fj, a.pc, t[h][0], t[h][1], t[h][2]);
-                }
-                AX[q] = add2(AX[q], pk2(t[0][0], t[1][0]));
-                AY[q] = add2(AY[q], pk2(t[0][1], t[1][1]));
-                AZ[q] = add2(AZ[q], pk2(t[0][2], t[1][2]));
-            }
-        }
-        // m = 1..31: lane-rotated sources, two targets per packed instruction, in
-        // groups of G; after each group one warp vote on the group's minimum r^2,
-        // and only if some lane met a source closer than 2a are that group's
-        // sources rescanned and the overlapping pairs listed (rare)
-        auto group = [&](int m0, auto G) {
-            constexpr int NG = decltype(G)::value;
-            float mg[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) mg[k] = 1.0e30f;
-#pragma unroll
-            for (int mm = 0; mm < NG; ++mm) {
-                const int j = 32 * jb + ((lane + m0 + mm) & 31);
-                const uint32_t pa = base + static_cast<uint32_t>(j * kDup * 4);
-                f2 PX, PY, PZ, FX, FY, FZ;
-                asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(PX), "=l"(PY) : "r"(pa));
-                asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(PZ), "=l"(FX) : "r"(pa + 16));
-                asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(FY), "=l"(FZ) : "r"(pa + 32));
-#pragma unroll
-                for (int q = 0; q < RP; ++q) {
-                    float ra, rb;
-                    pair_f32x2_t<TD, true, true>(XI[q], YI[q], ZI[q], PX, PY, PZ, FX, FY, FZ, c2, AX[q], AY[q],
-                                                 AZ[q], ra, rb);
-                    mg[2 * q] = fminf(mg[2 * q], ra);
-                    mg[2 * q + 1] = fminf(mg[2 * q + 1], rb);
-                }
-            }
-            bool any = false;
-#pragma unroll
-            for (int k = 0; k < R; ++k) any |= mg[k] < r2min;
-            if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-                for (int k = 0; k < R; ++k) {
-                    if (!(mg[k] < r2min)) continue;
-                    for (int mm = 0; mm < NG; ++mm) {
-                        const int j = 32 * jb + ((lane + m0 + mm) & 31);
-                        const float dx = __fsub_rn(xs[k], s_dup[j * kDup]), dy = __fsub_rn(ys[k], s_dup[j * kDup + 2]),
-                                    dz = __fsub_rn(zs[k], s_dup[j * kDup + 4]);
-                        if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) note(k, j);
-                    }
-                }
-            }
-        };
-        for (int m0 = 1; m0 < 29; m0 += 4) group(m0, std::integral_constant<int, 4>{});
-        group(29, std::integral_constant<int, 3>{});
-        // every 4 chunks (128 sources) and at the end: fold both lanes of every
-        // packed accumulator into its slot's (hi, lo)
-        if (((jb + 1) & 3) != 0 && jb + 1 != nchunk) continue;
-#pragma unroll
-        for (int q = 0; q < RP; ++q) {
-            const f2 acc[3] = {AX[q], AY[q], AZ[q]};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                float v0, v1;
-                upk2(acc[d], v0, v1);
-                float *q0 = s_acc + (2 * q * 6) * 32 + lane;
-                float *q1 = s_acc + ((2 * q + 1) * 6) * 32 + lane;
-                float h0 = q0[d * 32], l0 = q0[(3 + d) * 32], h1 = q1[d * 32], l1 = q1[(3 + d) * 32];
-                fold2(h0, l0, v0);
-                fold2(h1, l1, v1);
-                q0[d * 32] = h0;
-                q0[(3 + d) * 32] = l0;
-                q1[d * 32] = h1;
-                q1[(3 + d) * 32] = l1;
-            }
-            AX[q] = AY[q] = AZ[q] = 0ull;
-        }
-    }
-    // per slot: compensated sum with the self term mu_ii = mu0 I joined as
-    // (hi + F) + lo; then the clamped terms of the listed overlapping pairs are
-    // swapped for exact ones; the velocity and dt v stay in FP32 (FP64 throughput
-    // is scarce on GB300), only x += dt v is FP64
-    float V[R][3];
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const int i = lane + 32 * k;
-        const int ic = i < n ? i : 0;
-        const float *qa = s_acc + (k * 6) * 32 + lane;
-        for (int d = 0; d < 3; ++d) {
-            float h, e;
-            two_sum(qa[d * 32], s_dup[ic * kDup + 6 + 2 * d], h, e);
-            V[k][d] = __fadd_rn(h, __fadd_rn(e, qa[(3 + d) * 32]));
-        }
-    }
-    bool coincident = false;
-    auto fix = [&](int k, int j) {
-        const float4 pi = make_float4(xs[k], ys[k], zs[k], 0.0f);
-        const float4 pj = make_float4(s_dup[j * kDup], s_dup[j * kDup + 2], s_dup[j * kDup + 4], 0.0f);
-        const float4 fj = make_float4(s_dup[j * kDup + 6], s_dup[j * kDup + 8], s_dup[j * kDup + 10], 0.0f);
-        const float dx = __fsub_rn(pi.x, pj.x), dy = __fsub_rn(pi.y, pj.y), dz = __fsub_rn(pi.z, pj.z);
-        float cx = 0.f, cy = 0.f, cz = 0.f, ex, ey, ez;
-        pair_f32<TD, true>(pi.x, pi.y, pi.z, pj, fj, a.pc, cx, cy, cz);
-        exact_pair<TENSOR, float>(dx, dy, dz, fj.x, fj.y, fj.z, a.pc, ex, ey, ez, coincident);
-        const float c[3] = {__fsub_rn(ex, cx), __fsub_rn(ey, cy), __fsub_rn(ez, cz)};
-#pragma unroll
-        for (int kk = 0; kk < R; ++kk)
-            if (kk == k)
-                for (int d = 0; d < 3; ++d) V[kk][d] = __fadd_rn(V[kk][d], c[d]);
-    };
-    if (novl <= kOvlCap) {
-        for (int e = 0; e < novl; ++e) {
-            const int code = s_ovl[e * 32 + lane];
-            const int k = code >> 16, j = code & 0xffff;
-            if (k < R && j < n) fix(k, j);   // every counted entry was written by this cluster
-        }
-    } else {
-        // list overflow (more than kOvlCap overlapping pairs on this lane): scan
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const int i = lane + 32 * k;
-            if (i >= n) continue;
-            for (int j = 0; j < n; ++j) {
-                if (j == i) continue;
-                const float dx = __fsub_rn(xs[k], s_dup[j * kDup]), dy = __fsub_rn(ys[k], s_dup[j * kDup + 2]),
-                            dz = __fsub_rn(zs[k], s_dup[j * kDup + 4]);
-                if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) fix(k, j);
-            }
-        }
-    }
-    const float m0dt = static_cast<float>(a.pc.mu0 * a.dt);
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const int i = lane + 32 * k;
-        if (i >= n) continue;
-        const size_t g = static_cast<size_t>(o + i);
-        const double nx = a.x64[3 * g] + static_cast<double>(__fmul_rn(m0dt, V[k][0]));
-        const double ny = a.x64[3 * g + 1] + static_cast<double>(__fmul_rn(m0dt, V[k][1]));
-        const double nz = a.x64[3 * g + 2] + static_cast<double>(__fmul_rn(m0dt, V[k][2]));
-        if (!isfinite(nx) || !isfinite(ny) || !isfinite(nz)) atomicOr(a.err, DEV_ERR_NONFINITE);
-        a.x64[3 * g] = nx;
-        a.x64[3 * g + 1] = ny;
-        a.x64[3 * g + 2] = nz;
-    }
-    if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
-}
-
-template <int MODE>
-__host__ __device__ constexpr size_t warp_stage_size() {
-    return MODE == MODE_FP64 ? 2 * kMaxCluster * sizeof(dbl4)
-                             : (kMaxCluster * kDup + kMaxR * 6 * 32 + kOvlCap * 32) * sizeof(float);
-}
-
-template <int TENSOR, int MODE>
+template <int TENSOR>
 __global__ void batched_kernel(BatchArgs a) {
-    using V4 = typename BT<MODE>::V4;
-    constexpr size_t stage_bytes = warp_stage_size<MODE>();
+    using V4 = dbl4;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned char *mine = smem + static_cast<size_t>(wid) * stage_bytes;
+    unsigned char *mine = smem + static_cast<size_t>(wid) * kWarpStage;
     const V4 *frcm = static_cast<const V4 *>(a.frcm);
     for (;;) {
         unsigned long long t = 0;
@@ -479,89 +279,199 @@ __global__ void batched_kernel(BatchArgs a) {
         }
         const double3 anchor = make_double3(a.x64[3 * o], a.x64[3 * o + 1], a.x64[3 * o + 2]);
         const int R = (n + 31) >> 5;
-        if constexpr (MODE == MODE_FP64) {
-            V4 *s_pos = reinterpret_cast<V4 *>(mine);
-            V4 *s_frc = s_pos + kMaxCluster;
-            for (int p = lane; p < 32 * R; p += 32) {
-                V4 q, f;
-                if (p < n) {
-                    const size_t g = static_cast<size_t>(o + p);
-                    q.x = a.x64[3 * g] - anchor.x;
-                    q.y = a.x64[3 * g + 1] - anchor.y;
-                    q.z = a.x64[3 * g + 2] - anchor.z;
-                    f = frcm[g];
-                } else {
-                    // padding: far away (and far from the unused i-slots at -1e15), zero force
-                    q.x = 1.0e15;
-                    q.y = 0;
-                    q.z = 0;
-                    f.x = f.y = f.z = 0;
-                }
-                q.w = 0;
-                f.w = 0;
-                s_pos[p] = q;
-                s_frc[p] = f;
+        V4 *s_pos = reinterpret_cast<V4 *>(mine);
+        V4 *s_frc = s_pos + kMaxCluster;
+        for (int p = lane; p < 32 * R; p += 32) {
+            V4 q, f;
+            if (p < n) {
+                const size_t g = static_cast<size_t>(o + p);
+                q.x = a.x64[3 * g] - anchor.x;
+                q.y = a.x64[3 * g + 1] - anchor.y;
+                q.z = a.x64[3 * g + 2] - anchor.z;
+                f = frcm[g];
+            } else {
+                // padding: far away (and far from the unused i-slots at -1e15), zero force
+                q.x = 1.0e15;
+                q.y = 0;
+                q.z = 0;
+                f.x = f.y = f.z = 0;
             }
-            __syncwarp();
-            switch (R) {
+            q.w = 0;
+            f.w = 0;
+            s_pos[p] = q;
+            s_frc[p] = f;
+        }
+        __syncwarp();
+        switch (R) {
 #define SD_BR(RR) \
-    case RR: cluster_compute<TENSOR, MODE, RR>(a, o, n, anchor, s_pos, s_frc, nullptr, lane); break
-                SD_BR(1); SD_BR(2); SD_BR(3); SD_BR(4); SD_BR(5); SD_BR(6); SD_BR(7); SD_BR(8);
+    case RR: cluster_compute<TENSOR, MODE_FP64, RR>(a, o, n, anchor, s_pos, s_frc, nullptr, lane); break
+            SD_BR(1); SD_BR(2); SD_BR(3); SD_BR(4); SD_BR(5); SD_BR(6); SD_BR(7); SD_BR(8);
 #undef SD_BR
-                default: break;
-            }
-        } else {
-            float *s_dup = reinterpret_cast<float *>(mine);
-            float *s_acc = s_dup + kMaxCluster * kDup;
-            int *s_ovl = reinterpret_cast<int *>(s_acc + kMaxR * 6 * 32);
-            const int RP = (R + 1) >> 1;
-            for (int p = lane; p < 64 * RP; p += 32) {
-                float v[6];
-                if (p < n) {
-                    const size_t g = static_cast<size_t>(o + p);
-                    const V4 f = frcm[g];
-                    v[0] = static_cast<float>(a.x64[3 * g] - anchor.x);
-                    v[1] = static_cast<float>(a.x64[3 * g + 1] - anchor.y);
-                    v[2] = static_cast<float>(a.x64[3 * g + 2] - anchor.z);
-                    v[3] = f.x;
-                    v[4] = f.y;
-                    v[5] = f.z;
-                } else {
-                    // padding: far away (and far from the unused target slots at -1e15), zero force
-                    v[0] = 1.0e15f;
-                    v[1] = v[2] = v[3] = v[4] = v[5] = 0.0f;
-                }
-                float4 *d = reinterpret_cast<float4 *>(s_dup + p * kDup);
-                d[0] = make_float4(v[0], v[0], v[1], v[1]);
-                d[1] = make_float4(v[2], v[2], v[3], v[3]);
-                d[2] = make_float4(v[4], v[4], v[5], v[5]);
-            }
-            __syncwarp();
-            switch (RP) {
-                case 1: cluster_packed<TENSOR, 1>(a, o, n, s_dup, s_acc, s_ovl, lane); break;
-                case 2: cluster_packed<TENSOR, 2>(a, o, n, s_dup, s_acc, s_ovl, lane); break;
-                case 3: cluster_packed<TENSOR, 3>(a, o, n, s_dup, s_acc, s_ovl, lane); break;
-                case 4: cluster_packed<TENSOR, 4>(a, o, n, s_dup, s_acc, s_ovl, lane); break;
-                default: break;
-            }
+            default: break;
         }
         __syncwarp();
     }
 }
 
-static size_t stage_bytes(int mode) {
-    return mode == MODE_FP64 ? warp_stage_size<MODE_FP64>() : warp_stage_size<MODE_FP32C>();
+// FP32C path: target blocks.  At creation the clusters are laid out largest
+// first (a longest-processing-time order) as one sequence of P particles,
+// position q of the sequence being particle qperm[q] of cluster qcl[q] (whose
+// particles are the positions cbeg .. cend-1).  A persistent CTA of BT threads
+// pops blocks of BT consecutive positions from a ticket counter, so each thread
+// has a target and neighbouring targets belong to clusters of equal or
+// near-equal size (their loops are as long).  The CTA stages every cluster its
+// block touches -- at most BT + 2 (256 - 1) particles -- in shared memory as SoA
+// floats: positions relative to each cluster's first particle (FP64 difference,
+// then rounded, so FP32 separations keep full relative precision) and forces.
+// Each thread then sums over its own cluster with packed pairs (two sources per
+// f32x2 instruction, read as broadcasts), r^2 clamped to (2a)^2 throughout:
+//   * the self pair is met once and its clamped term subtracted again, as
+//     mu_ii = mu0 I joins the sum;
+//   * pairs with r < 2a are counted on the way; only a target that met one
+//     rescans its cluster and swaps those clamped terms for exact ones.
+// Both packed lanes, the scalar edge terms and the self terms meet in a TwoSum
+// (hi, lo) sum; v stays FP32, x_{n+1} = x_n + dt v in FP64.  Positions are read
+// from x64 and written to x64n (a cluster may span two blocks).
+constexpr int kStageExtra = 2 * (kMaxCluster - 1);
+
+template <int BT>
+__host__ __device__ constexpr int block_stage_len() {
+    return ((BT + kStageExtra) + 3) & ~3;   // per SoA array, floats (16-byte multiple)
 }
 
-static void *batched_fn(int tensor, int mode) {
-    if (mode == MODE_FP64) {
-        if (tensor == T_RPY) return reinterpret_cast<void *>(&batched_kernel<T_RPY, MODE_FP64>);
-        if (tensor == T_RP) return reinterpret_cast<void *>(&batched_kernel<T_RP, MODE_FP64>);
-        return reinterpret_cast<void *>(&batched_kernel<T_OSEEN, MODE_FP64>);
+template <int TENSOR, int BT>
+__global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
+    constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
+    constexpr int L = block_stage_len<BT>();
+    extern __shared__ __align__(16) float s_src[];   // [6][L]: x y z Fx Fy Fz
+    __shared__ int s_blk;
+    const int tid = threadIdx.x;
+    const float4 *frcm = static_cast<const float4 *>(a.frcm);
+    PairConst2 c2{};
+    c2.c1 = pk2(a.pc.c1_f, a.pc.c1_f);
+    c2.c3 = pk2(a.pc.c3_f, a.pc.c3_f);
+    c2.m3c3 = pk2(a.pc.m3c3_f, a.pc.m3c3_f);
+    c2.r2min = a.pc.r2min_f;
+    const float r2min = a.pc.r2min_f;
+    const float m0dt = static_cast<float>(a.pc.mu0 * a.dt);
+    for (;;) {
+        if (tid == 0) s_blk = static_cast<int>(atomicAdd(a.ctr, 1ULL));
+        __syncthreads();
+        const int blk = s_blk;
+        if (blk >= a.nblk) break;   // uniform over the CTA
+        const int q0 = blk * BT, q1 = min(q0 + BT, a.P);
+        const int s0 = a.cbeg[a.qcl[q0]], s1 = a.cend[a.qcl[q1 - 1]];   // s1 - s0 <= BT + kStageExtra
+        for (int k = s0 + tid; k < s1; k += BT) {
+            const int p = a.qperm[k];
+            const int anc = a.canchor[a.qcl[k]];
+            const float4 f = frcm[p];
+            const int l = k - s0;
+            s_src[l] = static_cast<float>(a.x64[3 * static_cast<size_t>(p)] - a.x64[3 * static_cast<size_t>(anc)]);
+            s_src[L + l] = static_cast<float>(a.x64[3 * static_cast<size_t>(p) + 1] -
+                                              a.x64[3 * static_cast<size_t>(anc) + 1]);
+            s_src[2 * L + l] = static_cast<float>(a.x64[3 * static_cast<size_t>(p) + 2] -
+                                                  a.x64[3 * static_cast<size_t>(anc) + 2]);
+            s_src[3 * L + l] = f.x;
+            s_src[4 * L + l] = f.y;
+            s_src[5 * L + l] = f.z;
+        }
+        __syncthreads();
+        const int q = q0 + tid;
+        if (q < q1) {
+            const int cq = a.qcl[q];
+            const int beg = a.cbeg[cq] - s0, end = a.cend[cq] - s0, me = q - s0;
+            const float xi = s_src[me], yi = s_src[L + me], zi = s_src[2 * L + me];
+            const float4 pi = make_float4(xi, yi, zi, 0.0f);
+            const float4 fi = make_float4(s_src[3 * L + me], s_src[4 * L + me], s_src[5 * L + me], 0.0f);
+            const f2 XI = pk2(xi, xi), YI = pk2(yi, yi), ZI = pk2(zi, zi);
+            f2 AX = 0ull, AY = 0ull, AZ = 0ull;
+            float tx = 0.0f, ty = 0.0f, tz = 0.0f;
+            int close = 0;   // pairs with r^2 < (2a)^2, the self pair included
+            auto scalar = [&](int j) {
+                const float4 pj = make_float4(s_src[j], s_src[L + j], s_src[2 * L + j], 0.0f);
+                const float4 fj = make_float4(s_src[3 * L + j], s_src[4 * L + j], s_src[5 * L + j], 0.0f);
+                const float dx = __fsub_rn(xi, pj.x), dy = __fsub_rn(yi, pj.y), dz = __fsub_rn(zi, pj.z);
+                close += __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min;
+                pair_f32<TD, true>(xi, yi, zi, pj, fj, a.pc, tx, ty, tz);
+            };
+            int j = beg;
+            if (j & 1) scalar(j++);   // packed loads need an even index
+            const f2 *sp = reinterpret_cast<const f2 *>(s_src);
+            constexpr int LH = L / 2;
+#pragma unroll 2
+            for (; j + 1 < end; j += 2) {
+                const int h = j >> 1;
+                const f2 PX = sp[h], PY = sp[LH + h], PZ = sp[2 * LH + h];
+                const f2 FX = sp[3 * LH + h], FY = sp[4 * LH + h], FZ = sp[5 * LH + h];
+                float ra, rb;
+                pair_f32x2_t<TD, true, true>(XI, YI, ZI, PX, PY, PZ, FX, FY, FZ, c2, AX, AY, AZ, ra, rb);
+                close += (ra < r2min) + (rb < r2min);
+            }
+            if (j < end) scalar(j);
+            // the clamped self term, met once in the loop, bit for bit
+            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+            pair_f32<TD, true>(xi, yi, zi, pi, fi, a.pc, sx, sy, sz);
+            const f2 acc[3] = {AX, AY, AZ};
+            const float tsc[3] = {tx, ty, tz}, ssc[3] = {sx, sy, sz}, fsc[3] = {fi.x, fi.y, fi.z};
+            float V[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                float lo, hi, h, l;
+                upk2(acc[d], lo, hi);
+                two_sum(lo, hi, h, l);
+                fold2(h, l, tsc[d]);
+                fold2(h, l, -ssc[d]);
+                fold2(h, l, fsc[d]);   // mu_ii F_i / mu0 = F_i
+                V[d] = __fadd_rn(h, l);
+            }
+            bool coincident = false;
+            if (close > 1) {   // some pair closer than 2a: exact terms for those pairs
+                for (int k = beg; k < end; ++k) {
+                    if (k == me) continue;
+                    const float4 pj = make_float4(s_src[k], s_src[L + k], s_src[2 * L + k], 0.0f);
+                    const float dx = __fsub_rn(xi, pj.x), dy = __fsub_rn(yi, pj.y), dz = __fsub_rn(zi, pj.z);
+                    if (!(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min)) continue;
+                    const float4 fj = make_float4(s_src[3 * L + k], s_src[4 * L + k], s_src[5 * L + k], 0.0f);
+                    float cx = 0.0f, cy = 0.0f, cz = 0.0f, ex, ey, ez;
+                    pair_f32<TD, true>(xi, yi, zi, pj, fj, a.pc, cx, cy, cz);
+                    exact_pair<TENSOR, float>(dx, dy, dz, fj.x, fj.y, fj.z, a.pc, ex, ey, ez, coincident);
+                    V[0] = __fadd_rn(V[0], __fsub_rn(ex, cx));
+                    V[1] = __fadd_rn(V[1], __fsub_rn(ey, cy));
+                    V[2] = __fadd_rn(V[2], __fsub_rn(ez, cz));
+                }
+            }
+            if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
+            const size_t g = static_cast<size_t>(a.qperm[q]);
+            const double nx = a.x64[3 * g] + static_cast<double>(__fmul_rn(m0dt, V[0]));
+            const double ny = a.x64[3 * g + 1] + static_cast<double>(__fmul_rn(m0dt, V[1]));
+            const double nz = a.x64[3 * g + 2] + static_cast<double>(__fmul_rn(m0dt, V[2]));
+            if (!isfinite(nx) || !isfinite(ny) || !isfinite(nz)) atomicOr(a.err, DEV_ERR_NONFINITE);
+            a.x64n[3 * g] = nx;
+            a.x64n[3 * g + 1] = ny;
+            a.x64n[3 * g + 2] = nz;
+        }
+        __syncthreads();   // the stage and s_blk are free for the next block
     }
-    if (tensor == T_RPY) return reinterpret_cast<void *>(&batched_kernel<T_RPY, MODE_FP32C>);
-    if (tensor == T_RP) return reinterpret_cast<void *>(&batched_kernel<T_RP, MODE_FP32C>);
-    return reinterpret_cast<void *>(&batched_kernel<T_OSEEN, MODE_FP32C>);
+}
+
+// Launch shapes: FP64 -- warps per CTA (one cluster per warp) x resident CTAs;
+// FP32C -- block of BT = 32 warps threads (one target each) x resident CTAs.
+static size_t shape_smem(int mode, const BatchShape &sh) {
+    if (mode == MODE_FP64) return static_cast<size_t>(sh.warps) * kWarpStage;
+    return 6 * sizeof(float) * static_cast<size_t>(sh.warps == 4 ? block_stage_len<128>() : block_stage_len<256>());
+}
+
+template <int TENSOR>
+static void *batched_fn_t(int mode, int warps) {
+    if (mode == MODE_FP64) return reinterpret_cast<void *>(&batched_kernel<TENSOR>);
+    return warps == 4 ? reinterpret_cast<void *>(&batched_blocks_kernel<TENSOR, 128>)
+                      : reinterpret_cast<void *>(&batched_blocks_kernel<TENSOR, 256>);
+}
+
+static void *batched_fn(int tensor, int mode, int warps) {
+    if (tensor == T_RPY) return batched_fn_t<T_RPY>(mode, warps);
+    if (tensor == T_RP) return batched_fn_t<T_RP>(mode, warps);
+    return batched_fn_t<T_OSEEN>(mode, warps);
 }
 
 static cudaError_t batch_launch(sd_batch *b, cudaStream_t st, double dt, const BatchShape &sh, bool prof) {
@@ -570,7 +480,15 @@ static cudaError_t batch_launch(sd_batch *b, cudaStream_t st, double dt, const B
     BatchArgs a;
     a.off = b->d_off;
     a.order = b->d_order;
-    a.x64 = b->x64;
+    a.qperm = b->qperm;
+    a.qcl = b->qcl;
+    a.cbeg = b->cbeg;
+    a.cend = b->cend;
+    a.canchor = b->canchor;
+    a.P = b->P;
+    a.nblk = (b->P + 32 * sh.warps - 1) / (32 * sh.warps);
+    a.x64 = b->x64[b->cur];
+    a.x64n = b->x64[1 - b->cur];
     a.F64 = b->F64;
     a.frcm = b->frcm;
     a.ctr = b->ctr;
@@ -578,9 +496,9 @@ static cudaError_t batch_launch(sd_batch *b, cudaStream_t st, double dt, const B
     a.pc = b->pc;
     a.dt = dt;
     a.err = b->d_err;
-    const size_t smem = static_cast<size_t>(sh.warps) * stage_bytes(b->mode);
+    const size_t smem = shape_smem(b->mode, sh);
     const int grid = b->num_sms * sh.ctas_per_sm;
-    void *fn = batched_fn(b->tensor, b->mode);
+    void *fn = batched_fn(b->tensor, b->mode, sh.warps);
     int kk = -1;
     if (prof && b->prof.on && b->prof.npending < Profiler::kMaxPending) {
         kk = b->prof.npending;
@@ -599,6 +517,7 @@ static cudaError_t batch_launch(sd_batch *b, cudaStream_t st, double dt, const B
         ++b->prof.npending;
     }
     ++b->launches;
+    b->cur = 1 - b->cur;
     return e;
 }
 
@@ -694,6 +613,7 @@ static sd_status capture_batch(sd_batch *b, double dt) {
     if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate");
     b->g_dt = dt;
     b->g_choice = b->choice;
+    b->g_cur = b->cur;   // 16 launches flip the buffers back: the graph starts and ends here
     return SD_OK;
 }
 
@@ -766,13 +686,21 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
     const size_t vb = b->mode == MODE_FP64 ? sizeof(dbl4) : sizeof(float4);
     b->d_off = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * (nclusters + 1)));
     b->d_order = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * std::max(nclusters, 1)));
-    b->x64 = static_cast<double *>(balloc(b, p3 * sizeof(double)));
+    b->x64[0] = static_cast<double *>(balloc(b, p3 * sizeof(double)));
+    b->x64[1] = static_cast<double *>(balloc(b, p3 * sizeof(double)));
+    const size_t c1 = static_cast<size_t>(std::max(nclusters, 1));
+    b->qperm = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * std::max(P, 1)));
+    b->qcl = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * std::max(P, 1)));
+    b->cbeg = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * c1));
+    b->cend = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * c1));
+    b->canchor = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * c1));
     b->F64 = static_cast<double *>(balloc(b, p3 * sizeof(double)));
     b->fext64 = static_cast<double *>(balloc(b, p3 * sizeof(double)));
     b->frcm = balloc(b, std::max(P, 1) * vb);
     b->ctr = static_cast<unsigned long long *>(balloc(b, sizeof(unsigned long long)));
     b->d_err = static_cast<int *>(balloc(b, sizeof(int)));
-    if (!b->d_off || !b->d_order || !b->x64 || !b->F64 || !b->fext64 || !b->frcm || !b->ctr || !b->d_err)
+    if (!b->d_off || !b->d_order || !b->x64[0] || !b->x64[1] || !b->F64 || !b->fext64 || !b->frcm || !b->ctr ||
+        !b->d_err || !b->qperm || !b->qcl || !b->cbeg || !b->cend || !b->canchor)
         return fail(SD_ERR_OOM, "device allocation of batch buffers");
 
     // largest-first order (stable in the cluster index)
@@ -781,24 +709,47 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         return offsets[x + 1] - offsets[x] > offsets[y + 1] - offsets[y];
     });
+    // the largest-first sequence of particles (block kernel)
+    std::vector<int32_t> qperm(std::max(P, 1)), qcl(std::max(P, 1)), cbeg(c1), cend(c1), canchor(c1);
+    int pos = 0;
+    for (int k = 0; k < nclusters; ++k) {
+        const int c = order[k], o = offsets[c], n = offsets[c + 1] - o;
+        cbeg[k] = pos;
+        canchor[k] = o;
+        for (int i = 0; i < n; ++i) {
+            qperm[pos + i] = o + i;
+            qcl[pos + i] = k;
+        }
+        pos += n;
+        cend[k] = pos;
+    }
     cudaStream_t st = b->stream;
     cudaError_t e = cudaMemcpyAsync(b->d_off, offsets, sizeof(int32_t) * (nclusters + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && nclusters > 0)
         e = cudaMemcpyAsync(b->d_order, order.data(), sizeof(int32_t) * nclusters, cudaMemcpyHostToDevice, st);
+    // (pageable host vectors: cudaMemcpyAsync returns once they are staged, so they may go out of scope)
+    for (auto [dst, src, cnt] : {std::make_tuple(b->qperm, qperm.data(), static_cast<size_t>(P)),
+                                 std::make_tuple(b->qcl, qcl.data(), static_cast<size_t>(P)),
+                                 std::make_tuple(b->cbeg, cbeg.data(), static_cast<size_t>(nclusters)),
+                                 std::make_tuple(b->cend, cend.data(), static_cast<size_t>(nclusters)),
+                                 std::make_tuple(b->canchor, canchor.data(), static_cast<size_t>(nclusters))})
+        if (e == cudaSuccess && cnt > 0)
+            e = cudaMemcpyAsync(dst, src, sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->fext64, 0, p3 * sizeof(double), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->x64, 0, p3 * sizeof(double), st);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMemsetAsync(b->x64[k], 0, p3 * sizeof(double), st);
     if (e == cudaSuccess) e = batch_stage_forces(b);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(SD_ERR_CUDA, std::string("batch initialisation: ") + cudaGetErrorString(e));
 
-    // candidate launch shapes: warps per CTA x resident CTAs per SM that fit
-    void *fn = batched_fn(b->tensor, b->mode);
-    const size_t sb = stage_bytes(b->mode);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(8 * sb)) != cudaSuccess)
-        return fail(SD_ERR_CUDA, "shared-memory opt-in for the batched kernel");
+    // candidate launch shapes that fit: FP64 -- warps per CTA x resident CTAs per SM;
+    // FP32C -- blocks of 128 or 256 targets (4 or 8 warps) x resident CTAs per SM
     for (int w : {4, 8}) {
-        const size_t smem = w * sb;
+        void *fn = batched_fn(b->tensor, b->mode, w);
+        const size_t smem = shape_smem(b->mode, BatchShape{w, 1});
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+            cudaSuccess)
+            return fail(SD_ERR_CUDA, "shared-memory opt-in for the batched kernel");
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * w, smem) != cudaSuccess) {
             cudaGetLastError();
@@ -807,15 +758,7 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
         for (int c = 1; c <= occ; ++c) b->shapes.push_back({w, c});
     }
     if (b->shapes.empty()) return fail(SD_ERR_CUDA, "no launch shape fits the device");
-    // default: the shape with the most resident warps (ties: fewer warps per CTA)
-    int best = 0;
-    for (int k = 1; k < static_cast<int>(b->shapes.size()); ++k) {
-        const int wk = b->shapes[k].warps * b->shapes[k].ctas_per_sm;
-        const int wb = b->shapes[best].warps * b->shapes[best].ctas_per_sm;
-        if (wk > wb) best = k;
-    }
     b->choice = -1;   // autotune on first step
-    (void)best;
     *out = b;
     return SD_OK;
 }
@@ -829,7 +772,8 @@ void sd_batch_destroy(sd_batch *b) {
         cudaEventDestroy(b->prof.ev0[k]);
         cudaEventDestroy(b->prof.ev1[k]);
     }
-    void *bufs[] = {b->d_off, b->d_order, b->x64, b->F64, b->fext64, b->frcm, b->ctr, b->d_err};
+    void *bufs[] = {b->d_off, b->d_order, b->x64[0], b->x64[1], b->F64, b->fext64, b->frcm, b->ctr, b->d_err,
+                    b->qperm, b->qcl, b->cbeg, b->cend, b->canchor};
     for (void *p : bufs) bfree(b, p);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
@@ -843,9 +787,9 @@ sd_status sd_batch_set_positions(sd_batch *b, const double *xyz, int on_device) 
         for (size_t k = 0; k < 3 * static_cast<size_t>(b->P); ++k)
             if (!std::isfinite(xyz[k])) return set_error(SD_ERR_NONFINITE, "non-finite position");
     if (b->P > 0) {
-        SD_CUDA(cudaMemcpyAsync(b->x64, xyz, 3 * sizeof(double) * b->P,
+        SD_CUDA(cudaMemcpyAsync(b->x64[b->cur], xyz, 3 * sizeof(double) * b->P,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
-        batch_check_pos_kernel<<<(3 * b->P + 255) / 256, 256, 0, b->stream>>>(b->x64, b->P, b->d_err);
+        batch_check_pos_kernel<<<(3 * b->P + 255) / 256, 256, 0, b->stream>>>(b->x64[b->cur], b->P, b->d_err);
         ++b->launches;
         SD_CUDA(cudaGetLastError());
     }
@@ -859,7 +803,7 @@ sd_status sd_batch_get_positions(sd_batch *b, double *xyz, int on_device) {
     if (!b->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
     cudaSetDevice(b->device);
     if (b->P > 0)
-        SD_CUDA(cudaMemcpyAsync(xyz, b->x64, 3 * sizeof(double) * b->P,
+        SD_CUDA(cudaMemcpyAsync(xyz, b->x64[b->cur], 3 * sizeof(double) * b->P,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
     return on_device ? SD_OK : batch_sync_check(b);
 }
@@ -943,7 +887,7 @@ sd_status sd_step_batched(sd_batch *b, double dt, int64_t nsteps) {
     int64_t left = nsteps;
     if (!b->prof.on) {
         while (left >= kBatchGraphSteps) {
-            if (!b->gexec || b->g_dt != dt || b->g_choice != b->choice) {
+            if (!b->gexec || b->g_dt != dt || b->g_choice != b->choice || b->g_cur != b->cur) {
                 sd_status s = capture_batch(b, dt);
                 if (s != SD_OK) return s;
             }
