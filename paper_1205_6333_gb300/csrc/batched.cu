@@ -53,6 +53,8 @@ struct sd_batch {
     // largest-first layout of the FP32C block kernel (see batched_blocks_kernel)
     int32_t *qperm = nullptr, *qcl = nullptr, *cbeg = nullptr, *cend = nullptr, *canchor = nullptr;
     double *x64[2] = {nullptr, nullptr};   // position ping-pong: step reads x64[cur], writes the other
+    float4 *rel[2] = {nullptr, nullptr};   // FP32C: positions relative to the cluster's reference point
+    int32_t *panchor = nullptr;            // first particle of each particle's cluster
     int cur = 0;
     double *F64 = nullptr, *fext64 = nullptr;
     void *frcm = nullptr;
@@ -88,6 +90,9 @@ struct BatchArgs {
     int P, nblk;
     const double *x64;   // positions of this step
     double *x64n;        // positions after it
+    const float4 *rel;   // FP32C: FP32 positions of this step relative to their cluster's reference point
+    float4 *reln;        // ... after it, relative to the reference point of this step (x64 of the anchor)
+    const int32_t *panchor;
     const double *F64;
     const void *frcm;
     unsigned long long *ctr;
@@ -333,6 +338,7 @@ __global__ void batched_kernel(BatchArgs a) {
 // (hi, lo) sum; v stays FP32, x_{n+1} = x_n + dt v in FP64.  Positions are read
 // from x64 and written to x64n (a cluster may span two blocks).
 constexpr int kStageExtra = 2 * (kMaxCluster - 1);
+constexpr int kNoteCap = 8;   // close pairs (self included) a target lists; more: full rescan
 
 template <int BT>
 __host__ __device__ constexpr int block_stage_len() {
@@ -343,8 +349,9 @@ template <int TENSOR, int BT>
 __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
     constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
     constexpr int L = block_stage_len<BT>();
-    extern __shared__ __align__(16) float s_src[];   // [6][L]: x y z Fx Fy Fz
+    extern __shared__ __align__(16) float s_src[];   // [6][L]: x y z Fx Fy Fz, then int [kNoteCap][BT]
     __shared__ int s_blk;
+    int *s_note = reinterpret_cast<int *>(s_src + 6 * L);
     const int tid = threadIdx.x;
     const float4 *frcm = static_cast<const float4 *>(a.frcm);
     PairConst2 c2{};
@@ -363,14 +370,11 @@ __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
         const int s0 = a.cbeg[a.qcl[q0]], s1 = a.cend[a.qcl[q1 - 1]];   // s1 - s0 <= BT + kStageExtra
         for (int k = s0 + tid; k < s1; k += BT) {
             const int p = a.qperm[k];
-            const int anc = a.canchor[a.qcl[k]];
-            const float4 f = frcm[p];
+            const float4 r = a.rel[p], f = frcm[p];
             const int l = k - s0;
-            s_src[l] = static_cast<float>(a.x64[3 * static_cast<size_t>(p)] - a.x64[3 * static_cast<size_t>(anc)]);
-            s_src[L + l] = static_cast<float>(a.x64[3 * static_cast<size_t>(p) + 1] -
-                                              a.x64[3 * static_cast<size_t>(anc) + 1]);
-            s_src[2 * L + l] = static_cast<float>(a.x64[3 * static_cast<size_t>(p) + 2] -
-                                                  a.x64[3 * static_cast<size_t>(anc) + 2]);
+            s_src[l] = r.x;
+            s_src[L + l] = r.y;
+            s_src[2 * L + l] = r.z;
             s_src[3 * L + l] = f.x;
             s_src[4 * L + l] = f.y;
             s_src[5 * L + l] = f.z;
@@ -386,28 +390,42 @@ __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
             const f2 XI = pk2(xi, xi), YI = pk2(yi, yi), ZI = pk2(zi, zi);
             f2 AX = 0ull, AY = 0ull, AZ = 0ull;
             float tx = 0.0f, ty = 0.0f, tz = 0.0f;
-            int close = 0;   // pairs with r^2 < (2a)^2, the self pair included
+            // pairs with r^2 < (2a)^2 (the self pair among them) are listed as they are met
+            int close = 0;
+            auto note = [&](int j) {
+                if (close < kNoteCap) s_note[close * BT + tid] = j;
+                ++close;
+            };
             auto scalar = [&](int j) {
                 const float4 pj = make_float4(s_src[j], s_src[L + j], s_src[2 * L + j], 0.0f);
                 const float4 fj = make_float4(s_src[3 * L + j], s_src[4 * L + j], s_src[5 * L + j], 0.0f);
                 const float dx = __fsub_rn(xi, pj.x), dy = __fsub_rn(yi, pj.y), dz = __fsub_rn(zi, pj.z);
-                close += __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min;
+                if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) note(j);
                 pair_f32<TD, true>(xi, yi, zi, pj, fj, a.pc, tx, ty, tz);
             };
             int j = beg;
-            if (j & 1) scalar(j++);   // packed loads need an even index
-            const f2 *sp = reinterpret_cast<const f2 *>(s_src);
-            constexpr int LH = L / 2;
-#pragma unroll 2
-            for (; j + 1 < end; j += 2) {
-                const int h = j >> 1;
-                const f2 PX = sp[h], PY = sp[LH + h], PZ = sp[2 * LH + h];
-                const f2 FX = sp[3 * LH + h], FY = sp[4 * LH + h], FZ = sp[5 * LH + h];
-                float ra, rb;
-                pair_f32x2_t<TD, true, true>(XI, YI, ZI, PX, PY, PZ, FX, FY, FZ, c2, AX, AY, AZ, ra, rb);
-                close += (ra < r2min) + (rb < r2min);
+            while ((j & 3) && j < end) scalar(j++);   // 128-bit loads need an index that is a multiple of 4
+            const uint32_t sbase = smem_addr(s_src);
+            constexpr uint32_t AB = L * sizeof(float);   // bytes per SoA array
+            for (; j + 3 < end; j += 4) {
+                const uint32_t at = sbase + static_cast<uint32_t>(j) * sizeof(float);
+                f2 P[6][2];
+#pragma unroll
+                for (int d = 0; d < 6; ++d)
+                    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(P[d][0]), "=l"(P[d][1]) : "r"(at + d * AB));
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float ra, rb;
+                    pair_f32x2_t<TD, true, true>(XI, YI, ZI, P[0][h], P[1][h], P[2][h], P[3][h], P[4][h], P[5][h], c2,
+                                                 AX, AY, AZ, ra, rb);
+                    const bool ca = ra < r2min, cb = rb < r2min;
+                    if (ca || cb) {   // rare: overlaps, and the self pair once
+                        if (ca) note(j + 2 * h);
+                        if (cb) note(j + 2 * h + 1);
+                    }
+                }
             }
-            if (j < end) scalar(j);
+            while (j < end) scalar(j++);
             // the clamped self term, met once in the loop, bit for bit
             float sx = 0.0f, sy = 0.0f, sz = 0.0f;
             pair_f32<TD, true>(xi, yi, zi, pi, fi, a.pc, sx, sy, sz);
@@ -425,19 +443,28 @@ __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
                 V[d] = __fadd_rn(h, l);
             }
             bool coincident = false;
-            if (close > 1) {   // some pair closer than 2a: exact terms for those pairs
+            auto fix = [&](int k) {   // swap the clamped term of an overlapping pair for the exact one
+                const float4 pj = make_float4(s_src[k], s_src[L + k], s_src[2 * L + k], 0.0f);
+                const float4 fj = make_float4(s_src[3 * L + k], s_src[4 * L + k], s_src[5 * L + k], 0.0f);
+                const float dx = __fsub_rn(xi, pj.x), dy = __fsub_rn(yi, pj.y), dz = __fsub_rn(zi, pj.z);
+                float cx = 0.0f, cy = 0.0f, cz = 0.0f, ex, ey, ez;
+                pair_f32<TD, true>(xi, yi, zi, pj, fj, a.pc, cx, cy, cz);
+                exact_pair<TENSOR, float>(dx, dy, dz, fj.x, fj.y, fj.z, a.pc, ex, ey, ez, coincident);
+                V[0] = __fadd_rn(V[0], __fsub_rn(ex, cx));
+                V[1] = __fadd_rn(V[1], __fsub_rn(ey, cy));
+                V[2] = __fadd_rn(V[2], __fsub_rn(ez, cz));
+            };
+            if (close > 1 && close <= kNoteCap) {   // the listed pairs, in the order met
+                for (int e = 0; e < close; ++e) {
+                    const int k = s_note[e * BT + tid];
+                    if (k != me && k >= beg && k < end) fix(k);   // every listed entry lies in [beg, end)
+                }
+            } else if (close > kNoteCap) {   // list overflow: scan the cluster again
                 for (int k = beg; k < end; ++k) {
                     if (k == me) continue;
-                    const float4 pj = make_float4(s_src[k], s_src[L + k], s_src[2 * L + k], 0.0f);
-                    const float dx = __fsub_rn(xi, pj.x), dy = __fsub_rn(yi, pj.y), dz = __fsub_rn(zi, pj.z);
-                    if (!(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min)) continue;
-                    const float4 fj = make_float4(s_src[3 * L + k], s_src[4 * L + k], s_src[5 * L + k], 0.0f);
-                    float cx = 0.0f, cy = 0.0f, cz = 0.0f, ex, ey, ez;
-                    pair_f32<TD, true>(xi, yi, zi, pj, fj, a.pc, cx, cy, cz);
-                    exact_pair<TENSOR, float>(dx, dy, dz, fj.x, fj.y, fj.z, a.pc, ex, ey, ez, coincident);
-                    V[0] = __fadd_rn(V[0], __fsub_rn(ex, cx));
-                    V[1] = __fadd_rn(V[1], __fsub_rn(ey, cy));
-                    V[2] = __fadd_rn(V[2], __fsub_rn(ez, cz));
+                    const float dx = __fsub_rn(xi, s_src[k]), dy = __fsub_rn(yi, s_src[L + k]),
+                                dz = __fsub_rn(zi, s_src[2 * L + k]);
+                    if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) fix(k);
                 }
             }
             if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
@@ -449,6 +476,12 @@ __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
             a.x64n[3 * g] = nx;
             a.x64n[3 * g + 1] = ny;
             a.x64n[3 * g + 2] = nz;
+            // the next step's FP32 position, relative to this step's position of the cluster's
+            // first particle (the same reference point for the whole cluster; unchanged
+            // during this step, x64 being read-only)
+            const size_t an = static_cast<size_t>(a.panchor[g]);
+            a.reln[g] = make_float4(static_cast<float>(nx - a.x64[3 * an]), static_cast<float>(ny - a.x64[3 * an + 1]),
+                                    static_cast<float>(nz - a.x64[3 * an + 2]), 0.0f);
         }
         __syncthreads();   // the stage and s_blk are free for the next block
     }
@@ -458,7 +491,9 @@ __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
 // FP32C -- block of BT = 32 warps threads (one target each) x resident CTAs.
 static size_t shape_smem(int mode, const BatchShape &sh) {
     if (mode == MODE_FP64) return static_cast<size_t>(sh.warps) * kWarpStage;
-    return 6 * sizeof(float) * static_cast<size_t>(sh.warps == 4 ? block_stage_len<128>() : block_stage_len<256>());
+    const size_t bt = 32 * static_cast<size_t>(sh.warps);
+    return 6 * sizeof(float) * static_cast<size_t>(sh.warps == 4 ? block_stage_len<128>() : block_stage_len<256>()) +
+           kNoteCap * bt * sizeof(int);
 }
 
 template <int TENSOR>
@@ -489,6 +524,9 @@ static cudaError_t batch_launch(sd_batch *b, cudaStream_t st, double dt, const B
     a.nblk = (b->P + 32 * sh.warps - 1) / (32 * sh.warps);
     a.x64 = b->x64[b->cur];
     a.x64n = b->x64[1 - b->cur];
+    a.rel = b->rel[b->cur];
+    a.reln = b->rel[1 - b->cur];
+    a.panchor = b->panchor;
     a.F64 = b->F64;
     a.frcm = b->frcm;
     a.ctr = b->ctr;
@@ -571,6 +609,18 @@ __global__ void batch_check_pos_kernel(const double *__restrict__ x, int P, int 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * P) return;
     if (!isfinite(x[i])) atomicOr(err, DEV_ERR_NONFINITE);
+}
+
+// FP32 position of every particle relative to the first particle of its cluster
+// (the reference point the FP32C block kernel stages from).
+__global__ void batch_rel_kernel(const double *__restrict__ x, const int32_t *__restrict__ panchor,
+                                 float4 *__restrict__ rel, int P) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const size_t an = static_cast<size_t>(panchor[i]);
+    rel[i] = make_float4(static_cast<float>(x[3 * static_cast<size_t>(i)] - x[3 * an]),
+                         static_cast<float>(x[3 * static_cast<size_t>(i) + 1] - x[3 * an + 1]),
+                         static_cast<float>(x[3 * static_cast<size_t>(i) + 2] - x[3 * an + 2]), 0.0f);
 }
 
 static cudaError_t batch_stage_forces(sd_batch *b) {
@@ -690,6 +740,8 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
     b->x64[1] = static_cast<double *>(balloc(b, p3 * sizeof(double)));
     const size_t c1 = static_cast<size_t>(std::max(nclusters, 1));
     b->qperm = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * std::max(P, 1)));
+    b->panchor = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * std::max(P, 1)));
+    for (int k = 0; k < 2; ++k) b->rel[k] = static_cast<float4 *>(balloc(b, sizeof(float4) * std::max(P, 1)));
     b->qcl = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * std::max(P, 1)));
     b->cbeg = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * c1));
     b->cend = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * c1));
@@ -700,7 +752,8 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
     b->ctr = static_cast<unsigned long long *>(balloc(b, sizeof(unsigned long long)));
     b->d_err = static_cast<int *>(balloc(b, sizeof(int)));
     if (!b->d_off || !b->d_order || !b->x64[0] || !b->x64[1] || !b->F64 || !b->fext64 || !b->frcm || !b->ctr ||
-        !b->d_err || !b->qperm || !b->qcl || !b->cbeg || !b->cend || !b->canchor)
+        !b->d_err || !b->qperm || !b->qcl || !b->cbeg || !b->cend || !b->canchor || !b->panchor || !b->rel[0] ||
+        !b->rel[1])
         return fail(SD_ERR_OOM, "device allocation of batch buffers");
 
     // largest-first order (stable in the cluster index)
@@ -710,7 +763,10 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
         return offsets[x + 1] - offsets[x] > offsets[y + 1] - offsets[y];
     });
     // the largest-first sequence of particles (block kernel)
-    std::vector<int32_t> qperm(std::max(P, 1)), qcl(std::max(P, 1)), cbeg(c1), cend(c1), canchor(c1);
+    std::vector<int32_t> qperm(std::max(P, 1)), qcl(std::max(P, 1)), cbeg(c1), cend(c1), canchor(c1),
+        panchor(std::max(P, 1));
+    for (int c = 0; c < nclusters; ++c)
+        for (int i = offsets[c]; i < offsets[c + 1]; ++i) panchor[i] = offsets[c];
     int pos = 0;
     for (int k = 0; k < nclusters; ++k) {
         const int c = order[k], o = offsets[c], n = offsets[c + 1] - o;
@@ -730,6 +786,7 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
     // (pageable host vectors: cudaMemcpyAsync returns once they are staged, so they may go out of scope)
     for (auto [dst, src, cnt] : {std::make_tuple(b->qperm, qperm.data(), static_cast<size_t>(P)),
                                  std::make_tuple(b->qcl, qcl.data(), static_cast<size_t>(P)),
+                                 std::make_tuple(b->panchor, panchor.data(), static_cast<size_t>(P)),
                                  std::make_tuple(b->cbeg, cbeg.data(), static_cast<size_t>(nclusters)),
                                  std::make_tuple(b->cend, cend.data(), static_cast<size_t>(nclusters)),
                                  std::make_tuple(b->canchor, canchor.data(), static_cast<size_t>(nclusters))})
@@ -773,7 +830,7 @@ void sd_batch_destroy(sd_batch *b) {
         cudaEventDestroy(b->prof.ev1[k]);
     }
     void *bufs[] = {b->d_off, b->d_order, b->x64[0], b->x64[1], b->F64, b->fext64, b->frcm, b->ctr, b->d_err,
-                    b->qperm, b->qcl, b->cbeg, b->cend, b->canchor};
+                    b->qperm, b->qcl, b->cbeg, b->cend, b->canchor, b->panchor, b->rel[0], b->rel[1]};
     for (void *p : bufs) bfree(b, p);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
@@ -791,6 +848,11 @@ sd_status sd_batch_set_positions(sd_batch *b, const double *xyz, int on_device) 
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
         batch_check_pos_kernel<<<(3 * b->P + 255) / 256, 256, 0, b->stream>>>(b->x64[b->cur], b->P, b->d_err);
         ++b->launches;
+        if (b->mode != MODE_FP64) {
+            batch_rel_kernel<<<(b->P + 255) / 256, 256, 0, b->stream>>>(b->x64[b->cur], b->panchor, b->rel[b->cur],
+                                                                       b->P);
+            ++b->launches;
+        }
         SD_CUDA(cudaGetLastError());
     }
     b->pos_set = true;
