@@ -413,16 +413,15 @@ __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
 #pragma unroll
                 for (int d = 0; d < 6; ++d)
                     asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(P[d][0]), "=l"(P[d][1]) : "r"(at + d * AB));
+                float r[4];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    float ra, rb;
+                for (int h = 0; h < 2; ++h)
                     pair_f32x2_t<TD, true, true>(XI, YI, ZI, P[0][h], P[1][h], P[2][h], P[3][h], P[4][h], P[5][h], c2,
-                                                 AX, AY, AZ, ra, rb);
-                    const bool ca = ra < r2min, cb = rb < r2min;
-                    if (ca || cb) {   // rare: overlaps, and the self pair once
-                        if (ca) note(j + 2 * h);
-                        if (cb) note(j + 2 * h + 1);
-                    }
+                                                 AX, AY, AZ, r[2 * h], r[2 * h + 1]);
+                if (fminf(fminf(r[0], r[1]), fminf(r[2], r[3])) < r2min) {   // rare: overlaps, and the self pair once
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (r[u] < r2min) note(j + u);
                 }
             }
             while (j < end) scalar(j++);
@@ -469,10 +468,12 @@ __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
             }
             if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
             const size_t g = static_cast<size_t>(a.qperm[q]);
-            const double nx = a.x64[3 * g] + static_cast<double>(__fmul_rn(m0dt, V[0]));
-            const double ny = a.x64[3 * g + 1] + static_cast<double>(__fmul_rn(m0dt, V[1]));
-            const double nz = a.x64[3 * g + 2] + static_cast<double>(__fmul_rn(m0dt, V[2]));
-            if (!isfinite(nx) || !isfinite(ny) || !isfinite(nz)) atomicOr(a.err, DEV_ERR_NONFINITE);
+            // the positions are finite (checked when set), so x + dt v is finite iff dt v is
+            const float ux = __fmul_rn(m0dt, V[0]), uy = __fmul_rn(m0dt, V[1]), uz = __fmul_rn(m0dt, V[2]);
+            if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) atomicOr(a.err, DEV_ERR_NONFINITE);
+            const double nx = a.x64[3 * g] + static_cast<double>(ux);
+            const double ny = a.x64[3 * g + 1] + static_cast<double>(uy);
+            const double nz = a.x64[3 * g + 2] + static_cast<double>(uz);
             a.x64n[3 * g] = nx;
             a.x64n[3 * g + 1] = ny;
             a.x64n[3 * g + 2] = nz;
