@@ -223,6 +223,38 @@ sd_status sd_batch_synchronize(sd_batch *b);
 sd_status sd_mobility_apply_noalloc(const double *x, const double *F, double *V, int32_t n, double a, double eta,
                                     int32_t tensor, void *stream);
 
+/* ---- memory-access study (App. A, Algorithms 3 and 4) -------------------- */
+
+/* Kernels of the study: every thread j < n starts from in[j] and adds the n
+ * elements in[map(k)], k = 0 .. n-1, storing the sum in out[j].
+ *   SD_ACCESS_NAIVE        each thread loads its own map(k) from global memory;
+ *   SD_ACCESS_TILING       the block stages tiles of `block` elements in shared
+ *                          memory, thread t of the block loading map(m + t) with
+ *                          its own j (App. A, Algorithm 4 with warpSize replaced
+ *                          by the block size);
+ *   SD_ACCESS_SMALLTILING  tiles of 32 elements loaded by the first warp (Algorithm 4);
+ *   SD_ACCESS_BULK         linear map only: the tiling kernel with tiles of `block`
+ *                          elements copied by cp.async.bulk into a double buffer.
+ * Tile positions m + t >= n contribute zero (n need not be a multiple of the tile). */
+typedef enum { SD_ACCESS_NAIVE = 0, SD_ACCESS_TILING = 1, SD_ACCESS_SMALLTILING = 2, SD_ACCESS_BULK = 3 } sd_access_algo;
+/* Maps of App. A with p = 131 and M = 32 (j: the global index of the loading thread):
+ * linear k -> k; strided k -> k p mod n; unordered k -> (k p + j M) mod n. */
+typedef enum { SD_ACCESS_LINEAR = 0, SD_ACCESS_STRIDED = 1, SD_ACCESS_UNORDERED = 2 } sd_access_map;
+
+/* Launch one study kernel on `stream` (asynchronous).  in, out: device arrays of n
+ * elements, float (vec4 = 0) or float4 (vec4 = 1, componentwise sums, 16-byte
+ * aligned), owned by the caller, not aliased.  block: threads per block, a multiple
+ * of 32 in [32, 1024]; grid ceil(n / block).  Sums are formed in FP32 round-to-
+ * nearest in the order k = 0 .. n-1 after in[j].  Errors: SD_ERR_ARG for an unknown
+ * algorithm or map, the bulk kernel with a non-linear map or an input not 16-byte
+ * aligned, a bad block size, n < 0 or NULL arrays with n > 0; SD_ERR_CUDA for a
+ * failed launch.  n = 0 launches nothing. */
+sd_status sd_access_run(int32_t algo, int32_t map, int32_t vec4, int32_t n, int32_t block, const void *in, void *out,
+                        void *stream);
+/* SD_ERR_TIMEOUT (and clears the flag) if a bulk kernel launched since the last call
+ * gave up a bounded wait for a copy (its output is then invalid); otherwise SD_OK. */
+sd_status sd_access_status(void);
+
 /* ---- instrumentation (used by benchmarks and tests) ---------------------- */
 
 /* Kernel families that can be timed with CUDA events on the handle's stream. */

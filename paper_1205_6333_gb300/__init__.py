@@ -146,6 +146,43 @@ def sd_mobility_apply_noalloc(x_ptr, F_ptr, V_ptr, n, a=1.0, eta=1.0, tensor="rp
            "sd_mobility_apply_noalloc")
 
 
+ACCESS_ALGOS = {"naive": 0, "tiling": 1, "smalltiling": 2, "bulk": 3}
+ACCESS_MAPS = {"linear": 0, "strided": 1, "unordered": 2}
+
+
+def sd_access_run(algo, map, vec4, n, block, in_ptr, out_ptr, stream=None):
+    """One kernel of the App. A memory-access study (device pointers; see include/sd.h)."""
+    a = ACCESS_ALGOS[algo] if isinstance(algo, str) else int(algo)
+    m = ACCESS_MAPS[map] if isinstance(map, str) else int(map)
+    _check(lib().sd_access_run(a, m, int(bool(vec4)), int(n), int(block), in_ptr, out_ptr, stream),
+           "sd_access_run")
+
+
+def sd_access_status():
+    _check(lib().sd_access_status(), "sd_access_status")
+
+
+def access_study(algo, map, data, block=128, out=None):
+    """Run one study kernel on a CUDA float32 tensor of shape (n,) (float) or (n, 4)
+    (float4) on torch's current stream; returns the output tensor (same shape)."""
+    import torch
+    if not (_is_torch(data) and data.is_cuda and data.dtype == torch.float32 and data.is_contiguous()):
+        raise TypeError("access_study needs a contiguous CUDA float32 tensor")
+    if data.dim() == 2 and data.shape[1] == 4:
+        vec4 = True
+    elif data.dim() == 1:
+        vec4 = False
+    else:
+        raise ValueError("data must have shape (n,) or (n, 4)")
+    if out is None:
+        out = torch.empty_like(data)
+    elif out.shape != data.shape or out.dtype != data.dtype or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must match data")
+    st = torch.cuda.current_stream(data.device).cuda_stream
+    sd_access_run(algo, map, vec4, data.shape[0], block, data.data_ptr(), out.data_ptr(), st)
+    return out
+
+
 def sd_last_error() -> str:
     return lib().sd_last_error().decode()
 

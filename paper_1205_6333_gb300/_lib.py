@@ -85,6 +85,8 @@ PROTOTYPES = {
     "sd_set_watchdog": (c_int32, [c_void_p, c_int64]),
     "sd_mobility_apply_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_double, c_int32,
                                             c_void_p]),
+    "sd_access_run": (c_int32, [c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
+    "sd_access_status": (c_int32, []),
     "sd_last_error": (c_char_p, []),
     "sd_version": (c_char_p, []),
 }

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsd_gb300.so")
-SOURCES = ["api.cu", "dense.cu", "cells.cu", "epilogue.cu", "vjp.cu", "batched.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "dense.cu", "cells.cu", "epilogue.cu", "vjp.cu", "batched.cu", "noalloc.cu", "access.cu"]
 HEADERS = ["sd_internal.h", "pair.cuh", "ptx.cuh", "neighbours.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -124,3 +124,27 @@ def test_create_without_gpu_fails_cleanly(sd):
     with pytest.raises(sd.SDError) as ei:
         sd.sd_create(cfg)
     assert ei.value.status_name == "SD_ERR_CUDA"
+
+
+@pytest.mark.parametrize("args", [
+    (4, 0, 0, 64, 128),     # unknown algorithm
+    (0, 3, 0, 64, 128),     # unknown map
+    (3, 1, 0, 64, 128),     # bulk tiles with the strided map
+    (3, 2, 1, 64, 128),     # bulk tiles with the unordered map
+    (0, 0, 0, -1, 128),     # n < 0
+    (1, 0, 0, 64, 48),      # block not a multiple of 32
+    (1, 0, 0, 64, 2048),    # block above 1024
+    (2, 0, 1, 64, 0),       # block 0
+])
+def test_access_study_rejects_bad_arguments_on_host(sd, args):
+    """Every argument check of sd_access_run runs before any CUDA call."""
+    algo, mp, vec4, n, block = args
+    assert sd.lib().sd_access_run(algo, mp, vec4, n, block, 256, 512, None) == 1
+
+
+def test_access_study_null_and_unaligned_pointers(sd):
+    lib = sd.lib()
+    assert lib.sd_access_run(0, 0, 0, 64, 128, None, 512, None) == 1
+    assert lib.sd_access_run(0, 0, 0, 64, 128, 256, None, None) == 1
+    assert lib.sd_access_run(3, 0, 0, 64, 128, 260, 512, None) == 1     # bulk input not 16-byte aligned
+    assert lib.sd_access_run(1, 2, 1, 0, 128, None, None, None) == 0    # n = 0: nothing to launch
