@@ -274,7 +274,8 @@ def run_ours(args):
 
     x, F, L = _main_inputs(N_MAIN)
     n = N_MAIN
-    s = sd.System(n, prec="fp32c", tensor="rpy", stream="torch", torch_allocator=True, device=dev)
+    s = sd.System(n, prec="fp32c", tensor="rpy", stream="torch", torch_allocator=True, device=dev,
+                  dense=args.dense)
     s.set_positions(x)
     s.set_forces(F)
     step = lambda: s.step(DT, 1)   # noqa: E731
@@ -804,6 +805,8 @@ def main():
                                                      "adjoint", "lubrication", "fcc", "access"],
                     help="run one leg alone and print its numbers (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--dense", default="auto", choices=["auto", "directed", "symmetric"],
+                    help="all-pairs kernel of the main leg (auto: the library's choice, symmetric at this N)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
