@@ -198,6 +198,16 @@ sd_status sd_step_batched(sd_batch *b, double dt, int64_t nsteps);
 /* Time the candidate launch shapes on the current state (state unchanged) and keep
  * the fastest.  *choice (may be NULL) receives the index of the chosen shape. */
 sd_status sd_batch_autotune(sd_batch *b, int32_t *choice);
+/* The candidate launch shapes, fixed at sd_batch_create: their number, and for shape
+ * k in [0, count) the threads per CTA, the resident CTAs per SM and the targets per
+ * thread (FP32C: 1 or 2; FP64: 1).  Any output pointer may be NULL.  SD_ERR_ARG for
+ * a NULL batch or k out of range. */
+int32_t sd_batch_shape_count(const sd_batch *b);
+sd_status sd_batch_shape_info(const sd_batch *b, int32_t k, int32_t *threads, int32_t *ctas_per_sm,
+                              int32_t *targets_per_thread);
+/* Run the following steps with shape k instead of the autotuner's choice (SD_ERR_ARG
+ * for k out of range). */
+sd_status sd_batch_set_shape(sd_batch *b, int32_t k);
 sd_status sd_batch_synchronize(sd_batch *b);
 
 /* Velocities V = mu(x) F for n particles, computed without allocating any GPU

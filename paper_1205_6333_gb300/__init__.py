@@ -433,6 +433,20 @@ class Batch:
     def autotune(self) -> int:
         return sd_batch_autotune(self.b)
 
+    def shapes(self):
+        """The candidate launch shapes: dicts of threads per CTA, resident CTAs per SM and
+        targets per thread, indexed as autotune() and set_shape() count them."""
+        out = []
+        for k in range(lib().sd_batch_shape_count(self.b)):
+            t, c, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+            _check(lib().sd_batch_shape_info(self.b, k, ctypes.byref(t), ctypes.byref(c), ctypes.byref(r)),
+                   "sd_batch_shape_info")
+            out.append({"threads": t.value, "ctas_per_sm": c.value, "targets_per_thread": r.value})
+        return out
+
+    def set_shape(self, k: int):
+        _check(lib().sd_batch_set_shape(self.b, int(k)), "sd_batch_set_shape")
+
     def synchronize(self):
         _check(lib().sd_batch_synchronize(self.b), "sd_batch_synchronize")
 

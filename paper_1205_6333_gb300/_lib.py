@@ -73,6 +73,10 @@ PROTOTYPES = {
     "sd_step_batched": (c_int32, [c_void_p, c_double, c_int64]),
     "sd_batch_autotune": (c_int32, [c_void_p, ctypes.POINTER(c_int32)]),
     "sd_batch_synchronize": (c_int32, [c_void_p]),
+    "sd_batch_shape_count": (c_int32, [c_void_p]),
+    "sd_batch_shape_info": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                                      ctypes.POINTER(c_int32)]),
+    "sd_batch_set_shape": (c_int32, [c_void_p, c_int32]),
     "sd_profile": (c_int32, [c_void_p, c_int32]),
     "sd_batch_profile": (c_int32, [c_void_p, c_int32]),
     "sd_profile_read": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),

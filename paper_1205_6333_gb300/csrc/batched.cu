@@ -33,11 +33,11 @@
 namespace sd {
 
 constexpr int kMaxCluster = 256;
-constexpr int kMaxR = kMaxCluster / 32;
 
 struct BatchShape {
     int warps;        // warps per CTA
     int ctas_per_sm;  // resident CTAs per SM requested
+    int r = 1;        // FP32C: targets per thread (1 or 2)
 };
 
 }  // namespace sd
@@ -52,6 +52,8 @@ struct sd_batch {
     int32_t *d_off = nullptr, *d_order = nullptr;
     // largest-first layout of the FP32C block kernel (see batched_blocks_kernel)
     int32_t *qperm = nullptr, *qcl = nullptr, *cbeg = nullptr, *cend = nullptr, *canchor = nullptr;
+    int32_t *tq = nullptr;   // slots of two targets (see batched_blocks_kernel)
+    int M2 = 0;              // number of such slots
     double *x64[2] = {nullptr, nullptr};   // position ping-pong: step reads x64[cur], writes the other
     float4 *rel[2] = {nullptr, nullptr};   // FP32C: positions relative to the cluster's reference point
     int32_t *panchor = nullptr;            // first particle of each particle's cluster
@@ -87,7 +89,8 @@ struct BT<MODE_FP64> {
 struct BatchArgs {
     const int32_t *off, *order;
     const int32_t *qperm, *qcl, *cbeg, *cend, *canchor;
-    int P, nblk;
+    const int32_t *tq;   // two-target slots: q (targets q, q + 1) or ~q (q alone)
+    int P, M2, nblk;
     const double *x64;   // positions of this step
     double *x64n;        // positions after it
     const float4 *rel;   // FP32C: FP32 positions of this step relative to their cluster's reference point
@@ -321,35 +324,39 @@ __global__ void batched_kernel(BatchArgs a) {
 // FP32C path: target blocks.  At creation the clusters are laid out largest
 // first (a longest-processing-time order) as one sequence of P particles,
 // position q of the sequence being particle qperm[q] of cluster qcl[q] (whose
-// particles are the positions cbeg .. cend-1).  A persistent CTA of BT threads
-// pops blocks of BT consecutive positions from a ticket counter, so each thread
-// has a target and neighbouring targets belong to clusters of equal or
-// near-equal size (their loops are as long).  The CTA stages every cluster its
-// block touches -- at most BT + 2 (256 - 1) particles -- in shared memory as SoA
-// floats: positions relative to each cluster's first particle (FP64 difference,
-// then rounded, so FP32 separations keep full relative precision) and forces.
-// Each thread then sums over its own cluster with packed pairs (two sources per
-// f32x2 instruction, read as broadcasts), r^2 clamped to (2a)^2 throughout:
+// particles are the positions cbeg .. cend-1).  A thread owns R targets of one
+// cluster: R = 1, the target q = its slot; R = 2, the slot's entry tq[m] = q
+// (targets q, q + 1) or ~q (a cluster's last, odd target q alone; the second
+// lane then repeats q and is not stored).  A persistent CTA of BT threads pops
+// blocks of BT consecutive slots from a ticket counter, so neighbouring threads
+// have targets in clusters of equal or near-equal size (their loops are as long).
+// The CTA stages every cluster its block touches -- at most R BT + 2 (256 - 1)
+// particles -- in shared memory as SoA floats: positions relative to each
+// cluster's first particle (FP64 difference, then rounded, so FP32 separations
+// keep full relative precision) and forces.  Each thread then sums over its own
+// cluster with packed pairs (two sources per f32x2 instruction, read as
+// broadcasts, each load serving the R targets), r^2 clamped to (2a)^2 throughout:
 //   * the self pair is met once and its clamped term subtracted again, as
 //     mu_ii = mu0 I joins the sum;
-//   * pairs with r < 2a are counted on the way; only a target that met one
-//     rescans its cluster and swaps those clamped terms for exact ones.
+//   * pairs with r < 2a are listed as they are met; only they are swapped for
+//     exact terms afterwards.
 // Both packed lanes, the scalar edge terms and the self terms meet in a TwoSum
 // (hi, lo) sum; v stays FP32, x_{n+1} = x_n + dt v in FP64.  Positions are read
 // from x64 and written to x64n (a cluster may span two blocks).
 constexpr int kStageExtra = 2 * (kMaxCluster - 1);
 constexpr int kNoteCap = 8;   // close pairs (self included) a target lists; more: full rescan
 
-template <int BT>
+template <int BT, int R>
 __host__ __device__ constexpr int block_stage_len() {
-    return ((BT + kStageExtra) + 3) & ~3;   // per SoA array, floats (16-byte multiple)
+    return ((R * BT + kStageExtra) + 3) & ~3;   // per SoA array, floats (16-byte multiple)
 }
 
-template <int TENSOR, int BT>
+template <int TENSOR, int BT, int R>
 __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
+    static_assert(R == 1 || R == 2, "one or two targets per thread");
     constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
-    constexpr int L = block_stage_len<BT>();
-    extern __shared__ __align__(16) float s_src[];   // [6][L]: x y z Fx Fy Fz, then int [kNoteCap][BT]
+    constexpr int L = block_stage_len<BT, R>();
+    extern __shared__ __align__(16) float s_src[];   // [6][L]: x y z Fx Fy Fz, then int [kNoteCap][R][BT]
     __shared__ int s_blk;
     int *s_note = reinterpret_cast<int *>(s_src + 6 * L);
     const int tid = threadIdx.x;
@@ -361,13 +368,30 @@ __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
     c2.r2min = a.pc.r2min_f;
     const float r2min = a.pc.r2min_f;
     const float m0dt = static_cast<float>(a.pc.mu0 * a.dt);
+    const int M = R == 1 ? a.P : a.M2;   // slots
+    // the first target of slot m, and whether it has a second one
+    auto slot = [&](int m, int &q, bool &pair) {
+        if constexpr (R == 1) {
+            q = m;
+            pair = false;
+        } else {
+            const int t = a.tq[m];
+            q = t < 0 ? ~t : t;
+            pair = t >= 0;
+        }
+    };
     for (;;) {
         if (tid == 0) s_blk = static_cast<int>(atomicAdd(a.ctr, 1ULL));
         __syncthreads();
         const int blk = s_blk;
         if (blk >= a.nblk) break;   // uniform over the CTA
-        const int q0 = blk * BT, q1 = min(q0 + BT, a.P);
-        const int s0 = a.cbeg[a.qcl[q0]], s1 = a.cend[a.qcl[q1 - 1]];   // s1 - s0 <= BT + kStageExtra
+        const int m0 = blk * BT, m1 = min(m0 + BT, M);
+        int qf, ql;
+        bool pf, pl;
+        slot(m0, qf, pf);
+        slot(m1 - 1, ql, pl);
+        if (pl) ++ql;
+        const int s0 = a.cbeg[a.qcl[qf]], s1 = a.cend[a.qcl[ql]];   // s1 - s0 <= R BT + kStageExtra
         for (int k = s0 + tid; k < s1; k += BT) {
             const int p = a.qperm[k];
             const float4 r = a.rel[p], f = frcm[p];
@@ -380,28 +404,45 @@ __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
             s_src[5 * L + l] = f.z;
         }
         __syncthreads();
-        const int q = q0 + tid;
-        if (q < q1) {
-            const int cq = a.qcl[q];
-            const int beg = a.cbeg[cq] - s0, end = a.cend[cq] - s0, me = q - s0;
-            const float xi = s_src[me], yi = s_src[L + me], zi = s_src[2 * L + me];
-            const float4 pi = make_float4(xi, yi, zi, 0.0f);
-            const float4 fi = make_float4(s_src[3 * L + me], s_src[4 * L + me], s_src[5 * L + me], 0.0f);
-            const f2 XI = pk2(xi, xi), YI = pk2(yi, yi), ZI = pk2(zi, zi);
-            f2 AX = 0ull, AY = 0ull, AZ = 0ull;
-            float tx = 0.0f, ty = 0.0f, tz = 0.0f;
-            // pairs with r^2 < (2a)^2 (the self pair among them) are listed as they are met
-            int close = 0;
-            auto note = [&](int j) {
-                if (close < kNoteCap) s_note[close * BT + tid] = j;
-                ++close;
+        const int m = m0 + tid;
+        if (m < m1) {
+            int q0;
+            bool two;
+            slot(m, q0, two);
+            const int cq = a.qcl[q0];
+            const int beg = a.cbeg[cq] - s0, end = a.cend[cq] - s0;
+            int me[R];
+            float xi[R], yi[R], zi[R];
+            f2 XI[R], YI[R], ZI[R], AX[R], AY[R], AZ[R];
+            float tx[R], ty[R], tz[R];
+            int close[R];   // pairs with r^2 < (2a)^2 (the self pair among them), listed as met
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                me[r] = q0 + (two ? r : 0) - s0;
+                xi[r] = s_src[me[r]];
+                yi[r] = s_src[L + me[r]];
+                zi[r] = s_src[2 * L + me[r]];
+                XI[r] = pk2(xi[r], xi[r]);
+                YI[r] = pk2(yi[r], yi[r]);
+                ZI[r] = pk2(zi[r], zi[r]);
+                AX[r] = AY[r] = AZ[r] = 0ull;
+                tx[r] = ty[r] = tz[r] = 0.0f;
+                close[r] = 0;
+            }
+            auto note = [&](int r, int j) {
+                if (close[r] < kNoteCap) s_note[(close[r] * R + r) * BT + tid] = j;
+                ++close[r];
             };
             auto scalar = [&](int j) {
                 const float4 pj = make_float4(s_src[j], s_src[L + j], s_src[2 * L + j], 0.0f);
                 const float4 fj = make_float4(s_src[3 * L + j], s_src[4 * L + j], s_src[5 * L + j], 0.0f);
-                const float dx = __fsub_rn(xi, pj.x), dy = __fsub_rn(yi, pj.y), dz = __fsub_rn(zi, pj.z);
-                if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) note(j);
-                pair_f32<TD, true>(xi, yi, zi, pj, fj, a.pc, tx, ty, tz);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float dx = __fsub_rn(xi[r], pj.x), dy = __fsub_rn(yi[r], pj.y),
+                                dz = __fsub_rn(zi[r], pj.z);
+                    if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) note(r, j);
+                    pair_f32<TD, true>(xi[r], yi[r], zi[r], pj, fj, a.pc, tx[r], ty[r], tz[r]);
+                }
             };
             int j = beg;
             while ((j & 3) && j < end) scalar(j++);   // 128-bit loads need an index that is a multiple of 4
@@ -413,101 +454,118 @@ __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
 #pragma unroll
                 for (int d = 0; d < 6; ++d)
                     asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(P[d][0]), "=l"(P[d][1]) : "r"(at + d * AB));
-                float r[4];
+                float rr[R][4];
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
-                    pair_f32x2_t<TD, true, true>(XI, YI, ZI, P[0][h], P[1][h], P[2][h], P[3][h], P[4][h], P[5][h], c2,
-                                                 AX, AY, AZ, r[2 * h], r[2 * h + 1]);
-                if (fminf(fminf(r[0], r[1]), fminf(r[2], r[3])) < r2min) {   // rare: overlaps, and the self pair once
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (r[u] < r2min) note(j + u);
+                    for (int r = 0; r < R; ++r)
+                        pair_f32x2_t<TD, true, true>(XI[r], YI[r], ZI[r], P[0][h], P[1][h], P[2][h], P[3][h], P[4][h],
+                                                     P[5][h], c2, AX[r], AY[r], AZ[r], rr[r][2 * h], rr[r][2 * h + 1]);
+                float mn = fminf(fminf(rr[0][0], rr[0][1]), fminf(rr[0][2], rr[0][3]));
+                if constexpr (R == 2) mn = fminf(mn, fminf(fminf(rr[1][0], rr[1][1]), fminf(rr[1][2], rr[1][3])));
+                if (mn < r2min) {   // rare: overlaps, and the self pair once per target
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (rr[r][u] < r2min) note(r, j + u);
                 }
             }
             while (j < end) scalar(j++);
-            // the clamped self term, met once in the loop, bit for bit
-            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-            pair_f32<TD, true>(xi, yi, zi, pi, fi, a.pc, sx, sy, sz);
-            const f2 acc[3] = {AX, AY, AZ};
-            const float tsc[3] = {tx, ty, tz}, ssc[3] = {sx, sy, sz}, fsc[3] = {fi.x, fi.y, fi.z};
-            float V[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                float lo, hi, h, l;
-                upk2(acc[d], lo, hi);
-                two_sum(lo, hi, h, l);
-                fold2(h, l, tsc[d]);
-                fold2(h, l, -ssc[d]);
-                fold2(h, l, fsc[d]);   // mu_ii F_i / mu0 = F_i
-                V[d] = __fadd_rn(h, l);
-            }
             bool coincident = false;
-            auto fix = [&](int k) {   // swap the clamped term of an overlapping pair for the exact one
-                const float4 pj = make_float4(s_src[k], s_src[L + k], s_src[2 * L + k], 0.0f);
-                const float4 fj = make_float4(s_src[3 * L + k], s_src[4 * L + k], s_src[5 * L + k], 0.0f);
-                const float dx = __fsub_rn(xi, pj.x), dy = __fsub_rn(yi, pj.y), dz = __fsub_rn(zi, pj.z);
-                float cx = 0.0f, cy = 0.0f, cz = 0.0f, ex, ey, ez;
-                pair_f32<TD, true>(xi, yi, zi, pj, fj, a.pc, cx, cy, cz);
-                exact_pair<TENSOR, float>(dx, dy, dz, fj.x, fj.y, fj.z, a.pc, ex, ey, ez, coincident);
-                V[0] = __fadd_rn(V[0], __fsub_rn(ex, cx));
-                V[1] = __fadd_rn(V[1], __fsub_rn(ey, cy));
-                V[2] = __fadd_rn(V[2], __fsub_rn(ez, cz));
-            };
-            if (close > 1 && close <= kNoteCap) {   // the listed pairs, in the order met
-                for (int e = 0; e < close; ++e) {
-                    const int k = s_note[e * BT + tid];
-                    if (k != me && k >= beg && k < end) fix(k);   // every listed entry lies in [beg, end)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r > 0 && !two) break;   // the repeated target of an odd cluster's last slot
+                // the clamped self term, met once in the loop, bit for bit
+                const float4 pi = make_float4(xi[r], yi[r], zi[r], 0.0f);
+                const float4 fi = make_float4(s_src[3 * L + me[r]], s_src[4 * L + me[r]], s_src[5 * L + me[r]], 0.0f);
+                float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+                pair_f32<TD, true>(xi[r], yi[r], zi[r], pi, fi, a.pc, sx, sy, sz);
+                const f2 acc[3] = {AX[r], AY[r], AZ[r]};
+                const float tsc[3] = {tx[r], ty[r], tz[r]}, ssc[3] = {sx, sy, sz}, fsc[3] = {fi.x, fi.y, fi.z};
+                float V[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    float lo, hi, h, l;
+                    upk2(acc[d], lo, hi);
+                    two_sum(lo, hi, h, l);
+                    fold2(h, l, tsc[d]);
+                    fold2(h, l, -ssc[d]);
+                    fold2(h, l, fsc[d]);   // mu_ii F_i / mu0 = F_i
+                    V[d] = __fadd_rn(h, l);
                 }
-            } else if (close > kNoteCap) {   // list overflow: scan the cluster again
-                for (int k = beg; k < end; ++k) {
-                    if (k == me) continue;
-                    const float dx = __fsub_rn(xi, s_src[k]), dy = __fsub_rn(yi, s_src[L + k]),
-                                dz = __fsub_rn(zi, s_src[2 * L + k]);
-                    if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) fix(k);
+                auto fix = [&](int k) {   // swap the clamped term of an overlapping pair for the exact one
+                    const float4 pj = make_float4(s_src[k], s_src[L + k], s_src[2 * L + k], 0.0f);
+                    const float4 fj = make_float4(s_src[3 * L + k], s_src[4 * L + k], s_src[5 * L + k], 0.0f);
+                    const float dx = __fsub_rn(xi[r], pj.x), dy = __fsub_rn(yi[r], pj.y), dz = __fsub_rn(zi[r], pj.z);
+                    float cx = 0.0f, cy = 0.0f, cz = 0.0f, ex, ey, ez;
+                    pair_f32<TD, true>(xi[r], yi[r], zi[r], pj, fj, a.pc, cx, cy, cz);
+                    exact_pair<TENSOR, float>(dx, dy, dz, fj.x, fj.y, fj.z, a.pc, ex, ey, ez, coincident);
+                    V[0] = __fadd_rn(V[0], __fsub_rn(ex, cx));
+                    V[1] = __fadd_rn(V[1], __fsub_rn(ey, cy));
+                    V[2] = __fadd_rn(V[2], __fsub_rn(ez, cz));
+                };
+                if (close[r] > 1 && close[r] <= kNoteCap) {   // the listed pairs, in the order met
+                    for (int e = 0; e < close[r]; ++e) {
+                        const int k = s_note[(e * R + r) * BT + tid];
+                        if (k != me[r] && k >= beg && k < end) fix(k);   // every listed entry lies in [beg, end)
+                    }
+                } else if (close[r] > kNoteCap) {   // list overflow: scan the cluster again
+                    for (int k = beg; k < end; ++k) {
+                        if (k == me[r]) continue;
+                        const float dx = __fsub_rn(xi[r], s_src[k]), dy = __fsub_rn(yi[r], s_src[L + k]),
+                                    dz = __fsub_rn(zi[r], s_src[2 * L + k]);
+                        if (__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < r2min) fix(k);
+                    }
                 }
+                const size_t g = static_cast<size_t>(a.qperm[me[r] + s0]);
+                // the positions are finite (checked when set), so x + dt v is finite iff dt v is
+                const float ux = __fmul_rn(m0dt, V[0]), uy = __fmul_rn(m0dt, V[1]), uz = __fmul_rn(m0dt, V[2]);
+                if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) atomicOr(a.err, DEV_ERR_NONFINITE);
+                const double nx = a.x64[3 * g] + static_cast<double>(ux);
+                const double ny = a.x64[3 * g + 1] + static_cast<double>(uy);
+                const double nz = a.x64[3 * g + 2] + static_cast<double>(uz);
+                a.x64n[3 * g] = nx;
+                a.x64n[3 * g + 1] = ny;
+                a.x64n[3 * g + 2] = nz;
+                // the next step's FP32 position, relative to this step's position of the cluster's
+                // first particle (the same reference point for the whole cluster; unchanged
+                // during this step, x64 being read-only)
+                const size_t an = static_cast<size_t>(a.panchor[g]);
+                a.reln[g] = make_float4(static_cast<float>(nx - a.x64[3 * an]),
+                                        static_cast<float>(ny - a.x64[3 * an + 1]),
+                                        static_cast<float>(nz - a.x64[3 * an + 2]), 0.0f);
             }
             if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
-            const size_t g = static_cast<size_t>(a.qperm[q]);
-            // the positions are finite (checked when set), so x + dt v is finite iff dt v is
-            const float ux = __fmul_rn(m0dt, V[0]), uy = __fmul_rn(m0dt, V[1]), uz = __fmul_rn(m0dt, V[2]);
-            if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) atomicOr(a.err, DEV_ERR_NONFINITE);
-            const double nx = a.x64[3 * g] + static_cast<double>(ux);
-            const double ny = a.x64[3 * g + 1] + static_cast<double>(uy);
-            const double nz = a.x64[3 * g + 2] + static_cast<double>(uz);
-            a.x64n[3 * g] = nx;
-            a.x64n[3 * g + 1] = ny;
-            a.x64n[3 * g + 2] = nz;
-            // the next step's FP32 position, relative to this step's position of the cluster's
-            // first particle (the same reference point for the whole cluster; unchanged
-            // during this step, x64 being read-only)
-            const size_t an = static_cast<size_t>(a.panchor[g]);
-            a.reln[g] = make_float4(static_cast<float>(nx - a.x64[3 * an]), static_cast<float>(ny - a.x64[3 * an + 1]),
-                                    static_cast<float>(nz - a.x64[3 * an + 2]), 0.0f);
         }
         __syncthreads();   // the stage and s_blk are free for the next block
     }
 }
 
 // Launch shapes: FP64 -- warps per CTA (one cluster per warp) x resident CTAs;
-// FP32C -- block of BT = 32 warps threads (one target each) x resident CTAs.
+// FP32C -- block of BT = 32 warps threads (R targets each) x resident CTAs.
 static size_t shape_smem(int mode, const BatchShape &sh) {
     if (mode == MODE_FP64) return static_cast<size_t>(sh.warps) * kWarpStage;
     const size_t bt = 32 * static_cast<size_t>(sh.warps);
-    return 6 * sizeof(float) * static_cast<size_t>(sh.warps == 4 ? block_stage_len<128>() : block_stage_len<256>()) +
-           kNoteCap * bt * sizeof(int);
+    const int len = sh.warps == 4 ? (sh.r == 2 ? block_stage_len<128, 2>() : block_stage_len<128, 1>())
+                                  : (sh.r == 2 ? block_stage_len<256, 2>() : block_stage_len<256, 1>());
+    return 6 * sizeof(float) * static_cast<size_t>(len) + kNoteCap * static_cast<size_t>(sh.r) * bt * sizeof(int);
 }
 
 template <int TENSOR>
-static void *batched_fn_t(int mode, int warps) {
+static void *batched_fn_t(int mode, const BatchShape &sh) {
     if (mode == MODE_FP64) return reinterpret_cast<void *>(&batched_kernel<TENSOR>);
-    return warps == 4 ? reinterpret_cast<void *>(&batched_blocks_kernel<TENSOR, 128>)
-                      : reinterpret_cast<void *>(&batched_blocks_kernel<TENSOR, 256>);
+    if (sh.r == 2)
+        return sh.warps == 4 ? reinterpret_cast<void *>(&batched_blocks_kernel<TENSOR, 128, 2>)
+                             : reinterpret_cast<void *>(&batched_blocks_kernel<TENSOR, 256, 2>);
+    return sh.warps == 4 ? reinterpret_cast<void *>(&batched_blocks_kernel<TENSOR, 128, 1>)
+                         : reinterpret_cast<void *>(&batched_blocks_kernel<TENSOR, 256, 1>);
 }
 
-static void *batched_fn(int tensor, int mode, int warps) {
-    if (tensor == T_RPY) return batched_fn_t<T_RPY>(mode, warps);
-    if (tensor == T_RP) return batched_fn_t<T_RP>(mode, warps);
-    return batched_fn_t<T_OSEEN>(mode, warps);
+static void *batched_fn(int tensor, int mode, const BatchShape &sh) {
+    if (tensor == T_RPY) return batched_fn_t<T_RPY>(mode, sh);
+    if (tensor == T_RP) return batched_fn_t<T_RP>(mode, sh);
+    return batched_fn_t<T_OSEEN>(mode, sh);
 }
 
 static cudaError_t batch_launch(sd_batch *b, cudaStream_t st, double dt, const BatchShape &sh, bool prof) {
@@ -521,8 +579,13 @@ static cudaError_t batch_launch(sd_batch *b, cudaStream_t st, double dt, const B
     a.cbeg = b->cbeg;
     a.cend = b->cend;
     a.canchor = b->canchor;
+    a.tq = b->tq;
     a.P = b->P;
-    a.nblk = (b->P + 32 * sh.warps - 1) / (32 * sh.warps);
+    a.M2 = b->M2;
+    {
+        const int slots = (b->mode == MODE_FP32C && sh.r == 2) ? b->M2 : b->P;
+        a.nblk = (slots + 32 * sh.warps - 1) / (32 * sh.warps);
+    }
     a.x64 = b->x64[b->cur];
     a.x64n = b->x64[1 - b->cur];
     a.rel = b->rel[b->cur];
@@ -537,7 +600,7 @@ static cudaError_t batch_launch(sd_batch *b, cudaStream_t st, double dt, const B
     a.err = b->d_err;
     const size_t smem = shape_smem(b->mode, sh);
     const int grid = b->num_sms * sh.ctas_per_sm;
-    void *fn = batched_fn(b->tensor, b->mode, sh.warps);
+    void *fn = batched_fn(b->tensor, b->mode, sh);
     int kk = -1;
     if (prof && b->prof.on && b->prof.npending < Profiler::kMaxPending) {
         kk = b->prof.npending;
@@ -780,6 +843,15 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
         pos += n;
         cend[k] = pos;
     }
+    // two-target slots over the same sequence: pairs of neighbours in a cluster, an odd
+    // cluster's last target alone (stored as ~q)
+    std::vector<int32_t> tq;
+    tq.reserve(static_cast<size_t>(P) / 2 + nclusters + 1);
+    for (int k = 0; k < nclusters; ++k)
+        for (int q = cbeg[k]; q < cend[k]; q += 2) tq.push_back(q + 1 < cend[k] ? q : ~q);
+    b->M2 = static_cast<int>(tq.size());
+    b->tq = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * std::max<size_t>(tq.size(), 1)));
+    if (!b->tq) return fail(SD_ERR_OOM, "device allocation of batch buffers");
     cudaStream_t st = b->stream;
     cudaError_t e = cudaMemcpyAsync(b->d_off, offsets, sizeof(int32_t) * (nclusters + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && nclusters > 0)
@@ -790,7 +862,8 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
                                  std::make_tuple(b->panchor, panchor.data(), static_cast<size_t>(P)),
                                  std::make_tuple(b->cbeg, cbeg.data(), static_cast<size_t>(nclusters)),
                                  std::make_tuple(b->cend, cend.data(), static_cast<size_t>(nclusters)),
-                                 std::make_tuple(b->canchor, canchor.data(), static_cast<size_t>(nclusters))})
+                                 std::make_tuple(b->canchor, canchor.data(), static_cast<size_t>(nclusters)),
+                                 std::make_tuple(b->tq, tq.data(), tq.size())})
         if (e == cudaSuccess && cnt > 0)
             e = cudaMemcpyAsync(dst, src, sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), st);
@@ -801,19 +874,24 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
     if (e != cudaSuccess) return fail(SD_ERR_CUDA, std::string("batch initialisation: ") + cudaGetErrorString(e));
 
     // candidate launch shapes that fit: FP64 -- warps per CTA x resident CTAs per SM;
-    // FP32C -- blocks of 128 or 256 targets (4 or 8 warps) x resident CTAs per SM
-    for (int w : {4, 8}) {
-        void *fn = batched_fn(b->tensor, b->mode, w);
-        const size_t smem = shape_smem(b->mode, BatchShape{w, 1});
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
-            cudaSuccess)
-            return fail(SD_ERR_CUDA, "shared-memory opt-in for the batched kernel");
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * w, smem) != cudaSuccess) {
-            cudaGetLastError();
-            continue;
+    // FP32C -- blocks of 128 or 256 threads (4 or 8 warps) with 1 or 2 targets per
+    // thread x resident CTAs per SM
+    for (int r : {1, 2}) {
+        if (r == 2 && b->mode != MODE_FP32C) continue;
+        for (int w : {4, 8}) {
+            const BatchShape sh1{w, 1, r};
+            void *fn = batched_fn(b->tensor, b->mode, sh1);
+            const size_t smem = shape_smem(b->mode, sh1);
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+                cudaSuccess)
+                return fail(SD_ERR_CUDA, "shared-memory opt-in for the batched kernel");
+            int occ = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * w, smem) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            for (int c = 1; c <= occ; ++c) b->shapes.push_back({w, c, r});
         }
-        for (int c = 1; c <= occ; ++c) b->shapes.push_back({w, c});
     }
     if (b->shapes.empty()) return fail(SD_ERR_CUDA, "no launch shape fits the device");
     b->choice = -1;   // autotune on first step
@@ -831,7 +909,7 @@ void sd_batch_destroy(sd_batch *b) {
         cudaEventDestroy(b->prof.ev1[k]);
     }
     void *bufs[] = {b->d_off, b->d_order, b->x64[0], b->x64[1], b->F64, b->fext64, b->frcm, b->ctr, b->d_err,
-                    b->qperm, b->qcl, b->cbeg, b->cend, b->canchor, b->panchor, b->rel[0], b->rel[1]};
+                    b->qperm, b->qcl, b->cbeg, b->cend, b->canchor, b->panchor, b->rel[0], b->rel[1], b->tq};
     for (void *p : bufs) bfree(b, p);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
@@ -935,6 +1013,28 @@ sd_status sd_batch_autotune(sd_batch *b, int32_t *choice) {
     drop_batch_graph(b);
     if (choice) *choice = best;
     return batch_sync_check(b);
+}
+
+int32_t sd_batch_shape_count(const sd_batch *b) { return b ? static_cast<int32_t>(b->shapes.size()) : 0; }
+
+sd_status sd_batch_shape_info(const sd_batch *b, int32_t k, int32_t *threads, int32_t *ctas_per_sm,
+                              int32_t *targets_per_thread) {
+    if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    if (k < 0 || k >= static_cast<int32_t>(b->shapes.size())) return set_error(SD_ERR_ARG, "shape index out of range");
+    const BatchShape &sh = b->shapes[k];
+    if (threads) *threads = 32 * sh.warps;
+    if (ctas_per_sm) *ctas_per_sm = sh.ctas_per_sm;
+    if (targets_per_thread) *targets_per_thread = sh.r;
+    return SD_OK;
+}
+
+sd_status sd_batch_set_shape(sd_batch *b, int32_t k) {
+    if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    if (k < 0 || k >= static_cast<int32_t>(b->shapes.size())) return set_error(SD_ERR_ARG, "shape index out of range");
+    cudaSetDevice(b->device);
+    b->choice = k;
+    drop_batch_graph(b);
+    return SD_OK;
 }
 
 sd_status sd_step_batched(sd_batch *b, double dt, int64_t nsteps) {

@@ -67,6 +67,62 @@ def test_batched_overlaps_and_odd_sizes(tensor):
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref - x).max()
 
 
+def _odd_sizes_with_overlaps(seed=3):
+    rng = np.random.default_rng(seed)
+    sizes = [0, 1, 2, 31, 32, 33, 255, 256, 5, 3, 7, 130, 129]
+    xs = []
+    for n in sizes:
+        p, _ = inputs.cube_rsa(max(n, 1), 0.05, int(rng.integers(1 << 30)))
+        p = p[:n]
+        if n >= 4:
+            p[1] = p[0] + np.array([0.7, 0.3, -0.2])    # r < 2a
+            p[3] = p[2] + np.array([1.95, 0.0, 0.0])
+        xs.append(p)
+    x = np.concatenate(xs)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    return x, off, inputs.normal_forces(x.shape[0], seed + 2)
+
+
+def _shape_kinds(prec):
+    """One shape index per (threads per CTA, targets per thread) the batch offers."""
+    b = sd.Batch(np.array([0, 4], dtype=np.int32), prec=prec)
+    kinds = {}
+    for k, sh in enumerate(b.shapes()):
+        kinds.setdefault((sh["threads"], sh["targets_per_thread"]), k)
+    b.close()
+    return kinds
+
+
+def test_batched_shapes_include_two_targets_per_thread():
+    kinds = _shape_kinds("fp32c")
+    assert {(128, 1), (256, 1), (128, 2), (256, 2)} <= set(kinds)
+    assert {r for (_, r) in _shape_kinds("fp64")} == {1}
+    b = sd.Batch(np.array([0, 4], dtype=np.int32))
+    with pytest.raises(sd.SDError):
+        b.set_shape(len(b.shapes()))
+    b.close()
+
+
+@pytest.mark.parametrize("threads,r", [(128, 1), (256, 1), (128, 2), (256, 2)])
+@pytest.mark.parametrize("tensor", ["rpy", "oseen"])
+def test_batched_every_shape_matches_oracle(threads, r, tensor):
+    """Each FP32C kernel variant, pinned instead of autotuned: clusters of sizes 0 to
+    256 (odd and even: the last target of an odd cluster has a slot of its own when a
+    thread owns two), overlapping pairs, 20 steps (one graph replay and 4 eager steps)."""
+    x, off, F = _odd_sizes_with_overlaps()
+    ref = _oracle_batch(x, off, F, 20, 0.01, tensor)
+    b = sd.Batch(off, tensor=tensor)
+    k = next(k for k, sh in enumerate(b.shapes())
+             if sh["threads"] == threads and sh["targets_per_thread"] == r)
+    b.set_shape(k)
+    b.set_positions(x)
+    b.set_forces(F)
+    b.step(0.01, 20)
+    got = b.get_positions()
+    b.close()
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref - x).max()
+
+
 def test_batched_coincident_pairs():
     x = np.array([[0.0, 0, 0], [4.0, 0, 0], [4.0, 0, 0], [0.0, 9, 0]])
     off = np.array([0, 3, 4], dtype=np.int32)
@@ -109,3 +165,28 @@ def test_batched_graph_equals_eager_and_autotune():
     b.synchronize()
     assert b.launch_count() == c0 + 16
     b.close()
+
+
+def test_batched_full_workload_sampled_clusters():
+    """The batched workload at full size (16,384 clusters, N_c ~ U{4..256}, 2.1M particles)
+    in the launch shape the autotuner picks, as timed: 5 FP32C steps, then 48 clusters
+    (the 8 largest, the 8 smallest and 32 seeded others) against the oracle run on each
+    cluster alone."""
+    w = inputs.config_inputs(4)
+    x, off, F = w["x"], w["offsets"], w["F"]
+    nsteps, dt = 5, 0.01
+    b = sd.Batch(off, prec="fp32c")
+    b.set_positions(x)
+    b.set_forces(F)
+    b.step(dt, nsteps)
+    got = b.get_positions()
+    b.close()
+    sizes = np.diff(off)
+    order = np.argsort(sizes, kind="stable")
+    rng = np.random.default_rng(inputs.SEED_BASE + 40)
+    picks = np.unique(np.concatenate([order[:8], order[-8:], rng.choice(len(sizes), 32, replace=False)]))
+    for c in picks:
+        a, e = off[c], off[c + 1]
+        ref = oracle.euler(x[a:e], nsteps, dt, fext=F[a:e])
+        disp = np.abs(ref - x[a:e]).max()
+        assert np.abs(got[a:e] - ref).max() <= 1e-5 * disp, (int(c), int(e - a))

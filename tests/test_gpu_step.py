@@ -78,6 +78,17 @@ def test_repulsion_gravity_matches_oracle(prec, tol):
     assert np.abs(got - ref).max() <= tol * np.abs(ref - x0).max()
 
 
+def test_repulsion_gravity_full_size_steps():
+    """Workload 3 at full size (N = 16,384, phi = 0.10, gravity + repulsion, dt = 1e-3),
+    in the FP32C step as the drift run takes it: 16 steps (one replay of the captured
+    16-step graph) against the oracle's trajectory."""
+    w = inputs.config_inputs(3)
+    x0 = w["x"]
+    ref = oracle.euler(x0, 16, 1e-3, gravity=(0, 0, -1.0), rep_eps=1.0, rep_rc=2.5, nthreads=8)
+    got = _run(x0, 16, 1e-3, "fp32c", rep_eps=1.0)
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref - x0).max()
+
+
 def test_external_forces_and_overlaps_step():
     n = 900
     x0, _ = system_with_overlaps(n, 0.05, seed=21, overlaps=5)
