@@ -351,8 +351,16 @@ __host__ __device__ constexpr int block_stage_len() {
     return ((R * BT + kStageExtra) + 3) & ~3;   // per SoA array, floats (16-byte multiple)
 }
 
+// Resident 128-thread CTAs per SM the two-target variant is compiled for: 6 keeps
+// it at 80 registers without spills (7 spills a little, and neither beats the
+// one-target variant's 8 CTAs of 64 registers on the batched workload).  The
+// one-target variant gets no bound.
+#ifndef SD_BATCH_R2_MINB
+#define SD_BATCH_R2_MINB 6
+#endif
+
 template <int TENSOR, int BT, int R>
-__global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(BT, R == 2 ? SD_BATCH_R2_MINB * 128 / BT : 0) batched_blocks_kernel(BatchArgs a) {
     static_assert(R == 1 || R == 2, "one or two targets per thread");
     constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
     constexpr int L = block_stage_len<BT, R>();
@@ -446,14 +454,18 @@ __global__ void __launch_bounds__(BT) batched_blocks_kernel(BatchArgs a) {
             };
             int j = beg;
             while ((j & 3) && j < end) scalar(j++);   // 128-bit loads need an index that is a multiple of 4
-            const uint32_t sbase = smem_addr(s_src);
-            constexpr uint32_t AB = L * sizeof(float);   // bytes per SoA array
             for (; j + 3 < end; j += 4) {
-                const uint32_t at = sbase + static_cast<uint32_t>(j) * sizeof(float);
+                // four sources: one 128-bit broadcast load per SoA array (j and L are multiples
+                // of 4, so every load is 16-byte aligned); plain loads leave the compiler free
+                // to schedule them (2.4% faster than volatile inline loads)
                 f2 P[6][2];
+                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(s_src + j);
 #pragma unroll
-                for (int d = 0; d < 6; ++d)
-                    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(P[d][0]), "=l"(P[d][1]) : "r"(at + d * AB));
+                for (int d = 0; d < 6; ++d) {
+                    const ulonglong2 v = src[d * (L / 4)];
+                    P[d][0] = v.x;
+                    P[d][1] = v.y;
+                }
                 float rr[R][4];
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
