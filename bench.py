@@ -211,9 +211,16 @@ def cpu_baseline(x, F, target_s=10.0):
     t0 = time.perf_counter()
     oracle.mobility_rows(x, F, rows, "rpy", nthreads=cores)
     dt = time.perf_counter() - t0
+    # the same loop on one core, on a smaller sample (about a second)
+    rows1 = rng.choice(n, max(8, min(n, int(rate / max(cores, 1) / n))), replace=False).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.mobility_rows(x, F, rows1, "rpy", nthreads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": nrows * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d of %d rows of the N=%d apply (RPY, FP64, ascending-j loop, OpenMP over rows); %.1f s"
-                      % (nrows, n, n, dt)}
+                      % (nrows, n, n, dt),
+            "value_one_core": len(rows1) * n / dt1,
+            "sample_one_core": "%d rows on 1 thread; %.2f s" % (len(rows1), dt1)}
 
 
 def _config(L, world):
