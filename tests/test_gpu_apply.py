@@ -213,3 +213,21 @@ def test_near_list_dense_packing():
         with sd.System(n, prec=prec) as s:
             s.set_positions(x)
             assert rel_err(s.mobility_apply(F), ref) <= TOL[prec], prec
+
+
+def test_apply_sweep_top_sampled_rows():
+    """The top of the benchmark's sweep, N = 262,144 at volume fraction 0.05 (the
+    symmetric kernel's largest working set: 1.6 GB of source-side partial rows),
+    checked on 256 seeded rows that the oracle computes one by one."""
+    w = inputs.config_inputs(2, n=262144)
+    x, F = w["x"].astype(np.float64), w["F"].astype(np.float64)
+    n = x.shape[0]
+    with sd.System(n) as s:
+        assert s.dense_kernel() == "symmetric"
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+    rows = np.random.default_rng(9).choice(n, 256, replace=False)
+    rows = np.concatenate([rows, [0, n - 1]]).astype(np.int32)
+    ref = oracle.mobility_rows(x, F, rows, "rpy", nthreads=8)
+    err = np.linalg.norm(v[rows] - ref, axis=1).max() / np.linalg.norm(ref, axis=1).max()
+    assert err <= TOL["fp32c"]
