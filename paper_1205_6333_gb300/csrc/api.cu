@@ -342,7 +342,7 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
         h->part2 = static_cast<double *>(dalloc(h, h->part2_bytes));
         if (!h->part || !h->part2) return fail(SD_ERR_OOM, "device allocation of partial sums");
         if (h->geom.sym) {
-            h->jpart_bytes = static_cast<size_t>(h->geom.nT) * 3 * kSymB * sizeof(float);
+            h->jpart_bytes = static_cast<size_t>(h->geom.nT) * 3 * h->geom.I * sizeof(float);
             h->jpart = static_cast<float *>(dalloc(h, h->jpart_bytes));
             if (!h->jpart) return fail(SD_ERR_OOM, "device allocation of source-side partial sums");
         }

@@ -365,16 +365,17 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
 // kernel evaluates every pair twice, once per thread of each particle (Sec. 3.2):
 // on its hardware, handing a result to another thread cost global-memory traffic.
 // Here the hand-off stays on chip:
-//   * the particles are cut into blocks of kSymB = 256; a tile is an unordered
-//     pair of blocks (ib <= jb), laid out row-major over the upper triangle and
-//     partitioned over the persistent grid like the directed kernel's plane;
-//   * off-diagonal tiles: each warp holds 64 targets of block ib (2 per lane,
+//   * the particles are cut into blocks of B = 128 R (R = 2, or R = 4 for large
+//     N); a tile is an unordered pair of blocks (ib <= jb), laid out row-major over
+//     the upper triangle and partitioned over the persistent grid like the
+//     directed kernel's plane;
+//   * off-diagonal tiles: each warp holds 32 R targets of block ib (R per lane,
 //     duplicated into both halves of a packed register) and walks block jb in
 //     groups of 64 sources = 32 packets of two.  At step m lane l takes packet
 //     (l + m) mod 32, so the 32 lanes read 32 different packets (conflict-free
 //     64-bit shared loads) and each packet's running source-side sum (3 packed
 //     registers) moves one lane down per step with a shuffle; after 32 steps
-//     lane l holds packet l, having met all 64 targets of the warp.  The four
+//     lane l holds packet l, having met all 32 R targets of the warp.  The four
 //     warps' source sums are added in fixed order and written, in FP32, to the
 //     tile's own slot of `jpart`; the epilogue adds a block's column of slots in
 //     FP64 in ascending ib;
@@ -395,12 +396,11 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
 #endif
 constexpr int kSymUnroll = SD_SYM_UNROLL;
 
-template <int TENSOR, bool CLAMP, bool PER>
-__device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, const f2 (&XI)[2], const f2 (&YI)[2],
-                                         const f2 (&ZI)[2], const f2 (&GX)[2], const f2 (&GY)[2], const f2 (&GZ)[2],
-                                         const PairConst2 &c, f2 (&AX)[2], f2 (&AY)[2], f2 (&AZ)[2],
+template <int TENSOR, bool CLAMP, bool PER, int R, int B>
+__device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, const f2 (&XI)[R], const f2 (&YI)[R],
+                                         const f2 (&ZI)[R], const f2 (&GX)[R], const f2 (&GY)[R], const f2 (&GZ)[R],
+                                         const PairConst2 &c, f2 (&AX)[R], f2 (&AY)[R], f2 (&AZ)[R],
                                          float *__restrict__ jw) {
-    constexpr int B = kSymB;
     constexpr int S = B / 2;   // packets per array
     const int nxt = (lane + 1) & 31;
 #pragma unroll 1
@@ -413,7 +413,7 @@ __device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, co
             const f2 PX = gp[p], PY = gp[S + p], PZ = gp[2 * S + p];
             const f2 FX = gp[3 * S + p], FY = gp[4 * S + p], FZ = gp[5 * S + p];
 #pragma unroll
-            for (int k = 0; k < 2; ++k)
+            for (int k = 0; k < R; ++k)
                 pair_sym_f32x2<TENSOR, CLAMP, PER>(XI[k], YI[k], ZI[k], GX[k], GY[k], GZ[k], PX, PY, PZ, FX, FY,
                                                    FZ, c, AX[k], AY[k], AZ[k], JX, JY, JZ);
             JX = __shfl_sync(0xffffffffu, JX, nxt);
@@ -428,14 +428,14 @@ __device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, co
     }
 }
 
-template <int TENSOR, bool COMP, bool PER>
+template <int TENSOR, bool COMP, bool PER, int B>
 __global__ void __launch_bounds__(kSymNT, SD_SYM_MINB) dense_sym_kernel(const float *__restrict__ pos,
                                                            const float *__restrict__ frc, double *__restrict__ part,
                                                            float *__restrict__ jpart, int npad, DenseGeom g,
                                                            PairConst2 c, const int *__restrict__ flag,
                                                            int *__restrict__ err, long long wd) {
-    constexpr int R = 2, NT = kSymNT, B = kSymB, NW = NT / 32;
-    static_assert(B == NT * R, "a block is two targets per thread");
+    constexpr int NT = kSymNT, R = B / NT, NW = NT / 32;
+    static_assert(B == NT * R, "a block is R targets per thread");
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_abort;
@@ -551,9 +551,9 @@ __global__ void __launch_bounds__(kSymNT, SD_SYM_MINB) dense_sym_kernel(const fl
             float *jw = s_jacc + warp * 3 * B;
             const bool pad = PER && geom_pad_tile(g, c.n, static_cast<long long>(ib) * B, static_cast<long long>(jb) * B);
             if (clamp_all || pad)
-                sym_tile<TENSOR, true, PER>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
+                sym_tile<TENSOR, true, PER, R, B>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
             else
-                sym_tile<TENSOR, false, PER>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
+                sym_tile<TENSOR, false, PER, R, B>(sp, lane, XI, YI, ZI, GX, GY, GZ, c, AX, AY, AZ, jw);
         }
         if constexpr (COMP) {
 #pragma unroll
@@ -619,17 +619,18 @@ static void *pick_dense(int tensor, int mode, bool per) {
     return per ? pick_dense_t<true>(tensor, mode) : pick_dense_t<false>(tensor, mode);
 }
 
-template <bool PER>
+template <bool PER, int B>
 static void *pick_sym_t(int tensor, int mode) {
     const bool oseen = tensor == T_OSEEN, comp = mode == MODE_FP32C;
     if (oseen)
-        return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, true, PER>)
-                    : reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, false, PER>);
-    return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_RP, true, PER>)
-                : reinterpret_cast<void *>(&dense_sym_kernel<T_RP, false, PER>);
+        return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, true, PER, B>)
+                    : reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, false, PER, B>);
+    return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_RP, true, PER, B>)
+                : reinterpret_cast<void *>(&dense_sym_kernel<T_RP, false, PER, B>);
 }
-static void *pick_sym(int tensor, int mode, bool per) {
-    return per ? pick_sym_t<true>(tensor, mode) : pick_sym_t<false>(tensor, mode);
+static void *pick_sym(int tensor, int mode, bool per, int B) {
+    if (B == kSymBLarge) return per ? pick_sym_t<true, kSymBLarge>(tensor, mode) : pick_sym_t<false, kSymBLarge>(tensor, mode);
+    return per ? pick_sym_t<true, kSymBSmall>(tensor, mode) : pick_sym_t<false, kSymBSmall>(tensor, mode);
 }
 
 // Dynamic shared memory of the dense kernel of this mode for tile J.
@@ -637,14 +638,26 @@ static size_t dense_smem(int mode, int J) {
     if (mode == MODE_FP64) return 4 * static_cast<size_t>(J) * sizeof(dbl4);
     return 12 * static_cast<size_t>(J) * sizeof(float) + static_cast<size_t>(kR32) * 6 * kNT * sizeof(float);
 }
-static constexpr size_t kSymSmem = (12 * kSymB + 2 * 6 * kSymNT + (kSymNT / 32) * 3 * kSymB) * sizeof(float);
+// Dynamic shared memory of the symmetric kernel for blocks of B: two stages of six
+// source arrays, the (hi, lo) target accumulators, the warps' source-side sums.
+static constexpr size_t sym_smem(int B) {
+    return (12 * static_cast<size_t>(B) + static_cast<size_t>(B / kSymNT) * 6 * kSymNT +
+            (kSymNT / 32) * 3 * static_cast<size_t>(B)) * sizeof(float);
+}
 
 // The symmetric kernel replaces the directed FP32 kernel once the triangle holds at
 // least one tile per SD_DENSE_SYM_SMS_PER_TILE SMs.  Measured on GB300 (step time,
 // N = 2^k at volume fraction 0.05): directed faster at N <= 2048 (36 tiles),
-// symmetric faster from N = 4096 (136 tiles) on.
+// symmetric faster from N = 4096 (136 tiles) on.  From SD_DENSE_SYM_LARGE_N
+// particles on, blocks of 512 (4 targets per thread: more independent work per
+// warp, half the source-side partial rows) replace blocks of 256: all-pairs kernel
+// 2.29 -> 2.23 ms at N = 65,536 and 36.3 -> 34.2 ms at 262,144, but 0.159 -> 0.170
+// ms at 16,384 (too few tiles for 2 CTAs per SM of 174 registers).
 #ifndef SD_DENSE_SYM_SMS_PER_TILE
 #define SD_DENSE_SYM_SMS_PER_TILE 2
+#endif
+#ifndef SD_DENSE_SYM_LARGE_N
+#define SD_DENSE_SYM_LARGE_N 32768
 #endif
 
 // Choose the tile J and the persistent grid for h->npad, and size the partials.
@@ -684,19 +697,20 @@ cudaError_t dense_setup(sd_handle *h) {
     g.nT = T;
     g.sym = 0;
     const int want_sym = h->cfg.dense_kernel;
-    if (h->mode != MODE_FP64 && h->npad % kSymB == 0 && want_sym != SD_DENSE_DIRECTED) {
-        void *sfn = pick_sym(h->tensor, h->mode, h->pc.periodic != 0);
+    const int B = (h->npad >= SD_DENSE_SYM_LARGE_N && h->npad % kSymBLarge == 0) ? kSymBLarge : kSymBSmall;
+    if (h->mode != MODE_FP64 && h->npad % B == 0 && want_sym != SD_DENSE_DIRECTED) {
+        void *sfn = pick_sym(h->tensor, h->mode, h->pc.periodic != 0, B);
         cudaError_t e = cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(kSymSmem));
+                                             static_cast<int>(sym_smem(B)));
         if (e != cudaSuccess) return e;
         int socc = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, sfn, kSymNT, kSymSmem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, sfn, kSymNT, sym_smem(B));
         if (e != cudaSuccess) return e;
         socc = std::max(socc, 1);
         DenseGeom s{};
         s.sym = 1;
-        s.I = s.J = kSymB;
-        s.nIB = s.nJT = h->npad / kSymB;
+        s.I = s.J = B;
+        s.nIB = s.nJT = h->npad / B;
         s.nT = static_cast<long long>(s.nIB) * (s.nIB + 1) / 2;
         if (want_sym == SD_DENSE_SYMMETRIC || s.nT * SD_DENSE_SYM_SMS_PER_TILE >= h->num_sms) {
             const long long swant = static_cast<long long>(h->num_sms) * socc * SD_DENSE_CTA_SCALE;
@@ -742,13 +756,22 @@ static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror fr
     c2.n = h->n;
     const bool comp = h->mode == MODE_FP32C;
     if (g.sym) {
-#define SD_DS(TT, CC)                                                                                          \
-    dense_sym_kernel<TT, CC, PER><<<g.grid, kSymNT, kSymSmem, st>>>(posm.soa, frcm.soa, part, h->jpart, h->npad, g, \
-                                                                    c2, h->d_flag, h->d_err, h->watchdog)
-        if (oseen) {
-            if (comp) SD_DS(T_OSEEN, true); else SD_DS(T_OSEEN, false);
+#define SD_DS(TT, CC, BB)                                                                                      \
+    dense_sym_kernel<TT, CC, PER, BB><<<g.grid, kSymNT, sym_smem(BB), st>>>(posm.soa, frcm.soa, part, h->jpart,  \
+                                                                            h->npad, g, c2, h->d_flag, h->d_err, \
+                                                                            h->watchdog)
+        if (g.I == kSymBLarge) {
+            if (oseen) {
+                if (comp) SD_DS(T_OSEEN, true, kSymBLarge); else SD_DS(T_OSEEN, false, kSymBLarge);
+            } else {
+                if (comp) SD_DS(T_RP, true, kSymBLarge); else SD_DS(T_RP, false, kSymBLarge);
+            }
         } else {
-            if (comp) SD_DS(T_RP, true); else SD_DS(T_RP, false);
+            if (oseen) {
+                if (comp) SD_DS(T_OSEEN, true, kSymBSmall); else SD_DS(T_OSEEN, false, kSymBSmall);
+            } else {
+                if (comp) SD_DS(T_RP, true, kSymBSmall); else SD_DS(T_RP, false, kSymBSmall);
+            }
         }
 #undef SD_DS
         return;

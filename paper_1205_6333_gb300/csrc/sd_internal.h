@@ -41,7 +41,8 @@ constexpr double kRSafe = 1.0;   // pairs closer than kRSafe * a make the FP32 k
 constexpr long long kDefaultWatchdog = 1LL << 22;
 constexpr int kNearPerParticle = 16;  // near-pass list capacity per particle (overflow: in-place path)
 constexpr int kSymNT = 128;      // threads per CTA of the symmetric FP32 kernel
-constexpr int kSymB = 256;       // particles per block (2 per thread) = sources per tile
+constexpr int kSymBSmall = 256;  // its particles per block (2 per thread) = sources per tile ...
+constexpr int kSymBLarge = 512;  // ... or 4 per thread, for large N
 
 // Partition of the (i-block, j-tile) plane over a persistent grid: CTA b takes
 // the row-major tile range [b*chunk, min((b+1)*chunk, nIB*nJT)).  The CTAs that
@@ -186,7 +187,7 @@ struct sd_handle {
     double *Wa64 = nullptr;  sd::Mirror wam;
     double *part = nullptr;  size_t part_bytes = 0;   // dense partial sums
     double *part2 = nullptr; size_t part2_bytes = 0;  // second output of the VJP kernel
-    float *jpart = nullptr;  size_t jpart_bytes = 0;   // symmetric kernel: source-side sums [tile][3][kSymB]
+    float *jpart = nullptr;  size_t jpart_bytes = 0;   // symmetric kernel: source-side sums [tile][3][block]
     sd::DenseGeom geom{}, geomv{};
     int dense_occ = 0, vjp_occ = 0;
 
