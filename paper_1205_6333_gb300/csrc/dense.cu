@@ -428,13 +428,13 @@ __device__ __forceinline__ void sym_tile(const f2 *__restrict__ sp, int lane, co
     }
 }
 
-template <int TENSOR, bool COMP, bool PER, int B>
-__global__ void __launch_bounds__(kSymNT, SD_SYM_MINB) dense_sym_kernel(const float *__restrict__ pos,
+template <int TENSOR, bool COMP, bool PER, int B, int NT>
+__global__ void __launch_bounds__(NT, SD_SYM_MINB) dense_sym_kernel(const float *__restrict__ pos,
                                                            const float *__restrict__ frc, double *__restrict__ part,
                                                            float *__restrict__ jpart, int npad, DenseGeom g,
                                                            PairConst2 c, const int *__restrict__ flag,
                                                            int *__restrict__ err, long long wd) {
-    constexpr int NT = kSymNT, R = B / NT, NW = NT / 32;
+    constexpr int R = B / NT, NW = NT / 32;
     static_assert(B == NT * R, "a block is R targets per thread");
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -619,18 +619,23 @@ static void *pick_dense(int tensor, int mode, bool per) {
     return per ? pick_dense_t<true>(tensor, mode) : pick_dense_t<false>(tensor, mode);
 }
 
-template <bool PER, int B>
+template <bool PER, int B, int NT>
 static void *pick_sym_t(int tensor, int mode) {
     const bool oseen = tensor == T_OSEEN, comp = mode == MODE_FP32C;
     if (oseen)
-        return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, true, PER, B>)
-                    : reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, false, PER, B>);
-    return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_RP, true, PER, B>)
-                : reinterpret_cast<void *>(&dense_sym_kernel<T_RP, false, PER, B>);
+        return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, true, PER, B, NT>)
+                    : reinterpret_cast<void *>(&dense_sym_kernel<T_OSEEN, false, PER, B, NT>);
+    return comp ? reinterpret_cast<void *>(&dense_sym_kernel<T_RP, true, PER, B, NT>)
+                : reinterpret_cast<void *>(&dense_sym_kernel<T_RP, false, PER, B, NT>);
 }
-static void *pick_sym(int tensor, int mode, bool per, int B) {
-    if (B == kSymBLarge) return per ? pick_sym_t<true, kSymBLarge>(tensor, mode) : pick_sym_t<false, kSymBLarge>(tensor, mode);
-    return per ? pick_sym_t<true, kSymBSmall>(tensor, mode) : pick_sym_t<false, kSymBSmall>(tensor, mode);
+template <bool PER>
+static void *pick_sym_p(int tensor, int mode, int B, int NT) {
+    if (B == 512) return pick_sym_t<PER, 512, 128>(tensor, mode);
+    if (NT == 64) return pick_sym_t<PER, 256, 64>(tensor, mode);
+    return pick_sym_t<PER, 256, 128>(tensor, mode);
+}
+static void *pick_sym(int tensor, int mode, bool per, int B, int NT) {
+    return per ? pick_sym_p<true>(tensor, mode, B, NT) : pick_sym_p<false>(tensor, mode, B, NT);
 }
 
 // Dynamic shared memory of the dense kernel of this mode for tile J.
@@ -640,9 +645,9 @@ static size_t dense_smem(int mode, int J) {
 }
 // Dynamic shared memory of the symmetric kernel for blocks of B: two stages of six
 // source arrays, the (hi, lo) target accumulators, the warps' source-side sums.
-static constexpr size_t sym_smem(int B) {
-    return (12 * static_cast<size_t>(B) + static_cast<size_t>(B / kSymNT) * 6 * kSymNT +
-            (kSymNT / 32) * 3 * static_cast<size_t>(B)) * sizeof(float);
+static constexpr size_t sym_smem(int B, int NT) {
+    return (12 * static_cast<size_t>(B) + static_cast<size_t>(B / NT) * 6 * NT +
+            static_cast<size_t>(NT / 32) * 3 * static_cast<size_t>(B)) * sizeof(float);
 }
 
 // The symmetric kernel replaces the directed FP32 kernel once the triangle holds at
@@ -658,6 +663,18 @@ static constexpr size_t sym_smem(int B) {
 #endif
 #ifndef SD_DENSE_SYM_LARGE_N
 #define SD_DENSE_SYM_LARGE_N 32768
+#endif
+// Below SD_DENSE_SYM_LARGE_N and from SD_DENSE_SYM_MID_N on, blocks of 256 go to
+// 64-thread CTAs (4 targets per thread): 0.159 -> 0.151 ms at N = 16,384 and
+// 0.053 -> 0.050 ms at 8,192; at 4,096 they leave too few CTAs (0.020 -> 0.030).
+#ifndef SD_DENSE_SYM_MID_N
+#define SD_DENSE_SYM_MID_N 8192
+#endif
+// CTA oversubscription of the symmetric kernel's grid (see SD_DENSE_CTA_SCALE).  At
+// N = 65,536: all-pairs + epilogue 2.265 ms at 8, 2.251 at 16, 2.251 at 32 (more
+// CTAs balance the SMs better but leave more partial rows for the epilogue).
+#ifndef SD_DENSE_SYM_CTA_SCALE
+#define SD_DENSE_SYM_CTA_SCALE 16
 #endif
 
 // Choose the tile J and the persistent grid for h->npad, and size the partials.
@@ -697,14 +714,17 @@ cudaError_t dense_setup(sd_handle *h) {
     g.nT = T;
     g.sym = 0;
     const int want_sym = h->cfg.dense_kernel;
-    const int B = (h->npad >= SD_DENSE_SYM_LARGE_N && h->npad % kSymBLarge == 0) ? kSymBLarge : kSymBSmall;
+    // block shape: 512 particles x 128 threads (4 targets each) for large N, 256 x 64
+    // (4 each) for mid-size N, 256 x 128 (2 each) below
+    const bool large = h->npad >= SD_DENSE_SYM_LARGE_N && h->npad % 512 == 0;
+    const int B = large ? 512 : 256, NT = (large || h->npad < SD_DENSE_SYM_MID_N) ? 128 : 64;
     if (h->mode != MODE_FP64 && h->npad % B == 0 && want_sym != SD_DENSE_DIRECTED) {
-        void *sfn = pick_sym(h->tensor, h->mode, h->pc.periodic != 0, B);
+        void *sfn = pick_sym(h->tensor, h->mode, h->pc.periodic != 0, B, NT);
         cudaError_t e = cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(sym_smem(B)));
+                                             static_cast<int>(sym_smem(B, NT)));
         if (e != cudaSuccess) return e;
         int socc = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, sfn, kSymNT, sym_smem(B));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, sfn, NT, sym_smem(B, NT));
         if (e != cudaSuccess) return e;
         socc = std::max(socc, 1);
         DenseGeom s{};
@@ -713,11 +733,12 @@ cudaError_t dense_setup(sd_handle *h) {
         s.nIB = s.nJT = h->npad / B;
         s.nT = static_cast<long long>(s.nIB) * (s.nIB + 1) / 2;
         if (want_sym == SD_DENSE_SYMMETRIC || s.nT * SD_DENSE_SYM_SMS_PER_TILE >= h->num_sms) {
-            const long long swant = static_cast<long long>(h->num_sms) * socc * SD_DENSE_CTA_SCALE;
+            const long long swant = static_cast<long long>(h->num_sms) * socc * SD_DENSE_SYM_CTA_SCALE;
             s.chunk = std::max(1LL, (s.nT + swant - 1) / swant);
             s.grid = static_cast<int>((s.nT + s.chunk - 1) / s.chunk);
             g = s;
             occ = socc;
+            h->sym_nt = NT;
         }
     }
     int ms = 0;
@@ -756,23 +777,24 @@ static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror fr
     c2.n = h->n;
     const bool comp = h->mode == MODE_FP32C;
     if (g.sym) {
-#define SD_DS(TT, CC, BB)                                                                                      \
-    dense_sym_kernel<TT, CC, PER, BB><<<g.grid, kSymNT, sym_smem(BB), st>>>(posm.soa, frcm.soa, part, h->jpart,  \
-                                                                            h->npad, g, c2, h->d_flag, h->d_err, \
-                                                                            h->watchdog)
-        if (g.I == kSymBLarge) {
-            if (oseen) {
-                if (comp) SD_DS(T_OSEEN, true, kSymBLarge); else SD_DS(T_OSEEN, false, kSymBLarge);
-            } else {
-                if (comp) SD_DS(T_RP, true, kSymBLarge); else SD_DS(T_RP, false, kSymBLarge);
-            }
+#define SD_DS(TT, CC, BB, NN)                                                                                  \
+    dense_sym_kernel<TT, CC, PER, BB, NN><<<g.grid, NN, sym_smem(BB, NN), st>>>(posm.soa, frcm.soa, part,     \
+                                                                                h->jpart, h->npad, g, c2,      \
+                                                                                h->d_flag, h->d_err, h->watchdog)
+#define SD_DS_SHAPE(BB, NN)                                                                                    \
+    if (oseen) {                                                                                               \
+        if (comp) SD_DS(T_OSEEN, true, BB, NN); else SD_DS(T_OSEEN, false, BB, NN);                            \
+    } else {                                                                                                   \
+        if (comp) SD_DS(T_RP, true, BB, NN); else SD_DS(T_RP, false, BB, NN);                                  \
+    }
+        if (g.I == 512) {
+            SD_DS_SHAPE(512, 128)
+        } else if (h->sym_nt == 64) {
+            SD_DS_SHAPE(256, 64)
         } else {
-            if (oseen) {
-                if (comp) SD_DS(T_OSEEN, true, kSymBSmall); else SD_DS(T_OSEEN, false, kSymBSmall);
-            } else {
-                if (comp) SD_DS(T_RP, true, kSymBSmall); else SD_DS(T_RP, false, kSymBSmall);
-            }
+            SD_DS_SHAPE(256, 128)
         }
+#undef SD_DS_SHAPE
 #undef SD_DS
         return;
     }

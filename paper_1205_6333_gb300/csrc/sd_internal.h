@@ -40,9 +40,6 @@ constexpr int kJmax = 256;       // largest j-tile
 constexpr double kRSafe = 1.0;   // pairs closer than kRSafe * a make the FP32 kernel clamp every tile
 constexpr long long kDefaultWatchdog = 1LL << 22;
 constexpr int kNearPerParticle = 16;  // near-pass list capacity per particle (overflow: in-place path)
-constexpr int kSymNT = 128;      // threads per CTA of the symmetric FP32 kernel
-constexpr int kSymBSmall = 256;  // its particles per block (2 per thread) = sources per tile ...
-constexpr int kSymBLarge = 512;  // ... or 4 per thread, for large N
 
 // Partition of the (i-block, j-tile) plane over a persistent grid: CTA b takes
 // the row-major tile range [b*chunk, min((b+1)*chunk, nIB*nJT)).  The CTAs that
@@ -190,6 +187,7 @@ struct sd_handle {
     float *jpart = nullptr;  size_t jpart_bytes = 0;   // symmetric kernel: source-side sums [tile][3][block]
     sd::DenseGeom geom{}, geomv{};
     int dense_occ = 0, vjp_occ = 0;
+    int sym_nt = 128;   // threads per CTA of the symmetric kernel's chosen block shape
 
     sd::CellList cl;
     double *near64 = nullptr;   // [n][6] FP64 near-pair corrections (clamped / unclamped variant)

@@ -34,7 +34,7 @@ def system_with_overlaps(n, phi=0.05, seed=1, overlaps=3):
     return x, L
 
 
-def periodic_rel_err(v, ref, x, F, box, tensor="rpy", a=1.0, eta=1.0, margin=4e-6):
+def periodic_rel_err(v, ref, x, F, box, tensor="rpy", a=1.0, eta=1.0, margin=4e-6, rows=None):
     """rel_err for a periodic box where the nearest image is ambiguous.
 
     A pair whose separation lies within margin * L of half a period in some
@@ -42,7 +42,7 @@ def periodic_rel_err(v, ref, x, F, box, tensor="rpy", a=1.0, eta=1.0, margin=4e-
     interacts), and FP32 separations decide that tie at FP32 precision.  Both
     choices are correct, so for every particle the error is taken against the
     closest of the oracle values with any subset of its tie pairs switched to the
-    other image."""
+    other image.  With `rows`, v and ref hold those particles' velocities only."""
     import itertools
 
     import oracle
@@ -54,20 +54,20 @@ def periodic_rel_err(v, ref, x, F, box, tensor="rpy", a=1.0, eta=1.0, margin=4e-
     L = np.asarray(box, dtype=np.float64)
     per = L > 0
     n = x.shape[0]
-    alts = {}   # particle -> list of velocity changes, one per tie pair
-    for i0 in range(0, n, 512):
-        d = x[i0:i0 + 512, None, :] - x[None, :, :]
+    idx = np.arange(n) if rows is None else np.asarray(rows)
+    alts = {}   # position in v -> list of velocity changes, one per tie pair
+    for i0 in range(0, idx.size, 512):
+        d = x[idx[i0:i0 + 512], None, :] - x[None, :, :]
         img = np.where(per, d - L * np.round(d / np.where(per, L, 1.0)), d)
         near_tie = per & (np.abs(np.abs(img) - 0.5 * L) < margin * L)
         for ii, j, k in zip(*np.nonzero(near_tie)):
-            i = i0 + ii
-            if i == j:
+            if idx[i0 + ii] == j:
                 continue
             r1 = img[ii, j]
             r2 = r1.copy()
             r2[k] -= np.sign(r1[k]) * L[k]
             dv = (oracle.pair_tensor(r2, tensor, a, eta) - oracle.pair_tensor(r1, tensor, a, eta)) @ F[j]
-            alts.setdefault(int(i), []).append(dv)
+            alts.setdefault(int(i0 + ii), []).append(dv)
     den = np.linalg.norm(ref, axis=1).max()
     err = np.linalg.norm(v - ref, axis=1)
     for i, dvs in alts.items():

@@ -7,7 +7,7 @@ import pytest
 import oracle
 import paper_1205_6333_gb300 as sd
 from paper_1205_6333_gb300 import inputs
-from helpers import TOL, rel_err, system_with_overlaps
+from helpers import TOL, periodic_rel_err, rel_err, system_with_overlaps
 
 pytestmark = pytest.mark.gpu
 
@@ -93,3 +93,28 @@ def test_auto_choice_and_fp64_rejection():
     with pytest.raises(sd.SDError) as ei:
         sd.System(100, prec="fp64", dense="symmetric")
     assert ei.value.status_name == "SD_ERR_UNSUPPORTED"
+
+
+@pytest.mark.parametrize("n", [9000, 33000])   # blocks of 256 x 64 threads, and of 512 x 128 threads
+@pytest.mark.parametrize("tensor", ["rpy", "oseen"])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_four_target_block_shapes(n, tensor, periodic):
+    """The block shapes with four targets per thread (mid-size and large N), ragged
+    last blocks, overlapping pairs, unbounded and periodic, on sampled rows; the
+    overlapping pairs are among the rows."""
+    x, L = system_with_overlaps(n, 0.05, seed=500 + n, overlaps=6)
+    box = (L, L, L) if periodic else None
+    if periodic:
+        x = x + L * np.random.default_rng(501).integers(-1, 2, x.shape)   # unwrapped images
+    F = inputs.normal_forces(n, seed=502 + n)
+    with sd.System(n, tensor=tensor, box=box) as s:
+        assert s.dense_kernel() == "symmetric"
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+    rows = np.concatenate([np.arange(12), np.random.default_rng(n).choice(n, 300, replace=False), [n - 1]])
+    rows = np.unique(rows).astype(np.int32)
+    ref = oracle.mobility_rows(x, F, rows, tensor, box=box, nthreads=8)
+    if periodic:
+        assert periodic_rel_err(v[rows], ref, x, F, box, tensor, rows=rows) <= TOL["fp32c"]
+    else:
+        assert rel_err(v[rows], ref) <= TOL["fp32c"]
