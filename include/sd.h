@@ -71,9 +71,11 @@ typedef enum { SD_DTYPE_F32 = 0, SD_DTYPE_F64 = 1 } sd_dtype;
  *   DIRECTED : every ordered pair (i, j) separately, as in Sec. 3.2.
  *   SYMMETRIC: every unordered pair once, its term used for both particles
  *              (mu_ij = mu_ji, Sec. 2.2).  Each direction's FP32 term is the same
- *              as DIRECTED's; only the order of the sums differs.  Needs
- *              ceil(n/1024)*1024 / 256 = nb blocks and nb (nb + 1) / 2 * 3 KB of
- *              device memory for the source-side partial sums.
+ *              as DIRECTED's; only the order of the sums differs.  The
+ *              particles are cut into nb = npad / B blocks (npad = n rounded up
+ *              to a multiple of 1024; B = 512 from npad = 32768 on, else 256),
+ *              and the source-side partial sums take nb (nb + 1) / 2 * 12 B
+ *              bytes of device memory.
  *   AUTO     : SYMMETRIC once there is at least one block pair per two SMs
  *              (nb (nb + 1) / 2 >= SMs / 2; n > 2048 on a 152-SM GB300), else
  *              DIRECTED. */
