@@ -139,41 +139,46 @@ static cudaError_t launch_step(sd_handle *h, cudaStream_t st, double dt, const d
     return e;
 }
 
-static void drop_graphs(sd_handle *h) {
-    if (h->gexec) cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
-    h->g_steps = 0;
-}
-
 constexpr int kGraphSteps = 16;   // steps per captured graph (even: ends on the starting buffer)
 
-static sd_status capture_steps(sd_handle *h, double dt, int cur) {
-    drop_graphs(h);
+static void drop_graphs(sd_handle *h) {
+    for (int k = 0; k < 2; ++k)
+        for (int c = 0; c < 2; ++c) {
+            if (h->gexec[k][c]) cudaGraphExecDestroy(h->gexec[k][c]);
+            h->gexec[k][c] = nullptr;
+        }
+}
+
+// kGraphSteps (k = 0) or one (k = 1) Euler steps from buffer `cur`, captured into a
+// graph and cached per (k, cur, dt): a step's dozen launches become one graph launch
+// (the GPU no longer waits on each small launch at small N, nor after a host round trip).
+static sd_status capture_steps(sd_handle *h, double dt, int cur, int k) {
+    if (h->gexec[k][cur]) cudaGraphExecDestroy(h->gexec[k][cur]);
+    h->gexec[k][cur] = nullptr;
     cudaGraph_t graph = nullptr;
     SD_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     h->capturing = true;
     const int64_t l0 = h->launches;
     cudaError_t e = cudaSuccess;
     int c = cur;
-    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+    const int steps = k == 0 ? kGraphSteps : 1;
+    for (int q = 0; q < steps && e == cudaSuccess; ++q) {
         e = launch_step(h, h->cap, dt, h->x64[c], h->x64[1 - c]);
         c = 1 - c;
     }
     h->capturing = false;
     cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
-    h->g_kernels = h->launches - l0;
+    h->g_kernels[k][cur] = h->launches - l0;
     h->launches = l0;
     if (e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         return cuda_status(e, "capture of Euler steps");
     }
     if (e2 != cudaSuccess) return cuda_status(e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    e = cudaGraphInstantiate(&h->gexec[k][cur], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate");
-    h->g_steps = kGraphSteps;
-    h->g_dt = dt;
-    h->g_cur = cur;
+    h->g_dt[k][cur] = dt;
     return SD_OK;
 }
 
@@ -564,21 +569,34 @@ sd_status sd_step(sd_handle *h, double dt, int64_t nsteps) {
     if (h->n == 0 || nsteps == 0) return SD_OK;
     cudaSetDevice(h->device);
     int64_t left = nsteps;
+    // replay cached graphs (16 steps, then single steps); with the profiler on, launch
+    // eagerly so that every kernel family gets its own event pair
+    auto replay = [&](int k) -> sd_status {
+        const int c = h->cur;
+        if (!h->gexec[k][c] || h->g_dt[k][c] != dt) {
+            sd_status s = capture_steps(h, dt, c, k);
+            if (s != SD_OK) return s;
+        }
+        SD_CUDA(cudaGraphLaunch(h->gexec[k][c], h->stream));
+        h->launches += h->g_kernels[k][c];
+        return SD_OK;
+    };
     if (!h->prof.on) {
         while (left >= kGraphSteps) {
-            if (!h->gexec || h->g_dt != dt || h->g_cur != h->cur) {
-                sd_status s = capture_steps(h, dt, h->cur);
-                if (s != SD_OK) return s;
-            }
-            SD_CUDA(cudaGraphLaunch(h->gexec, h->stream));
-            h->launches += h->g_kernels;
+            sd_status s = replay(0);
+            if (s != SD_OK) return s;
             left -= kGraphSteps;   // even count: the state ends in buffer h->cur again
         }
     }
     for (; left > 0; --left) {
         const int c = h->cur;
-        sd_status s = launch_check(launch_step(h, h->stream, dt, h->x64[c], h->x64[1 - c]), "Euler step");
-        if (s != SD_OK) return s;
+        if (!h->prof.on) {
+            sd_status s = replay(1);
+            if (s != SD_OK) return s;
+        } else {
+            sd_status s = launch_check(launch_step(h, h->stream, dt, h->x64[c], h->x64[1 - c]), "Euler step");
+            if (s != SD_OK) return s;
+        }
         h->cur = 1 - c;
     }
     h->cells_valid = false;

@@ -199,16 +199,11 @@ struct sd_handle {
     int *d_flag = nullptr;      // set by the near pass when some pair has r < kRSafe a
     int *d_err = nullptr;
 
-    // graph cache for sd_step
-    cudaGraphExec_t gexec = nullptr;
-    int g_steps = 0;
-    double g_dt = 0.0;
-    int g_cur = -1;
-    int64_t g_kernels = 0;   // kernel nodes in the cached graph
-    cudaGraphExec_t gexec1 = nullptr;   // single-step graph (odd remainder)
-    int g1_cur = -1;
-    double g1_dt = 0.0;
-    int64_t g1_kernels = 0;
+    // graph cache for sd_step: [0] 16 steps, [1] one step; each for both parities of
+    // the position buffer the first step reads
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    double g_dt[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    int64_t g_kernels[2][2] = {{0, 0}, {0, 0}};   // kernel nodes in each cached graph
 
     // adjoint storage (allocated on first use)
     double *ckpt = nullptr; size_t ckpt_bytes = 0;

@@ -99,16 +99,24 @@ def test_external_forces_and_overlaps_step():
 
 
 def test_graph_replay_equals_eager_steps():
+    """16-step graphs + single-step graphs, single-step graphs alone, and eager
+    launches (the profiler's mode) give the same trajectory bit for bit."""
     n = 1000
     x0, _ = inputs.cube_rsa(n, 0.05, 31)
     with sd.System(n, gravity=(0, 0, -1.0), rep_eps=1.0) as s:
         s.set_positions(x0)
-        s.step(0.01, 35)          # two graph replays + 3 eager steps
+        s.step(0.01, 35)          # two 16-step replays + 3 single-step replays
         a = s.get_positions()
         s.set_positions(x0)
         for _ in range(35):
             s.step(0.01, 1)
         b = s.get_positions()
+        s.set_positions(x0)
+        s.profile(True)           # eager launches, one event pair per kernel family
+        s.step(0.01, 35)
+        s.profile(False)
+        e = s.get_positions()
+        np.testing.assert_array_equal(a, e)
         c0 = s.launch_count()
         s.step(0.01, 16)
         s.synchronize()
