@@ -141,12 +141,20 @@ static cudaError_t launch_step(sd_handle *h, cudaStream_t st, double dt, const d
 
 constexpr int kGraphSteps = 16;   // steps per captured graph (even: ends on the starting buffer)
 
+static void drop_adjoint_graphs(sd_handle *h) {
+    if (h->adj_rec) cudaGraphExecDestroy(h->adj_rec);
+    if (h->adj_rev) cudaGraphExecDestroy(h->adj_rev);
+    h->adj_rec = h->adj_rev = nullptr;
+    h->adj_K = 0;
+}
+
 static void drop_graphs(sd_handle *h) {
     for (int k = 0; k < 2; ++k)
         for (int c = 0; c < 2; ++c) {
             if (h->gexec[k][c]) cudaGraphExecDestroy(h->gexec[k][c]);
             h->gexec[k][c] = nullptr;
         }
+    drop_adjoint_graphs(h);
 }
 
 // kGraphSteps (k = 0) or one (k = 1) Euler steps from buffer `cur`, captured into a
@@ -179,6 +187,101 @@ static sd_status capture_steps(sd_handle *h, double dt, int cur, int k) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate");
     h->g_dt[k][cur] = dt;
+    return SD_OK;
+}
+
+// nsteps Euler steps: cached 16-step graphs, then cached single-step graphs; with the
+// profiler on, eager launches so that every kernel family gets its own event pair.
+static sd_status run_steps(sd_handle *h, double dt, int64_t nsteps) {
+    int64_t left = nsteps;
+    auto replay = [&](int k) -> sd_status {
+        const int c = h->cur;
+        if (!h->gexec[k][c] || h->g_dt[k][c] != dt) {
+            sd_status s = capture_steps(h, dt, c, k);
+            if (s != SD_OK) return s;
+        }
+        SD_CUDA(cudaGraphLaunch(h->gexec[k][c], h->stream));
+        h->launches += h->g_kernels[k][c];
+        return SD_OK;
+    };
+    if (!h->prof.on) {
+        while (left >= kGraphSteps) {
+            sd_status s = replay(0);
+            if (s != SD_OK) return s;
+            left -= kGraphSteps;   // even count: the state ends in buffer h->cur again
+        }
+    }
+    for (; left > 0; --left) {
+        const int c = h->cur;
+        if (!h->prof.on) {
+            sd_status s = replay(1);
+            if (s != SD_OK) return s;
+        } else {
+            sd_status s = launch_check(launch_step(h, h->stream, dt, h->x64[c], h->x64[1 - c]), "Euler step");
+            if (s != SD_OK) return s;
+        }
+        h->cur = 1 - c;
+    }
+    h->cells_valid = false;
+    return SD_OK;
+}
+
+// The adjoint's work on one checkpoint segment of K steps, on stream st:
+//   recompute (part 0): x_{k+1} = x_k + dt v(x_k) into seg, k = 0 .. K-2;
+//   reverse (part 1), k = K-1 .. 0: W = lambda; lambda += dt (dv/dx(x_k))^T W; gF += dt mu(x_k) W.
+static cudaError_t adjoint_segment(sd_handle *h, cudaStream_t st, double dt, int64_t len, int part) {
+    const size_t n3 = 3 * static_cast<size_t>(h->n);
+    auto segx = [&](int64_t k) { return h->seg + static_cast<size_t>(k) * n3; };
+    cudaError_t e = cudaSuccess;
+    if (part == 0) {
+        for (int64_t k = 0; k + 1 < len && e == cudaSuccess; ++k) e = launch_step(h, st, dt, segx(k), segx(k + 1));
+        return e;
+    }
+    for (int64_t k = len - 1; k >= 0 && e == cudaSuccess; --k) {
+        e = launch_stage_forces(h, st, h->lam, SD_DTYPE_F64, 0, h->Wa64, h->wam);
+        if (e == cudaSuccess) e = launch_build_cells(h, st, segx(k), h->posm);
+        if (e == cudaSuccess) e = launch_vjp_dense(h, st, h->posm.aos, h->frcm.aos, h->wam.aos, h->part, h->part2);
+        if (e == cudaSuccess)
+            e = launch_vjp_epilogue(h, st, segx(k), h->posm.aos, h->F64, h->frcm.aos, h->Wa64, h->wam.aos, -1,
+                                    nullptr, nullptr, dt, h->lam, h->gFacc);
+    }
+    return e;
+}
+
+// Graphs of both parts for a full segment of K steps (the recompute part only when
+// K > 1), cached per (dt, K).
+static sd_status capture_adjoint(sd_handle *h, double dt, int64_t K) {
+    drop_adjoint_graphs(h);
+    for (int part = 0; part < 2; ++part) {
+        if (part == 0 && K < 2) continue;
+        cudaGraph_t graph = nullptr;
+        SD_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        h->capturing = true;
+        const int64_t l0 = h->launches;
+        cudaError_t e = adjoint_segment(h, h->cap, dt, K, part);
+        h->capturing = false;
+        cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
+        const int64_t kernels = h->launches - l0;
+        h->launches = l0;
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            drop_adjoint_graphs(h);
+            return cuda_status(e, "capture of an adjoint segment");
+        }
+        if (e2 != cudaSuccess) {
+            drop_adjoint_graphs(h);
+            return cuda_status(e2, "cudaStreamEndCapture");
+        }
+        e = cudaGraphInstantiate(part == 0 ? &h->adj_rec : &h->adj_rev, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            drop_adjoint_graphs(h);
+            return cuda_status(e, "cudaGraphInstantiate");
+        }
+        (part == 0 ? h->adj_rec_kernels : h->adj_rev_kernels) = kernels;
+    }
+    h->adj_dt = dt;
+    h->adj_K = K;
     return SD_OK;
 }
 
@@ -568,39 +671,7 @@ sd_status sd_step(sd_handle *h, double dt, int64_t nsteps) {
     if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
     if (h->n == 0 || nsteps == 0) return SD_OK;
     cudaSetDevice(h->device);
-    int64_t left = nsteps;
-    // replay cached graphs (16 steps, then single steps); with the profiler on, launch
-    // eagerly so that every kernel family gets its own event pair
-    auto replay = [&](int k) -> sd_status {
-        const int c = h->cur;
-        if (!h->gexec[k][c] || h->g_dt[k][c] != dt) {
-            sd_status s = capture_steps(h, dt, c, k);
-            if (s != SD_OK) return s;
-        }
-        SD_CUDA(cudaGraphLaunch(h->gexec[k][c], h->stream));
-        h->launches += h->g_kernels[k][c];
-        return SD_OK;
-    };
-    if (!h->prof.on) {
-        while (left >= kGraphSteps) {
-            sd_status s = replay(0);
-            if (s != SD_OK) return s;
-            left -= kGraphSteps;   // even count: the state ends in buffer h->cur again
-        }
-    }
-    for (; left > 0; --left) {
-        const int c = h->cur;
-        if (!h->prof.on) {
-            sd_status s = replay(1);
-            if (s != SD_OK) return s;
-        } else {
-            sd_status s = launch_check(launch_step(h, h->stream, dt, h->x64[c], h->x64[1 - c]), "Euler step");
-            if (s != SD_OK) return s;
-        }
-        h->cur = 1 - c;
-    }
-    h->cells_valid = false;
-    return SD_OK;
+    return run_steps(h, dt, nsteps);
 }
 
 sd_status sd_mobility_vjp(sd_handle *h, const void *F, const void *W, void *gX, void *gF, int dtype, int on_device) {
@@ -618,6 +689,7 @@ sd_status sd_mobility_vjp(sd_handle *h, const void *F, const void *W, void *gX, 
         // four n x 3 arrays: F, W in; gX, gF out
         const size_t need = 4 * 3 * sizeof(double) * static_cast<size_t>(h->n);
         if (!h->seg || h->seg_bytes < need) {
+            drop_adjoint_graphs(h);   // they hold the old buffer
             dfree(h, h->seg);
             h->seg = static_cast<double *>(dalloc(h, need));
             h->seg_bytes = h->seg ? need : 0;
@@ -676,6 +748,7 @@ sd_status sd_adjoint(sd_handle *h, double dt, int64_t nsteps, int32_t ckpt_every
     }
     const size_t seg_need = static_cast<size_t>(K) * xb;
     if (!h->seg || h->seg_bytes < seg_need) {
+        drop_adjoint_graphs(h);   // they hold the old buffer
         dfree(h, h->seg);
         h->seg = static_cast<double *>(dalloc(h, seg_need));
         h->seg_bytes = h->seg ? seg_need : 0;
@@ -688,15 +761,17 @@ sd_status sd_adjoint(sd_handle *h, double dt, int64_t nsteps, int32_t ckpt_every
     auto segx = [&](int64_t k) { return h->seg + static_cast<size_t>(k) * n3; };
 
     const int c0 = h->cur;
-    // forward with checkpoints (the state ping-pongs through x64[0], x64[1])
+    const int64_t nseg = (nsteps + K - 1) / K;
+    // forward with checkpoints, segment by segment through the step graphs (the state
+    // ping-pongs through x64[0], x64[1])
     SD_CUDA(cudaMemcpyAsync(h->ckpt, h->x64[c0], xb, cudaMemcpyDeviceToDevice, st));
-    int c = c0;
-    for (int64_t s = 0; s < nsteps; ++s) {
-        sd_status ss = launch_check(launch_step(h, st, dt, h->x64[c], h->x64[1 - c]), "adjoint forward");
+    for (int64_t sg = 0; sg < nseg; ++sg) {
+        const int64_t len = std::min(K, nsteps - sg * K);
+        sd_status ss = run_steps(h, dt, len);
         if (ss != SD_OK) return ss;
-        c = 1 - c;
-        if ((s + 1) % K == 0 && (s + 1) / K < nck)
-            SD_CUDA(cudaMemcpyAsync(h->ckpt + static_cast<size_t>((s + 1) / K) * n3, h->x64[c], xb,
+        const int64_t s1 = sg * K + len;
+        if (s1 % K == 0 && s1 / K < nck)
+            SD_CUDA(cudaMemcpyAsync(h->ckpt + static_cast<size_t>(s1 / K) * n3, h->x64[h->cur], xb,
                                     cudaMemcpyDeviceToDevice, st));
     }
     // lambda_T
@@ -705,25 +780,28 @@ sd_status sd_adjoint(sd_handle *h, double dt, int64_t nsteps, int32_t ckpt_every
     else
         SD_CUDA(cudaMemcpyAsync(h->lam, gxT, xb, cudaMemcpyHostToDevice, st));
     SD_CUDA(cudaMemsetAsync(h->gFacc, 0, xb, st));
-    const int64_t nseg = (nsteps + K - 1) / K;
+    // reverse sweep, last segment first: recompute the segment's positions from its
+    // checkpoint, then walk it backwards.  Full segments replay cached graphs (eager
+    // with the profiler on, and for a shorter last segment).
     for (int64_t sg = nseg - 1; sg >= 0; --sg) {
-        const int64_t s0 = sg * K, s1 = std::min(s0 + K, nsteps);
+        const int64_t len = std::min(K, nsteps - sg * K);
         SD_CUDA(cudaMemcpyAsync(segx(0), h->ckpt + static_cast<size_t>(sg) * n3, xb, cudaMemcpyDeviceToDevice, st));
-        sd_status ss = SD_OK;
-        for (int64_t k = 0; k + 1 < s1 - s0 && ss == SD_OK; ++k)
-            ss = launch_check(launch_step(h, st, dt, segx(k), segx(k + 1)), "recompute");
-        for (int64_t k = s1 - s0 - 1; k >= 0 && ss == SD_OK; --k) {
-            // W = lambda_{n+1} (FP64 copy + mirror); lambda_n = W + dt gX; gF += dt mu W
-            ss = launch_check(launch_stage_forces(h, st, h->lam, SD_DTYPE_F64, 0, h->Wa64, h->wam), "stage lambda");
-            if (ss == SD_OK) ss = launch_check(launch_build_cells(h, st, segx(k), h->posm), "cells");
-            if (ss == SD_OK)
-                ss = launch_check(launch_vjp_dense(h, st, h->posm.aos, h->frcm.aos, h->wam.aos, h->part, h->part2), "vjp");
-            if (ss == SD_OK)
-                ss = launch_check(launch_vjp_epilogue(h, st, segx(k), h->posm.aos, h->F64, h->frcm.aos, h->Wa64, h->wam.aos, -1,
-                                                      nullptr, nullptr, dt, h->lam, h->gFacc),
-                                  "vjp epilogue");
+        if (len == K && !h->prof.on) {
+            if (!h->adj_rev || h->adj_dt != dt || h->adj_K != K) {
+                sd_status ss = capture_adjoint(h, dt, K);
+                if (ss != SD_OK) return ss;
+            }
+            if (h->adj_rec) {
+                SD_CUDA(cudaGraphLaunch(h->adj_rec, st));
+                h->launches += h->adj_rec_kernels;
+            }
+            SD_CUDA(cudaGraphLaunch(h->adj_rev, st));
+            h->launches += h->adj_rev_kernels;
+        } else {
+            sd_status ss = launch_check(adjoint_segment(h, st, dt, len, 0), "recompute");
+            if (ss == SD_OK) ss = launch_check(adjoint_segment(h, st, dt, len, 1), "adjoint sweep");
+            if (ss != SD_OK) return ss;
         }
-        if (ss != SD_OK) return ss;
     }
     // restore x0 into the current buffers
     SD_CUDA(cudaMemcpyAsync(h->x64[c0], h->ckpt, xb, cudaMemcpyDeviceToDevice, st));

@@ -209,6 +209,11 @@ struct sd_handle {
     double *ckpt = nullptr; size_t ckpt_bytes = 0;
     double *seg = nullptr;  size_t seg_bytes = 0;
     double *lam = nullptr;  double *gFacc = nullptr;
+    // adjoint graphs of one full checkpoint segment (cached per dt and segment length;
+    // they hold seg, lam and gFacc: dropped whenever seg is reallocated)
+    cudaGraphExec_t adj_rec = nullptr, adj_rev = nullptr;
+    double adj_dt = 0.0;
+    int64_t adj_K = 0, adj_rec_kernels = 0, adj_rev_kernels = 0;
 
     sd::Profiler prof;
     int64_t launches = 0;

@@ -276,25 +276,27 @@ struct VjpEpiArgs {
     int *err;
 };
 
+// One lane's share of particle i's VJP terms: the CTA slots sub, sub + kWalkLanes, ...
+// of the dense partial sums, the self term (sub-lane 0), and the FP64 near pairs of
+// the neighbour cells sub, sub + kWalkLanes, ... of the 27.  MG = (M, G): the mu W
+// part and the x-derivative part, before the factor mu0.
 template <int TENSOR, int MODE>
-__global__ void __launch_bounds__(128) vjp_epilogue_kernel(VjpEpiArgs a) {
+__device__ __forceinline__ void vjp_epilogue_lane(const VjpEpiArgs &a, int i, int sub,
+                                                  const typename VjpT<MODE>::V4 *pm,
+                                                  const typename VjpT<MODE>::V4 *fm,
+                                                  const typename VjpT<MODE>::V4 *wm, double (&MG)[6],
+                                                  bool &coincident) {
     using V4 = typename VjpT<MODE>::V4;
     using V3 = typename VjpT<MODE>::V3;
     using S = typename VjpT<MODE>::S;
     constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const V4 *pm = static_cast<const V4 *>(a.posm);
-    const V4 *fm = static_cast<const V4 *>(a.frcm);
-    const V4 *wm = static_cast<const V4 *>(a.wm);
-    double M[3] = {0.0, 0.0, 0.0}, G[3] = {0.0, 0.0, 0.0};
     {
         const int ib = i / a.g.I;
         const int ns = geom_last(a.g, ib) - geom_first(a.g, ib) + 1;
-        for (int s = 0; s < ns; ++s)
+        for (int s = sub; s < ns; s += kWalkLanes)
             for (int d = 0; d < 3; ++d) {
-                M[d] += a.partM[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
-                G[d] += a.partG[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+                MG[d] += a.partM[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+                MG[3 + d] += a.partG[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
             }
     }
     const V4 pi = pm[i], fi4 = fm[i], wi4 = wm[i];
@@ -312,19 +314,18 @@ __global__ void __launch_bounds__(128) vjp_epilogue_kernel(VjpEpiArgs a) {
         tm[0] = m.x; tm[1] = m.y; tm[2] = m.z;
         tg[0] = g.x; tg[1] = g.y; tg[2] = g.z;
     };
-    {   // self: mu_ii W_i / mu0 = W_i; its x-derivative is zero
+    if (sub == 0) {   // self: mu_ii W_i / mu0 = W_i; its x-derivative is zero
         double tm[3], tg[3];
         dense(pi, fi4, wi4, tm, tg);
         for (int d = 0; d < 3; ++d) {
-            M[d] += a.W64[3 * i + d] - tm[d];
-            G[d] -= tg[d];
+            MG[d] += a.W64[3 * i + d] - tm[d];
+            MG[3 + d] -= tg[d];
         }
     }
     const double xi = a.x64[3 * i], yi = a.x64[3 * i + 1], zi = a.x64[3 * i + 2];
     const double Fx = a.F64[3 * i], Fy = a.F64[3 * i + 1], Fz = a.F64[3 * i + 2];
     const double Wx = a.W64[3 * i], Wy = a.W64[3 * i + 1], Wz = a.W64[3 * i + 2];
-    bool coincident = false;
-    for_each_neighbour(a.cl, i, a.cl.cell[i], [&](int j) {
+    for_each_neighbour_part(a.cl, i, a.cl.cell[i], sub, kWalkLanes, [&](int j) {
         double dx = xi - a.x64[3 * j], dy = yi - a.x64[3 * j + 1], dz = zi - a.x64[3 * j + 2];
         box_image(a.cl.box, dx, dy, dz);
         const double r2 = dx * dx + dy * dy + dz * dz;
@@ -344,18 +345,37 @@ __global__ void __launch_bounds__(128) vjp_epilogue_kernel(VjpEpiArgs a) {
         const double cr = dA * U + dB * Q;
         double tm[3], tg[3];
         dense(pm[j], fm[j], wm[j], tm, tg);
-        M[0] += A * wx + B * Wjr * dx - tm[0];
-        M[1] += A * wy + B * Wjr * dy - tm[1];
-        M[2] += A * wz + B * Wjr * dz - tm[2];
-        G[0] += cr * dx + B * (Wx * Fjr + fx * Wir + wx * Fir + Fx * Wjr) - tg[0];
-        G[1] += cr * dy + B * (Wy * Fjr + fy * Wir + wy * Fir + Fy * Wjr) - tg[1];
-        G[2] += cr * dz + B * (Wz * Fjr + fz * Wir + wz * Fir + Fz * Wjr) - tg[2];
+        MG[0] += A * wx + B * Wjr * dx - tm[0];
+        MG[1] += A * wy + B * Wjr * dy - tm[1];
+        MG[2] += A * wz + B * Wjr * dz - tm[2];
+        MG[3] += cr * dx + B * (Wx * Fjr + fx * Wir + wx * Fir + Fx * Wjr) - tg[0];
+        MG[4] += cr * dy + B * (Wy * Fjr + fy * Wir + wy * Fir + Fy * Wjr) - tg[1];
+        MG[5] += cr * dz + B * (Wz * Fjr + fz * Wir + wz * Fir + Fz * Wjr) - tg[2];
     });
+}
+
+// kWalkLanes threads per particle; their partial sums meet in the fixed shuffle tree
+// of walk_sum (deterministic), and sub-lane 0 writes the particle's results.
+template <int TENSOR, int MODE>
+__global__ void __launch_bounds__(128) vjp_epilogue_kernel(VjpEpiArgs a) {
+    using V4 = typename VjpT<MODE>::V4;
+    const long long gt = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int i = static_cast<int>(gt / kWalkLanes), sub = static_cast<int>(gt % kWalkLanes);
+    const bool active = i < a.n;
+    double MG[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    bool coincident = false;
+    if (active)
+        vjp_epilogue_lane<TENSOR, MODE>(a, i, sub, static_cast<const V4 *>(a.posm), static_cast<const V4 *>(a.frcm),
+                                        static_cast<const V4 *>(a.wm), MG, coincident);
+    for (int d = 0; d < 6; ++d) MG[d] = walk_sum(MG[d]);
+    coincident = walk_any(coincident);
+    if (!active || sub != 0) return;
     if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
     const double m0 = a.pc.mu0;
+    double M[3], G[3];
     for (int d = 0; d < 3; ++d) {
-        M[d] *= m0;
-        G[d] *= m0;
+        M[d] = MG[d] * m0;
+        G[d] = MG[3 + d] * m0;
     }
     if (a.out_dtype == SD_DTYPE_F32) {
         float *gx = static_cast<float *>(a.gx_out), *gF = static_cast<float *>(a.gF_out);
@@ -404,7 +424,7 @@ cudaError_t launch_vjp_epilogue(sd_handle *h, cudaStream_t st, const double *x64
     a.lam_out = lam_out;
     a.gF_acc = gF_acc;
     a.err = h->d_err;
-    const int nb = (h->n + 127) / 128;
+    const int nb = static_cast<int>((static_cast<long long>(h->n) * kWalkLanes + 127) / 128);
     prof_begin(h, SD_KERNEL_EPILOGUE, st);
     const bool f64 = h->mode == MODE_FP64;
     switch (h->tensor) {

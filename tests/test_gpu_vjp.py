@@ -52,6 +52,34 @@ def test_adjoint_matches_oracle_n64():
         assert rel_err(gF, rF) <= tol, prec
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_adjoint_graphs_equal_eager(prec):
+    """Full checkpoint segments replay cached graphs; with the profiler on every launch
+    is eager.  Both give the same gradients bit for bit: a ragged last segment
+    (nsteps not a multiple of K), K = 1 (no recompute part), a repeated call, and a
+    call after sd_mobility_vjp has reallocated the staging buffer the graphs use."""
+    n = 700
+    x0, target = _adjoint_case(n, inputs.SEED_BASE + 7)
+    g = (0.0, 0.0, -1.0)
+    F = inputs.normal_forces(n, 8)
+    with sd.System(n, prec=prec, gravity=g) as s:
+        s.set_positions(x0)
+        xT = x0 + 0.1
+        gxT = 2.0 * (xT - target)
+        for nsteps, K in [(40, 1), (130, 50), (100, 25)]:   # staging buffer 24n, then 96n (vjp), then 1200n B
+            s.profile(True)
+            ref = s.adjoint(0.01, nsteps, K, gxT)
+            s.profile(False)
+            got = s.adjoint(0.01, nsteps, K, gxT)          # captures the segment graphs
+            again = s.adjoint(0.01, nsteps, K, gxT)        # replays them
+            for a, b, c in zip(ref, got, again):
+                np.testing.assert_array_equal(a, b)
+                np.testing.assert_array_equal(a, c)
+            s.vjp(F, gxT)                                   # host arrays: reallocates the staging buffer
+            np.testing.assert_array_equal(s.adjoint(0.01, nsteps, K, gxT)[0], ref[0])
+        np.testing.assert_array_equal(s.get_positions(), x0)
+
+
 def test_adjoint_finite_differences_fp64():
     """Central differences (h = 1e-4) of the GPU FP64 trajectory loss."""
     x0, target = _adjoint_case()
