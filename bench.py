@@ -38,7 +38,7 @@ UNIT = "pair-interactions/s"
 N_MAIN = 65536
 PHI = 0.05
 DT = 0.01
-FLOPS_PER_PAIR = 34          # RPY pair term, FMA = 2 flops
+FLOPS_PER_PAIR = 34          # RPY pair term: 3 FADD, 7 FMUL, 12 FFMA (FMA = 2 flops), plus one rsqrt
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
@@ -310,17 +310,22 @@ def run_ours(args):
     ms_step = t_ms / args.steps
     value = world * float(n) * n / (ms_step * 1e-3)
 
-    # ---- end to end through the public API with pinned host buffers
+    # ---- end to end through the public API with pinned host buffers: every step
+    # copies its input positions in (H2D) and its result out (D2H), each as one
+    # asynchronous copy on the stream; the last result is read after the final sync
     xh = torch.from_numpy(x).pin_memory()
     outh = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     _barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s.set_positions(xh)          # H2D of the step's input (synchronous call)
+        s.set_positions(xh, asynchronous=True)     # H2D of the step's input
         s.step(DT, 1)
-        s.get_positions(outh)        # D2H of the step's result
+        s.get_positions(outh, asynchronous=True)   # D2H of the step's result
+    torch.cuda.synchronize()
     e2e_s = _max_over_ranks(time.perf_counter() - t0, world)
+    if not np.all(np.isfinite(outh.numpy())):
+        raise RuntimeError("end-to-end loop produced non-finite positions")
     e2e_value = world * float(n) * n * args.steps / e2e_s
 
     clocks = clk.summary()
@@ -332,8 +337,10 @@ def run_ours(args):
     s.close()
 
     extra = {}
+    if world > 1:
+        extra.update(_leg_tile_sharded(args, x, F, stream, world, rank))
     if rank == 0 and not args.quick:
-        extra = legs(args, x, F, stream, flush)
+        extra.update(legs(args, x, F, stream, flush, workloads=(world == 1)))
 
     if rank != 0:
         return
@@ -361,6 +368,37 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def _leg_tile_sharded(args, x, F, stream, world, rank):
+    """One N = 65,536 system split over all ranks by tile shards (strong scaling): per
+    step each rank runs its share of the all-pairs kernel, an NCCL all-gather brings
+    every share to every rank, and every rank finishes the step.  Timed like the main
+    leg (barrier, CUDA events, max over ranks)."""
+    import torch
+    import paper_1205_6333_gb300 as sd
+    from paper_1205_6333_gb300.distributed import tile_sharded_steps
+    n = x.shape[0]
+    s = sd.System(n, prec="fp32c", stream="torch", torch_allocator=True, device=torch.cuda.current_device())
+    s.set_positions(x)
+    s.set_forces(F)
+    tile_sharded_steps(s, DT, max(args.warmup, 3), rank, world)
+    torch.cuda.synchronize()
+    _barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tile_sharded_steps(s, DT, args.steps, rank, world)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(world)
+    t_ms = _max_over_ranks(e0.elapsed_time(e1), world)
+    kind = s.dense_kernel()
+    s.close()
+    ms = t_ms / args.steps
+    return {"tile_sharded": {"value": float(n) * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                             "scaling": "strong", "ranks": world, "n": n, "all_pairs_kernel": kind,
+                             "exchange": "NCCL all-gather of 24 B per particle and rank per step"}}
+
+
 def run_leg(args):
     """One extra leg alone (used for profiling it): prints its JSON object."""
     import torch
@@ -370,8 +408,10 @@ def run_leg(args):
     print(json.dumps(legs(args, x, F, stream, flush, only=args.leg)), flush=True)
 
 
-def legs(args, x, F, stream, flush, only=None):
-    """FP64 path, batched workload and the CPU oracle baseline (rank 0 only)."""
+def legs(args, x, F, stream, flush, only=None, workloads=True):
+    """FP64 path, batched workload, Oseen variant and the CPU oracle baseline (rank 0
+    only); with `workloads` (single-GPU runs) also the trajectory drift of workload 3
+    and the adjoint of workload 5."""
     out = {}
     if only in (None, "fp64"):
         out.update(_leg_fp64(args, x, F, stream, flush))
@@ -379,6 +419,9 @@ def legs(args, x, F, stream, flush, only=None):
         out.update(_leg_batched(args, stream, flush))
     if only in (None, "oseen"):
         out.update(_leg_oseen(args, x, F, stream, flush))
+    if only is None and workloads:
+        out.update(leg_drift(args))
+        out.update(leg_adjoint(args))
     if only is None:
         out["cpu_baseline"] = cpu_baseline(x, F, target_s=args.cpu_seconds)
     return out
@@ -485,7 +528,11 @@ def leg_sweep(args):
 def leg_drift(args):
     """Workload 3: N = 16,384, phi = 0.10, gravity + eps (2a/r)^12 repulsion cut at
     2.5a, Euler dt = 1e-3.  FP32C trajectory drift against the FP64 GPU path at 10^2,
-    10^3, 10^4 steps, oracle parity at 10^2 steps, FP32C steps/s."""
+    10^3, 10^4 steps, oracle parity of both at 10^2 steps, FP32C and FP64 steps/s.
+    The oracle's 100 steps run on the host cores (one left free to drive the GPU) in
+    a thread beside the GPU trajectories."""
+    import threading
+
     import torch
     import oracle
     import paper_1205_6333_gb300 as sd
@@ -493,37 +540,57 @@ def leg_drift(args):
     w = inputs.config_inputs(3)
     x0 = w["x"]
     n = x0.shape[0]
+    cores = os.cpu_count() or 1
+    ref_box = {}
+
+    def run_oracle():
+        t = time.perf_counter()
+        ref_box["x"] = oracle.euler(x0, 100, 1e-3, gravity=(0.0, 0.0, -1.0), rep_eps=1.0, rep_rc=2.5,
+                                    nthreads=max(1, cores - 1))
+        ref_box["s"] = time.perf_counter() - t
+
+    th = threading.Thread(target=run_oracle)
+    th.start()
     kw = dict(gravity=(0.0, 0.0, -1.0), rep_eps=1.0, rep_rc=2.5, stream="torch", torch_allocator=True)
     s32 = sd.System(n, prec="fp32c", **kw)
     s64 = sd.System(n, prec="fp64", **kw)
     for s in (s32, s64):
         s.set_positions(x0)
-    out = {"n": n, "checkpoints": []}
+    out = {"n": n, "dt": 1e-3, "checkpoints": [], "fp64_kernel": s64.dense_kernel()}
     done = 0
-    t32 = 0.0
+    t32 = t64 = 0.0
+    snaps = {}
     for target in (100, 1000, 10000):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        s32.step(1e-3, target - done)
-        e1.record()
-        torch.cuda.synchronize()
-        t32 += e0.elapsed_time(e1)
-        s64.step(1e-3, target - done)
+        for sys_, key in ((s32, "32"), (s64, "64")):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sys_.step(1e-3, target - done)
+            e1.record()
+            torch.cuda.synchronize()
+            if key == "32":
+                t32 += e0.elapsed_time(e1)
+            else:
+                t64 += e0.elapsed_time(e1)
         done = target
         a, b = s32.get_positions(), s64.get_positions()
+        snaps[target] = (a, b)
         disp = np.abs(b - x0).max()
         rec = {"step": target, "max_abs_diff": float(np.abs(a - b).max()),
                "rel_to_max_displacement": float(np.abs(a - b).max() / disp), "max_displacement": float(disp)}
-        if target == 100:
-            ref = oracle.euler(x0, 100, 1e-3, gravity=(0.0, 0.0, -1.0), rep_eps=1.0, rep_rc=2.5,
-                               nthreads=os.cpu_count())
-            dref = np.abs(ref - x0).max()
-            rec["oracle_rel_err_fp32c"] = float(np.abs(a - ref).max() / dref)
-            rec["oracle_rel_err_fp64"] = float(np.abs(b - ref).max() / dref)
         out["checkpoints"].append(rec)
         print(json.dumps(rec), file=sys.stderr, flush=True)
+    th.join()
+    a, b = snaps[100]
+    ref = ref_box["x"]
+    dref = np.abs(ref - x0).max()
+    out["checkpoints"][0]["oracle_rel_err_fp32c"] = float(np.abs(a - ref).max() / dref)
+    out["checkpoints"][0]["oracle_rel_err_fp64"] = float(np.abs(b - ref).max() / dref)
+    out["oracle_100_steps_s"] = ref_box["s"]
     out["fp32c_steps_per_s"] = 1e3 * done / t32
+    out["fp64_steps_per_s"] = 1e3 * done / t64
+    s32.close()
+    s64.close()
     return {"drift": out}
 
 

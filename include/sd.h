@@ -21,6 +21,11 @@
  *     synchronising call (sd_synchronize or any host-pointer call).
  *     `on_device` = 0: the pointer is host memory; the call copies, runs, and
  *     synchronises the stream before returning.
+ *     `on_device` = 2 (sd_set_positions, sd_get_positions, sd_set_forces only):
+ *     host memory, copied asynchronously on the handle's stream (a DMA when the
+ *     memory is page-locked).  The caller keeps it alive and unchanged (or unread,
+ *     for sd_get_positions) until the stream has passed the copy; errors are
+ *     deferred as for device pointers.
  *   - Caller pointers are borrowed for the duration of the call only.
  *   - The handle owns its device buffers, allocated through cfg.alloc/cfg.free
  *     when given (e.g. bound to a framework's caching allocator), else cudaMalloc.
@@ -66,19 +71,19 @@ typedef enum { SD_PREC_FP32C = 0, SD_PREC_FP64 = 1, SD_PREC_FP32 = 2 } sd_precis
 
 typedef enum { SD_DTYPE_F32 = 0, SD_DTYPE_F64 = 1 } sd_dtype;
 
-/* How the FP32 all-pairs kernel visits the pairs (FP32C and FP32 only; FP64 is
- * always DIRECTED).
+/* How the all-pairs kernel visits the pairs.
  *   DIRECTED : every ordered pair (i, j) separately, as in Sec. 3.2.
  *   SYMMETRIC: every unordered pair once, its term used for both particles
- *              (mu_ij = mu_ji, Sec. 2.2).  Each direction's FP32 term is the same
- *              as DIRECTED's; only the order of the sums differs.  The
+ *              (mu_ij = mu_ji, Sec. 2.2).  Each direction's term is the same as
+ *              DIRECTED's, bit for bit; only the order of the sums differs.  The
  *              particles are cut into nb = npad / B blocks (npad = n rounded up
- *              to a multiple of 1024; B = 512 from npad = 32768 on, else 256),
- *              and the source-side partial sums take nb (nb + 1) / 2 * 12 B
- *              bytes of device memory.
+ *              to a multiple of 1024; FP32 modes: B = 512 from npad = 32768 on,
+ *              else 256; FP64: B = 128), and the source-side partial sums take
+ *              nb (nb + 1) / 2 * 3 B words (FP32 modes: 4-byte, FP64: 8-byte) of
+ *              device memory.
  *   AUTO     : SYMMETRIC once there is at least one block pair per two SMs
- *              (nb (nb + 1) / 2 >= SMs / 2; n > 2048 on a 152-SM GB300), else
- *              DIRECTED. */
+ *              (nb (nb + 1) / 2 >= SMs / 2; on a 152-SM GB300: n > 2048 in the FP32
+ *              modes, n > 1024 in FP64), else DIRECTED. */
 typedef enum { SD_DENSE_AUTO = 0, SD_DENSE_DIRECTED = 1, SD_DENSE_SYMMETRIC = 2 } sd_dense_kernel;
 
 typedef struct sd_config {
@@ -103,7 +108,7 @@ typedef struct sd_config {
     void *(*alloc)(size_t bytes, void *ctx);   /* optional device allocator              */
     void (*free)(void *ptr, void *ctx);        /* its matching free                      */
     void *alloc_ctx;
-    int32_t dense_kernel;    /* sd_dense_kernel; SYMMETRIC with FP64 gives SD_ERR_UNSUPPORTED */
+    int32_t dense_kernel;    /* sd_dense_kernel                                             */
     int32_t lubrication;     /* 1: sd_step adds to each particle's force the singular lubrication
                                 friction of the pairs with 2a < r < 3a (Sec. 2.3 Eq. lubrication,
                                 truncated at s = r/a - 2 = 1), -sum_j zeta_ij (v_i - v_j), with the
@@ -163,6 +168,37 @@ sd_status sd_step(sd_handle *h, double dt, int64_t nsteps);
 sd_status sd_mobility_apply_rows(sd_handle *h, const void *F, void *V, int dtype, int on_device, int32_t row0,
                                  int32_t row1);
 sd_status sd_step_rows(sd_handle *h, double dt, int32_t row0, int32_t row1);
+
+/* Tile shards: one system split over nshards ranks by pairs, with either all-pairs
+ * kernel (directed or symmetric) and every precision (Sec. 3.1 step 3: the N^2 sum
+ * is divided, not the rows).  Every rank holds the whole state (all n positions and
+ * forces).  Shard s runs the all-pairs kernel's persistent CTAs
+ * [s G / nshards, (s + 1) G / nshards) of the full launch of G CTAs, which hold
+ * equal runs of tiles, so the shards do equal pair work; for the symmetric kernel a
+ * tile serves both particles of every pair in it, so a shard's share reaches rows
+ * outside any one block of rows.
+ *   *_part    : writes to P (device, n x 3 doubles) the shard's raw share of
+ *               sum_{j != i} T(r_i - r_j) F_j / mu0 for every row i (no self term,
+ *               no FP64 near-pair correction).  The near pass runs in every shard
+ *               (the kernel's clamping follows it).
+ *   *_combine : Pall (device, nparts x n x 3 doubles) holds the shards' P in shard
+ *               order (e.g. from an all-gather); the call adds them in that order,
+ *               then the self term and the near-pair corrections, and gives
+ *               V = mu(x) F (sd_mobility_apply_combine) or the Euler update
+ *               x <- x + dt V (sd_step_combine).
+ * A combine must follow its part on the same handle with no other computing call
+ * in between (SD_ERR_STATE otherwise); sd_mobility_apply_combine uses the forces
+ * staged by sd_mobility_apply_part.  Every rank that combines the same Pall gets the
+ * same result bit for bit, so replicated states stay identical.  The result equals
+ * the unsharded call up to the order of the FP64 sums.  Asynchronous on the
+ * handle's stream except for host F / V (on_device = 0), which synchronise.
+ * 0 <= shard < nshards, nparts >= 1, else SD_ERR_ARG. */
+sd_status sd_mobility_apply_part(sd_handle *h, const void *F, int dtype, int on_device, int32_t shard,
+                                 int32_t nshards, double *P);
+sd_status sd_mobility_apply_combine(sd_handle *h, const double *Pall, int32_t nparts, void *V, int dtype,
+                                    int on_device);
+sd_status sd_step_part(sd_handle *h, int32_t shard, int32_t nshards, double *P);
+sd_status sd_step_combine(sd_handle *h, double dt, const double *Pall, int32_t nparts);
 
 /* Synchronise the handle's stream and report deferred device-side errors. */
 sd_status sd_synchronize(sd_handle *h);
@@ -231,7 +267,9 @@ sd_status sd_batch_synchronize(sd_batch *b);
  * capture begins.  All calls share the array, so calls whose kernels overlap on
  * the GPU (different streams, or different host threads) race and give wrong
  * results: order them on one stream.  Coincident distinct particles in RP or
- * Oseen mode give NaN velocities (no error word is kept). */
+ * Oseen mode give NaN velocities (no error word is kept).  If a CUDA error from
+ * the caller's earlier work is already pending when the call starts, it returns
+ * SD_ERR_CUDA, queues nothing and leaves that error in place (it is not cleared). */
 sd_status sd_mobility_apply_noalloc(const double *x, const double *F, double *V, int32_t n, double a, double eta,
                                     int32_t tensor, void *stream);
 
@@ -297,6 +335,15 @@ int32_t sd_dense_kernel_used(const sd_handle *h);
 int64_t sd_batch_launch_count(const sd_batch *b);
 /* Iteration limit of every bounded device-side wait (default 1 << 22). */
 sd_status sd_set_watchdog(sd_handle *h, int64_t iterations);
+/* Failure injection for tests of the time-out path (no GPU fault, no unbounded
+ * wait).  While on != 0, the first CTA of every all-pairs kernel launch of this
+ * handle (sd_mobility_apply, sd_step, the row shards) never issues the bulk copy of
+ * its first tile: its waits for that tile give up after the watchdog limit, the
+ * kernel records the time-out, drains the copies it did issue and exits, and the
+ * next synchronising call returns SD_ERR_TIMEOUT.  Results of such calls are
+ * invalid (a step's positions too: set them again after switching it off).
+ * Cached step graphs are dropped on every change. */
+sd_status sd_inject_stall(sd_handle *h, int32_t on);
 
 /* Thread-local message describing the last non-OK status ("" if none). */
 const char *sd_last_error(void);

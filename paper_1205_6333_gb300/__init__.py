@@ -91,6 +91,24 @@ def sd_step_rows(h, dt, row0, row1):
     _check(lib().sd_step_rows(h, float(dt), int(row0), int(row1)), "sd_step_rows")
 
 
+def sd_mobility_apply_part(h, F_ptr, dtype, on_device, shard, nshards, P_ptr):
+    _check(lib().sd_mobility_apply_part(h, F_ptr, int(dtype), int(on_device), int(shard), int(nshards), P_ptr),
+           "sd_mobility_apply_part")
+
+
+def sd_mobility_apply_combine(h, Pall_ptr, nparts, V_ptr, dtype, on_device):
+    _check(lib().sd_mobility_apply_combine(h, Pall_ptr, int(nparts), V_ptr, int(dtype), int(on_device)),
+           "sd_mobility_apply_combine")
+
+
+def sd_step_part(h, shard, nshards, P_ptr):
+    _check(lib().sd_step_part(h, int(shard), int(nshards), P_ptr), "sd_step_part")
+
+
+def sd_step_combine(h, dt, Pall_ptr, nparts):
+    _check(lib().sd_step_combine(h, float(dt), Pall_ptr, int(nparts)), "sd_step_combine")
+
+
 def sd_synchronize(h):
     _check(lib().sd_synchronize(h), "sd_synchronize")
 
@@ -197,15 +215,21 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
-def _as_arg(x, dtype):
-    """(pointer, on_device, keepalive) for a numpy array or torch tensor of n x 3 values."""
+def _as_arg(x, dtype, asynchronous=False):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor of n x 3 values.
+    With `asynchronous`, a page-locked CPU tensor is passed as on_device = 2 (copied
+    on the stream without a host synchronisation)."""
     if _is_torch(x):
         import torch
         want = torch.float64 if dtype == np.float64 else torch.float32
         t = x.detach()
         if t.dtype != want or not t.is_contiguous():
+            if asynchronous:
+                raise ValueError("an asynchronous copy needs a contiguous tensor of the right dtype")
             t = t.to(want).contiguous()
-        return t.data_ptr(), int(t.is_cuda), t
+        if t.is_cuda:
+            return t.data_ptr(), 1, t
+        return t.data_ptr(), 2 if (asynchronous and t.is_pinned()) else 0, t
     a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
     return a.ctypes.data, 0, a
 
@@ -312,19 +336,21 @@ class System:
     def __exit__(self, *exc):
         self.close()
 
-    def set_positions(self, x):
-        p, dev, _k = _as_arg(x, np.float64)
+    def set_positions(self, x, asynchronous=False):
+        """Positions from a numpy array, a CUDA tensor or (asynchronous=True: copied on
+        the stream, no host synchronisation) a page-locked CPU tensor."""
+        p, dev, _k = _as_arg(x, np.float64, asynchronous)
         sd_set_positions(self.h, p, dev)
 
-    def get_positions(self, out=None):
+    def get_positions(self, out=None, asynchronous=False):
         if out is None:
             out = np.empty((self.n, 3))
-        p, dev, _k = _as_arg(out, np.float64)
+        p, dev, _k = _as_arg(out, np.float64, asynchronous)
         sd_get_positions(self.h, p, dev)
         return out
 
-    def set_forces(self, f):
-        p, dev, _k = _as_arg(f, np.float64)
+    def set_forces(self, f, asynchronous=False):
+        p, dev, _k = _as_arg(f, np.float64, asynchronous)
         sd_set_forces(self.h, p, dev)
 
     def mobility_apply(self, F):
@@ -351,6 +377,56 @@ class System:
 
     def synchronize(self):
         sd_synchronize(self.h)
+
+    def _part_buffer(self, P):
+        import torch
+        if P is None:
+            P = torch.empty((self.n, 3), dtype=torch.float64, device="cuda:%d" % self.cfg.device)
+        if not (P.is_cuda and P.dtype == torch.float64 and P.is_contiguous() and tuple(P.shape) == (self.n, 3)):
+            raise ValueError("P must be a contiguous CUDA float64 tensor of shape (n, 3)")
+        return P
+
+    @staticmethod
+    def _parts(Pall):
+        import torch
+        if not (Pall.is_cuda and Pall.dtype == torch.float64 and Pall.is_contiguous() and Pall.dim() == 3):
+            raise ValueError("Pall must be a contiguous CUDA float64 tensor of shape (nparts, n, 3)")
+        return Pall.data_ptr(), Pall.shape[0]
+
+    def mobility_apply_part(self, F, shard, nshards, P=None):
+        """This shard's raw share of the all-pairs sum for forces F (a CUDA float64
+        tensor P of shape (n, 3) is returned); see sd_mobility_apply_part."""
+        dt = _dtype_of(F)
+        pf, dev, _kf = _as_arg(F, dt)
+        P = self._part_buffer(P)
+        sd_mobility_apply_part(self.h, pf, SD_DTYPE_F32 if dt == np.float32 else SD_DTYPE_F64, dev, shard, nshards,
+                               P.data_ptr())
+        return P
+
+    def mobility_apply_combine(self, Pall, like=None, dtype=np.float64):
+        """V = mu(x) F from the shards' results Pall (nparts, n, 3), added in shard
+        order.  The output is a CUDA tensor, or a numpy array when `like` is numpy."""
+        pp, k = self._parts(Pall)
+        import torch
+        if like is not None and not _is_torch(like):
+            pv, dev, V = _out_like(like, self.n, dtype)
+        else:
+            V = torch.empty((self.n, 3), dtype=torch.float64 if dtype == np.float64 else torch.float32,
+                            device=Pall.device)
+            pv, dev = V.data_ptr(), 1
+        sd_mobility_apply_combine(self.h, pp, k, pv, SD_DTYPE_F32 if dtype == np.float32 else SD_DTYPE_F64, dev)
+        return V
+
+    def step_part(self, shard, nshards, P=None):
+        """This shard's raw share of one Euler step's all-pairs sum (P returned)."""
+        P = self._part_buffer(P)
+        sd_step_part(self.h, shard, nshards, P.data_ptr())
+        return P
+
+    def step_combine(self, dt, Pall):
+        """Finish the Euler step from the shards' results Pall (nparts, n, 3)."""
+        pp, k = self._parts(Pall)
+        sd_step_combine(self.h, dt, pp, k)
 
     def vjp(self, F, W):
         dt = _dtype_of(F)
@@ -387,6 +463,10 @@ class System:
 
     def set_watchdog(self, iterations):
         _check(lib().sd_set_watchdog(self.h, int(iterations)), "sd_set_watchdog")
+
+    def inject_stall(self, on=True):
+        """Test hook: make the all-pairs kernels' bounded waits run out (SD_ERR_TIMEOUT)."""
+        _check(lib().sd_inject_stall(self.h, int(bool(on))), "sd_inject_stall")
 
 
 class Batch:

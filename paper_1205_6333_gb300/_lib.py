@@ -85,8 +85,13 @@ PROTOTYPES = {
     "sd_dense_kernel_used": (c_int32, [c_void_p]),
     "sd_mobility_apply_rows": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32]),
     "sd_step_rows": (c_int32, [c_void_p, c_double, c_int32, c_int32]),
+    "sd_mobility_apply_part": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p]),
+    "sd_mobility_apply_combine": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_int32]),
+    "sd_step_part": (c_int32, [c_void_p, c_int32, c_int32, c_void_p]),
+    "sd_step_combine": (c_int32, [c_void_p, c_double, c_void_p, c_int32]),
     "sd_batch_launch_count": (c_int64, [c_void_p]),
     "sd_set_watchdog": (c_int32, [c_void_p, c_int64]),
+    "sd_inject_stall": (c_int32, [c_void_p, c_int32]),
     "sd_mobility_apply_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_double, c_int32,
                                             c_void_p]),
     "sd_access_run": (c_int32, [c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),

@@ -157,6 +157,19 @@ static void drop_graphs(sd_handle *h) {
     drop_adjoint_graphs(h);
 }
 
+// The handle's one staging buffer `seg` (host-pointer calls, the adjoint's recompute
+// segment) holds at least `need` bytes.  Every reallocation goes through here: the
+// cached adjoint graphs captured the old address, so they are dropped first.
+static sd_status ensure_seg(sd_handle *h, size_t need, const char *what) {
+    if (h->seg && h->seg_bytes >= need) return SD_OK;
+    drop_adjoint_graphs(h);
+    dfree(h, h->seg);
+    h->seg = static_cast<double *>(dalloc(h, need));
+    h->seg_bytes = h->seg ? need : 0;
+    if (!h->seg) return set_error(SD_ERR_OOM, what);
+    return SD_OK;
+}
+
 // kGraphSteps (k = 0) or one (k = 1) Euler steps from buffer `cur`, captured into a
 // graph and cached per (k, cur, dt): a step's dozen launches become one graph launch
 // (the GPU no longer waits on each small launch at small N, nor after a host round trip).
@@ -317,8 +330,6 @@ static sd_status validate_common(const sd_config *cfg) {
         if (!std::isfinite(cfg->gravity[d])) return set_error(SD_ERR_ARG, "gravity must be finite");
     }
     if (cfg->dense_kernel < 0 || cfg->dense_kernel > 2) return set_error(SD_ERR_ARG, "unknown dense kernel");
-    if (cfg->dense_kernel == SD_DENSE_SYMMETRIC && cfg->prec == SD_PREC_FP64)
-        return set_error(SD_ERR_UNSUPPORTED, "the symmetric all-pairs kernel is FP32 only");
     if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
         return set_error(SD_ERR_ARG, "alloc and free callbacks must be given together");
     return SD_OK;
@@ -450,8 +461,9 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
         h->part2 = static_cast<double *>(dalloc(h, h->part2_bytes));
         if (!h->part || !h->part2) return fail(SD_ERR_OOM, "device allocation of partial sums");
         if (h->geom.sym) {
-            h->jpart_bytes = static_cast<size_t>(h->geom.nT) * 3 * h->geom.I * sizeof(float);
-            h->jpart = static_cast<float *>(dalloc(h, h->jpart_bytes));
+            const size_t es = h->mode == MODE_FP64 ? sizeof(double) : sizeof(float);
+            h->jpart_bytes = static_cast<size_t>(h->geom.nT) * 3 * h->geom.I * es;
+            h->jpart = dalloc(h, h->jpart_bytes);
             if (!h->jpart) return fail(SD_ERR_OOM, "device allocation of source-side partial sums");
         }
     }
@@ -495,17 +507,39 @@ void sd_destroy(sd_handle *h) {
     delete h;
 }
 
+// Memory kind of a caller pointer (the on_device argument): 0 host (the call
+// synchronises), 1 device, 2 host memory the caller keeps alive and unchanged until
+// the stream reaches the copy (asynchronous; pinned memory makes it a DMA).
+static bool valid_kind(int on_device) { return on_device >= 0 && on_device <= 2; }
+static cudaMemcpyKind to_device_kind(int on_device) {
+    return on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+static cudaMemcpyKind from_device_kind(int on_device) {
+    return on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+// True when any of the k doubles is NaN or infinite (exponent bits all set); a
+// branch-free OR over the array, so the check costs a pass over memory.
+static bool any_nonfinite(const double *v, size_t k) {
+    uint64_t bad = 0;
+    for (size_t i = 0; i < k; ++i) {
+        uint64_t b;
+        std::memcpy(&b, v + i, sizeof(b));
+        bad |= static_cast<uint64_t>((b & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
+    }
+    return bad != 0;
+}
+
 sd_status sd_set_positions(sd_handle *h, const double *xyz, int on_device) {
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (!xyz && h->n > 0) return set_error(SD_ERR_ARG, "positions pointer is NULL");
+    if (!valid_kind(on_device)) return set_error(SD_ERR_ARG, "on_device must be 0, 1 or 2");
     cudaSetDevice(h->device);
-    if (!on_device) {
-        for (size_t k = 0; k < 3 * static_cast<size_t>(h->n); ++k)
-            if (!std::isfinite(xyz[k])) return set_error(SD_ERR_NONFINITE, "non-finite position");
-    }
+    if (on_device == 0 && any_nonfinite(xyz, 3 * static_cast<size_t>(h->n)))
+        return set_error(SD_ERR_NONFINITE, "non-finite position");
     if (h->n > 0) {
-        SD_CUDA(cudaMemcpyAsync(h->x64[h->cur], xyz, 3 * sizeof(double) * h->n,
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        SD_CUDA(cudaMemcpyAsync(h->x64[h->cur], xyz, 3 * sizeof(double) * h->n, to_device_kind(on_device),
+                                h->stream));
         sd_status s = launch_check(launch_stage_pos(h, h->stream, h->x64[h->cur], h->posm), "stage positions");
         if (s != SD_OK) return s;
         // new positions: the previous step's velocities no longer apply (lubrication)
@@ -519,25 +553,24 @@ sd_status sd_set_positions(sd_handle *h, const double *xyz, int on_device) {
 sd_status sd_get_positions(sd_handle *h, double *xyz, int on_device) {
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (!xyz && h->n > 0) return set_error(SD_ERR_ARG, "positions pointer is NULL");
+    if (!valid_kind(on_device)) return set_error(SD_ERR_ARG, "on_device must be 0, 1 or 2");
     if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
     cudaSetDevice(h->device);
     if (h->n > 0)
-        SD_CUDA(cudaMemcpyAsync(xyz, h->x64[h->cur], 3 * sizeof(double) * h->n,
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+        SD_CUDA(cudaMemcpyAsync(xyz, h->x64[h->cur], 3 * sizeof(double) * h->n, from_device_kind(on_device),
+                                h->stream));
     return on_device ? SD_OK : sync_check(h);
 }
 
 sd_status sd_set_forces(sd_handle *h, const double *f, int on_device) {
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (!f && h->n > 0) return set_error(SD_ERR_ARG, "forces pointer is NULL");
+    if (!valid_kind(on_device)) return set_error(SD_ERR_ARG, "on_device must be 0, 1 or 2");
     cudaSetDevice(h->device);
-    if (!on_device) {
-        for (size_t k = 0; k < 3 * static_cast<size_t>(h->n); ++k)
-            if (!std::isfinite(f[k])) return set_error(SD_ERR_NONFINITE, "non-finite force");
-    }
+    if (on_device == 0 && any_nonfinite(f, 3 * static_cast<size_t>(h->n)))
+        return set_error(SD_ERR_NONFINITE, "non-finite force");
     if (h->n > 0) {
-        SD_CUDA(cudaMemcpyAsync(h->fext64, f, 3 * sizeof(double) * h->n,
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        SD_CUDA(cudaMemcpyAsync(h->fext64, f, 3 * sizeof(double) * h->n, to_device_kind(on_device), h->stream));
         sd_status s =
             launch_check(launch_stage_forces(h, h->stream, nullptr, SD_DTYPE_F64, 1, h->F64, h->frcm), "stage forces");
         if (s != SD_OK) return s;
@@ -554,12 +587,8 @@ sd_status sd_synchronize(sd_handle *h) {
 // Device staging buffers for host-pointer calls.
 static sd_status host_io(sd_handle *h, void *&in, void *&out) {
     const size_t bytes = 3 * sizeof(double) * static_cast<size_t>(std::max(h->n, 1));
-    if (!h->seg || h->seg_bytes < 2 * bytes) {
-        dfree(h, h->seg);
-        h->seg = static_cast<double *>(dalloc(h, 2 * bytes));
-        h->seg_bytes = h->seg ? 2 * bytes : 0;
-        if (!h->seg) return set_error(SD_ERR_OOM, "device allocation of staging buffers");
-    }
+    sd_status s = ensure_seg(h, 2 * bytes, "device allocation of staging buffers");
+    if (s != SD_OK) return s;
     in = h->seg;
     out = reinterpret_cast<char *>(h->seg) + bytes;
     return SD_OK;
@@ -586,6 +615,7 @@ static sd_status apply_rows(sd_handle *h, const void *F, void *V, int dtype, int
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (dtype != SD_DTYPE_F32 && dtype != SD_DTYPE_F64) return set_error(SD_ERR_ARG, "dtype must be F32 or F64");
     if (row0 < 0 || row1 < row0 || row1 > h->n) return set_error(SD_ERR_ARG, "rows must satisfy 0 <= row0 <= row1 <= n");
+    if (on_device != 0 && on_device != 1) return set_error(SD_ERR_ARG, "on_device must be 0 or 1");
     const bool all = row0 == 0 && row1 == h->n;
     if (!all && h->geom.sym)
         return set_error(SD_ERR_UNSUPPORTED, "row shards need the directed all-pairs kernel (SD_DENSE_DIRECTED)");
@@ -665,6 +695,159 @@ sd_status sd_step_rows(sd_handle *h, double dt, int32_t row0, int32_t row1) {
     return SD_OK;
 }
 
+// ---------------------------------------------------------------- tile shards
+
+enum { PART_NONE = 0, PART_APPLY = 1, PART_STEP = 2 };
+
+// Shard `shard` of `nshards`: CTAs [b0, b1) of the all-pairs kernel's persistent grid
+// (either kernel), i.e. the tiles [b0 chunk, min(b1 chunk, nT)).  The CTAs hold equal
+// runs of tiles, so the shards get equal pair work.
+static void shard_window(const sd_handle *h, int shard, int nshards, TileWin &w, EpiShard &es) {
+    const DenseGeom &g = h->geom;
+    const int b0 = static_cast<int>(static_cast<long long>(shard) * g.grid / nshards);
+    const int b1 = static_cast<int>(static_cast<long long>(shard + 1) * g.grid / nshards);
+    w.b0 = b0;
+    w.lo = static_cast<long long>(b0) * g.chunk;
+    w.hi = std::min(static_cast<long long>(b1) * g.chunk, g.nT);
+    es.b0 = b0;
+    es.b1 = b1;
+    es.tlo = w.lo;
+    es.thi = w.hi;
+}
+
+static sd_status check_shard(const sd_handle *h, int shard, int nshards, const double *P) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    if (nshards < 1 || shard < 0 || shard >= nshards) return set_error(SD_ERR_ARG, "need 0 <= shard < nshards");
+    if (!P && h->n > 0) return set_error(SD_ERR_ARG, "P is NULL");
+    if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
+    return SD_OK;
+}
+
+}  // extern "C"
+
+// This shard's raw share of the all-pairs sum for the staged positions and forces:
+// near pass (every shard: the all-pairs kernel's clamping follows its flag), the
+// shard's CTAs of the all-pairs kernel, and the epilogue's sum over their slots.
+static sd_status run_part(sd_handle *h, int shard, int nshards, const double *F64, Mirror frcm, double *P) {
+    TileWin w;
+    EpiShard es;
+    shard_window(h, shard, nshards, w, es);
+    cudaStream_t st = h->stream;
+    sd_status s = launch_check(launch_near(h, st, h->x64[h->cur], h->posm.aos, F64, frcm.aos), "near pass");
+    if (s == SD_OK) s = launch_check(launch_dense(h, st, h->posm, frcm, h->part, &w), "dense kernel (shard)");
+    if (s == SD_OK)
+        s = launch_check(launch_epilogue(h, st, OUT_PART, h->x64[h->cur], h->posm.aos, F64, frcm.aos, P, 0.0, nullptr,
+                                         0, h->n, &es),
+                         "epilogue (shard)");
+    return s;
+}
+
+extern "C" {
+
+sd_status sd_mobility_apply_part(sd_handle *h, const void *F, int dtype, int on_device, int32_t shard,
+                                 int32_t nshards, double *P) {
+    sd_status s = check_shard(h, shard, nshards, P);
+    if (s != SD_OK) return s;
+    if (dtype != SD_DTYPE_F32 && dtype != SD_DTYPE_F64) return set_error(SD_ERR_ARG, "dtype must be F32 or F64");
+    if (on_device != 0 && on_device != 1) return set_error(SD_ERR_ARG, "on_device must be 0 or 1");
+    if (h->n > 0 && !F) return set_error(SD_ERR_ARG, "F is NULL");
+    h->part_kind = PART_NONE;
+    if (h->n == 0) {
+        h->part_kind = PART_APPLY;
+        return SD_OK;
+    }
+    cudaSetDevice(h->device);
+    const void *Fd = F;
+    if (!on_device) {
+        void *in = nullptr, *out = nullptr;
+        s = host_io(h, in, out);
+        if (s != SD_OK) return s;
+        const size_t es = dtype == SD_DTYPE_F32 ? sizeof(float) : sizeof(double);
+        SD_CUDA(cudaMemcpyAsync(in, F, 3 * es * h->n, cudaMemcpyHostToDevice, h->stream));
+        Fd = in;
+    }
+    s = launch_check(launch_stage_forces(h, h->stream, Fd, dtype, 0, h->Fa64, h->frcam), "stage F");
+    if (s == SD_OK) s = ensure_cells(h);
+    if (s == SD_OK) s = run_part(h, shard, nshards, h->Fa64, h->frcam, P);
+    if (s != SD_OK) return s;
+    h->part_kind = PART_APPLY;
+    return on_device ? SD_OK : sync_check(h);
+}
+
+sd_status sd_mobility_apply_combine(sd_handle *h, const double *Pall, int32_t nparts, void *V, int dtype,
+                                    int on_device) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    if (dtype != SD_DTYPE_F32 && dtype != SD_DTYPE_F64) return set_error(SD_ERR_ARG, "dtype must be F32 or F64");
+    if (on_device != 0 && on_device != 1) return set_error(SD_ERR_ARG, "on_device must be 0 or 1");
+    if (nparts < 1 || (h->n > 0 && (!Pall || !V))) return set_error(SD_ERR_ARG, "Pall, nparts or V");
+    if (h->part_kind != PART_APPLY) return set_error(SD_ERR_STATE, "sd_mobility_apply_part must come first");
+    h->part_kind = PART_NONE;
+    if (h->n == 0) return SD_OK;
+    cudaSetDevice(h->device);
+    EpiShard es;
+    es.pall = Pall;
+    es.nparts = nparts;
+    void *Vd = V;
+    if (!on_device) {
+        void *in = nullptr, *out = nullptr;
+        sd_status s = host_io(h, in, out);
+        if (s != SD_OK) return s;
+        Vd = out;
+    }
+    sd_status s = launch_check(launch_epilogue(h, h->stream, dtype == SD_DTYPE_F32 ? OUT_F32 : OUT_F64, h->x64[h->cur],
+                                               h->posm.aos, h->Fa64, h->frcam.aos, Vd, 0.0, nullptr, 0, h->n, &es),
+                               "epilogue (combine)");
+    if (s != SD_OK) return s;
+    if (!on_device) {
+        const size_t es2 = dtype == SD_DTYPE_F32 ? sizeof(float) : sizeof(double);
+        SD_CUDA(cudaMemcpyAsync(V, Vd, 3 * es2 * h->n, cudaMemcpyDeviceToHost, h->stream));
+        return sync_check(h);
+    }
+    return SD_OK;
+}
+
+sd_status sd_step_part(sd_handle *h, int32_t shard, int32_t nshards, double *P) {
+    sd_status s = check_shard(h, shard, nshards, P);
+    if (s != SD_OK) return s;
+    h->part_kind = PART_NONE;
+    if (h->n == 0) {
+        h->part_kind = PART_STEP;
+        return SD_OK;
+    }
+    cudaSetDevice(h->device);
+    cudaStream_t st = h->stream;
+    const double *x_in = h->x64[h->cur];
+    cudaError_t e = launch_build_cells(h, st, x_in, h->posm);
+    if (e == cudaSuccess && !h->forces_const) e = launch_forces_rep(h, st, x_in);
+    if (e != cudaSuccess) return cuda_status(e, "cells / forces (shard)");
+    h->cells_valid = true;
+    s = run_part(h, shard, nshards, h->F64, h->frcm, P);
+    if (s != SD_OK) return s;
+    h->part_kind = PART_STEP;
+    return SD_OK;
+}
+
+sd_status sd_step_combine(sd_handle *h, double dt, const double *Pall, int32_t nparts) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    if (!std::isfinite(dt)) return set_error(SD_ERR_ARG, "dt must be finite");
+    if (nparts < 1 || (h->n > 0 && !Pall)) return set_error(SD_ERR_ARG, "Pall or nparts");
+    if (h->part_kind != PART_STEP) return set_error(SD_ERR_STATE, "sd_step_part must come first");
+    h->part_kind = PART_NONE;
+    if (h->n == 0) return SD_OK;
+    cudaSetDevice(h->device);
+    EpiShard es;
+    es.pall = Pall;
+    es.nparts = nparts;
+    const double *x_in = h->x64[h->cur];
+    sd_status s = launch_check(launch_epilogue(h, h->stream, OUT_EULER, x_in, h->posm.aos, h->F64, h->frcm.aos, nullptr,
+                                               dt, h->x64[1 - h->cur], 0, h->n, &es),
+                               "epilogue (combine)");
+    if (s != SD_OK) return s;
+    h->cur = 1 - h->cur;
+    h->cells_valid = false;
+    return SD_OK;
+}
+
 sd_status sd_step(sd_handle *h, double dt, int64_t nsteps) {
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (nsteps < 0 || !std::isfinite(dt)) return set_error(SD_ERR_ARG, "nsteps must be >= 0 and dt finite");
@@ -678,6 +861,7 @@ sd_status sd_mobility_vjp(sd_handle *h, const void *F, const void *W, void *gX, 
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (dtype != SD_DTYPE_F32 && dtype != SD_DTYPE_F64) return set_error(SD_ERR_ARG, "dtype must be F32 or F64");
     if (h->n > 0 && (!F || !W || (!gX && !gF))) return set_error(SD_ERR_ARG, "null argument");
+    if (on_device != 0 && on_device != 1) return set_error(SD_ERR_ARG, "on_device must be 0 or 1");
     if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
     if (h->n == 0) return SD_OK;
     cudaSetDevice(h->device);
@@ -688,13 +872,8 @@ sd_status sd_mobility_vjp(sd_handle *h, const void *F, const void *W, void *gX, 
     if (!on_device) {
         // four n x 3 arrays: F, W in; gX, gF out
         const size_t need = 4 * 3 * sizeof(double) * static_cast<size_t>(h->n);
-        if (!h->seg || h->seg_bytes < need) {
-            drop_adjoint_graphs(h);   // they hold the old buffer
-            dfree(h, h->seg);
-            h->seg = static_cast<double *>(dalloc(h, need));
-            h->seg_bytes = h->seg ? need : 0;
-            if (!h->seg) return set_error(SD_ERR_OOM, "device allocation of staging buffers");
-        }
+        sd_status s0 = ensure_seg(h, need, "device allocation of staging buffers");
+        if (s0 != SD_OK) return s0;
         char *b = reinterpret_cast<char *>(h->seg);
         SD_CUDA(cudaMemcpyAsync(b, F, bytes, cudaMemcpyHostToDevice, h->stream));
         SD_CUDA(cudaMemcpyAsync(b + bytes, W, bytes, cudaMemcpyHostToDevice, h->stream));
@@ -727,6 +906,7 @@ sd_status sd_adjoint(sd_handle *h, double dt, int64_t nsteps, int32_t ckpt_every
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (nsteps < 0 || ckpt_every < 1 || !std::isfinite(dt)) return set_error(SD_ERR_ARG, "nsteps, ckpt_every or dt");
     if (h->n > 0 && (!gxT || !gx0 || !gF)) return set_error(SD_ERR_ARG, "null argument");
+    if (on_device != 0 && on_device != 1) return set_error(SD_ERR_ARG, "on_device must be 0 or 1");
     if (!h->forces_const)
         return set_error(SD_ERR_UNSUPPORTED, "adjoint with soft repulsion or lubrication is not implemented");
     if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
@@ -747,12 +927,9 @@ sd_status sd_adjoint(sd_handle *h, double dt, int64_t nsteps, int32_t ckpt_every
         if (!h->ckpt) return set_error(SD_ERR_OOM, "device allocation of checkpoints");
     }
     const size_t seg_need = static_cast<size_t>(K) * xb;
-    if (!h->seg || h->seg_bytes < seg_need) {
-        drop_adjoint_graphs(h);   // they hold the old buffer
-        dfree(h, h->seg);
-        h->seg = static_cast<double *>(dalloc(h, seg_need));
-        h->seg_bytes = h->seg ? seg_need : 0;
-        if (!h->seg) return set_error(SD_ERR_OOM, "device allocation of the recompute segment");
+    {
+        sd_status s0 = ensure_seg(h, seg_need, "device allocation of the recompute segment");
+        if (s0 != SD_OK) return s0;
     }
     if (!h->lam) {
         if (!dalloc_t(h, h->lam, n3) || !dalloc_t(h, h->gFacc, n3))
@@ -852,6 +1029,13 @@ sd_status sd_set_watchdog(sd_handle *h, int64_t iterations) {
     if (!h || iterations < 1) return set_error(SD_ERR_ARG, "bad handle or iteration limit");
     h->watchdog = iterations;
     drop_graphs(h);   // graphs captured the old limit
+    return SD_OK;
+}
+
+sd_status sd_inject_stall(sd_handle *h, int32_t on) {
+    if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
+    h->inject_stall = on != 0;
+    drop_graphs(h);   // graphs captured the launch arguments
     return SD_OK;
 }
 

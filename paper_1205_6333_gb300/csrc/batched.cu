@@ -929,6 +929,7 @@ void sd_batch_destroy(sd_batch *b) {
 
 sd_status sd_batch_set_positions(sd_batch *b, const double *xyz, int on_device) {
     if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    if (on_device != 0 && on_device != 1) return set_error(SD_ERR_ARG, "on_device must be 0 or 1");
     if (b->P > 0 && !xyz) return set_error(SD_ERR_ARG, "positions pointer is NULL");
     cudaSetDevice(b->device);
     if (!on_device)
@@ -952,6 +953,7 @@ sd_status sd_batch_set_positions(sd_batch *b, const double *xyz, int on_device) 
 
 sd_status sd_batch_get_positions(sd_batch *b, double *xyz, int on_device) {
     if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    if (on_device != 0 && on_device != 1) return set_error(SD_ERR_ARG, "on_device must be 0 or 1");
     if (b->P > 0 && !xyz) return set_error(SD_ERR_ARG, "positions pointer is NULL");
     if (!b->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
     cudaSetDevice(b->device);
@@ -963,6 +965,7 @@ sd_status sd_batch_get_positions(sd_batch *b, double *xyz, int on_device) {
 
 sd_status sd_batch_set_forces(sd_batch *b, const double *f, int on_device) {
     if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
+    if (on_device != 0 && on_device != 1) return set_error(SD_ERR_ARG, "on_device must be 0 or 1");
     if (b->P > 0 && !f) return set_error(SD_ERR_ARG, "forces pointer is NULL");
     cudaSetDevice(b->device);
     if (!on_device)

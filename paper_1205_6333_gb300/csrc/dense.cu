@@ -20,6 +20,13 @@
 
 namespace sd {
 
+// Failure injection for tests (sd_inject_stall): the launcher passes the watchdog
+// limit negated, and the first CTA of the launch then never issues the copy of its
+// first tile.  Its bounded waits on that stage run out, the kernel records
+// DEV_ERR_TIMEOUT, stops issuing copies, drains the copies it did issue and exits;
+// no wait is unbounded and no memory outside the kernel's buffers is touched.
+__device__ __forceinline__ bool stall_first_copy(long long wd) { return wd < 0 && blockIdx.x == 0; }
+
 template <int MODE>
 struct DenseT;
 template <>
@@ -76,6 +83,7 @@ __global__ void __launch_bounds__(kNT) dense_kernel(const typename DenseT<MODE>:
     const long long t1 = (tb + g.chunk < thi) ? tb + g.chunk : thi;
     if (t0 >= t1) return;  // uniform over the CTA
     const uint32_t tile_bytes = static_cast<uint32_t>(g.J * sizeof(V4));
+    const long long lim = wd < 0 ? -wd : wd;   // wd < 0: injected stall (stall_first_copy)
 
     int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0;  // bookkeeping of thread 0 only
     if (tid == 0) {
@@ -87,6 +95,7 @@ __global__ void __launch_bounds__(kNT) dense_kernel(const typename DenseT<MODE>:
     __syncthreads();
     if (tid == 0) {
         for (int q = 0; q < 2 && t0 + q < t1; ++q) {
+            if (q == 0 && stall_first_copy(wd)) continue;
             const size_t jt = static_cast<size_t>((t0 + q) % g.nJT);
             mbar_arrive_expect_tx(&bars[q], 2 * tile_bytes);
             bulk_g2s(s_pos + q * g.J, pos + jt * g.J, tile_bytes, &bars[q]);
@@ -140,7 +149,7 @@ __global__ void __launch_bounds__(kNT) dense_kernel(const typename DenseT<MODE>:
         const int q = static_cast<int>(t - t0);
         const int st = q & 1;
         if (!aborted) {
-            if (mbar_wait_bounded(&bars[st], (q >> 1) & 1, wd)) {
+            if (mbar_wait_bounded(&bars[st], (q >> 1) & 1, lim)) {
                 if (tid == 0) { if (st == 0) ++waited0; else ++waited1; }
             } else {
                 atomicOr(err, DEV_ERR_TIMEOUT);
@@ -181,9 +190,9 @@ __global__ void __launch_bounds__(kNT) dense_kernel(const typename DenseT<MODE>:
         // After a time-out, wait (bounded) for copies still in flight into this CTA's
         // shared memory before the CTA exits.
         for (int k = waited0; k < issued0; ++k)
-            if (!mbar_wait_bounded(&bars[0], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+            if (!mbar_wait_bounded(&bars[0], k & 1, drain_limit(lim))) atomicOr(err, DEV_ERR_TIMEOUT);
         for (int k = waited1; k < issued1; ++k)
-            if (!mbar_wait_bounded(&bars[1], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+            if (!mbar_wait_bounded(&bars[1], k & 1, drain_limit(lim))) atomicOr(err, DEV_ERR_TIMEOUT);
     }
 }
 
@@ -241,6 +250,7 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
     const long long t1 = (tb + g.chunk < thi) ? tb + g.chunk : thi;
     if (t0 >= t1) return;
     const uint32_t arr_bytes = static_cast<uint32_t>(g.J * sizeof(float));
+    const long long lim = wd < 0 ? -wd : wd;   // wd < 0: injected stall (stall_first_copy)
 
     int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0;  // bookkeeping of thread 0 only
     if (tid == 0) {
@@ -261,7 +271,8 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
         if (stg == 0) ++issued0; else ++issued1;
     };
     if (tid == 0)
-        for (int q = 0; q < 2 && t0 + q < t1; ++q) issue(t0 + q, q);
+        for (int q = 0; q < 2 && t0 + q < t1; ++q)
+            if (q != 0 || !stall_first_copy(wd)) issue(t0 + q, q);
 
     f2 XI[R], YI[R], ZI[R], AX[R], AY[R], AZ[R];
     int cur_ib = -1;
@@ -310,7 +321,7 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
         const int q = static_cast<int>(t - t0);
         const int st = q & 1;
         if (!aborted) {
-            if (mbar_wait_bounded(&bars[st], (q >> 1) & 1, wd)) {
+            if (mbar_wait_bounded(&bars[st], (q >> 1) & 1, lim)) {
                 if (tid == 0) { if (st == 0) ++waited0; else ++waited1; }
             } else {
                 atomicOr(err, DEV_ERR_TIMEOUT);
@@ -353,9 +364,9 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
         // After a time-out, wait (bounded) for copies still in flight into this CTA's
         // shared memory before the CTA exits.
         for (int k = waited0; k < issued0; ++k)
-            if (!mbar_wait_bounded(&bars[0], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+            if (!mbar_wait_bounded(&bars[0], k & 1, drain_limit(lim))) atomicOr(err, DEV_ERR_TIMEOUT);
         for (int k = waited1; k < issued1; ++k)
-            if (!mbar_wait_bounded(&bars[1], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+            if (!mbar_wait_bounded(&bars[1], k & 1, drain_limit(lim))) atomicOr(err, DEV_ERR_TIMEOUT);
     }
 }
 
@@ -433,7 +444,7 @@ __global__ void __launch_bounds__(NT, SD_SYM_MINB) dense_sym_kernel(const float 
                                                            const float *__restrict__ frc, double *__restrict__ part,
                                                            float *__restrict__ jpart, int npad, DenseGeom g,
                                                            PairConst2 c, const int *__restrict__ flag,
-                                                           int *__restrict__ err, long long wd) {
+                                                           int *__restrict__ err, long long wd, int b0) {
     constexpr int R = B / NT, NW = NT / 32;
     static_assert(B == NT * R, "a block is R targets per thread");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -445,10 +456,12 @@ __global__ void __launch_bounds__(NT, SD_SYM_MINB) dense_sym_kernel(const float 
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nb = g.nIB;
-    const long long t0 = static_cast<long long>(blockIdx.x) * g.chunk;
+    const int cta = static_cast<int>(blockIdx.x) + b0;   // index in the full launch
+    const long long t0 = static_cast<long long>(cta) * g.chunk;
     const long long t1 = (t0 + g.chunk < g.nT) ? t0 + g.chunk : g.nT;
     if (t0 >= t1) return;
     constexpr uint32_t arr_bytes = B * sizeof(float);
+    const long long lim = wd < 0 ? -wd : wd;   // wd < 0: injected stall (stall_first_copy)
 
     // (ib, jb) of tile t0: row ib starts at ib nb - ib (ib - 1) / 2
     int ib0;
@@ -482,7 +495,13 @@ __global__ void __launch_bounds__(NT, SD_SYM_MINB) dense_sym_kernel(const float 
         if (++qj == nb) { ++qi; qj = qi; }
     };
     if (tid == 0)
-        for (int q = 0; q < 2 && t0 + q < t1; ++q) issue(q);
+        for (int q = 0; q < 2 && t0 + q < t1; ++q) {
+            if (q == 0 && stall_first_copy(wd)) {   // the tile is skipped, not staged
+                if (++qj == nb) { ++qi; qj = qi; }
+                continue;
+            }
+            issue(q);
+        }
 
     f2 XI[R], YI[R], ZI[R], GX[R], GY[R], GZ[R], AX[R], AY[R], AZ[R];
     int cur_ib = -1;
@@ -490,7 +509,7 @@ __global__ void __launch_bounds__(NT, SD_SYM_MINB) dense_sym_kernel(const float 
     const bool clamp_all = *flag != 0;
 
     auto flush = [&](int ib) {
-        const int slot = static_cast<int>(blockIdx.x) - geom_first(g, ib);
+        const int slot = cta - geom_first(g, ib);
         double *dst = part + static_cast<size_t>(slot) * 3 * npad;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
@@ -535,7 +554,7 @@ __global__ void __launch_bounds__(NT, SD_SYM_MINB) dense_sym_kernel(const float 
         const int q = static_cast<int>(t - t0);
         const int st = q & 1;
         if (!aborted) {
-            if (mbar_wait_bounded(&bars[st], (q >> 1) & 1, wd)) {
+            if (mbar_wait_bounded(&bars[st], (q >> 1) & 1, lim)) {
                 if (tid == 0) { if (st == 0) ++waited0; else ++waited1; }
             } else {
                 atomicOr(err, DEV_ERR_TIMEOUT);
@@ -592,10 +611,176 @@ __global__ void __launch_bounds__(NT, SD_SYM_MINB) dense_sym_kernel(const float 
         // After a time-out, wait (bounded) for copies still in flight into this CTA's
         // shared memory before the CTA exits.
         for (int k = waited0; k < issued0; ++k)
-            if (!mbar_wait_bounded(&bars[0], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+            if (!mbar_wait_bounded(&bars[0], k & 1, drain_limit(lim))) atomicOr(err, DEV_ERR_TIMEOUT);
         for (int k = waited1; k < issued1; ++k)
-            if (!mbar_wait_bounded(&bars[1], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+            if (!mbar_wait_bounded(&bars[1], k & 1, drain_limit(lim))) atomicOr(err, DEV_ERR_TIMEOUT);
     }
+}
+
+// ---------------------------------------------------------------- FP64, symmetric
+
+// The FP64 all-pairs kernel using mu_ij = mu_ji (Sec. 2.2), the reference path's
+// counterpart of dense_sym_kernel.  GB300 issues FP64 at a small fraction of its
+// FP32 rate, so this kernel is bound by the FP64 pipe alone and its only aim is
+// fewer FP64 operations per pair: r, 1/r, A and B are formed once per unordered
+// pair (pair_sym_f64), 19 FP64 operations per ordered pair against 30 directed.
+//   * blocks of kB64 = 128 particles, one target per thread (128 threads); a tile
+//     is an unordered block pair (ib <= jb), partitioned over the persistent grid
+//     as in dense_sym_kernel; the positions and forces of block jb (dbl4, AoS) are
+//     staged by two bulk copies per tile, double-buffered;
+//   * off-diagonal tiles: warp w holds targets 32 w .. 32 w + 31 of block ib and
+//     walks block jb in groups of 32 sources; at step m lane l takes source
+//     (l + m) mod 32 of the group, and the source's running sum (3 doubles) moves one
+//     lane down per step by shuffle, so after 32 steps lane l holds source l.  The
+//     four warps' source sums are added in fixed order into the tile's row of
+//     `jpart` (FP64);
+//   * diagonal tiles hold the self pairs and run the directed pair term;
+//   * r^2 is clamped to (2a)^2 everywhere, as in the directed FP64 kernel, so the
+//     near pass's FP64 correction applies unchanged.
+constexpr int kB64 = 128;
+
+template <int TENSOR, bool PER>
+__global__ void __launch_bounds__(kB64) dense_sym64_kernel(const dbl4 *__restrict__ pos, const dbl4 *__restrict__ frc,
+                                                          double *__restrict__ part, double *__restrict__ jpart,
+                                                          int npad, DenseGeom g, PairConst c,
+                                                          int *__restrict__ err, long long wd, int b0) {
+    constexpr int B = kB64, NW = B / 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+    dbl4 *s_pos = reinterpret_cast<dbl4 *>(smem);            // [2 stages][B]
+    dbl4 *s_frc = s_pos + 2 * B;                              // [2 stages][B]
+    double *s_jacc = reinterpret_cast<double *>(s_frc + 2 * B);   // [NW][3][B]
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nb = g.nIB;
+    const int cta = static_cast<int>(blockIdx.x) + b0;   // index in the full launch
+    const long long t0 = static_cast<long long>(cta) * g.chunk;
+    const long long t1 = (t0 + g.chunk < g.nT) ? t0 + g.chunk : g.nT;
+    if (t0 >= t1) return;
+    constexpr uint32_t tile_bytes = B * sizeof(dbl4);
+    const long long lim = wd < 0 ? -wd : wd;   // wd < 0: injected stall (stall_first_copy)
+
+    int ib0;
+    {
+        const double q = 2.0 * nb + 1.0;
+        ib0 = static_cast<int>(0.5 * (q - sqrt(q * q - 8.0 * static_cast<double>(t0))));
+        ib0 = ib0 < 0 ? 0 : (ib0 > nb - 1 ? nb - 1 : ib0);
+        while (ib0 > 0 && geom_rowstart(g, ib0) > t0) --ib0;
+        while (ib0 + 1 < nb && geom_rowstart(g, ib0 + 1) <= t0) ++ib0;
+    }
+    const int jb0 = ib0 + static_cast<int>(t0 - geom_rowstart(g, ib0));
+
+    int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0;  // bookkeeping of thread 0 only
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    int qi = ib0, qj = jb0;   // next tile to stage (thread 0)
+    auto issue = [&](int stg) {
+        const size_t j0 = static_cast<size_t>(qj) * B;
+        mbar_arrive_expect_tx(&bars[stg], 2 * tile_bytes);
+        bulk_g2s(s_pos + stg * B, pos + j0, tile_bytes, &bars[stg]);
+        bulk_g2s(s_frc + stg * B, frc + j0, tile_bytes, &bars[stg]);
+        if (stg == 0) ++issued0; else ++issued1;
+        if (++qj == nb) { ++qi; qj = qi; }
+    };
+    if (tid == 0)
+        for (int q = 0; q < 2 && t0 + q < t1; ++q) {
+            if (q == 0 && stall_first_copy(wd)) {   // the tile is skipped, not staged
+                if (++qj == nb) { ++qi; qj = qi; }
+                continue;
+            }
+            issue(q);
+        }
+
+    double xi = 0.0, yi = 0.0, zi = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
+    int cur_ib = -1;
+    bool aborted = false;
+    auto flush = [&](int ib) {
+        const int slot = cta - geom_first(g, ib);
+        double *dst = part + static_cast<size_t>(slot) * 3 * npad + static_cast<size_t>(ib) * B + tid;
+        dst[0] = ax;
+        dst[npad] = ay;
+        dst[2 * static_cast<size_t>(npad)] = az;
+    };
+
+    int ib = ib0, jb = jb0;
+    for (long long t = t0; t < t1; ++t) {
+        if (ib != cur_ib) {
+            if (cur_ib >= 0) flush(cur_ib);
+            cur_ib = ib;
+            const dbl4 p = pos[static_cast<size_t>(ib) * B + tid], f = frc[static_cast<size_t>(ib) * B + tid];
+            xi = p.x; yi = p.y; zi = p.z;
+            gx = f.x; gy = f.y; gz = f.z;
+            ax = ay = az = 0.0;
+        }
+        const int q = static_cast<int>(t - t0);
+        const int st = q & 1;
+        if (!aborted) {
+            if (mbar_wait_bounded(&bars[st], (q >> 1) & 1, lim)) {
+                if (tid == 0) { if (st == 0) ++waited0; else ++waited1; }
+            } else {
+                atomicOr(err, DEV_ERR_TIMEOUT);
+                s_abort = 1;
+            }
+        }
+        const dbl4 *P = s_pos + st * B;
+        const dbl4 *Fq = s_frc + st * B;
+        const bool diag = ib == jb;
+        if (diag) {
+#pragma unroll 2
+            for (int jj = 0; jj < B; ++jj) pair_f64<TENSOR, PER>(xi, yi, zi, P[jj], Fq[jj], c, ax, ay, az);
+        } else {
+            const int nxt = (lane + 1) & 31;
+#pragma unroll 1
+            for (int gq = 0; gq < B / 32; ++gq) {
+                double bx = 0.0, by = 0.0, bz = 0.0;
+#pragma unroll 4
+                for (int m = 0; m < 32; ++m) {
+                    const int k = gq * 32 + ((lane + m) & 31);
+                    pair_sym_f64<TENSOR, PER>(xi, yi, zi, gx, gy, gz, P[k], Fq[k], c, ax, ay, az, bx, by, bz);
+                    bx = __shfl_sync(0xffffffffu, bx, nxt);
+                    by = __shfl_sync(0xffffffffu, by, nxt);
+                    bz = __shfl_sync(0xffffffffu, bz, nxt);
+                }
+                double *jw = s_jacc + warp * 3 * B + gq * 32 + lane;   // source 32 gq + lane
+                jw[0] = bx;
+                jw[B] = by;
+                jw[2 * B] = bz;
+            }
+        }
+        __syncthreads();  // stage st consumed; every warp's source sums are in s_jacc
+        if (!diag) {
+            double *dst = jpart + static_cast<size_t>(t) * 3 * B;
+            for (int e = tid; e < 3 * B; e += B) {
+                double v = s_jacc[e];
+#pragma unroll
+                for (int w = 1; w < NW; ++w) v += s_jacc[w * 3 * B + e];
+                dst[e] = v;
+            }
+            __syncthreads();  // s_jacc free for the next tile
+        }
+        aborted = s_abort != 0;
+        if (tid == 0 && !aborted && t + 2 < t1) issue(st);
+        if (++jb == nb) { ++ib; jb = ib; }
+    }
+    flush(cur_ib);
+    if (tid == 0) {
+        // After a time-out, wait (bounded) for copies still in flight into this CTA's
+        // shared memory before the CTA exits.
+        for (int k = waited0; k < issued0; ++k)
+            if (!mbar_wait_bounded(&bars[0], k & 1, drain_limit(lim))) atomicOr(err, DEV_ERR_TIMEOUT);
+        for (int k = waited1; k < issued1; ++k)
+            if (!mbar_wait_bounded(&bars[1], k & 1, drain_limit(lim))) atomicOr(err, DEV_ERR_TIMEOUT);
+    }
+}
+
+constexpr size_t sym64_smem() {
+    return 4 * static_cast<size_t>(kB64) * sizeof(dbl4) + (kB64 / 32) * 3 * static_cast<size_t>(kB64) * sizeof(double);
 }
 
 // ---------------------------------------------------------------- dispatch
@@ -718,6 +903,32 @@ cudaError_t dense_setup(sd_handle *h) {
     // (4 each) for mid-size N, 256 x 128 (2 each) below
     const bool large = h->npad >= SD_DENSE_SYM_LARGE_N && h->npad % 512 == 0;
     const int B = large ? 512 : 256, NT = (large || h->npad < SD_DENSE_SYM_MID_N) ? 128 : 64;
+    if (h->mode == MODE_FP64 && want_sym != SD_DENSE_DIRECTED) {
+        void *sfn = h->tensor == T_OSEEN ? (h->pc.periodic ? reinterpret_cast<void *>(&dense_sym64_kernel<T_OSEEN, true>)
+                                                           : reinterpret_cast<void *>(&dense_sym64_kernel<T_OSEEN, false>))
+                                         : (h->pc.periodic ? reinterpret_cast<void *>(&dense_sym64_kernel<T_RP, true>)
+                                                           : reinterpret_cast<void *>(&dense_sym64_kernel<T_RP, false>));
+        cudaError_t e = cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(sym64_smem()));
+        if (e != cudaSuccess) return e;
+        int socc = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&socc, sfn, kB64, sym64_smem());
+        if (e != cudaSuccess) return e;
+        socc = std::max(socc, 1);
+        DenseGeom s{};
+        s.sym = 1;
+        s.I = s.J = kB64;
+        s.nIB = s.nJT = h->npad / kB64;
+        s.nT = static_cast<long long>(s.nIB) * (s.nIB + 1) / 2;
+        if (want_sym == SD_DENSE_SYMMETRIC || s.nT * SD_DENSE_SYM_SMS_PER_TILE >= h->num_sms) {
+            const long long swant = static_cast<long long>(h->num_sms) * socc * SD_DENSE_SYM_CTA_SCALE;
+            s.chunk = std::max(1LL, (s.nT + swant - 1) / swant);
+            s.grid = static_cast<int>((s.nT + s.chunk - 1) / s.chunk);
+            g = s;
+            occ = socc;
+            h->sym_nt = kB64;
+        }
+    }
     if (h->mode != MODE_FP64 && h->npad % B == 0 && want_sym != SD_DENSE_DIRECTED) {
         void *sfn = pick_sym(h->tensor, h->mode, h->pc.periodic != 0, B, NT);
         cudaError_t e = cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -749,6 +960,9 @@ cudaError_t dense_setup(sd_handle *h) {
     return cudaSuccess;
 }
 
+// The watchdog limit the all-pairs kernels get: negated while a stall is injected.
+static long long dense_wd(const sd_handle *h) { return h->inject_stall ? -h->watchdog : h->watchdog; }
+
 template <bool PER>
 static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part, const TileWin &w,
                            int grid) {
@@ -757,12 +971,22 @@ static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror fr
     const bool oseen = h->tensor == T_OSEEN;
     if (h->mode == MODE_FP64) {
         const dbl4 *p = static_cast<const dbl4 *>(posm.aos), *f = static_cast<const dbl4 *>(frcm.aos);
+        if (g.sym) {
+            double *jp = static_cast<double *>(h->jpart);
+            if (oseen)
+                dense_sym64_kernel<T_OSEEN, PER><<<grid, kB64, sym64_smem(), st>>>(p, f, part, jp, h->npad, g, h->pc,
+                                                                                 h->d_err, dense_wd(h), w.b0);
+            else
+                dense_sym64_kernel<T_RP, PER><<<grid, kB64, sym64_smem(), st>>>(p, f, part, jp, h->npad, g, h->pc,
+                                                                              h->d_err, dense_wd(h), w.b0);
+            return;
+        }
         if (oseen)
             dense_kernel<T_OSEEN, MODE_FP64, PER><<<grid, kNT, smem, st>>>(p, f, part, h->npad, g, h->pc,
-                                                                            h->d_err, h->watchdog, w);
+                                                                            h->d_err, dense_wd(h), w);
         else
             dense_kernel<T_RP, MODE_FP64, PER><<<grid, kNT, smem, st>>>(p, f, part, h->npad, g, h->pc, h->d_err,
-                                                                         h->watchdog, w);
+                                                                         dense_wd(h), w);
         return;
     }
     PairConst2 c2{};
@@ -778,9 +1002,10 @@ static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror fr
     const bool comp = h->mode == MODE_FP32C;
     if (g.sym) {
 #define SD_DS(TT, CC, BB, NN)                                                                                  \
-    dense_sym_kernel<TT, CC, PER, BB, NN><<<g.grid, NN, sym_smem(BB, NN), st>>>(posm.soa, frcm.soa, part,     \
-                                                                                h->jpart, h->npad, g, c2,      \
-                                                                                h->d_flag, h->d_err, h->watchdog)
+    dense_sym_kernel<TT, CC, PER, BB, NN><<<grid, NN, sym_smem(BB, NN), st>>>(posm.soa, frcm.soa, part,       \
+                                                                              static_cast<float *>(h->jpart), h->npad, \
+                                                                              g, c2, h->d_flag, h->d_err, dense_wd(h), \
+                                                                              w.b0)
 #define SD_DS_SHAPE(BB, NN)                                                                                    \
     if (oseen) {                                                                                               \
         if (comp) SD_DS(T_OSEEN, true, BB, NN); else SD_DS(T_OSEEN, false, BB, NN);                            \
@@ -800,7 +1025,7 @@ static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror fr
     }
 #define SD_D2(TT, CC)                                                                                          \
     dense2_kernel<TT, CC, PER><<<grid, kNT, smem, st>>>(posm.soa, frcm.soa, part, h->npad, g, c2, h->d_flag, \
-                                                        h->d_err, h->watchdog, w)
+                                                        h->d_err, dense_wd(h), w)
     if (oseen) {
         if (comp) SD_D2(T_OSEEN, true); else SD_D2(T_OSEEN, false);
     } else {
@@ -814,14 +1039,15 @@ cudaError_t launch_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm
     const DenseGeom &g = h->geom;
     TileWin w{};
     int grid = g.grid;
-    if (win) {   // a shard of whole i-blocks (directed kernels only): the CTAs of the full launch touching it
-        if (g.sym) return cudaErrorInvalidValue;
+    if (win) {   // a window of tiles: the CTAs of the full launch touching it
         w = *win;
-        const long long T = static_cast<long long>(g.nIB) * g.nJT;
+        const long long T = g.nT;
         const long long hi = (w.hi >= 0 && w.hi < T) ? w.hi : T;
         if (w.lo >= hi) return cudaSuccess;
         w.b0 = static_cast<int>(w.lo / g.chunk);
         grid = static_cast<int>((hi - 1) / g.chunk) - w.b0 + 1;
+        // the symmetric kernels take whole CTAs of the full launch only
+        if (g.sym && (w.lo != w.b0 * g.chunk || (hi != T && hi % g.chunk != 0))) return cudaErrorInvalidValue;
     }
     prof_begin(h, SD_KERNEL_DENSE, st);
     if (h->pc.periodic)

@@ -355,7 +355,8 @@ struct EpiArgs {
     const double *ent_out;   // near-pass list results, per particle noff/ncnt
     const int *noff, *ncnt;
     const double *part;
-    const float *jpart;   // source-side sums of the symmetric kernel (g.sym)
+    const float *jpart;     // source-side sums of the symmetric kernel (g.sym), FP32 modes
+    const double *jpart64;  // ... FP64 mode
     int npad;
     DenseGeom g;
     const double *x64;
@@ -372,7 +373,20 @@ struct EpiArgs {
     double *vlag;   // OUT_EULER with lubrication: this step's FP64 velocities, for the next step's forces
     int *err;
     int row0, row1; // rows written (a shard); vout holds rows row0 .. row1-1
+    EpiShard sh;    // a tile shard's share, or the shards' results to combine
 };
+
+// First r in [0, ib] whose source-side row of block ib, tile rowstart(r) + ib - r,
+// is >= t (the row index grows with r).
+__device__ __forceinline__ int first_row_at(const DenseGeom &g, int ib, long long t) {
+    int lo = 0, hi = ib;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (geom_rowstart(g, mid) + (ib - mid) >= t) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
 
 // Each CTA finishes 32 consecutive particles.  Warp w of the kEpiWarps adds the
 // slots s = w, w + kEpiWarps, ... of the dense partial sums (and, after the
@@ -407,27 +421,45 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
     {
         double v[3] = {0.0, 0.0, 0.0};
         float hi[3] = {0.0f, 0.0f, 0.0f}, lo[3] = {0.0f, 0.0f, 0.0f};
-        if (active) {
+        if (active && a.sh.pall) {
+            // the shards' results, added in shard order (warp 0)
+            if (w == 0)
+                for (int q = 0; q < a.sh.nparts; ++q)
+                    for (int d = 0; d < 3; ++d) v[d] += a.sh.pall[(static_cast<size_t>(q) * a.n + i) * 3 + d];
+        } else if (active) {
             const int ib = i / a.g.I;
-            const int ns = geom_last(a.g, ib) - geom_first(a.g, ib) + 1;
-            const int nc = a.g.sym ? ib : 0;
+            const int first = geom_first(a.g, ib);
+            const int s0 = max(0, a.sh.b0 - first);
+            const int ns = min(geom_last(a.g, ib) - first + 1, a.sh.b1 - first);
+            int r0 = 0, nc = a.g.sym ? ib : 0;
+            if (a.g.sym && (a.sh.tlo > 0 || a.sh.thi < a.g.nT)) {
+                r0 = first_row_at(a.g, ib, a.sh.tlo);
+                nc = first_row_at(a.g, ib, a.sh.thi);
+            }
             const int o = i - ib * a.g.I;
             const int J = a.g.J;
             const size_t cs = 3 * static_cast<size_t>(J);
             if constexpr (MODE == MODE_FP32) {
-                for (int s = w; s < ns; s += kEpiWarps)
+                for (int s = s0 + w; s < ns; s += kEpiWarps)
                     for (int d = 0; d < 3; ++d)
                         hi[d] = __fadd_rn(hi[d],
                                           static_cast<float>(a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i]));
-                for (int r = w; r < nc; r += kEpiWarps) {
+                for (int r = r0 + w; r < nc; r += kEpiWarps) {
                     const float *src = a.jpart + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
                     for (int d = 0; d < 3; ++d) hi[d] = __fadd_rn(hi[d], src[d * J]);
                 }
+            } else if constexpr (MODE == MODE_FP64) {
+                for (int s = s0 + w; s < ns; s += kEpiWarps)
+                    for (int d = 0; d < 3; ++d) v[d] += a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+                for (int r = r0 + w; r < nc; r += kEpiWarps) {
+                    const double *src = a.jpart64 + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
+                    for (int d = 0; d < 3; ++d) v[d] += src[d * J];
+                }
             } else {
-                for (int s = w; s < ns; s += kEpiWarps)
+                for (int s = s0 + w; s < ns; s += kEpiWarps)
                     for (int d = 0; d < 3; ++d) v[d] += a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
 #pragma unroll kEpiUnroll
-                for (int r = w; r < nc; r += kEpiWarps) {
+                for (int r = r0 + w; r < nc; r += kEpiWarps) {
                     const float *src = a.jpart + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
                     for (int d = 0; d < 3; ++d) fold2(hi[d], lo[d], src[d * J]);
                 }
@@ -459,6 +491,13 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
             }
             V[d] = v + (static_cast<double>(h) + static_cast<double>(l));
         }
+    }
+    if constexpr (OUT == OUT_PART) {   // a shard's raw share: no self or near terms, no mu0
+        double *o = static_cast<double *>(a.vout) + 3 * static_cast<size_t>(i);
+        o[0] = V[0];
+        o[1] = V[1];
+        o[2] = V[2];
+        return;
     }
     // self term: the tile holding it was clamped; replace by mu_ii / mu0 = I
     {
@@ -513,6 +552,7 @@ static void epi_launch(int out, int nb, cudaStream_t st, const EpiArgs &a) {
     switch (out) {
         case OUT_F32: epilogue_kernel<TDENSE, MODE, OUT_F32><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
         case OUT_F64: epilogue_kernel<TDENSE, MODE, OUT_F64><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
+        case OUT_PART: epilogue_kernel<TDENSE, MODE, OUT_PART><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
         default: epilogue_kernel<TDENSE, MODE, OUT_EULER><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
     }
 }
@@ -528,7 +568,7 @@ static void epi_launch_mode(int mode, int out, int nb, cudaStream_t st, const Ep
 
 cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double *x64, const void *posm,
                             const double *F64, const void *frcm, void *vout, double dt, double *x64n, int row0,
-                            int row1) {
+                            int row1, const EpiShard *shard) {
     if (h->n == 0) return cudaSuccess;
     if (row1 < 0 || row1 > h->n) row1 = h->n;
     if (row0 < 0) row0 = 0;
@@ -538,7 +578,8 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
     a.noff = h->near_off;
     a.ncnt = h->near_cnt;
     a.part = h->part;
-    a.jpart = h->jpart;
+    a.jpart = h->mode == MODE_FP64 ? nullptr : static_cast<const float *>(h->jpart);
+    a.jpart64 = h->mode == MODE_FP64 ? static_cast<const double *>(h->jpart) : nullptr;
     a.npad = h->npad;
     a.g = h->geom;
     a.x64 = x64;
@@ -556,6 +597,7 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
     a.err = h->d_err;
     a.row0 = row0;
     a.row1 = row1;
+    if (shard) a.sh = *shard;
     const int nb = (row1 - row0 + 31) / 32;
     prof_begin(h, SD_KERNEL_EPILOGUE, st);
     if (h->tensor == T_OSEEN)

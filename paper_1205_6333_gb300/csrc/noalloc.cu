@@ -223,16 +223,26 @@ extern "C" sd_status sd_mobility_apply_noalloc(const double *x, const double *F,
     pc.c3_f = static_cast<float>(pc.c3_d);
     pc.m3c3_f = static_cast<float>(pc.m3c3_d);
 
+    // An error left by the caller's earlier work is reported as such and left in
+    // place (peeked, not cleared); each launch below is then checked on its own.
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess)
+        return set_error(SD_ERR_CUDA, std::string("sd_mobility_apply_noalloc: a CUDA error from earlier work is "
+                                                  "pending (not cleared): ") + cudaGetErrorString(e));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     na_stage_kernel<<<(g.npad + 255) / 256, 256, 0, st>>>(g);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, "sd_mobility_apply_noalloc: staging launch");
     const dim3 grid(g.npad / kThreads, nsplit);
     switch (tensor) {
         case SD_TENSOR_RPY: na_dense_kernel<T_RPY><<<grid, kThreads, 0, st>>>(g); break;
         case SD_TENSOR_RP: na_dense_kernel<T_RP><<<grid, kThreads, 0, st>>>(g); break;
         default: na_dense_kernel<T_OSEEN><<<grid, kThreads, 0, st>>>(g); break;
     }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, "sd_mobility_apply_noalloc: all-pairs launch");
     na_finish_kernel<<<(n + 127) / 128, 128, 0, st>>>(g, nsplit);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_status(e, "sd_mobility_apply_noalloc launch");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, "sd_mobility_apply_noalloc: reduction launch");
     return SD_OK;
 }

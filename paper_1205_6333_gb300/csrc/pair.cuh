@@ -284,6 +284,46 @@ __device__ __forceinline__ void pair_f64(double xi, double yi, double zi, dbl4 p
     az = __fma_rn(s, dz, __fma_rn(A, f.z, az));
 }
 
+// The pair (i, j) used in both directions in FP64 (mu_ij = mu_ji, Sec. 2.2): r, r^2,
+// 1/r, A and B once, then
+//   a += mu(r_i - r_j) F_j / mu0    (target i),   b += mu(r_j - r_i) F_i / mu0   (source j).
+// r_j - r_i = -(r_i - r_j) exactly and every step is a round-to-nearest operation,
+// so each direction is bit-identical to pair_f64 evaluated for that ordered pair.
+template <int TENSOR, bool PER = false>
+__device__ __forceinline__ void pair_sym_f64(double xi, double yi, double zi, double gx, double gy, double gz,
+                                             const dbl4 &p, const dbl4 &f, const PairConst &c, double &ax,
+                                             double &ay, double &az, double &bx, double &by, double &bz) {
+    double dx = __dsub_rn(xi, p.x);
+    double dy = __dsub_rn(yi, p.y);
+    double dz = __dsub_rn(zi, p.z);
+    if (PER) {
+        dx = min_image_f64(dx, c.Ld[0], c.invLd[0]);
+        dy = min_image_f64(dy, c.Ld[1], c.invLd[1]);
+        dz = min_image_f64(dz, c.Ld[2], c.invLd[2]);
+    }
+    double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+    r2 = fmax(r2, c.r2min_d);
+    const double ri = rsqrt_nr64(r2);
+    const double ri2 = __dmul_rn(ri, ri);
+    double A, B;
+    if (TENSOR == T_OSEEN) {
+        A = __dmul_rn(c.c1_d, ri);
+        B = __dmul_rn(A, ri2);
+    } else {
+        A = __dmul_rn(ri, __fma_rn(c.c3_d, ri2, c.c1_d));
+        const double ri3 = __dmul_rn(ri, ri2);
+        B = __dmul_rn(ri3, __fma_rn(c.m3c3_d, ri2, c.c1_d));
+    }
+    const double s = __dmul_rn(B, __fma_rn(dz, f.z, __fma_rn(dy, f.y, __dmul_rn(dx, f.x))));
+    ax = __fma_rn(s, dx, __fma_rn(A, f.x, ax));
+    ay = __fma_rn(s, dy, __fma_rn(A, f.y, ay));
+    az = __fma_rn(s, dz, __fma_rn(A, f.z, az));
+    const double u = __dmul_rn(B, __fma_rn(dz, gz, __fma_rn(dy, gy, __dmul_rn(dx, gx))));
+    bx = __fma_rn(u, dx, __fma_rn(A, gx, bx));
+    by = __fma_rn(u, dy, __fma_rn(A, gy, by));
+    bz = __fma_rn(u, dz, __fma_rn(A, gz, bz));
+}
+
 // ---------------------------------------------------------------- exact FP64 profile
 
 // A(r), B(r) and the radial derivatives divided by r, dA = A'(r)/r, dB = B'(r)/r,

@@ -72,14 +72,16 @@ __device__ __forceinline__ float rcp_sfu(float x) {
     return y;
 }
 
-// FP64 reciprocal square root: SFU seed refined by two Newton-Raphson steps
-// y <- y (3 - x y^2) / 2 (quadratic convergence: 2^-22 -> 2^-44 -> below 2^-53).
+// FP64 reciprocal square root from the FP32 SFU seed y0 (relative error below
+// 2^-22) and one third-order correction: with e = 1 - x y0^2,
+//   x^(-1/2) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + 5e^3/16 + ...),
+// and the truncated e^3 term is below 2^-64 relative.  Five FP64 operations instead
+// of the seven of two Newton steps (FP64 issues at a small fraction of the FP32 rate
+// on this GPU, so the operation count is the cost).
 __device__ __forceinline__ double rsqrt_nr64(double x) {
-    double y = static_cast<double>(rsqrt_sfu(static_cast<float>(x)));
-    double h = 0.5 * x;
-    y = y * fma(-h * y, y, 1.5);
-    y = y * fma(-h * y, y, 1.5);
-    return y;
+    const double y0 = static_cast<double>(rsqrt_sfu(static_cast<float>(x)));
+    const double e = fma(-x * y0, y0, 1.0);
+    return fma(y0 * e, fma(0.375, e, 0.5), y0);
 }
 
 }  // namespace sd

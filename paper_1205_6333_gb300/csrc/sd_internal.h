@@ -19,7 +19,20 @@ enum : int {
 };
 
 enum { MODE_FP32C = 0, MODE_FP64 = 1, MODE_FP32 = 2 };
-enum { OUT_F32 = 0, OUT_F64 = 1, OUT_EULER = 2 };
+// Epilogue outputs: velocities (FP32 / FP64), the Euler update, or (OUT_PART) a
+// shard's raw share of the all-pairs sum (FP64, no self or near-pair terms).
+enum { OUT_F32 = 0, OUT_F64 = 1, OUT_EULER = 2, OUT_PART = 3 };
+
+// A shard of the all-pairs sum for the epilogue: only the slots written by CTAs
+// b0 .. b1-1 of the full launch, and (symmetric kernels) the source-side rows of the
+// tiles tlo .. thi-1, enter the sum; or, with pall, the sum is replaced by the
+// nparts shard results pall[g][n][3] added in shard order.
+struct EpiShard {
+    int b0 = 0, b1 = 0x7fffffff;
+    long long tlo = 0, thi = 0x7fffffffffffffffLL;
+    const double *pall = nullptr;
+    int nparts = 0;
+};
 
 constexpr int kPadTo = 1024;     // particle arrays are padded to a multiple of this
 #ifndef SD_DENSE_THREADS
@@ -162,6 +175,7 @@ struct sd_handle {
     sd::PairConst pc{};
     double r_near = 0.0, rep_rc = 0.0;
     long long watchdog = sd::kDefaultWatchdog;
+    bool inject_stall = false;   // sd_inject_stall: the all-pairs kernels' first CTA skips a copy
 
     // FP64 state (ping-pong) and the mirror the dense kernel reads: float4 or
     // double4 [npad], positions relative to particle 0 of the state, rewritten by
@@ -184,7 +198,8 @@ struct sd_handle {
     double *Wa64 = nullptr;  sd::Mirror wam;
     double *part = nullptr;  size_t part_bytes = 0;   // dense partial sums
     double *part2 = nullptr; size_t part2_bytes = 0;  // second output of the VJP kernel
-    float *jpart = nullptr;  size_t jpart_bytes = 0;   // symmetric kernel: source-side sums [tile][3][block]
+    void *jpart = nullptr;  size_t jpart_bytes = 0;   // symmetric kernels: source-side sums [tile][3][block],
+                                                       // float (FP32 modes) or double (FP64)
     sd::DenseGeom geom{}, geomv{};
     int dense_occ = 0, vjp_occ = 0;
     int sym_nt = 128;   // threads per CTA of the symmetric kernel's chosen block shape
@@ -218,6 +233,7 @@ struct sd_handle {
     sd::Profiler prof;
     int64_t launches = 0;
     bool capturing = false;
+    int part_kind = 0;   // 1: sd_mobility_apply_part done, 2: sd_step_part done (their combine may follow)
 };
 
 namespace sd {
@@ -252,7 +268,7 @@ cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const 
                         const void *frcm);
 cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double *x64, const void *posm,
                             const double *F64, const void *frcm, void *vout, double dt, double *x64n, int row0 = 0,
-                            int row1 = -1);
+                            int row1 = -1, const EpiShard *shard = nullptr);
 // vjp.cu
 cudaError_t vjp_setup(sd_handle *h);
 cudaError_t launch_vjp_dense(sd_handle *h, cudaStream_t st, const void *posm, const void *frcm, const void *wm,

@@ -1,21 +1,24 @@
-"""One system split over several devices by target rows (one process per GPU,
-torch.distributed; Sec. 3.1 step 3 with the rows of the sum divided between ranks).
+"""One system split over several devices (one process per GPU, torch.distributed).
 
-Every rank holds the whole state (all n positions and forces) in its own
-``System`` created with ``dense="directed"``.  Rank r owns the rows of
-``shard_rows(n, r, world)``:
+Two splits of the all-pairs sum of Sec. 3.1 step 3 are offered; in both, every
+rank holds the whole state (all n positions and forces) in its own ``System``.
 
-* ``sharded_apply``: the rank computes v for its rows with
-  ``sd_mobility_apply_rows`` (the whole sum over j, in the library's kernels),
-  and an all-gather assembles the n velocities;
-* ``sharded_steps``: per step the rank advances its rows with ``sd_step_rows``,
-  and an all-gather of positions (24 B per particle) restores the replicated
-  state before the next step.
+Tile shards (either all-pairs kernel, every precision; the default):
+  Rank r runs the CTAs [r G / world, (r + 1) G / world) of the all-pairs kernel's
+  persistent launch of G CTAs (``sd_*_part``): its share of the pair sum for every
+  row.  One all-gather of those FP64 shares (24 B per particle and rank) brings all
+  of them to every rank, and ``sd_*_combine`` adds them in rank order with the self
+  term and the FP64 near-pair corrections.  Each rank therefore finishes the step
+  for every particle, identically, and no positions need to be exchanged.
 
-Each row is bit-identical to the unsharded result.  This module only partitions
-rows and moves data (device-to-device copies and the collective); it does no
-arithmetic of the method.  Collectives run on the default process group unless
-``group`` is given (NCCL between GPUs, gloo for host tensors).
+Row shards (the directed kernel only):
+  Rank r computes the velocities of its own rows (``sd_*_rows``) and an all-gather
+  of those rows (24 B per particle) restores the replicated state.
+
+This module only partitions the work and moves data (the collective and nothing
+else); every step of the method runs in the library's kernels.  Collectives run on
+the default process group unless ``group`` is given (NCCL between GPUs; gloo with
+host staging, ``via_host=True``, for tests that share one GPU between processes).
 """
 from __future__ import annotations
 
@@ -28,6 +31,39 @@ def shard_rows(n: int, rank: int, world: int, block: int = ROW_BLOCK):
     b0 = rank * nb // world
     b1 = (rank + 1) * nb // world
     return min(b0 * block, n), min(b1 * block, n)
+
+
+def _all_gather_parts(P, world, group=None, via_host=False, out=None):
+    """(world, n, 3) tensor of every rank's P, in rank order."""
+    import torch
+    import torch.distributed as dist
+    if via_host:
+        src = P.cpu()
+        recv = [torch.empty_like(src) for _ in range(world)]
+        dist.all_gather(recv, src, group=group)
+        return torch.stack(recv).to(P.device)
+    if out is None:
+        out = torch.empty((world,) + tuple(P.shape), dtype=P.dtype, device=P.device)
+    dist.all_gather_into_tensor(out, P, group=group)
+    return out
+
+
+def tile_sharded_apply(system, F, rank: int, world: int, group=None, via_host=False):
+    """v = mu(x) F on `world` ranks by tile shards: F is the whole n x 3 force tensor on
+    every rank; returns the whole n x 3 FP64 velocity tensor (CUDA) on every rank."""
+    P = system.mobility_apply_part(F, rank, world)
+    Pall = _all_gather_parts(P, world, group, via_host)
+    return system.mobility_apply_combine(Pall)
+
+
+def tile_sharded_steps(system, dt: float, nsteps: int, rank: int, world: int, group=None, via_host=False):
+    """nsteps Euler steps of a replicated system by tile shards (one all-gather of the
+    FP64 shares per step; the state stays identical on every rank)."""
+    P = Pall = None
+    for _ in range(int(nsteps)):
+        P = system.step_part(rank, world, P)
+        Pall = _all_gather_parts(P, world, group, via_host, out=Pall)
+        system.step_combine(dt, Pall)
 
 
 def _gather_rows(local_full, rank, world, group=None):
@@ -50,8 +86,8 @@ def _gather_rows(local_full, rank, world, group=None):
 
 
 def sharded_apply(system, F, rank: int, world: int, group=None):
-    """v = mu(x) F on `world` ranks: F is the whole n x 3 force tensor on every rank;
-    returns the whole n x 3 velocity tensor on every rank."""
+    """Row shards: v = mu(x) F on `world` ranks (directed kernel); F is the whole n x 3
+    force tensor on every rank; returns the whole n x 3 velocity tensor on every rank."""
     import torch
     n = system.n
     r0, r1 = shard_rows(n, rank, world)
@@ -62,9 +98,9 @@ def sharded_apply(system, F, rank: int, world: int, group=None):
 
 
 def sharded_steps(system, dt: float, nsteps: int, rank: int, world: int, x=None, group=None):
-    """nsteps Euler steps of a replicated system, each rank advancing its own rows.
-    `x` (n x 3 float64 tensor on the system's device, optional) is used as the
-    exchange buffer and holds the positions after the last step."""
+    """Row shards: nsteps Euler steps of a replicated system, each rank advancing its
+    own rows.  `x` (n x 3 float64 tensor on the system's device, optional) is used as
+    the exchange buffer and holds the positions after the last step."""
     import torch
     n = system.n
     r0, r1 = shard_rows(n, rank, world)

@@ -162,7 +162,17 @@ def fcc_lattice(n_cells: int, density: float = 0.1, a: float = 1.0):
 
 
 def config_inputs(idx: int, n: int | None = None):
-    """Inputs of the five named workloads (see the design doc for the recipe).
+    """Inputs of the five named workloads, seeded with SEED_BASE + idx:
+
+      1. four spheres on a horizontal square of side 4a with U(+-0.01a) jitter, gravity;
+      2. n = 65,536 spheres uniform in a cube at volume fraction 0.05 without overlap
+         (random sequential addition), forces N(0,1) per component, both as float32;
+      3. n = 16,384 spheres in a cube at volume fraction 0.10, gravity and the soft
+         repulsion eps (2a/r)^12 (eps = 1) cut at 2.5a;
+      4. 16,384 clusters of U{4..256} spheres, each uniform in a ball at volume
+         fraction 0.05 without overlap, forces N(0,1);
+      5. n = 4,096 spheres in a cube at volume fraction 0.05, gravity, and targets
+         x(0) + N(0,1) for the loss sum |x(T) - x*|^2.
 
     Returns a dict of numpy arrays and scalars; positions and forces are float64
     except where the workload specifies float32 inputs (workload 2).

@@ -1,5 +1,6 @@
 """Shared helpers of the tests: error metrics and seeded inputs with the
-structure of the paper's workloads (see the design doc for the recipe)."""
+structure of the paper's workloads (random non-overlapping packings at a given
+volume fraction, N(0,1) forces, deliberately planted overlapping pairs)."""
 import numpy as np
 
 from paper_1205_6333_gb300 import inputs

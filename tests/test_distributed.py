@@ -1,7 +1,13 @@
-"""Row sharding of one system over ranks (paper_1205_6333_gb300.distributed): the
-partition and the all-gather logic on CPU with gloo ranks (a stand-in system whose
-rows are computed by the FP64 oracle), and the shard calls of the library on one GPU
-as logical shards, bit-identical to the unsharded result."""
+"""One system split over ranks (paper_1205_6333_gb300.distributed).
+
+Tile shards (the all-pairs sum divided by pairs, either kernel, every precision):
+  * gloo ranks on CPU drive the partition / all-gather / combine logic with a
+    stand-in system whose shares are computed from the oracle's mobility matrix;
+  * on one GPU, logical shards through the library's part/combine calls against the
+    FP64 oracle element by element, for the apply and for Euler steps;
+  * two processes sharing one GPU run the real kernels and exchange their shares
+    over gloo (host staging), as distributed.tile_sharded_steps does between GPUs.
+Row shards (directed kernel): the same on CPU, and bit-identical logical shards."""
 import os
 import socket
 
@@ -94,6 +100,87 @@ def test_sharded_apply_and_steps_gloo(world):
         np.testing.assert_array_equal(xT, xref)
 
 
+class _OracleTiles:
+    """Stand-in for a System on a CPU rank with the tile-shard interface: shard s of G
+    owns the source columns [s n / G, (s + 1) n / G) of the oracle's assembled mobility
+    matrix; its share is that block of columns times the forces."""
+
+    def __init__(self, x, fext, g):
+        self.n = x.shape[0]
+        self.x = np.array(x, dtype=np.float64)
+        self.F = fext + g
+        self.staged = None
+
+    def _share(self, F, shard, nshards):
+        import torch
+        M = oracle.assemble(self.x)
+        j0, j1 = shard * self.n // nshards, (shard + 1) * self.n // nshards
+        P = (M[:, 3 * j0:3 * j1] @ np.asarray(F, dtype=np.float64).reshape(-1)[3 * j0:3 * j1]).reshape(self.n, 3)
+        return torch.from_numpy(P)
+
+    def mobility_apply_part(self, F, shard, nshards):
+        return self._share(F.numpy(), shard, nshards)
+
+    def mobility_apply_combine(self, Pall):
+        V = Pall[0].clone()
+        for q in range(1, Pall.shape[0]):
+            V += Pall[q]
+        return V
+
+    def step_part(self, shard, nshards, P=None):
+        return self._share(self.F, shard, nshards)
+
+    def step_combine(self, dt, Pall):
+        self.x = self.x + dt * self.mobility_apply_combine(Pall).numpy()
+
+
+def _tile_worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    from paper_1205_6333_gb300.distributed import tile_sharded_apply, tile_sharded_steps
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    n = 200
+    x0, _ = inputs.cube_rsa(n, 0.05, 903)
+    fe = inputs.normal_forces(n, 904)
+    g = np.array([0.0, 0.0, -1.0])
+    sysr = _OracleTiles(x0, fe, g)
+    V = tile_sharded_apply(sysr, torch.from_numpy(fe), rank, world, via_host=True)
+    tile_sharded_steps(sysr, 0.05, 3, rank, world, via_host=True)
+    out[rank] = (V.numpy().tobytes(), sysr.x.tobytes())
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_tile_sharded_apply_and_steps_gloo(world):
+    """Every rank computes a share of the sum for every row; after the all-gather and
+    the combine in rank order every rank holds the same result, the full product."""
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_tile_worker, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(180)
+        assert p.exitcode == 0
+    n = 200
+    x0, _ = inputs.cube_rsa(n, 0.05, 903)
+    fe = inputs.normal_forces(n, 904)
+    g = np.array([0.0, 0.0, -1.0])
+    Vref = oracle.mobility_apply(x0, fe)
+    xref = oracle.euler(x0, 3, 0.05, fe, g)
+    V0 = np.frombuffer(out[0][0]).reshape(n, 3)
+    x0r = np.frombuffer(out[0][1]).reshape(n, 3)
+    for r in range(world):   # identical on every rank, bit for bit
+        np.testing.assert_array_equal(np.frombuffer(out[r][0]).reshape(n, 3), V0)
+        np.testing.assert_array_equal(np.frombuffer(out[r][1]).reshape(n, 3), x0r)
+    assert np.abs(V0 - Vref).max() <= 1e-13 * np.abs(Vref).max()
+    assert np.abs(x0r - xref).max() <= 1e-13 * np.abs(xref - x0).max()
+
+
 def test_shard_rows_partition():
     for n in [1, 255, 256, 257, 5000, 65536]:
         for world in [1, 2, 3, 8]:
@@ -172,3 +259,148 @@ def test_row_shards_need_the_directed_kernel():
         with pytest.raises(sd.SDError) as ei:
             s.step_rows(0.01, 0, 32)
         assert ei.value.status_name == "SD_ERR_UNSUPPORTED"
+
+
+# ---------------------------------------------------------------- tile shards on one GPU
+
+_TILE_CASES = [("fp32c", "symmetric", 1e-5), ("fp32c", "directed", 1e-5), ("fp64", "symmetric", 1e-12),
+               ("fp64", "directed", 1e-12)]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,dense,tol", _TILE_CASES)
+def test_tile_shards_apply_match_oracle(prec, dense, tol):
+    """Logical tile shards (1, 2, 3 and 7 of them) of the apply, combined in shard order,
+    against the oracle element by element; overlapping pairs included."""
+    import torch
+    import paper_1205_6333_gb300 as sd
+    from helpers import rel_err, system_with_overlaps
+    n = 5000
+    x, _ = system_with_overlaps(n, 0.05, seed=940, overlaps=5)
+    F = inputs.normal_forces(n, 941)
+    ref = oracle.mobility_apply(x, F, "rpy", nthreads=8)
+    Ft = torch.tensor(F, dtype=torch.float64, device="cuda")
+    with sd.System(n, prec=prec, dense=dense) as s:
+        assert s.dense_kernel() == dense
+        s.set_positions(x)
+        full = s.mobility_apply(F)
+        for G in (1, 2, 3, 7):
+            Pall = torch.stack([s.mobility_apply_part(Ft, r, G) for r in range(G)])
+            V = s.mobility_apply_combine(Pall).cpu().numpy()
+            assert rel_err(V, ref) <= tol, (G, rel_err(V, ref))
+            assert rel_err(V, full) <= (1e-14 if prec == "fp64" else 2e-6), G
+        # host forces in, host velocities out
+        Pall = torch.stack([s.mobility_apply_part(F, r, 2) for r in range(2)])
+        assert rel_err(s.mobility_apply_combine(Pall, like=F), ref) <= tol
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,dense,tol", [("fp32c", "symmetric", 1e-5), ("fp64", "symmetric", 1e-10),
+                                            ("fp64", "directed", 1e-10)])
+def test_tile_shards_steps_match_oracle(prec, dense, tol):
+    """Three logical ranks (three handles on one GPU), each computing its tile shard of
+    every step; the shares are exchanged (stacked in rank order) and every rank
+    finishes the step.  The three states stay identical bit for bit and follow the
+    oracle's trajectory (gravity + soft repulsion, 10 steps)."""
+    import torch
+    import paper_1205_6333_gb300 as sd
+    n, world, steps, dt = 3000, 3, 10, 0.02
+    x0, _ = inputs.cube_rsa(n, 0.10, 950)
+    fe = inputs.normal_forces(n, 951)
+    g = (0.0, 0.0, -1.0)
+    kw = dict(prec=prec, dense=dense, gravity=g, rep_eps=1.0, rep_rc=2.5)
+    ref = oracle.euler(x0, steps, dt, fe, g, rep_eps=1.0, rep_rc=2.5, nthreads=8)
+    ranks = [sd.System(n, **kw) for _ in range(world)]
+    try:
+        for s in ranks:
+            s.set_positions(x0)
+            s.set_forces(fe)
+        for _ in range(steps):
+            Pall = torch.stack([s.step_part(r, world) for r, s in enumerate(ranks)])
+            for s in ranks:
+                s.step_combine(dt, Pall)
+        xs = [s.get_positions() for s in ranks]
+    finally:
+        for s in ranks:
+            s.close()
+    for xr in xs[1:]:
+        np.testing.assert_array_equal(xr, xs[0])
+    disp = np.linalg.norm(ref - x0, axis=1).max()
+    assert np.linalg.norm(xs[0] - ref, axis=1).max() <= tol * disp
+
+
+@pytest.mark.gpu
+def test_tile_shards_lubrication_and_call_order():
+    """Lubrication works with tile shards (every rank finishes every row, so the lagged
+    velocities are complete); a combine without its part is refused."""
+    import torch
+    import paper_1205_6333_gb300 as sd
+    m, spacing = 8, 2.8
+    g1 = np.arange(m) * spacing
+    x0 = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3)
+    x0 = x0 + np.random.default_rng(960).uniform(-0.05, 0.05, x0.shape)
+    n = x0.shape[0]
+    fe = inputs.normal_forces(n, 961)
+    ref = oracle.euler(x0, 6, 0.02, fe, lubrication=True, nthreads=8)
+    with sd.System(n, prec="fp64", lubrication=True) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        with pytest.raises(sd.SDError) as ei:
+            s.step_combine(0.02, torch.zeros((1, n, 3), dtype=torch.float64, device="cuda"))
+        assert ei.value.status_name == "SD_ERR_STATE"
+        for _ in range(6):
+            Pall = torch.stack([s.step_part(r, 2).clone() for r in range(2)])
+            s.step_combine(0.02, Pall)
+        xT = s.get_positions()
+    disp = np.linalg.norm(ref - x0, axis=1).max()
+    assert np.linalg.norm(xT - ref, axis=1).max() <= 1e-10 * disp
+
+
+def _gpu_tile_worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    import paper_1205_6333_gb300 as sd
+    from paper_1205_6333_gb300.distributed import tile_sharded_apply, tile_sharded_steps
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    n = 4000
+    x0, _ = inputs.cube_rsa(n, 0.05, 970)
+    fe = inputs.normal_forces(n, 971)
+    with sd.System(n, gravity=(0.0, 0.0, -1.0)) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        V = tile_sharded_apply(s, torch.tensor(fe, device="cuda"), rank, world, via_host=True)
+        tile_sharded_steps(s, 0.05, 4, rank, world, via_host=True)
+        out[rank] = (V.cpu().numpy().tobytes(), s.get_positions().tobytes(), s.dense_kernel())
+    dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_tile_sharded_two_processes_one_gpu():
+    """distributed.tile_sharded_apply / tile_sharded_steps in two processes that share
+    the GPU: real kernels, shares exchanged over gloo through host memory (no kernel
+    waits on another process)."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_gpu_tile_worker, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    from helpers import rel_err
+    n = 4000
+    x0, _ = inputs.cube_rsa(n, 0.05, 970)
+    fe = inputs.normal_forces(n, 971)
+    assert out[0][2] == "symmetric"
+    V0 = np.frombuffer(out[0][0]).reshape(n, 3)
+    X0 = np.frombuffer(out[0][1]).reshape(n, 3)
+    np.testing.assert_array_equal(np.frombuffer(out[1][0]).reshape(n, 3), V0)
+    np.testing.assert_array_equal(np.frombuffer(out[1][1]).reshape(n, 3), X0)
+    assert rel_err(V0, oracle.mobility_apply(x0, fe, nthreads=8)) <= 1e-5
+    ref = oracle.euler(x0, 4, 0.05, fe, (0.0, 0.0, -1.0), nthreads=8)
+    assert np.linalg.norm(X0 - ref, axis=1).max() <= 1e-5 * np.linalg.norm(ref - x0, axis=1).max()

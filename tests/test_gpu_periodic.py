@@ -73,20 +73,44 @@ def test_periodic_images_are_equivalent():
     assert periodic_rel_err(v2, v1, x, F, (L, L, L), margin=1e-12) <= 1e-13
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32c", 2e-4)])
+def _odd_lattice(m=13, spacing=2.4, jitter=0.1, seed=720):
+    """A jittered simple-cubic lattice filling a periodic cube of m (odd) cells per
+    side.  Every separation component is a whole number of spacings plus at most
+    2 jitter, while half a period is m/2 spacings, a half-integer number: no pair
+    comes within spacing/2 - 2 jitter of a nearest-image tie, at any step of a
+    short trajectory."""
+    g1 = np.arange(m) * spacing
+    x = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3)
+    x = x + np.random.default_rng(seed).uniform(-jitter, jitter, x.shape)
+    return x, m * spacing
+
+
+def _min_tie_distance(x, L):
+    """Smallest distance, over pairs and dimensions, of a separation component's
+    nearest image from half a period."""
+    best = np.inf
+    for i0 in range(0, x.shape[0], 256):
+        d = x[i0:i0 + 256, None, :] - x[None, :, :]
+        img = d - L * np.round(d / L)
+        best = min(best, float(np.abs(np.abs(img) - 0.5 * L).min()))
+    return best
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32c", 2e-6)])
 def test_periodic_steps_match_oracle(prec, tol):
-    """Gravity + soft repulsion in a periodic box, 20 Euler steps (workload-3 physics).
-    FP32C gets a wider gate than unbounded trajectories: every step about one pair
-    sits within FP32 rounding of half a period, where the two nearest images are
-    equally near and the FP32 and FP64 choices may differ (both correct), which
-    moves that pair's term by O(1e-3) of the velocity for one step."""
-    n = 2500
-    x0, L = inputs.cube_rsa(n, 0.10, 720)
-    L = L + 2.5          # the packing is non-overlapping across the faces as well
+    """Gravity + soft repulsion + random forces in a periodic box, 20 Euler steps
+    (workload-3 physics, neighbours at 2.4a inside the repulsion range), at the
+    gates of unbounded trajectories.  The start is a lattice with an odd number of
+    cells per side, so no pair is ever near a nearest-image tie (half a period),
+    where FP32 and FP64 separations may pick different, equally correct images;
+    the oracle trajectory confirms the margin at the first and last step."""
+    x0, L = _odd_lattice()
+    n = x0.shape[0]
     box = (L, L, L)
     g = (0.0, 0.0, -1.0)
     fe = inputs.normal_forces(n, 721)
     ref = oracle.euler(x0, 20, 0.01, fe, g, rep_eps=1.0, rep_rc=2.5, box=box, nthreads=8)
+    assert min(_min_tie_distance(x0, L), _min_tie_distance(ref, L)) > 0.5
     with sd.System(n, prec=prec, gravity=g, rep_eps=1.0, rep_rc=2.5, box=box) as s:
         s.set_positions(x0)
         s.set_forces(fe)
@@ -94,6 +118,31 @@ def test_periodic_steps_match_oracle(prec, tol):
         xT = s.get_positions()
     disp = np.linalg.norm(ref - x0, axis=1).max()
     assert np.linalg.norm(xT - ref, axis=1).max() <= tol * disp
+
+
+def test_periodic_random_packing_steps_tie_aware():
+    """A random packing has a few pairs per step within FP32 rounding of half a
+    period.  Each of 10 FP32C Euler steps is checked on its own: the step's
+    velocities (x_{k+1} - x_k) / dt against the oracle's velocities at x_k, with
+    the forces of x_k, under the tie-aware error of the apply tests."""
+    n = 2500
+    x0, L = inputs.cube_rsa(n, 0.10, 722)
+    L = L + 2.5          # the packing is non-overlapping across the faces as well
+    box = (L, L, L)
+    g = (0.0, 0.0, -1.0)
+    fe = inputs.normal_forces(n, 723)
+    dt = 0.01
+    with sd.System(n, prec="fp32c", gravity=g, rep_eps=1.0, rep_rc=2.5, box=box) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        xk = x0
+        for k in range(10):
+            s.step(dt, 1)
+            x1 = s.get_positions()
+            F = oracle.forces(xk, fe, g, rep_eps=1.0, rep_rc=2.5, box=box)
+            ref = oracle.mobility_apply(xk, F, "rpy", box=box, nthreads=8)
+            assert periodic_rel_err((x1 - xk) / dt, ref, xk, F, box) <= TOL["fp32c"], k
+            xk = x1
 
 
 def test_periodic_lubrication_lattice():

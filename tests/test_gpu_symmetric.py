@@ -12,12 +12,13 @@ from helpers import TOL, periodic_rel_err, rel_err, system_with_overlaps
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", ["fp32c", "fp32"])
+@pytest.mark.parametrize("prec", ["fp32c", "fp32", "fp64"])
 @pytest.mark.parametrize("tensor", ["rpy", "rp", "oseen"])
 @pytest.mark.parametrize("n", [1, 2, 3, 33, 257, 513, 1500, 4133])
 def test_symmetric_matches_oracle(prec, tensor, n):
-    """Forced symmetric kernel; sizes below, at and across the 256-particle blocks
-    (ragged last block, padding), overlapping pairs (RPY branch and clamp)."""
+    """Forced symmetric kernel; sizes below, at and across the blocks (256 particles,
+    128 in FP64; ragged last block, padding), overlapping pairs (RPY branch and
+    clamp)."""
     x, _ = system_with_overlaps(n, 0.05, seed=300 + n, overlaps=5)
     F = inputs.normal_forces(n, seed=400 + n)
     with sd.System(n, tensor=tensor, prec=prec, dense="symmetric") as s:
@@ -81,7 +82,7 @@ def test_symmetric_euler_steps_match_oracle():
     assert np.linalg.norm(xT - ref, axis=1).max() <= 1e-5 * disp
 
 
-def test_auto_choice_and_fp64_rejection():
+def test_auto_choice():
     with sd.System(65536) as s:
         assert s.dense_kernel() == "symmetric"
     with sd.System(1024) as s:
@@ -89,10 +90,60 @@ def test_auto_choice_and_fp64_rejection():
     with sd.System(8192) as s:
         assert s.dense_kernel() == "symmetric"
     with sd.System(65536, prec="fp64") as s:
+        assert s.dense_kernel() == "symmetric"
+    with sd.System(1024, prec="fp64") as s:
         assert s.dense_kernel() == "directed"
-    with pytest.raises(sd.SDError) as ei:
-        sd.System(100, prec="fp64", dense="symmetric")
-    assert ei.value.status_name == "SD_ERR_UNSUPPORTED"
+    with sd.System(100, prec="fp64", dense="symmetric") as s:
+        assert s.dense_kernel() == "symmetric"
+
+
+def test_fp64_symmetric_and_directed_agree_and_repeat():
+    """FP64: each direction's term of the symmetric kernel is bit-identical to the
+    directed kernel's; the sums differ by order only (far below the 1e-12 gate)."""
+    n = 6000
+    x, _ = system_with_overlaps(n, 0.05, seed=81, overlaps=4)
+    F = inputs.normal_forces(n, 82)
+    out = {}
+    for dense in ["directed", "symmetric"]:
+        with sd.System(n, prec="fp64", dense=dense) as s:
+            assert s.dense_kernel() == dense
+            s.set_positions(x)
+            v1 = s.mobility_apply(F)
+            np.testing.assert_array_equal(v1, s.mobility_apply(F))
+            out[dense] = v1
+    assert rel_err(out["symmetric"], out["directed"]) <= 1e-14
+    rows = np.arange(0, n, 17, dtype=np.int32)
+    ref = oracle.mobility_rows(x, F, rows, "rpy", nthreads=8)
+    assert rel_err(out["symmetric"][rows], ref) <= TOL["fp64"]
+
+
+@pytest.mark.parametrize("tensor", ["rpy", "oseen"])
+def test_fp64_symmetric_periodic(tensor):
+    n = 3000
+    x, L = system_with_overlaps(n, 0.05, seed=83, overlaps=4)
+    L = max(L, 10.0)
+    box = (L, L, L)
+    x = x + L * np.random.default_rng(84).integers(-1, 2, x.shape)
+    F = inputs.normal_forces(n, 85)
+    with sd.System(n, prec="fp64", tensor=tensor, box=box, dense="symmetric") as s:
+        s.set_positions(x)
+        v = s.mobility_apply(F)
+    ref = oracle.mobility_apply(x, F, tensor, box=box, nthreads=8)
+    assert periodic_rel_err(v, ref, x, F, box, tensor, margin=1e-12) <= TOL["fp64"]
+
+
+def test_fp64_symmetric_euler_steps_match_oracle():
+    n, steps, dt = 2500, 20, 0.05
+    x0, _ = inputs.cube_rsa(n, 0.10, 92)
+    g = (0.0, 0.0, -1.0)
+    ref = oracle.euler(x0, steps, dt, gravity=g, rep_eps=1.0, rep_rc=2.5, nthreads=8)
+    with sd.System(n, prec="fp64", gravity=g, rep_eps=1.0, rep_rc=2.5) as s:
+        assert s.dense_kernel() == "symmetric"
+        s.set_positions(x0)
+        s.step(dt, steps)
+        xT = s.get_positions()
+    disp = np.linalg.norm(ref - x0, axis=1).max()
+    assert np.linalg.norm(xT - ref, axis=1).max() <= 1e-10 * disp
 
 
 @pytest.mark.parametrize("n", [9000, 33000])   # blocks of 256 x 64 threads, and of 512 x 128 threads

@@ -80,6 +80,28 @@ def test_adjoint_graphs_equal_eager(prec):
         np.testing.assert_array_equal(s.get_positions(), x0)
 
 
+def test_adjoint_graphs_survive_host_apply_reallocation():
+    """The adjoint's cached segment graphs read the handle's staging buffer.  With
+    K = 1 that buffer holds one position array; a host-array mobility apply then
+    needs two and reallocates it, which must drop the graphs: the next adjoint
+    equals the eager one bit for bit."""
+    n = 300
+    x0, target = _adjoint_case(n, inputs.SEED_BASE + 9)
+    F = inputs.normal_forces(n, 10)
+    gxT = 2.0 * (x0 + 0.1 - target)
+    with sd.System(n, prec="fp64", gravity=(0.0, 0.0, -1.0)) as s:
+        s.set_positions(x0)
+        s.profile(True)
+        ref = s.adjoint(0.01, 12, 1, gxT)                  # eager
+        s.profile(False)
+        first = s.adjoint(0.01, 12, 1, gxT)                # captures the K = 1 graphs
+        s.mobility_apply(F)                                # host arrays: staging buffer grows
+        again = s.adjoint(0.01, 12, 1, gxT)
+    for a, b, c in zip(ref, first, again):
+        np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(a, c)
+
+
 def test_adjoint_finite_differences_fp64():
     """Central differences (h = 1e-4) of the GPU FP64 trajectory loss."""
     x0, target = _adjoint_case()
@@ -108,6 +130,40 @@ def test_adjoint_finite_differences_fp64():
             fdF = (loss(x0, fe + e) - loss(x0, fe - e)) / (2 * h)
             assert abs(gx0[i, d] - fdx) <= 1e-6 * max(abs(fdx), np.abs(gx0).max() * 1e-3)
             assert abs(gF[i, d] - fdF) <= 1e-6 * max(abs(fdF), np.abs(gF).max() * 1e-3)
+
+
+def test_adjoint_finite_differences_workload5_n4096():
+    """Workload 5 at its own size: N = 4,096 at volume fraction 0.05, gravity, 1000
+    Euler steps at dt = 0.01, loss sum |x(T) - x*|^2, checkpoints every 50 steps.
+    The FP64 adjoint against central differences (h = 1e-4) of the GPU FP64
+    trajectory on three seeded components of x0 and of F, gate 1e-6."""
+    w = inputs.config_inputs(5)
+    x0, target = w["x"], w["target"]
+    n = x0.shape[0]
+    nsteps, dt, K, h = 1000, 0.01, 50, 1e-4
+    fe = np.zeros_like(x0)
+    with sd.System(n, prec="fp64", gravity=(0.0, 0.0, -1.0)) as s:
+        def loss(x, f):
+            s.set_positions(x)
+            s.set_forces(f)
+            s.step(dt, nsteps)
+            return float(((s.get_positions() - target) ** 2).sum())
+
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(dt, nsteps)
+        xT = s.get_positions()
+        s.set_positions(x0)
+        gx0, gF = s.adjoint(dt, nsteps, K, 2.0 * (xT - target))
+        rng = np.random.default_rng(inputs.SEED_BASE + 56)
+        for comp in rng.choice(3 * n, 3, replace=False):
+            i, d = divmod(int(comp), 3)
+            e = np.zeros_like(x0)
+            e[i, d] = h
+            fdx = (loss(x0 + e, fe) - loss(x0 - e, fe)) / (2 * h)
+            fdF = (loss(x0, fe + e) - loss(x0, fe - e)) / (2 * h)
+            assert abs(gx0[i, d] - fdx) <= 1e-6 * max(abs(fdx), np.abs(gx0).max() * 1e-3), (i, d, gx0[i, d], fdx)
+            assert abs(gF[i, d] - fdF) <= 1e-6 * max(abs(fdF), np.abs(gF).max() * 1e-3), (i, d, gF[i, d], fdF)
 
 
 def test_adjoint_rejects_repulsion():

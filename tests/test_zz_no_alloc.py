@@ -56,3 +56,26 @@ def test_noalloc_rejects_oversized_systems():
         sd.sd_mobility_apply_noalloc(0, 0, 0, 65537)
     assert ei.value.status_name == "SD_ERR_ARG"
     assert "65536" in sd.sd_last_error()
+
+
+def test_noalloc_at_its_size_limit():
+    # n = 65,536 fills the scratch stride and all eight splits; separations taken
+    # relative to particle 0 are least accurate here (cube side 176a)
+    x, _ = inputs.cube_rsa(65536, 0.05, seed=311)
+    F = inputs.normal_forces(65536, 312)
+    v = _noalloc(x, F, "rpy")
+    assert np.all(np.isfinite(v))
+    assert rel_err(v, _handle_apply(x, F, "rpy")) <= TOL["fp32c"]
+    rows = np.sort(np.random.default_rng(313).choice(65536, 192, replace=False))
+    ref = oracle.mobility_rows(x, F, rows, "rpy")
+    assert rel_err(v[rows], ref) <= TOL["fp32c"]
+
+
+def test_noalloc_coincident_spheres_rpy():
+    # two distinct spheres at the same point: the RPY overlap form gives T(0) = mu0 I
+    x, _ = inputs.cube_rsa(300, 0.05, seed=321)
+    x[7] = x[3]
+    x[11] = x[10] + np.array([0.3, 0.0, 0.0])
+    F = inputs.normal_forces(300, 322)
+    v = _noalloc(x, F, "rpy")
+    assert rel_err(v, oracle.mobility_apply(x, F, "rpy")) <= TOL["fp32c"]
