@@ -52,7 +52,8 @@ typedef enum {
     SD_ERR_NONFINITE = 5,    /* NaN or Inf in positions or forces                                */
     SD_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up (results of that call invalid) */
     SD_ERR_STATE = 7,        /* call out of order (e.g. step before positions were set)          */
-    SD_ERR_UNSUPPORTED = 8   /* valid request this build does not implement                      */
+    SD_ERR_UNSUPPORTED = 8,  /* valid request this build does not implement                      */
+    SD_ERR_INTERNAL = 9      /* a device-side index check failed (debug builds, -DSD_DEBUG)      */
 } sd_status;
 
 /* Pair tensor.  RPY = Rotne-Prager for r >= 2a continued inside r < 2a by the

@@ -9,7 +9,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsd_gb300.so")
+# SD_LIBRARY selects another build of the library, e.g. the debug build
+# libsd_gb300_debug.so (device-side index checks) that the tests load in a subprocess.
+LIB_PATH = os.environ.get("SD_LIBRARY") or os.path.join(HERE, "libsd_gb300.so")
 
 c_int32, c_int64, c_double, c_void_p, c_char_p = (ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
                                                   ctypes.c_void_p, ctypes.c_char_p)
@@ -19,9 +21,9 @@ FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_void_p)
 
 # sd_status
 SD_OK, SD_ERR_ARG, SD_ERR_CUDA, SD_ERR_OOM, SD_ERR_COINCIDENT, SD_ERR_NONFINITE, SD_ERR_TIMEOUT, \
-    SD_ERR_STATE, SD_ERR_UNSUPPORTED = range(9)
+    SD_ERR_STATE, SD_ERR_UNSUPPORTED, SD_ERR_INTERNAL = range(10)
 STATUS_NAMES = ["SD_OK", "SD_ERR_ARG", "SD_ERR_CUDA", "SD_ERR_OOM", "SD_ERR_COINCIDENT", "SD_ERR_NONFINITE",
-                "SD_ERR_TIMEOUT", "SD_ERR_STATE", "SD_ERR_UNSUPPORTED"]
+                "SD_ERR_TIMEOUT", "SD_ERR_STATE", "SD_ERR_UNSUPPORTED", "SD_ERR_INTERNAL"]
 SD_TENSOR_RPY, SD_TENSOR_RP, SD_TENSOR_OSEEN = 0, 1, 2
 SD_PREC_FP32C, SD_PREC_FP64, SD_PREC_FP32 = 0, 1, 2
 SD_DTYPE_F32, SD_DTYPE_F64 = 0, 1

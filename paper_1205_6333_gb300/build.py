@@ -3,6 +3,11 @@
 Every translation unit under csrc/ is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a`` and linked into one shared object
 that exports the C ABI of include/sd.h.  Rebuilds only what changed.
+
+``build(debug=True)`` makes libsd_gb300_debug.so from the same sources with
+-DSD_DEBUG: the kernels then check their data-dependent indices (cell list,
+near-pair list, partial-sum slots, batched staging) and report a violation as
+SD_ERR_INTERNAL instead of touching memory outside a buffer.
 """
 from __future__ import annotations
 
@@ -17,6 +22,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsd_gb300.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libsd_gb300_debug.so")
 SOURCES = ["api.cu", "dense.cu", "cells.cu", "epilogue.cu", "vjp.cu", "batched.cu", "noalloc.cu", "access.cu"]
 HEADERS = ["sd_internal.h", "pair.cuh", "ptx.cuh", "neighbours.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,8 +42,10 @@ def _newest(paths):
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    flags = FLAGS + (["-DSD_DEBUG"] if debug else [])
+    os.makedirs(build_dir, exist_ok=True)
     hdr = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "sd.h")]
     hdr_time = _newest(hdr)
     cc = nvcc()
@@ -44,10 +53,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr_time):
-            jobs.append([cc] + FLAGS + ["-c", s, "-o", o])
+            jobs.append([cc] + flags + ["-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -60,12 +69,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < _newest(objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or jobs or not os.path.exists(lib) or os.path.getmtime(lib) < _newest(objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-ldl", "-lrt", "-lpthread"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False, verbose: bool = False):
+    """The release and the debug library, their translation units compiled together."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        futs = [ex.submit(build, force, verbose, dbg) for dbg in (False, True)]
+        return [f.result() for f in futs]
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

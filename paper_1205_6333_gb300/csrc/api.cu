@@ -110,6 +110,7 @@ static sd_status status_from_bits(int bits) {
     if (bits & DEV_ERR_COINCIDENT)
         return set_error(SD_ERR_COINCIDENT, "two distinct particles at zero separation (RP/Oseen tensor undefined)");
     if (bits & DEV_ERR_NONFINITE) return set_error(SD_ERR_NONFINITE, "non-finite value in positions or forces");
+    if (bits & DEV_ERR_BOUNDS) return set_error(SD_ERR_INTERNAL, "a device-side index check failed");
     return SD_OK;
 }
 
@@ -441,6 +442,8 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
         c.nc[d] = pc.Ld[d] > 0.0 ? static_cast<int>(std::floor(pc.Ld[d] / c.h)) : 0;   // >= 3, checked above
     }
     c.box.periodic = pc.periodic;
+    c.n = h->n;
+    c.err = h->d_err;
     int H = 1024;
     while (H < 2 * h->n) H <<= 1;
     c.H = H;
@@ -531,6 +534,7 @@ static bool any_nonfinite(const double *v, size_t k) {
 }
 
 sd_status sd_set_positions(sd_handle *h, const double *xyz, int on_device) {
+    NvtxRange nvtx_range("sd_set_positions");
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (!xyz && h->n > 0) return set_error(SD_ERR_ARG, "positions pointer is NULL");
     if (!valid_kind(on_device)) return set_error(SD_ERR_ARG, "on_device must be 0, 1 or 2");
@@ -551,6 +555,7 @@ sd_status sd_set_positions(sd_handle *h, const double *xyz, int on_device) {
 }
 
 sd_status sd_get_positions(sd_handle *h, double *xyz, int on_device) {
+    NvtxRange nvtx_range("sd_get_positions");
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (!xyz && h->n > 0) return set_error(SD_ERR_ARG, "positions pointer is NULL");
     if (!valid_kind(on_device)) return set_error(SD_ERR_ARG, "on_device must be 0, 1 or 2");
@@ -655,15 +660,18 @@ static sd_status apply_rows(sd_handle *h, const void *F, void *V, int dtype, int
 }
 
 sd_status sd_mobility_apply(sd_handle *h, const void *F, void *V, int dtype, int on_device) {
+    NvtxRange nvtx_range("sd_mobility_apply");
     return apply_rows(h, F, V, dtype, on_device, 0, h ? h->n : 0);
 }
 
 sd_status sd_mobility_apply_rows(sd_handle *h, const void *F, void *V, int dtype, int on_device, int32_t row0,
                                  int32_t row1) {
+    NvtxRange nvtx_range("sd_mobility_apply_rows");
     return apply_rows(h, F, V, dtype, on_device, row0, row1);
 }
 
 sd_status sd_step_rows(sd_handle *h, double dt, int32_t row0, int32_t row1) {
+    NvtxRange nvtx_range("sd_step_rows");
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (!std::isfinite(dt)) return set_error(SD_ERR_ARG, "dt must be finite");
     if (row0 < 0 || row1 < row0 || row1 > h->n) return set_error(SD_ERR_ARG, "rows must satisfy 0 <= row0 <= row1 <= n");
@@ -746,6 +754,7 @@ extern "C" {
 
 sd_status sd_mobility_apply_part(sd_handle *h, const void *F, int dtype, int on_device, int32_t shard,
                                  int32_t nshards, double *P) {
+    NvtxRange nvtx_range("sd_mobility_apply_part");
     sd_status s = check_shard(h, shard, nshards, P);
     if (s != SD_OK) return s;
     if (dtype != SD_DTYPE_F32 && dtype != SD_DTYPE_F64) return set_error(SD_ERR_ARG, "dtype must be F32 or F64");
@@ -776,6 +785,7 @@ sd_status sd_mobility_apply_part(sd_handle *h, const void *F, int dtype, int on_
 
 sd_status sd_mobility_apply_combine(sd_handle *h, const double *Pall, int32_t nparts, void *V, int dtype,
                                     int on_device) {
+    NvtxRange nvtx_range("sd_mobility_apply_combine");
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (dtype != SD_DTYPE_F32 && dtype != SD_DTYPE_F64) return set_error(SD_ERR_ARG, "dtype must be F32 or F64");
     if (on_device != 0 && on_device != 1) return set_error(SD_ERR_ARG, "on_device must be 0 or 1");
@@ -807,6 +817,7 @@ sd_status sd_mobility_apply_combine(sd_handle *h, const double *Pall, int32_t np
 }
 
 sd_status sd_step_part(sd_handle *h, int32_t shard, int32_t nshards, double *P) {
+    NvtxRange nvtx_range("sd_step_part");
     sd_status s = check_shard(h, shard, nshards, P);
     if (s != SD_OK) return s;
     h->part_kind = PART_NONE;
@@ -828,6 +839,7 @@ sd_status sd_step_part(sd_handle *h, int32_t shard, int32_t nshards, double *P) 
 }
 
 sd_status sd_step_combine(sd_handle *h, double dt, const double *Pall, int32_t nparts) {
+    NvtxRange nvtx_range("sd_step_combine");
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (!std::isfinite(dt)) return set_error(SD_ERR_ARG, "dt must be finite");
     if (nparts < 1 || (h->n > 0 && !Pall)) return set_error(SD_ERR_ARG, "Pall or nparts");
@@ -849,6 +861,7 @@ sd_status sd_step_combine(sd_handle *h, double dt, const double *Pall, int32_t n
 }
 
 sd_status sd_step(sd_handle *h, double dt, int64_t nsteps) {
+    NvtxRange nvtx_range("sd_step");
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (nsteps < 0 || !std::isfinite(dt)) return set_error(SD_ERR_ARG, "nsteps must be >= 0 and dt finite");
     if (!h->pos_set) return set_error(SD_ERR_STATE, "positions were never set");
@@ -858,6 +871,7 @@ sd_status sd_step(sd_handle *h, double dt, int64_t nsteps) {
 }
 
 sd_status sd_mobility_vjp(sd_handle *h, const void *F, const void *W, void *gX, void *gF, int dtype, int on_device) {
+    NvtxRange nvtx_range("sd_mobility_vjp");
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (dtype != SD_DTYPE_F32 && dtype != SD_DTYPE_F64) return set_error(SD_ERR_ARG, "dtype must be F32 or F64");
     if (h->n > 0 && (!F || !W || (!gX && !gF))) return set_error(SD_ERR_ARG, "null argument");
@@ -903,6 +917,7 @@ sd_status sd_mobility_vjp(sd_handle *h, const void *F, const void *W, void *gX, 
 
 sd_status sd_adjoint(sd_handle *h, double dt, int64_t nsteps, int32_t ckpt_every, const double *gxT, double *gx0,
                      double *gF, int on_device) {
+    NvtxRange nvtx_range("sd_adjoint");
     if (!h) return set_error(SD_ERR_ARG, "handle is NULL");
     if (nsteps < 0 || ckpt_every < 1 || !std::isfinite(dt)) return set_error(SD_ERR_ARG, "nsteps, ckpt_every or dt");
     if (h->n > 0 && (!gxT || !gx0 || !gF)) return set_error(SD_ERR_ARG, "null argument");

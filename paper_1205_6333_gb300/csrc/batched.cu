@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(BT, R == 2 ? SD_BATCH_R2_MINB * 128 / BT : 0) 
         slot(m1 - 1, ql, pl);
         if (pl) ++ql;
         const int s0 = a.cbeg[a.qcl[qf]], s1 = a.cend[a.qcl[ql]];   // s1 - s0 <= R BT + kStageExtra
+        if (s1 > s0 && tid == 0) dbg_index(s1 - s0 - 1, L, a.err);
         for (int k = s0 + tid; k < s1; k += BT) {
             const int p = a.qperm[k];
             const float4 r = a.rel[p], f = frcm[p];
@@ -643,6 +644,7 @@ static sd_status batch_sync_check(sd_batch *b) {
     if (bits & (DEV_ERR_TIMEOUT | DEV_ERR_QUEUE)) return set_error(SD_ERR_TIMEOUT, "batched kernel gave up");
     if (bits & DEV_ERR_COINCIDENT) return set_error(SD_ERR_COINCIDENT, "two distinct particles at zero separation");
     if (bits & DEV_ERR_NONFINITE) return set_error(SD_ERR_NONFINITE, "non-finite value in positions or forces");
+    if (bits & DEV_ERR_BOUNDS) return set_error(SD_ERR_INTERNAL, "a device-side index check failed");
     return SD_OK;
 }
 
@@ -1053,6 +1055,7 @@ sd_status sd_batch_set_shape(sd_batch *b, int32_t k) {
 }
 
 sd_status sd_step_batched(sd_batch *b, double dt, int64_t nsteps) {
+    NvtxRange nvtx_range("sd_step_batched");
     if (!b) return set_error(SD_ERR_ARG, "batch is NULL");
     if (nsteps < 0 || !std::isfinite(dt)) return set_error(SD_ERR_ARG, "nsteps must be >= 0 and dt finite");
     if (!b->pos_set) return set_error(SD_ERR_STATE, "positions were never set");

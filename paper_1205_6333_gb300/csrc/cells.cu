@@ -255,11 +255,11 @@ __global__ void scan_add_kernel(int *__restrict__ start, const int *__restrict__
 }
 
 __global__ void cells_scatter_kernel(const uint32_t *__restrict__ key, int n, const int *__restrict__ start,
-                                     int *__restrict__ fill, int *__restrict__ sorted) {
+                                     int *__restrict__ fill, int *__restrict__ sorted, int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t k = key[i];
-    sorted[start[k] + atomicAdd(&fill[k], 1)] = i;
+    sorted[dbg_index(start[k] + atomicAdd(&fill[k], 1), n, err)] = i;
 }
 
 // Sort each bucket by particle index (buckets hold ~1 particle; a bucket larger
@@ -300,7 +300,7 @@ cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64,
     scan_blocks_kernel<<<c.nblk, kScanThreads, 0, st>>>(c.cnt, c.start, c.bsum, c.H);
     scan_top_kernel<<<1, kScanThreads, 0, st>>>(c.bsum, c.nblk, c.start, c.H);
     scan_add_kernel<<<(c.H + 255) / 256, 256, 0, st>>>(c.start, c.bsum, c.H);
-    cells_scatter_kernel<<<nb, 256, 0, st>>>(c.key, h->n, c.start, c.fill, c.sorted);
+    cells_scatter_kernel<<<nb, 256, 0, st>>>(c.key, h->n, c.start, c.fill, c.sorted, h->d_err);
     cells_sort_kernel<<<(c.H + 255) / 256, 256, 0, st>>>(c.start, c.sorted, c.H);
     prof_end(h, SD_KERNEL_CELLS, st);
     h->launches += 6;

@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(128) near_collect_kernel(NearArgs a) {
 #pragma unroll
             for (int k = 0; k < kNearRegs; ++k)
                 if (k < cnt) a.ent[first + k] = make_int2(i, js[k]);
+            for (int k = 0; k < kNearRegs && k < cnt; ++k) dbg_index(first + k, a.cap, a.err);
             if (cnt > kNearRegs) {   // rare: walk again for the candidates beyond the registers
                 const V4 pi = pm[i];
                 int k = 0;
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(128) near_pair_kernel(NearArgs a) {
         const int2 p = a.ent[e];
         double c6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (p.x >= 0) {
-            const int i = p.x, j = p.y;
+            const int i = static_cast<int>(dbg_index(p.x, a.n, a.err)), j = static_cast<int>(dbg_index(p.y, a.n, a.err));
             double dx = a.x64[3 * i] - a.x64[3 * j], dy = a.x64[3 * i + 1] - a.x64[3 * j + 1],
                    dz = a.x64[3 * i + 2] - a.x64[3 * j + 2];
             box_image(a.cl.box, dx, dy, dz);
@@ -372,6 +373,7 @@ struct EpiArgs {
     double *x64n;
     double *vlag;   // OUT_EULER with lubrication: this step's FP64 velocities, for the next step's forces
     int *err;
+    int cap;        // capacity of the near-pass list
     int row0, row1; // rows written (a shard); vout holds rows row0 .. row1-1
     EpiShard sh;    // a tile shard's share, or the shards' results to combine
 };
@@ -431,6 +433,8 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
             const int first = geom_first(a.g, ib);
             const int s0 = max(0, a.sh.b0 - first);
             const int ns = min(geom_last(a.g, ib) - first + 1, a.sh.b1 - first);
+            if (ns > 0) dbg_index(ns - 1, a.g.maxSlots, a.err);
+            if (a.g.sym && ib > 0) dbg_index(geom_rowstart(a.g, ib - 1) + 1, a.g.nT, a.err);
             int r0 = 0, nc = a.g.sym ? ib : 0;
             if (a.g.sym && (a.sh.tlo > 0 || a.sh.thi < a.g.nT)) {
                 r0 = first_row_at(a.g, ib, a.sh.tlo);
@@ -515,7 +519,8 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
             const double *c = a.near + 6 * static_cast<size_t>(i) + var;
             for (int d = 0; d < 3; ++d) V[d] += c[d];
         } else {
-            const double *c = a.ent_out + 6 * static_cast<size_t>(a.noff[i]) + var;
+            const long long e0 = dbg_index(a.noff[i], static_cast<long long>(a.cap) - cnt + 1, a.err);
+            const double *c = a.ent_out + 6 * static_cast<size_t>(e0) + var;
             for (int k = 0; k < cnt; ++k, c += 6)
                 for (int d = 0; d < 3; ++d) V[d] += c[d];
         }
@@ -595,6 +600,7 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
     a.x64n = x64n;
     a.vlag = (out == OUT_EULER && h->lub) ? h->vlag : nullptr;
     a.err = h->d_err;
+    a.cap = h->near_cap;
     a.row0 = row0;
     a.row1 = row1;
     if (shard) a.sh = *shard;

@@ -22,7 +22,7 @@ __device__ __forceinline__ void for_each_neighbour(const CellList &c, int i, int
                 const uint32_t b = cell_hash(cx, cy, cz, c.H);
                 const int s1 = c.start[b + 1];
                 for (int s = c.start[b]; s < s1; ++s) {
-                    const int j = c.sorted[s];
+                    const int j = static_cast<int>(dbg_index(c.sorted[dbg_index(s, c.n, c.err)], c.n, c.err));
                     if (j == i) continue;
                     const int4 cj = c.cell[j];
                     if (cj.x != cx || cj.y != cy || cj.z != cz) continue;  // another cell in the same bucket
@@ -42,7 +42,7 @@ __device__ __forceinline__ void for_each_neighbour_part(const CellList &c, int i
         const uint32_t b = cell_hash(cx, cy, cz, c.H);
         const int s1 = c.start[b + 1];
         for (int s = c.start[b]; s < s1; ++s) {
-            const int j = c.sorted[s];
+            const int j = static_cast<int>(dbg_index(c.sorted[dbg_index(s, c.n, c.err)], c.n, c.err));
             if (j == i) continue;
             const int4 cj = c.cell[j];
             if (cj.x != cx || cj.y != cy || cj.z != cz) continue;

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sd.h"
 #include "pair.cuh"
 
@@ -16,7 +18,27 @@ enum : int {
     DEV_ERR_COINCIDENT = 2,
     DEV_ERR_TIMEOUT = 4,
     DEV_ERR_QUEUE = 8,
+    DEV_ERR_BOUNDS = 16,   // a device-side index check failed (SD_DEBUG builds)
 };
+
+// Debug builds (-DSD_DEBUG) check the data-dependent indices of the kernels (cell
+// list, near-pair list, partial-sum slots, batched staging) against the buffers they
+// address: an index outside [0, bound) sets DEV_ERR_BOUNDS (reported as
+// SD_ERR_INTERNAL) and is replaced by 0, so the access stays inside the buffer and no
+// thread leaves a warp-collective section early.  Release builds compile the check
+// away.
+__device__ __forceinline__ long long dbg_index(long long idx, long long bound, int *err) {
+#ifdef SD_DEBUG
+    if (idx < 0 || idx >= bound) {
+        if (err) atomicOr(err, DEV_ERR_BOUNDS);
+        return 0;
+    }
+#else
+    (void)bound;
+    (void)err;
+#endif
+    return idx;
+}
 
 enum { MODE_FP32C = 0, MODE_FP64 = 1, MODE_FP32 = 2 };
 // Epilogue outputs: velocities (FP32 / FP64), the Euler update, or (OUT_PART) a
@@ -126,6 +148,8 @@ struct CellList {
     int *start = nullptr;  // [H+1]
     int *bsum = nullptr;   // [nblk]
     int *sorted = nullptr; // [n]
+    int n = 0;             // particles binned
+    int *err = nullptr;    // device error word (debug index checks)
 };
 
 __device__ __forceinline__ uint32_t cell_hash(int cx, int cy, int cz, int H) {
@@ -237,6 +261,14 @@ struct sd_handle {
 };
 
 namespace sd {
+
+// An NVTX range around an entry point (visible to Nsight tools; a no-op without one).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // errors
 sd_status set_error(sd_status st, const std::string &msg);
