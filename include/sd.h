@@ -239,8 +239,10 @@ sd_status sd_step_batched(sd_batch *b, double dt, int64_t nsteps);
 sd_status sd_batch_autotune(sd_batch *b, int32_t *choice);
 /* The candidate launch shapes, fixed at sd_batch_create: their number, and for shape
  * k in [0, count) the threads per CTA, the resident CTAs per SM and the targets per
- * thread (FP32C: 1 or 2; FP64: 1).  Any output pointer may be NULL.  SD_ERR_ARG for
- * a NULL batch or k out of range. */
+ * thread (FP32C: 1 or 2 for the block kernel, which evaluates every ordered pair; 0
+ * for the symmetric kernel, in which each warp takes two clusters and evaluates each
+ * unordered pair once, mu_ij = mu_ji; FP64: 1).  Any output pointer may be NULL.
+ * SD_ERR_ARG for a NULL batch or k out of range. */
 int32_t sd_batch_shape_count(const sd_batch *b);
 sd_status sd_batch_shape_info(const sd_batch *b, int32_t k, int32_t *threads, int32_t *ctas_per_sm,
                               int32_t *targets_per_thread);

@@ -37,7 +37,7 @@ constexpr int kMaxCluster = 256;
 struct BatchShape {
     int warps;        // warps per CTA
     int ctas_per_sm;  // resident CTAs per SM requested
-    int r = 1;        // FP32C: targets per thread (1 or 2)
+    int r = 1;        // FP32C block kernel: targets per thread (1 or 2); 0: the symmetric kernel
 };
 
 }  // namespace sd
@@ -54,6 +54,8 @@ struct sd_batch {
     int32_t *qperm = nullptr, *qcl = nullptr, *cbeg = nullptr, *cend = nullptr, *canchor = nullptr;
     int32_t *tq = nullptr;   // slots of two targets (see batched_blocks_kernel)
     int M2 = 0;              // number of such slots
+    int4 *stask = nullptr;   // symmetric kernel: (cluster, cluster, 32-blocks) per warp task
+    int nstask = 0;
     double *x64[2] = {nullptr, nullptr};   // position ping-pong: step reads x64[cur], writes the other
     float4 *rel[2] = {nullptr, nullptr};   // FP32C: positions relative to the cluster's reference point
     int32_t *panchor = nullptr;            // first particle of each particle's cluster
@@ -90,6 +92,7 @@ struct BatchArgs {
     const int32_t *off, *order;
     const int32_t *qperm, *qcl, *cbeg, *cend, *canchor;
     const int32_t *tq;   // two-target slots: q (targets q, q + 1) or ~q (q alone)
+    const int4 *stask;   // symmetric kernel's tasks
     int P, M2, nblk;
     const double *x64;   // positions of this step
     double *x64n;        // positions after it
@@ -555,10 +558,328 @@ __global__ void __launch_bounds__(BT, R == 2 ? SD_BATCH_R2_MINB * 128 / BT : 0) 
     }
 }
 
+// ---------------------------------------------------------------- FP32C, symmetric
+
+// The symmetric batched kernel: each unordered pair of a cluster once, its term
+// used for both particles (mu_ij = mu_ji, Sec. 2.2), as dense_sym_kernel does for
+// one large system.
+//   * A warp takes a task from the ticket counter: two clusters of the largest-first
+//     order (equal or nearly equal sizes), cut into the same number nb of 32-particle
+//     blocks.  The two clusters ride the two halves of every packed f32x2 register,
+//     so each packed instruction evaluates one pair of each cluster.  The warp stages
+//     both clusters in its shared memory, interleaved (slot k holds particle k of
+//     each), with padding slots far apart and far away, with zero force.
+//   * Block pairs (p, q), p <= q: lane l holds target 32 p + l; at step m it takes
+//     source 32 q + ((l + m) mod 32), and the source's running sum moves one lane down
+//     per step by shuffle (after 32 steps lane l holds source l again).  A diagonal
+//     block (p = q) takes the steps m = 1 .. 16 only (lanes l < 16 at m = 16): every
+//     pair of the block once, no self pair.
+//   * Sums: a tile's FP32 partials; the target's are folded into a TwoSum (hi, lo)
+//     per block row, the sources' added to a per-particle shared sum.  Block p is
+//     complete after its row (every tile that reaches it has run) and is finalised
+//     at once: + F_i (the self term mu_ii = mu0 I), v = mu0 V, x <- x + dt v in FP64.
+//   * r^2 is clamped to (2a)^2; the smallest unclamped r^2 of each tile is tracked,
+//     and a tile that met a pair with r < 2a is walked again: each such pair's
+//     clamped terms (bit-identical, recomputed) are replaced by the exact ones, in
+//     both directions.
+constexpr int kSymSlots = kMaxCluster;                 // particles per cluster half (8 blocks of 32)
+constexpr size_t kSymWarpSmem = 9 * static_cast<size_t>(kSymSlots) * sizeof(f2);   // 6 staged + 3 sum arrays
+
+// One pair of each half, both directions, with the unclamped r^2 of each half
+// tracked (the order of operations of pair_sym_f32x2 with CLAMP).
+template <int TENSOR>
+__device__ __forceinline__ void bsym_pair(f2 XI, f2 YI, f2 ZI, f2 GX, f2 GY, f2 GZ, f2 PX, f2 PY, f2 PZ, f2 FX,
+                                          f2 FY, f2 FZ, const PairConst2 &c, f2 &AX, f2 &AY, f2 &AZ, f2 &JX,
+                                          f2 &JY, f2 &JZ, float &mn0, float &mn1) {
+    const f2 dx = sub2(XI, PX), dy = sub2(YI, PY), dz = sub2(ZI, PZ);
+    const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    float ra, rb;
+    upk2(r2, ra, rb);
+    mn0 = fminf(mn0, ra);
+    mn1 = fminf(mn1, rb);
+    ra = fmaxf(ra, c.r2min);
+    rb = fmaxf(rb, c.r2min);
+    const f2 ri = pk2(rsqrt_sfu(ra), rsqrt_sfu(rb));
+    const f2 ri2 = mul2(ri, ri);
+    f2 A, B;
+    if (TENSOR == T_OSEEN) {
+        A = mul2(c.c1, ri);
+        B = mul2(A, ri2);
+    } else {
+        A = mul2(ri, fma2(c.c3, ri2, c.c1));
+        const f2 ri3 = mul2(ri, ri2);
+        B = mul2(ri3, fma2(c.m3c3, ri2, c.c1));
+    }
+    const f2 s = mul2(B, fma2(dz, FZ, fma2(dy, FY, mul2(dx, FX))));
+    AX = fma2(s, dx, fma2(A, FX, AX));
+    AY = fma2(s, dy, fma2(A, FY, AY));
+    AZ = fma2(s, dz, fma2(A, FZ, AZ));
+    const f2 u = mul2(B, fma2(dz, GZ, fma2(dy, GY, mul2(dx, GX))));
+    JX = fma2(u, dx, fma2(A, GX, JX));
+    JY = fma2(u, dy, fma2(A, GY, JY));
+    JZ = fma2(u, dz, fma2(A, GZ, JZ));
+}
+
+__device__ __forceinline__ float half_of(f2 v, int h) {
+    float lo, hi;
+    upk2(v, lo, hi);
+    return h ? hi : lo;
+}
+__device__ __forceinline__ f2 add_half(f2 v, int h, float d) {
+    float lo, hi;
+    upk2(v, lo, hi);
+    if (h) hi = __fadd_rn(hi, d);
+    else lo = __fadd_rn(lo, d);
+    return pk2(lo, hi);
+}
+
+// Tile (p, q) of the warp's task: lane l holds target 32 p + l (XI..GZ); adds the
+// tile's target partials to AX..AZ and its source sums to the shared sums.
+template <int TENSOR, bool DIAG>
+__device__ __forceinline__ void bsym_tile(const f2 *__restrict__ S, f2 *__restrict__ SUM, int q, int lane, f2 XI,
+                                          f2 YI, f2 ZI, f2 GX, f2 GY, f2 GZ, const PairConst2 &c, f2 &AX, f2 &AY,
+                                          f2 &AZ, float &mn0, float &mn1) {
+    const f2 *SX = S + 32 * q, *SY = SX + kSymSlots, *SZ = SY + kSymSlots, *SFX = SZ + kSymSlots,
+             *SFY = SFX + kSymSlots, *SFZ = SFY + kSymSlots;
+    const int nxt = (lane + 1) & 31;
+    f2 JX = 0ull, JY = 0ull, JZ = 0ull;
+    constexpr int M0 = DIAG ? 1 : 0, M1 = DIAG ? 15 : 31;
+#pragma unroll 4
+    for (int m = M0; m <= M1; ++m) {
+        const int k = (lane + m) & 31;
+        bsym_pair<TENSOR>(XI, YI, ZI, GX, GY, GZ, SX[k], SY[k], SZ[k], SFX[k], SFY[k], SFZ[k], c, AX, AY, AZ, JX, JY,
+                          JZ, mn0, mn1);
+        JX = __shfl_sync(0xffffffffu, JX, nxt);
+        JY = __shfl_sync(0xffffffffu, JY, nxt);
+        JZ = __shfl_sync(0xffffffffu, JZ, nxt);
+    }
+    int sj = (lane + M1 + 1) & 31;   // the source whose sum this lane holds
+    if (DIAG) {   // m = 16: the pair (l, l + 16) once, by the lanes l < 16
+        const int k = (lane + 16) & 31;
+        if (lane < 16)
+            bsym_pair<TENSOR>(XI, YI, ZI, GX, GY, GZ, SX[k], SY[k], SZ[k], SFX[k], SFY[k], SFZ[k], c, AX, AY, AZ, JX,
+                              JY, JZ, mn0, mn1);
+        sj = k;
+    }
+    f2 *D = SUM + 32 * q + sj;
+    D[0] = add2(D[0], JX);
+    D[kSymSlots] = add2(D[kSymSlots], JY);
+    D[2 * kSymSlots] = add2(D[2 * kSymSlots], JZ);
+    __syncwarp();
+}
+
+// Tiles (p, q) and (p + 1, q), q > p + 1, in one walk of source block q: lane l holds
+// targets 32 p + l (T0) and 32 (p + 1) + l (T1); each source's running sum collects
+// both targets' terms before it moves on, and every source load serves both.
+template <int TENSOR>
+__device__ __forceinline__ void bsym_tile2(const f2 *__restrict__ S, f2 *__restrict__ SUM, int q, int lane,
+                                           const f2 (&T0)[6], const f2 (&T1)[6], const PairConst2 &c, f2 (&A0)[3],
+                                           f2 (&A1)[3], float &mn0, float &mn1) {
+    const f2 *SX = S + 32 * q, *SY = SX + kSymSlots, *SZ = SY + kSymSlots, *SFX = SZ + kSymSlots,
+             *SFY = SFX + kSymSlots, *SFZ = SFY + kSymSlots;
+    const int nxt = (lane + 1) & 31;
+    f2 JX = 0ull, JY = 0ull, JZ = 0ull;
+#pragma unroll 2
+    for (int m = 0; m < 32; ++m) {
+        const int k = (lane + m) & 31;
+        const f2 PX = SX[k], PY = SY[k], PZ = SZ[k], FX = SFX[k], FY = SFY[k], FZ = SFZ[k];
+        bsym_pair<TENSOR>(T0[0], T0[1], T0[2], T0[3], T0[4], T0[5], PX, PY, PZ, FX, FY, FZ, c, A0[0], A0[1], A0[2], JX,
+                          JY, JZ, mn0, mn1);
+        bsym_pair<TENSOR>(T1[0], T1[1], T1[2], T1[3], T1[4], T1[5], PX, PY, PZ, FX, FY, FZ, c, A1[0], A1[1], A1[2], JX,
+                          JY, JZ, mn0, mn1);
+        JX = __shfl_sync(0xffffffffu, JX, nxt);
+        JY = __shfl_sync(0xffffffffu, JY, nxt);
+        JZ = __shfl_sync(0xffffffffu, JZ, nxt);
+    }
+    f2 *D = SUM + 32 * q + lane;
+    D[0] = add2(D[0], JX);
+    D[kSymSlots] = add2(D[kSymSlots], JY);
+    D[2 * kSymSlots] = add2(D[2 * kSymSlots], JZ);
+    __syncwarp();
+}
+
+// Second walk of a tile that met a pair closer than 2a: such pairs' clamped terms
+// are replaced by the exact ones (Yamakawa form for RPY), in both directions.  The
+// target side goes to FIX (this lane's target), the source side to the shared sums
+// (distinct sources per step; steps ordered by __syncwarp).
+template <int TENSOR, bool DIAG>
+__device__ void bsym_fix(const f2 *__restrict__ S, f2 *__restrict__ SUM, int p, int q, int lane, const int (&nh)[2],
+                         const PairConst &pc, float (&FIX)[2][3], bool &coincident) {
+    constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
+    constexpr int M0 = DIAG ? 1 : 0, M1 = DIAG ? 16 : 31;
+    const int i = 32 * p + lane;
+    for (int m = M0; m <= M1; ++m) {
+        const int j = 32 * q + ((lane + m) & 31);
+        if (!(DIAG && m == 16 && lane >= 16)) {
+            for (int h = 0; h < 2; ++h) {
+                if (i >= nh[h] || j >= nh[h]) continue;
+                const float4 pi = make_float4(half_of(S[i], h), half_of(S[kSymSlots + i], h),
+                                              half_of(S[2 * kSymSlots + i], h), 0.0f);
+                const float4 fi = make_float4(half_of(S[3 * kSymSlots + i], h), half_of(S[4 * kSymSlots + i], h),
+                                              half_of(S[5 * kSymSlots + i], h), 0.0f);
+                const float4 pj = make_float4(half_of(S[j], h), half_of(S[kSymSlots + j], h),
+                                              half_of(S[2 * kSymSlots + j], h), 0.0f);
+                const float4 fj = make_float4(half_of(S[3 * kSymSlots + j], h), half_of(S[4 * kSymSlots + j], h),
+                                              half_of(S[5 * kSymSlots + j], h), 0.0f);
+                const float dx = __fsub_rn(pi.x, pj.x), dy = __fsub_rn(pi.y, pj.y), dz = __fsub_rn(pi.z, pj.z);
+                if (!(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < pc.r2min_f)) continue;
+                float cx = 0.0f, cy = 0.0f, cz = 0.0f, ex, ey, ez;
+                pair_f32<TD, true>(pi.x, pi.y, pi.z, pj, fj, pc, cx, cy, cz);
+                exact_pair<TENSOR, float>(dx, dy, dz, fj.x, fj.y, fj.z, pc, ex, ey, ez, coincident);
+                FIX[h][0] = __fadd_rn(FIX[h][0], __fsub_rn(ex, cx));
+                FIX[h][1] = __fadd_rn(FIX[h][1], __fsub_rn(ey, cy));
+                FIX[h][2] = __fadd_rn(FIX[h][2], __fsub_rn(ez, cz));
+                float bx = 0.0f, by = 0.0f, bz = 0.0f;
+                pair_f32<TD, true>(pj.x, pj.y, pj.z, pi, fi, pc, bx, by, bz);
+                exact_pair<TENSOR, float>(-dx, -dy, -dz, fi.x, fi.y, fi.z, pc, ex, ey, ez, coincident);
+                SUM[j] = add_half(SUM[j], h, __fsub_rn(ex, bx));
+                SUM[kSymSlots + j] = add_half(SUM[kSymSlots + j], h, __fsub_rn(ey, by));
+                SUM[2 * kSymSlots + j] = add_half(SUM[2 * kSymSlots + j], h, __fsub_rn(ez, bz));
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int TENSOR>
+__global__ void __launch_bounds__(128) batched_sym_kernel(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    f2 *S = reinterpret_cast<f2 *>(smem) + static_cast<size_t>(wid) * 9 * kSymSlots;   // x y z Fx Fy Fz
+    f2 *SUM = S + 6 * kSymSlots;                                                         // sums x y z
+    const float4 *frcm = static_cast<const float4 *>(a.frcm);
+    PairConst2 c2{};
+    c2.c1 = pk2(a.pc.c1_f, a.pc.c1_f);
+    c2.c3 = pk2(a.pc.c3_f, a.pc.c3_f);
+    c2.m3c3 = pk2(a.pc.m3c3_f, a.pc.m3c3_f);
+    c2.r2min = a.pc.r2min_f;
+    const float m0dt = static_cast<float>(a.pc.mu0 * a.dt);
+    const float far = 1.0e4f * static_cast<float>(a.pc.a), gap = 4.0f * static_cast<float>(a.pc.a);
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(a.ctr, 1ULL);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= static_cast<unsigned long long>(a.nblk)) break;
+        const int4 task = a.stask[t];
+        const int cl[2] = {task.x, task.y};
+        const int nb = task.z;
+        int o[2], nh[2];
+        for (int h = 0; h < 2; ++h) {
+            o[h] = cl[h] >= 0 ? a.off[cl[h]] : 0;
+            nh[h] = cl[h] >= 0 ? a.off[cl[h] + 1] - o[h] : 0;
+        }
+        // stage both clusters, interleaved; padding slots far away, 4a apart, zero force
+        for (int k = lane; k < 32 * nb; k += 32) {
+            float v[2][6];
+            for (int h = 0; h < 2; ++h) {
+                if (k < nh[h]) {
+                    const float4 r = a.rel[o[h] + k], f = frcm[o[h] + k];
+                    v[h][0] = r.x; v[h][1] = r.y; v[h][2] = r.z;
+                    v[h][3] = f.x; v[h][4] = f.y; v[h][5] = f.z;
+                } else {
+                    v[h][0] = far + gap * static_cast<float>(k);
+                    v[h][1] = v[h][2] = v[h][3] = v[h][4] = v[h][5] = 0.0f;
+                }
+            }
+            for (int d = 0; d < 6; ++d) S[d * kSymSlots + k] = pk2(v[0][d], v[1][d]);
+            for (int d = 0; d < 3; ++d) SUM[d * kSymSlots + k] = 0ull;
+        }
+        __syncwarp();
+        bool coincident = false;
+        // the block rows in pairs (p, p + 1): their tiles against the blocks q > p + 1
+        // share each walk of q (bsym_tile2); the rest run one row at a time
+        for (int p = 0; p < nb; p += 2) {
+            const bool two = p + 1 < nb;
+            f2 T[2][6];
+            for (int r = 0; r < 2; ++r) {
+                const int i = 32 * (p + r) + lane;   // (a padding row when !two: never used)
+                for (int d = 0; d < 6; ++d) T[r][d] = S[d * kSymSlots + i];
+            }
+            // (hi, lo) sums of the rows' targets [row][half][dim], and exact-term fixes
+            float hs[2][2][3] = {}, ls[2][2][3] = {};
+            float FIX[2][2][3] = {};
+            auto fold = [&](int r, const f2 (&A)[3]) {
+                for (int d = 0; d < 3; ++d) {
+                    float v0, v1;
+                    upk2(A[d], v0, v1);
+                    fold2(hs[r][0][d], ls[r][0][d], v0);
+                    fold2(hs[r][1][d], ls[r][1][d], v1);
+                }
+            };
+            auto one = [&](int r, int q) {   // tile (p + r, q) alone
+                f2 A[3] = {0ull, 0ull, 0ull};
+                float mn0 = 3.0e38f, mn1 = 3.0e38f;
+                if (q == p + r)
+                    bsym_tile<TENSOR, true>(S, SUM, q, lane, T[r][0], T[r][1], T[r][2], T[r][3], T[r][4], T[r][5], c2,
+                                            A[0], A[1], A[2], mn0, mn1);
+                else
+                    bsym_tile<TENSOR, false>(S, SUM, q, lane, T[r][0], T[r][1], T[r][2], T[r][3], T[r][4], T[r][5],
+                                             c2, A[0], A[1], A[2], mn0, mn1);
+                fold(r, A);
+                if (__any_sync(0xffffffffu, fminf(mn0, mn1) < c2.r2min)) {   // rare: pairs closer than 2a
+                    if (q == p + r)
+                        bsym_fix<TENSOR, true>(S, SUM, p + r, q, lane, nh, a.pc, FIX[r], coincident);
+                    else
+                        bsym_fix<TENSOR, false>(S, SUM, p + r, q, lane, nh, a.pc, FIX[r], coincident);
+                }
+            };
+            one(0, p);
+            if (two) {
+                one(0, p + 1);
+                one(1, p + 1);
+            }
+            for (int q = p + (two ? 2 : 1); q < nb; ++q) {
+                if (!two) {
+                    one(0, q);
+                    continue;
+                }
+                f2 A0[3] = {0ull, 0ull, 0ull}, A1[3] = {0ull, 0ull, 0ull};
+                float mn0 = 3.0e38f, mn1 = 3.0e38f;
+                bsym_tile2<TENSOR>(S, SUM, q, lane, T[0], T[1], c2, A0, A1, mn0, mn1);
+                fold(0, A0);
+                fold(1, A1);
+                if (__any_sync(0xffffffffu, fminf(mn0, mn1) < c2.r2min)) {
+                    bsym_fix<TENSOR, false>(S, SUM, p, q, lane, nh, a.pc, FIX[0], coincident);
+                    bsym_fix<TENSOR, false>(S, SUM, p + 1, q, lane, nh, a.pc, FIX[1], coincident);
+                }
+            }
+            // rows p (and p + 1) are complete: finalise their particles
+            for (int r = 0; r < (two ? 2 : 1); ++r)
+            for (int h = 0; h < 2; ++h) {
+                const int i = 32 * (p + r) + lane;
+                if (i >= nh[h]) continue;
+                float V[3];
+                for (int d = 0; d < 3; ++d) {
+                    float hh = hs[r][h][d], ll = ls[r][h][d];
+                    fold2(hh, ll, half_of(SUM[d * kSymSlots + i], h));
+                    fold2(hh, ll, FIX[r][h][d]);
+                    fold2(hh, ll, half_of(S[(3 + d) * kSymSlots + i], h));   // mu_ii F_i / mu0 = F_i
+                    V[d] = __fadd_rn(hh, ll);
+                }
+                const size_t g = static_cast<size_t>(o[h] + i);
+                const float ux = __fmul_rn(m0dt, V[0]), uy = __fmul_rn(m0dt, V[1]), uz = __fmul_rn(m0dt, V[2]);
+                if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) atomicOr(a.err, DEV_ERR_NONFINITE);
+                const double nx = a.x64[3 * g] + static_cast<double>(ux);
+                const double ny = a.x64[3 * g + 1] + static_cast<double>(uy);
+                const double nz = a.x64[3 * g + 2] + static_cast<double>(uz);
+                a.x64n[3 * g] = nx;
+                a.x64n[3 * g + 1] = ny;
+                a.x64n[3 * g + 2] = nz;
+                const size_t an = static_cast<size_t>(o[h]);
+                a.reln[g] = make_float4(static_cast<float>(nx - a.x64[3 * an]), static_cast<float>(ny - a.x64[3 * an + 1]),
+                                        static_cast<float>(nz - a.x64[3 * an + 2]), 0.0f);
+            }
+        }
+        if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
+        __syncwarp();   // the warp's shared memory is free for the next task
+    }
+}
+
 // Launch shapes: FP64 -- warps per CTA (one cluster per warp) x resident CTAs;
 // FP32C -- block of BT = 32 warps threads (R targets each) x resident CTAs.
 static size_t shape_smem(int mode, const BatchShape &sh) {
     if (mode == MODE_FP64) return static_cast<size_t>(sh.warps) * kWarpStage;
+    if (sh.r == 0) return static_cast<size_t>(sh.warps) * kSymWarpSmem;
     const size_t bt = 32 * static_cast<size_t>(sh.warps);
     const int len = sh.warps == 4 ? (sh.r == 2 ? block_stage_len<128, 2>() : block_stage_len<128, 1>())
                                   : (sh.r == 2 ? block_stage_len<256, 2>() : block_stage_len<256, 1>());
@@ -568,6 +889,7 @@ static size_t shape_smem(int mode, const BatchShape &sh) {
 template <int TENSOR>
 static void *batched_fn_t(int mode, const BatchShape &sh) {
     if (mode == MODE_FP64) return reinterpret_cast<void *>(&batched_kernel<TENSOR>);
+    if (sh.r == 0) return reinterpret_cast<void *>(&batched_sym_kernel<TENSOR>);
     if (sh.r == 2)
         return sh.warps == 4 ? reinterpret_cast<void *>(&batched_blocks_kernel<TENSOR, 128, 2>)
                              : reinterpret_cast<void *>(&batched_blocks_kernel<TENSOR, 256, 2>);
@@ -593,9 +915,12 @@ static cudaError_t batch_launch(sd_batch *b, cudaStream_t st, double dt, const B
     a.cend = b->cend;
     a.canchor = b->canchor;
     a.tq = b->tq;
+    a.stask = b->stask;
     a.P = b->P;
     a.M2 = b->M2;
-    {
+    if (b->mode == MODE_FP32C && sh.r == 0) {
+        a.nblk = b->nstask;   // warp tasks
+    } else {
         const int slots = (b->mode == MODE_FP32C && sh.r == 2) ? b->M2 : b->P;
         a.nblk = (slots + 32 * sh.warps - 1) / (32 * sh.warps);
     }
@@ -866,6 +1191,22 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
     b->M2 = static_cast<int>(tq.size());
     b->tq = static_cast<int32_t *>(balloc(b, sizeof(int32_t) * std::max<size_t>(tq.size(), 1)));
     if (!b->tq) return fail(SD_ERR_OOM, "device allocation of batch buffers");
+    // symmetric kernel: neighbouring non-empty clusters of the largest-first order in
+    // pairs, each pair with its number of 32-particle blocks
+    std::vector<int4> stask;
+    {
+        std::vector<int> ne;
+        for (int k = 0; k < nclusters; ++k)
+            if (offsets[order[k] + 1] > offsets[order[k]]) ne.push_back(order[k]);
+        for (size_t k = 0; k < ne.size(); k += 2) {
+            const int cA = ne[k], cB = k + 1 < ne.size() ? ne[k + 1] : -1;
+            const int nA = offsets[cA + 1] - offsets[cA], nB = cB >= 0 ? offsets[cB + 1] - offsets[cB] : 0;
+            stask.push_back(make_int4(cA, cB, (std::max(nA, nB) + 31) / 32, 0));
+        }
+    }
+    b->nstask = static_cast<int>(stask.size());
+    b->stask = static_cast<int4 *>(balloc(b, sizeof(int4) * std::max<size_t>(stask.size(), 1)));
+    if (!b->stask) return fail(SD_ERR_OOM, "device allocation of batch buffers");
     cudaStream_t st = b->stream;
     cudaError_t e = cudaMemcpyAsync(b->d_off, offsets, sizeof(int32_t) * (nclusters + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && nclusters > 0)
@@ -880,6 +1221,8 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
                                  std::make_tuple(b->tq, tq.data(), tq.size())})
         if (e == cudaSuccess && cnt > 0)
             e = cudaMemcpyAsync(dst, src, sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !stask.empty())
+        e = cudaMemcpyAsync(b->stask, stask.data(), sizeof(int4) * stask.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->fext64, 0, p3 * sizeof(double), st);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMemsetAsync(b->x64[k], 0, p3 * sizeof(double), st);
@@ -890,9 +1233,10 @@ sd_status sd_batch_create(const sd_config *cfg, const int32_t *offsets, int32_t 
     // candidate launch shapes that fit: FP64 -- warps per CTA x resident CTAs per SM;
     // FP32C -- blocks of 128 or 256 threads (4 or 8 warps) with 1 or 2 targets per
     // thread x resident CTAs per SM
-    for (int r : {1, 2}) {
-        if (r == 2 && b->mode != MODE_FP32C) continue;
+    for (int r : {1, 2, 0}) {
+        if (r != 1 && b->mode != MODE_FP32C) continue;
         for (int w : {4, 8}) {
+            if (r == 0 && w != 4) continue;   // symmetric kernel: 4 warps (tasks) per CTA
             const BatchShape sh1{w, 1, r};
             void *fn = batched_fn(b->tensor, b->mode, sh1);
             const size_t smem = shape_smem(b->mode, sh1);
@@ -923,7 +1267,8 @@ void sd_batch_destroy(sd_batch *b) {
         cudaEventDestroy(b->prof.ev1[k]);
     }
     void *bufs[] = {b->d_off, b->d_order, b->x64[0], b->x64[1], b->F64, b->fext64, b->frcm, b->ctr, b->d_err,
-                    b->qperm, b->qcl, b->cbeg, b->cend, b->canchor, b->panchor, b->rel[0], b->rel[1], b->tq};
+                    b->qperm, b->qcl, b->cbeg, b->cend, b->canchor, b->panchor, b->rel[0], b->rel[1], b->tq,
+                    b->stask};
     for (void *p : bufs) bfree(b, p);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;

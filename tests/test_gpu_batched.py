@@ -95,7 +95,7 @@ def _shape_kinds(prec):
 
 def test_batched_shapes_include_two_targets_per_thread():
     kinds = _shape_kinds("fp32c")
-    assert {(128, 1), (256, 1), (128, 2), (256, 2)} <= set(kinds)
+    assert {(128, 1), (256, 1), (128, 2), (256, 2), (128, 0)} <= set(kinds)
     assert {r for (_, r) in _shape_kinds("fp64")} == {1}
     b = sd.Batch(np.array([0, 4], dtype=np.int32))
     with pytest.raises(sd.SDError):
@@ -103,12 +103,13 @@ def test_batched_shapes_include_two_targets_per_thread():
     b.close()
 
 
-@pytest.mark.parametrize("threads,r", [(128, 1), (256, 1), (128, 2), (256, 2)])
+@pytest.mark.parametrize("threads,r", [(128, 1), (256, 1), (128, 2), (256, 2), (128, 0)])
 @pytest.mark.parametrize("tensor", ["rpy", "oseen"])
 def test_batched_every_shape_matches_oracle(threads, r, tensor):
-    """Each FP32C kernel variant, pinned instead of autotuned: clusters of sizes 0 to
-    256 (odd and even: the last target of an odd cluster has a slot of its own when a
-    thread owns two), overlapping pairs, 20 steps (one graph replay and 4 eager steps)."""
+    """Each FP32C kernel variant, pinned instead of autotuned (r = 0: the symmetric
+    kernel, two clusters per warp): clusters of sizes 0 to 256 (odd and even: the last
+    target of an odd cluster has a slot of its own when a thread owns two), overlapping
+    pairs, 20 steps (one graph replay and 4 eager steps)."""
     x, off, F = _odd_sizes_with_overlaps()
     ref = _oracle_batch(x, off, F, 20, 0.01, tensor)
     b = sd.Batch(off, tensor=tensor)
@@ -190,3 +191,38 @@ def test_batched_full_workload_sampled_clusters():
         ref = oracle.euler(x[a:e], nsteps, dt, fext=F[a:e])
         disp = np.abs(ref - x[a:e]).max()
         assert np.abs(got[a:e] - ref).max() <= 1e-5 * disp, (int(c), int(e - a))
+
+
+@pytest.mark.parametrize("tensor", ["rpy", "rp", "oseen"])
+def test_batched_symmetric_kernel_overlaps_and_coincident(tensor):
+    """The symmetric kernel pinned: many overlapping pairs in clusters of every block
+    count (1 to 8 blocks of 32), including pairs inside one 32-block and across blocks,
+    and, for RPY, two coincident spheres; 3 steps against the oracle."""
+    rng = np.random.default_rng(11)
+    sizes = [1, 2, 5, 32, 33, 64, 65, 100, 130, 200, 255, 256, 17]
+    xs = []
+    for n in sizes:
+        p, _ = inputs.cube_rsa(n, 0.05, int(rng.integers(1 << 30)))
+        for k in range(0, n - 1, 7):      # an overlapping partner every 7 particles
+            j = (k + 1 + 37 * (k // 7)) % n
+            if j != k:
+                d = rng.standard_normal(3)
+                p[j] = p[k] + d / np.linalg.norm(d) * rng.uniform(0.3, 1.9)
+        if tensor == "rpy" and n >= 40:
+            p[39] = p[38]
+        xs.append(p)
+    x = np.concatenate(xs)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    F = inputs.normal_forces(x.shape[0], 12)
+    ref = _oracle_batch(x, off, F, 3, 0.01, tensor)
+    b = sd.Batch(off, tensor=tensor)
+    b.set_shape(next(k for k, sh in enumerate(b.shapes()) if sh["targets_per_thread"] == 0))
+    b.set_positions(x)
+    b.set_forces(F)
+    b.step(0.01, 3)
+    got = b.get_positions()
+    b.close()
+    for c in range(len(sizes)):
+        a, e = off[c], off[c + 1]
+        disp = max(np.abs(ref[a:e] - x[a:e]).max(), 1e-300)
+        assert np.abs(got[a:e] - ref[a:e]).max() <= 1e-5 * disp, (c, sizes[c])
