@@ -311,15 +311,17 @@ def run_ours(args):
     value = world * float(n) * n / (ms_step * 1e-3)
 
     # ---- end to end through the public API with pinned host buffers: every step
-    # copies its input positions in (H2D) and its result out (D2H), each as one
-    # asynchronous copy on the stream; the last result is read after the final sync
-    xh = torch.from_numpy(x).pin_memory()
+    # copies its input (the per-particle forces) in (H2D) and its result (the
+    # positions) out (D2H), each as one asynchronous copy on the stream; the host
+    # synchronises once and checks the last result
+    fh = torch.from_numpy(F).pin_memory()
     outh = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    s.set_positions(x)
     _barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s.set_positions(xh, asynchronous=True)     # H2D of the step's input
+        s.set_forces(fh, asynchronous=True)        # H2D of the step's input
         s.step(DT, 1)
         s.get_positions(outh, asynchronous=True)   # D2H of the step's result
     torch.cuda.synchronize()
@@ -829,7 +831,13 @@ def _leg_batched(args, stream, flush):
     b = sd.Batch(off, prec="fp32c", stream="torch", torch_allocator=True)
     b.set_positions(w["x"])
     b.set_forces(w["F"])
-    choice = b.autotune()
+    shapes = b.shapes()
+    if args.batched_shape == "auto":
+        choice = b.autotune()
+    else:   # pinned: the most resident CTAs of the symmetric kernel, or of the one-target block kernel
+        r = 0 if args.batched_shape == "sym" else 1
+        choice = max(k for k, sh in enumerate(shapes) if sh["targets_per_thread"] == r and sh["threads"] == 128)
+        b.set_shape(choice)
     b.step(0.01, 3)
     torch.cuda.synchronize()
     kb = max(args.steps, 10)
@@ -865,7 +873,7 @@ def _leg_batched(args, stream, flush):
         "kernel_avg_ms": bk_ms / max(bk_n, 1),
         "kernel_tflops": FLOPS_PER_PAIR * pairs / (bk_ms / max(bk_n, 1) * 1e-3) / 1e12,
         "algorithmic_gbs": bytes_step / (bk_ms / max(bk_n, 1) * 1e-3) / 1e9,
-        "autotune_choice": int(choice), "steps": kb}}
+        "autotune_choice": int(choice), "shape": shapes[choice], "steps": kb}}
 
 
 def main():
@@ -879,6 +887,8 @@ def main():
                                                      "adjoint", "lubrication", "fcc", "access"],
                     help="run one leg alone and print its numbers (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--batched-shape", default="auto", choices=["auto", "sym", "blocks"],
+                    help="batched leg: the autotuner's shape, or the symmetric / block kernel pinned (profiling)")
     ap.add_argument("--dense", default="auto", choices=["auto", "directed", "symmetric"],
                     help="all-pairs kernel of the main leg (auto: the library's choice, symmetric at this N)")
     args = ap.parse_args()

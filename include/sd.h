@@ -117,13 +117,23 @@ typedef struct sd_config {
                                 first step and after sd_set_positions).  Overlapping pairs (s <= 0)
                                 get no term.  FP64.  Not with sd_adjoint or sd_batch_create
                                 (SD_ERR_UNSUPPORTED). */
+    double verlet_skin;      /* neighbour-list skin of sd_step (Sec. 3.1 step 2, Verlet lists): 0 = default
+                                0.5a, < 0 = off.  With constant forces (no repulsion, no lubrication),
+                                the FP64 near-pair list holds the pairs within r_near + skin and is
+                                rebuilt only when some particle has moved more than skin / 2 relative
+                                to particle 0 since the last build (a uniform translation never forces
+                                one); each particle's list is in ascending partner order, so a step
+                                gives the same result bit for bit from a fresh or a reused list.  Off
+                                automatically when forces are not constant or a periodic side is
+                                below 3 (max cutoff + skin). */
 } sd_config;
 
 typedef struct sd_handle sd_handle;
 typedef struct sd_batch sd_batch;
 
 /* Fill *cfg with defaults: a = eta = 1, RPY, FP32C, unbounded, r_near = 2.5a,
- * no repulsion (rep_rc = 2.5a), no gravity, device 0, default stream, cudaMalloc. */
+ * no repulsion (rep_rc = 2.5a), no gravity, device 0, default stream, cudaMalloc,
+ * Verlet skin 0.5a. */
 void sd_config_init(sd_config *cfg);
 
 /* Create a system of cfg->n particles.  Positions must be set before use; forces

@@ -273,8 +273,9 @@ def _torch_allocator(device: int):
 
 def _make_config(n=0, a=1.0, eta=1.0, tensor="rpy", prec="fp32c", r_near=None, rep_eps=0.0, rep_rc=None,
                  gravity=(0.0, 0.0, 0.0), device=0, stream=None, torch_allocator=False, dense="auto",
-                 lubrication=False, box=None):
+                 lubrication=False, box=None, verlet_skin=None):
     cfg = sd_config_init()
+    cfg.verlet_skin = 0.5 * float(a) if verlet_skin is None else float(verlet_skin)
     cfg.lubrication = int(bool(lubrication))
     if box is not None:
         for d in range(3):
@@ -313,9 +314,12 @@ class System:
 
     def __init__(self, n, a=1.0, eta=1.0, tensor="rpy", prec="fp32c", r_near=None, rep_eps=0.0, rep_rc=None,
                  gravity=(0.0, 0.0, 0.0), device=0, stream=None, torch_allocator=False, dense="auto",
-                 lubrication=False, box=None):
+                 lubrication=False, box=None, verlet_skin=None):
+        """verlet_skin: neighbour-list skin of the steps (None: 0.5a; <= 0: no list reuse)."""
+        if verlet_skin is not None and verlet_skin <= 0:
+            verlet_skin = -1.0
         self.cfg, self._keep = _make_config(n, a, eta, tensor, prec, r_near, rep_eps, rep_rc, gravity, device,
-                                            stream, torch_allocator, dense, lubrication, box)
+                                            stream, torch_allocator, dense, lubrication, box, verlet_skin)
         self.n = int(n)
         self.h = sd_create(self.cfg)
 

@@ -51,6 +51,7 @@ class sd_config(ctypes.Structure):
         ("alloc_ctx", c_void_p),
         ("dense_kernel", c_int32),
         ("lubrication", c_int32),
+        ("verlet_skin", c_double),
     ]
 
 

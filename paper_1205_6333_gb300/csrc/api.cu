@@ -32,7 +32,7 @@ sd_status cuda_status(cudaError_t e, const char *what) {
 
 void prof_begin(sd_handle *h, int kind, cudaStream_t st) {
     Profiler &p = h->prof;
-    if (!p.on || h->capturing || p.npending >= Profiler::kMaxPending) return;
+    if (!p.on || h->capturing || p.open || p.npending >= Profiler::kMaxPending) return;
     const int k = p.npending;
     if (k >= p.nevents) {
         cudaEventCreate(&p.ev0[k]);
@@ -41,14 +41,15 @@ void prof_begin(sd_handle *h, int kind, cudaStream_t st) {
     }
     p.kind[k] = kind;
     cudaEventRecord(p.ev0[k], st);
+    p.open = true;
 }
 
 void prof_end(sd_handle *h, int kind, cudaStream_t st) {
     Profiler &p = h->prof;
-    if (!p.on || h->capturing || p.npending >= Profiler::kMaxPending) return;
-    (void)kind;
+    if (!p.on || h->capturing || !p.open || p.kind[p.npending] != kind) return;
     cudaEventRecord(p.ev1[p.npending], st);
     ++p.npending;
+    p.open = false;
 }
 
 static cudaError_t prof_collect(Profiler &p) {
@@ -130,11 +131,72 @@ static sd_status launch_check(cudaError_t e, const char *what) {
 
 // ---------------------------------------------------------------- one Euler step
 
+// The neighbour-list rebuild of a Verlet step: cell list (and xref = x_in), the
+// candidate list within r_near + skin, sorted by partner.
+static cudaError_t verlet_rebuild(sd_handle *h, cudaStream_t st, const double *x_in) {
+    cudaError_t e = launch_build_cells(h, st, x_in, h->posm, h->xref);
+    if (e == cudaSuccess) e = launch_near_collect(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true, true);
+    return e;
+}
+
+// A Verlet step (constant forces): check kernel (mirror, rebuild decision), the
+// rebuild only when needed, FP64 terms of the listed pairs (which clear the request),
+// all-pairs kernel, Euler epilogue.  Under graph capture the rebuild is the body of a
+// conditional node set by the check kernel; launched eagerly its kernels read the
+// request and return at once without one.  A fresh and a reused list give the same
+// result bit for bit: each particle's list is sorted by partner and entries beyond
+// r_near add exact zeros.
+static cudaError_t launch_verlet_step(sd_handle *h, cudaStream_t st, double dt, const double *x_in, double *x_out) {
+    cudaError_t e = cudaSuccess;
+    if (h->capturing) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g);
+        cudaGraphConditionalHandle cond = 0;
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) e = launch_verlet_check(h, st, x_in, h->posm, cond, true);
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &ndeps);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp);
+        if (e == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(h->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t eb = verlet_rebuild(h, h->cap2, x_in);
+                cudaGraph_t out = nullptr;
+                e = cudaStreamEndCapture(h->cap2, &out);
+                if (eb != cudaSuccess) e = eb;
+            }
+        }
+        if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess) e = launch_near_pairs(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true);
+    } else {   // (profiler event pairs do not nest: cells, then the near pass)
+        e = launch_verlet_check(h, st, x_in, h->posm, 0, false);
+        if (e == cudaSuccess) e = launch_build_cells(h, st, x_in, h->posm, h->xref);
+        prof_begin(h, SD_KERNEL_NEAR, st);
+        if (e == cudaSuccess) e = launch_near_collect(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true, true);
+        if (e == cudaSuccess) e = launch_near_pairs(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true);
+        prof_end(h, SD_KERNEL_NEAR, st);
+    }
+    if (e == cudaSuccess) e = launch_dense(h, st, h->posm, h->frcm, h->part);
+    if (e == cudaSuccess)
+        e = launch_epilogue(h, st, OUT_EULER, x_in, h->posm.aos, h->F64, h->frcm.aos, nullptr, dt, x_out);
+    return e;
+}
+
 // x_out = x_in + dt mu(x_in) F(x_in); the cell-list build also writes the mirror of x_in.
 static cudaError_t launch_step(sd_handle *h, cudaStream_t st, double dt, const double *x_in, double *x_out) {
+    if (h->verlet) return launch_verlet_step(h, st, dt, x_in, x_out);
     cudaError_t e = launch_build_cells(h, st, x_in, h->posm);
     if (e == cudaSuccess && !h->forces_const) e = launch_forces_rep(h, st, x_in);
-    if (e == cudaSuccess) e = launch_near(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos);
+    if (e == cudaSuccess) e = launch_near(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true);
     if (e == cudaSuccess) e = launch_dense(h, st, h->posm, h->frcm, h->part);
     if (e == cudaSuccess) e = launch_epilogue(h, st, OUT_EULER, x_in, h->posm.aos, h->F64, h->frcm.aos, nullptr, dt, x_out);
     return e;
@@ -318,6 +380,7 @@ void sd_config_init(sd_config *cfg) {
     cfg->prec = SD_PREC_FP32C;
     cfg->r_near = 2.5;
     cfg->rep_rc = 2.5;
+    cfg->verlet_skin = 0.5;
 }
 
 static sd_status validate_common(const sd_config *cfg) {
@@ -348,12 +411,21 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     const double rep_rc = cfg->rep_rc > 0.0 ? cfg->rep_rc : 2.5 * a;
     if (!std::isfinite(cfg->rep_eps) || !std::isfinite(rep_rc)) return set_error(SD_ERR_ARG, "repulsion parameters");
     // cell side: every FP64 neighbour pass (near pairs, repulsion, lubrication) within one cell
-    const double cell_h = std::max(r_near, std::max(cfg->rep_eps != 0.0 ? rep_rc : 0.0,
+    const double cutoff = std::max(r_near, std::max(cfg->rep_eps != 0.0 ? rep_rc : 0.0,
                                                     cfg->lubrication != 0 ? 3.0 * a : 0.0));
     for (int d = 0; d < 3; ++d)
-        if (cfg->box[d] > 0.0 && cfg->box[d] < 3.0 * cell_h)
+        if (cfg->box[d] > 0.0 && cfg->box[d] < 3.0 * cutoff)
             return set_error(SD_ERR_ARG, "a periodic box side must be at least 3 max(r_near, rep_rc, 3a if "
                                          "lubrication)");
+    if (!std::isfinite(cfg->verlet_skin)) return set_error(SD_ERR_ARG, "verlet_skin must be finite");
+    // Verlet lists for the steps of a system with constant forces, when the box allows
+    // cells of side cutoff + skin
+    double skin = cfg->verlet_skin == 0.0 ? 0.5 * a : cfg->verlet_skin;
+    bool verlet = skin > 0.0 && cfg->rep_eps == 0.0 && cfg->lubrication == 0;
+    for (int d = 0; d < 3 && verlet; ++d)
+        if (cfg->box[d] > 0.0 && cfg->box[d] < 3.0 * (cutoff + skin)) verlet = false;
+    if (!verlet) skin = 0.0;
+    const double cell_h = cutoff + skin;
 
     sd_handle *h = new (std::nothrow) sd_handle();
     if (!h) return set_error(SD_ERR_OOM, "host allocation");
@@ -371,6 +443,8 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     h->rep_rc = rep_rc;
     h->lub = cfg->lubrication != 0;
     h->forces_const = (cfg->rep_eps == 0.0) && !h->lub;
+    h->verlet = verlet;
+    h->skin = skin;
 
     PairConst &pc = h->pc;
     pc.a = a;
@@ -406,6 +480,7 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return fail(SD_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
     e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking);
     if (e != cudaSuccess) return fail(SD_ERR_CUDA, "stream creation");
 
     const size_t n3 = 3 * static_cast<size_t>(std::max(h->n, 1));
@@ -413,11 +488,13 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     const size_t vb = v4size(h);
     h->near_cap = static_cast<int>(std::min<long long>(static_cast<long long>(kNearPerParticle) * h->n + 1024,
                                                         1LL << 30));
-    bool ok = dalloc_t(h, h->d_err, 1) && dalloc_t(h, h->d_flag, 1) && dalloc_t(h, h->near64, 2 * n3) &&
+    bool ok = dalloc_t(h, h->d_err, 1) && dalloc_t(h, h->d_flag, 1) && dalloc_t(h, h->d_vl, 2) &&
+              dalloc_t(h, h->near64, 2 * n3) &&
               dalloc_t(h, h->near_ent, h->near_cap) && dalloc_t(h, h->near_out, 6 * static_cast<size_t>(h->near_cap)) &&
               dalloc_t(h, h->near_n, 1) && dalloc_t(h, h->near_off, n3 / 3 + 1) && dalloc_t(h, h->near_cnt, n3 / 3 + 1);
     for (int b = 0; b < 2 && ok; ++b) ok = dalloc_t(h, h->x64[b], n3);
     if (ok && h->lub) ok = dalloc_t(h, h->vlag, n3);
+    if (ok && h->verlet) ok = dalloc_t(h, h->xref, n3);
     ok = ok && dalloc_t(h, h->fext64, n3) && dalloc_t(h, h->F64, n3) && dalloc_t(h, h->Fa64, n3) &&
          dalloc_t(h, h->Wa64, n3);
     const bool soa = h->mode != MODE_FP64;
@@ -447,9 +524,9 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     int H = 1024;
     while (H < 2 * h->n) H <<= 1;
     c.H = H;
-    c.nblk = (H + 4095) / 4096;
+    c.nblk = (H + 16383) / 16384;   // scan blocks of 16,384 buckets (cells.cu)
     ok = dalloc_t(h, c.cell, n3 / 3) && dalloc_t(h, c.key, n3 / 3) && dalloc_t(h, c.cnt, H) &&
-         dalloc_t(h, c.fill, H) && dalloc_t(h, c.start, H + 1) && dalloc_t(h, c.bsum, c.nblk) &&
+         dalloc_t(h, c.start, H + 1) && dalloc_t(h, c.bsum, c.nblk) &&
          dalloc_t(h, c.sorted, n3 / 3);
     if (!ok) return fail(SD_ERR_OOM, "device allocation of the cell list");
 
@@ -475,12 +552,15 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     cudaStream_t st = h->stream;
     e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_vl, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_vl, 0xff, sizeof(int), st);   // the first step builds
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(h->x64[b], 0, n3 * sizeof(double), st);
     for (Mirror *m : {&h->posm, &h->frcm, &h->frcam, &h->wam}) {
         if (e == cudaSuccess) e = cudaMemsetAsync(m->aos, 0, np * vb, st);
         if (e == cudaSuccess && m->soa) e = cudaMemsetAsync(m->soa, 0, 3 * np * sizeof(float), st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fext64, 0, n3 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->cl.cnt, 0, sizeof(int) * static_cast<size_t>(h->cl.H), st);
     if (e == cudaSuccess && h->vlag) e = cudaMemsetAsync(h->vlag, 0, n3 * sizeof(double), st);
     if (e == cudaSuccess) e = launch_pad_mirror(h, st, h->posm);
     if (e == cudaSuccess) e = launch_stage_forces(h, st, nullptr, SD_DTYPE_F64, 1, h->F64, h->frcm);
@@ -502,11 +582,12 @@ void sd_destroy(sd_handle *h) {
         dfree(h, m->soa);
     }
     void *bufs[] = {h->fext64, h->F64, h->Fa64, h->Wa64, h->part, h->part2, h->jpart,
-                    h->cl.cell, h->cl.key, h->cl.cnt, h->cl.fill, h->cl.start, h->cl.bsum, h->cl.sorted,
+                    h->cl.cell, h->cl.key, h->cl.cnt, h->cl.start, h->cl.bsum, h->cl.sorted,
                     h->ckpt, h->seg, h->lam, h->gFacc, h->near64, h->d_flag, h->d_err,
-                    h->near_ent, h->near_out, h->near_n, h->near_off, h->near_cnt, h->vlag};
+                    h->near_ent, h->near_out, h->near_n, h->near_off, h->near_cnt, h->vlag, h->xref, h->d_vl};
     for (void *p : bufs) dfree(h, p);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->cap2) cudaStreamDestroy(h->cap2);
     delete h;
 }
 
@@ -546,8 +627,10 @@ sd_status sd_set_positions(sd_handle *h, const double *xyz, int on_device) {
                                 h->stream));
         sd_status s = launch_check(launch_stage_pos(h, h->stream, h->x64[h->cur], h->posm), "stage positions");
         if (s != SD_OK) return s;
-        // new positions: the previous step's velocities no longer apply (lubrication)
+        // new positions: the previous step's velocities no longer apply (lubrication),
+        // and the next step builds its neighbour list afresh
         if (h->vlag) SD_CUDA(cudaMemsetAsync(h->vlag, 0, 3 * sizeof(double) * h->n, h->stream));
+        if (h->verlet) SD_CUDA(cudaMemsetAsync(h->d_vl, 0xff, sizeof(int), h->stream));
     }
     h->pos_set = true;
     h->cells_valid = false;
@@ -1018,6 +1101,7 @@ sd_status sd_profile(sd_handle *h, int on) {
     Profiler &p = h->prof;
     p.on = on != 0;
     p.npending = 0;
+    p.open = false;
     for (int k = 0; k < SD_KERNEL_COUNT; ++k) {
         p.ms[k] = 0.0;
         p.launches[k] = 0;

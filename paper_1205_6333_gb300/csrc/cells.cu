@@ -71,6 +71,64 @@ cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, M
     return cudaGetLastError();
 }
 
+// The Verlet step's first kernel: the mirror of x (as the cell-list build writes it),
+// the clamp flag reset, and the rebuild decision.  The list stays valid while every
+// particle's displacement since the build, relative to particle 0's, is below
+// skin / 2 (pair distances then changed by less than the skin; a uniform
+// translation moves no pair).  A list that overflowed (its particles corrected in
+// place at build time) is rebuilt every step.  The last block to finish hands the
+// decision to the conditional graph node.
+template <typename V4>
+__global__ void verlet_check_kernel(const double *__restrict__ x, const double *__restrict__ xref, int n, int npad,
+                                    Box b, double half_skin2, V4 *__restrict__ m, float *__restrict__ soa, int *flag,
+                                    int *vl, const unsigned long long *near_n, int cap,
+                                    cudaGraphConditionalHandle cond, int use_cond, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+        if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicOr(err, DEV_ERR_NONFINITE);
+        put_pos_mirror(m, soa, npad, i, x, b);
+        const double ux = (px - xref[3 * i]) - (x[0] - xref[0]);
+        const double uy = (py - xref[3 * i + 1]) - (x[1] - xref[1]);
+        const double uz = (pz - xref[3 * i + 2]) - (x[2] - xref[2]);
+        if (!(ux * ux + uy * uy + uz * uz < half_skin2)) atomicOr(&vl[0], 1);   // (also NaN)
+        if (i == 0) {
+            *flag = 0;   // the near pass of these positions raises it again if needed
+            if (*near_n > static_cast<unsigned long long>(cap)) atomicOr(&vl[0], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int done = atomicAdd(&vl[1], 1);
+        if (done == static_cast<int>(gridDim.x) - 1) {   // every block's decision is in
+            __threadfence();
+            const int rebuild = atomicOr(&vl[0], 0);
+            vl[1] = 0;
+            if (use_cond) cudaGraphSetConditional(cond, rebuild != 0 ? 1u : 0u);
+        }
+    }
+}
+
+cudaError_t launch_verlet_check(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm,
+                                cudaGraphConditionalHandle cond, bool use_cond) {
+    if (h->n == 0) return cudaSuccess;
+    const int nb = (h->n + 255) / 256;
+    const double hs2 = 0.25 * h->skin * h->skin;
+    prof_begin(h, SD_KERNEL_CELLS, st);
+    if (h->mode == MODE_FP64)
+        verlet_check_kernel<dbl4><<<nb, 256, 0, st>>>(x64, h->xref, h->n, h->npad, h->cl.box, hs2,
+                                                      static_cast<dbl4 *>(posm.aos), posm.soa, h->d_flag, h->d_vl,
+                                                      h->near_n, h->near_cap, cond, use_cond ? 1 : 0, h->d_err);
+    else
+        verlet_check_kernel<float4><<<nb, 256, 0, st>>>(x64, h->xref, h->n, h->npad, h->cl.box, hs2,
+                                                        static_cast<float4 *>(posm.aos), posm.soa, h->d_flag, h->d_vl,
+                                                        h->near_n, h->near_cap, cond, use_cond ? 1 : 0, h->d_err);
+    prof_end(h, SD_KERNEL_CELLS, st);
+    ++h->launches;
+    return cudaGetLastError();
+}
+
 // dst64 = src (+ fext + gravity when add_ext) and its mirror; src is n x 3 float or double.
 template <typename V4, typename Src>
 __global__ void stage_forces_kernel(const Src *__restrict__ src, const double *__restrict__ fext, double gx,
@@ -163,10 +221,23 @@ __device__ __forceinline__ int cell_coord_d(const CellList &c, int d, double x) 
 template <typename V4>
 __global__ void cells_hash_kernel(const double *__restrict__ x, int n, CellList c, int4 *__restrict__ cell,
                                   uint32_t *__restrict__ key, int *__restrict__ cnt, V4 *__restrict__ m,
-                                  float *__restrict__ soa, int npad, int *flag, int *err) {
+                                  float *__restrict__ soa, int npad, int *flag, unsigned long long *near_n,
+                                  double *__restrict__ xref, int *rebuild, const int *gate, int *err) {
+    if (gate && *gate == 0) return;   // a Verlet step without a rebuild request
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (i == 0) *flag = 0;   // the near pass of these positions raises it again if needed
+    if (i == 0) {
+        *flag = 0;     // the near pass of these positions raises it again if needed
+        *near_n = 0;   // ... and fills its candidate list from the start
+        // any build outside a Verlet step replaces the near-pair list with one the
+        // steps cannot reuse (a Verlet step's request is cleared by its near pass)
+        if (rebuild && !xref) *rebuild = 1;
+    }
+    if (xref) {
+        xref[3 * i] = x[3 * i];
+        xref[3 * i + 1] = x[3 * i + 1];
+        xref[3 * i + 2] = x[3 * i + 2];
+    }
     const int H = c.H;
     const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
     if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicOr(err, DEV_ERR_NONFINITE);
@@ -181,8 +252,8 @@ __global__ void cells_hash_kernel(const double *__restrict__ x, int n, CellList 
 }
 
 constexpr int kScanThreads = 1024;
-constexpr int kScanPer = 4;
-constexpr int kScanBlock = kScanThreads * kScanPer;
+constexpr int kScanPer = 16;
+constexpr int kScanBlock = kScanThreads * kScanPer;   // buckets one scan block covers (one kernel up to this)
 
 // Exclusive scan of kScanPer values per thread across a block; returns the
 // block total.  Warp shuffles within warps, shared memory across warps.
@@ -220,7 +291,8 @@ __device__ __forceinline__ int block_exclusive_scan(int v[kScanPer], int *s_warp
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(const int *__restrict__ in, int *__restrict__ out,
-                                                                   int *__restrict__ bsum, int H) {
+                                                                   int *__restrict__ bsum, int H, const int *gate) {
+    if (gate && *gate == 0) return;
     __shared__ int s_warp[33];
     const int base = blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
     int v[kScanPer];
@@ -228,13 +300,17 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(const int *__
     const int total = block_exclusive_scan(v, s_warp);
     for (int k = 0; k < kScanPer; ++k)
         if (base + k < H) out[base + k] = v[k];
-    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+    if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = total;
+        if (gridDim.x == 1) out[H] = total;   // one block: the scan is complete
+    }
 }
 
 // One block: exclusive scan of the block totals in place (nblk <= kScanBlock
 // per pass, looping with a carry), then start[H] = grand total.
 __global__ void __launch_bounds__(kScanThreads) scan_top_kernel(int *__restrict__ bsum, int nblk,
-                                                                int *__restrict__ start, int H) {
+                                                                int *__restrict__ start, int H, const int *gate) {
+    if (gate && *gate == 0) return;
     __shared__ int s_warp[33];
     int carry = 0;
     for (int b0 = 0; b0 < nblk; b0 += kScanBlock) {
@@ -249,23 +325,32 @@ __global__ void __launch_bounds__(kScanThreads) scan_top_kernel(int *__restrict_
     if (threadIdx.x == 0) start[H] = carry;
 }
 
-__global__ void scan_add_kernel(int *__restrict__ start, const int *__restrict__ bsum, int H) {
+__global__ void scan_add_kernel(int *__restrict__ start, const int *__restrict__ bsum, int H, const int *gate) {
+    if (gate && *gate == 0) return;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < H) start[e] += bsum[e / kScanBlock];
 }
 
+// Each particle takes a place in its bucket by counting the bucket's occupancy
+// down, which leaves every counter at zero for the next build (no memset).
 __global__ void cells_scatter_kernel(const uint32_t *__restrict__ key, int n, const int *__restrict__ start,
-                                     int *__restrict__ fill, int *__restrict__ sorted, int *err) {
+                                     int *__restrict__ cnt, int *__restrict__ sorted, const int *gate, int *err) {
+    if (gate && *gate == 0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t k = key[i];
-    sorted[dbg_index(start[k] + atomicAdd(&fill[k], 1), n, err)] = i;
+    const int pos = start[k] + atomicSub(&cnt[k], 1) - 1;
+    if (pos >= start[k] && pos < start[k + 1])   // always, unless a counter was left non-zero
+        sorted[pos] = i;
+    else
+        atomicOr(err, DEV_ERR_BOUNDS);
 }
 
 // Sort each bucket by particle index (buckets hold ~1 particle; a bucket larger
 // than 256 -- only possible for unphysically dense input -- stays unsorted, which
 // changes only the FP64 summation order of its near pairs).
-__global__ void cells_sort_kernel(const int *__restrict__ start, int *__restrict__ sorted, int H) {
+__global__ void cells_sort_kernel(const int *__restrict__ start, int *__restrict__ sorted, int H, const int *gate) {
+    if (gate && *gate == 0) return;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= H) return;
     const int s0 = start[b], s1 = start[b + 1];
@@ -281,29 +366,34 @@ __global__ void cells_sort_kernel(const int *__restrict__ start, int *__restrict
     }
 }
 
-cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm) {
+cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm, double *xref) {
     CellList &c = h->cl;
     if (h->n == 0) return cudaSuccess;
+    // a Verlet build runs only when the step's check asked for it (graph: the conditional
+    // node; launched eagerly: every kernel reads the request and returns at once without it)
+    const int *gate = xref ? h->d_vl : nullptr;
     prof_begin(h, SD_KERNEL_CELLS, st);
-    cudaError_t e = cudaMemsetAsync(c.cnt, 0, sizeof(int) * static_cast<size_t>(c.H), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c.fill, 0, sizeof(int) * static_cast<size_t>(c.H), st);
-    if (e != cudaSuccess) return e;
+    // (the bucket counters are zero: zeroed at creation, counted back to zero by
+    // every build's scatter)
     const int nb = (h->n + 255) / 256;
     if (h->mode == MODE_FP64)
         cells_hash_kernel<dbl4><<<nb, 256, 0, st>>>(x64, h->n, c, c.cell, c.key, c.cnt,
                                                     static_cast<dbl4 *>(posm.aos), posm.soa, h->npad, h->d_flag,
-                                                    h->d_err);
+                                                    h->near_n, xref, h->d_vl, gate, h->d_err);
     else
         cells_hash_kernel<float4><<<nb, 256, 0, st>>>(x64, h->n, c, c.cell, c.key, c.cnt,
                                                       static_cast<float4 *>(posm.aos), posm.soa, h->npad,
-                                                      h->d_flag, h->d_err);
-    scan_blocks_kernel<<<c.nblk, kScanThreads, 0, st>>>(c.cnt, c.start, c.bsum, c.H);
-    scan_top_kernel<<<1, kScanThreads, 0, st>>>(c.bsum, c.nblk, c.start, c.H);
-    scan_add_kernel<<<(c.H + 255) / 256, 256, 0, st>>>(c.start, c.bsum, c.H);
-    cells_scatter_kernel<<<nb, 256, 0, st>>>(c.key, h->n, c.start, c.fill, c.sorted, h->d_err);
-    cells_sort_kernel<<<(c.H + 255) / 256, 256, 0, st>>>(c.start, c.sorted, c.H);
+                                                      h->d_flag, h->near_n, xref, h->d_vl, gate, h->d_err);
+    scan_blocks_kernel<<<c.nblk, kScanThreads, 0, st>>>(c.cnt, c.start, c.bsum, c.H, gate);
+    if (c.nblk > 1) {
+        scan_top_kernel<<<1, kScanThreads, 0, st>>>(c.bsum, c.nblk, c.start, c.H, gate);
+        scan_add_kernel<<<(c.H + 255) / 256, 256, 0, st>>>(c.start, c.bsum, c.H, gate);
+        h->launches += 2;
+    }
+    cells_scatter_kernel<<<nb, 256, 0, st>>>(c.key, h->n, c.start, c.cnt, c.sorted, gate, h->d_err);
+    cells_sort_kernel<<<(c.H + 255) / 256, 256, 0, st>>>(c.start, c.sorted, c.H, gate);
     prof_end(h, SD_KERNEL_CELLS, st);
-    h->launches += 6;
+    h->launches += 4;
     return cudaGetLastError();
 }
 

@@ -816,6 +816,7 @@ static void *pick_sym_t(int tensor, int mode) {
 template <bool PER>
 static void *pick_sym_p(int tensor, int mode, int B, int NT) {
     if (B == 512) return pick_sym_t<PER, 512, 128>(tensor, mode);
+    if (B == 128) return pick_sym_t<PER, 128, 64>(tensor, mode);
     if (NT == 64) return pick_sym_t<PER, 256, 64>(tensor, mode);
     return pick_sym_t<PER, 256, 128>(tensor, mode);
 }
@@ -854,6 +855,12 @@ static constexpr size_t sym_smem(int B, int NT) {
 // 0.053 -> 0.050 ms at 8,192; at 4,096 they leave too few CTAs (0.020 -> 0.030).
 #ifndef SD_DENSE_SYM_MID_N
 #define SD_DENSE_SYM_MID_N 8192
+#endif
+// Below SD_DENSE_SYM_SMALL_N, blocks of 128 particles in 64-thread CTAs (2 targets
+// per thread): four times the tiles of 256-blocks, so a small system still spreads
+// over every SM.
+#ifndef SD_DENSE_SYM_SMALL_N
+#define SD_DENSE_SYM_SMALL_N 8192
 #endif
 // CTA oversubscription of the symmetric kernel's grid (see SD_DENSE_CTA_SCALE).  At
 // N = 65,536: all-pairs + epilogue 2.265 ms at 8, 2.251 at 16, 2.251 at 32 (more
@@ -902,7 +909,9 @@ cudaError_t dense_setup(sd_handle *h) {
     // block shape: 512 particles x 128 threads (4 targets each) for large N, 256 x 64
     // (4 each) for mid-size N, 256 x 128 (2 each) below
     const bool large = h->npad >= SD_DENSE_SYM_LARGE_N && h->npad % 512 == 0;
-    const int B = large ? 512 : 256, NT = (large || h->npad < SD_DENSE_SYM_MID_N) ? 128 : 64;
+    const bool small = h->npad < SD_DENSE_SYM_SMALL_N;
+    const int B = large ? 512 : (small ? 128 : 256);
+    const int NT = large ? 128 : (small ? 64 : (h->npad < SD_DENSE_SYM_MID_N ? 128 : 64));
     if (h->mode == MODE_FP64 && want_sym != SD_DENSE_DIRECTED) {
         void *sfn = h->tensor == T_OSEEN ? (h->pc.periodic ? reinterpret_cast<void *>(&dense_sym64_kernel<T_OSEEN, true>)
                                                            : reinterpret_cast<void *>(&dense_sym64_kernel<T_OSEEN, false>))
@@ -943,7 +952,10 @@ cudaError_t dense_setup(sd_handle *h) {
         s.I = s.J = B;
         s.nIB = s.nJT = h->npad / B;
         s.nT = static_cast<long long>(s.nIB) * (s.nIB + 1) / 2;
-        if (want_sym == SD_DENSE_SYMMETRIC || s.nT * SD_DENSE_SYM_SMS_PER_TILE >= h->num_sms) {
+        // (blocks of 128: four times as many, and smaller, tiles are needed to beat the
+        // directed kernel: measured directed faster at n = 2048, symmetric at 4096)
+        const long long need = static_cast<long long>(h->num_sms) * (B == 128 ? 4 : 1);
+        if (want_sym == SD_DENSE_SYMMETRIC || s.nT * SD_DENSE_SYM_SMS_PER_TILE >= need) {
             const long long swant = static_cast<long long>(h->num_sms) * socc * SD_DENSE_SYM_CTA_SCALE;
             s.chunk = std::max(1LL, (s.nT + swant - 1) / swant);
             s.grid = static_cast<int>((s.nT + s.chunk - 1) / s.chunk);
@@ -1014,6 +1026,8 @@ static void launch_dense_t(sd_handle *h, cudaStream_t st, Mirror posm, Mirror fr
     }
         if (g.I == 512) {
             SD_DS_SHAPE(512, 128)
+        } else if (g.I == 128) {
+            SD_DS_SHAPE(128, 64)
         } else if (h->sym_nt == 64) {
             SD_DS_SHAPE(256, 64)
         } else {

@@ -105,6 +105,8 @@ struct NearArgs {
     unsigned long long *ent_n;   // entries claimed (zeroed before the collect kernel)
     int *noff, *ncnt; // per particle: first entry and count; ncnt = -1: correction is in near[i]
     int cap;
+    const int *gate;  // Verlet list build: run only when the step's check asked for a rebuild
+    int *gate_reset;  // the step's FP64 pass clears that request once the list is (re)built
 };
 
 // The correction of one near pair (FP64 r^2 < r_near^2), added to c6: the exact
@@ -200,6 +202,7 @@ constexpr int kNearRegs = 4;   // candidates a lane keeps in registers; more -> 
 
 template <int TENSOR, int MODE>
 __global__ void __launch_bounds__(128) near_collect_kernel(NearArgs a) {
+    if (a.gate && *a.gate == 0) return;   // (uniform over the grid)
     using V4 = typename EpiT<MODE>::V4;
     const V4 *pm = static_cast<const V4 *>(a.posm);
     const long long gt = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -270,6 +273,7 @@ __global__ void __launch_bounds__(128) near_collect_kernel(NearArgs a) {
 // two correction variants of the pair, written to its entry.
 template <int TENSOR, int MODE>
 __global__ void __launch_bounds__(128) near_pair_kernel(NearArgs a) {
+    if (a.gate_reset && blockIdx.x == 0 && threadIdx.x == 0) *a.gate_reset = 0;   // the list is current
     const int total = static_cast<int>(min(*a.ent_n, static_cast<unsigned long long>(a.cap)));
     bool coincident = false, close = false;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -296,23 +300,40 @@ __global__ void __launch_bounds__(128) near_pair_kernel(NearArgs a) {
     if (close) atomicOr(a.flag, 1);
 }
 
-template <int TENSOR, int MODE>
-static void near_launch2(int nb, int np, cudaStream_t st, const NearArgs &a) {
-    near_collect_kernel<TENSOR, MODE><<<nb, 128, 0, st>>>(a);
-    near_pair_kernel<TENSOR, MODE><<<np, 128, 0, st>>>(a);
-}
-
-template <int TENSOR>
-static void near_launch_mode(int mode, int nb, int np, cudaStream_t st, const NearArgs &a) {
-    switch (mode) {
-        case MODE_FP64: near_launch2<TENSOR, MODE_FP64>(nb, np, st, a); break;
-        default: near_launch2<TENSOR, MODE_FP32C>(nb, np, st, a); break;   // FP32 and FP32C share it
+// A Verlet list: each particle's run of entries in ascending partner index, so that the
+// epilogue adds a particle's near terms in an order that does not depend on when, or
+// from which cell list, the list was built (entries beyond r_near add exact zeros).
+__global__ void near_sort_kernel(int2 *__restrict__ ent, const int *__restrict__ noff, const int *__restrict__ ncnt,
+                                 int n, int cap, const int *gate) {
+    if (gate && *gate == 0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int cnt = ncnt[i];
+    if (cnt < 2) return;   // (cnt < 0: corrected in place)
+    const int e0 = noff[i];
+    if (e0 < 0 || e0 + cnt > cap) return;
+    for (int p = e0 + 1; p < e0 + cnt; ++p) {
+        const int2 v = ent[p];
+        int q = p - 1;
+        while (q >= e0 && ent[q].y > v.y) {
+            ent[q + 1] = ent[q];
+            --q;
+        }
+        ent[q + 1] = v;
     }
 }
 
-cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const void *posm, const double *F64,
-                        const void *frcm) {
-    if (h->n == 0) return cudaSuccess;
+template <int TENSOR, int MODE>
+static void near_launch_collect(int nb, cudaStream_t st, const NearArgs &a) {
+    near_collect_kernel<TENSOR, MODE><<<nb, 128, 0, st>>>(a);
+}
+template <int TENSOR, int MODE>
+static void near_launch_pairs(int np, cudaStream_t st, const NearArgs &a) {
+    near_pair_kernel<TENSOR, MODE><<<np, 128, 0, st>>>(a);
+}
+
+static NearArgs near_args(sd_handle *h, const double *x64, const void *posm, const double *F64, const void *frcm,
+                          double screen) {
     NearArgs a;
     a.x64 = x64;
     a.posm = posm;
@@ -321,7 +342,7 @@ cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const 
     a.cl = h->cl;
     a.rnear2 = h->r_near * h->r_near;
     a.rsafe2 = kRSafe * kRSafe * h->pc.a * h->pc.a;
-    a.rscreen2 = static_cast<float>(1.0201 * a.rnear2);
+    a.rscreen2 = static_cast<float>(1.0201 * screen * screen);
     a.pc = h->pc;
     a.n = h->n;
     a.near = h->near64;
@@ -334,20 +355,65 @@ cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const 
     a.noff = h->near_off;
     a.ncnt = h->near_cnt;
     a.cap = h->near_cap;
+    a.gate = nullptr;
+    a.gate_reset = nullptr;
+    return a;
+}
+
+#define SD_NEAR_DISPATCH(FN, ARG)                                                                                \
+    do {                                                                                                         \
+        const bool f64_ = h->mode == MODE_FP64;                                                                  \
+        switch (h->tensor) {                                                                                     \
+            case T_RPY: if (f64_) FN<T_RPY, MODE_FP64>(ARG, st, a); else FN<T_RPY, MODE_FP32C>(ARG, st, a); break; \
+            case T_RP: if (f64_) FN<T_RP, MODE_FP64>(ARG, st, a); else FN<T_RP, MODE_FP32C>(ARG, st, a); break;    \
+            default: if (f64_) FN<T_OSEEN, MODE_FP64>(ARG, st, a); else FN<T_OSEEN, MODE_FP32C>(ARG, st, a); break; \
+        }                                                                                                        \
+    } while (0)
+
+cudaError_t launch_near_collect(sd_handle *h, cudaStream_t st, const double *x64, const void *posm,
+                                const double *F64, const void *frcm, bool count_zeroed, bool verlet_list) {
+    if (h->n == 0) return cudaSuccess;
+    NearArgs a = near_args(h, x64, posm, F64, frcm, verlet_list ? h->r_near + h->skin : h->r_near);
+    if (verlet_list) a.gate = h->d_vl;
     const int nb = static_cast<int>((static_cast<long long>(h->n) * kWalkLanes + 127) / 128);
+    if (!count_zeroed) {
+        cudaError_t e = cudaMemsetAsync(a.ent_n, 0, sizeof(*a.ent_n), st);
+        if (e != cudaSuccess) return e;
+    }
+    SD_NEAR_DISPATCH(near_launch_collect, nb);
+    ++h->launches;
+    if (verlet_list) {
+        near_sort_kernel<<<(h->n + 127) / 128, 128, 0, st>>>(a.ent, a.noff, a.ncnt, h->n, a.cap, a.gate);
+        ++h->launches;
+    } else if (h->verlet) {
+        // a list the steps cannot reuse (no skin, unsorted): their next step rebuilds
+        cudaError_t e = cudaMemsetAsync(h->d_vl, 0xff, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_pairs(sd_handle *h, cudaStream_t st, const double *x64, const void *posm, const double *F64,
+                              const void *frcm, bool verlet_step) {
+    if (h->n == 0) return cudaSuccess;
+    NearArgs a = near_args(h, x64, posm, F64, frcm, h->r_near);
+    if (verlet_step) a.gate_reset = h->d_vl;
     const int np = static_cast<int>(std::min<long long>((static_cast<long long>(a.cap) + 127) / 128,
                                                         8LL * h->num_sms));
-    prof_begin(h, SD_KERNEL_NEAR, st);
-    cudaError_t e = cudaMemsetAsync(a.ent_n, 0, sizeof(*a.ent_n), st);
-    if (e != cudaSuccess) return e;
-    switch (h->tensor) {
-        case T_RPY: near_launch_mode<T_RPY>(h->mode, nb, np, st, a); break;
-        case T_RP: near_launch_mode<T_RP>(h->mode, nb, np, st, a); break;
-        default: near_launch_mode<T_OSEEN>(h->mode, nb, np, st, a); break;
-    }
-    prof_end(h, SD_KERNEL_NEAR, st);
-    h->launches += 2;
+    SD_NEAR_DISPATCH(near_launch_pairs, np);
+    ++h->launches;
     return cudaGetLastError();
+}
+#undef SD_NEAR_DISPATCH
+
+cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const void *posm, const double *F64,
+                        const void *frcm, bool count_zeroed) {
+    if (h->n == 0) return cudaSuccess;
+    prof_begin(h, SD_KERNEL_NEAR, st);
+    cudaError_t e = launch_near_collect(h, st, x64, posm, F64, frcm, count_zeroed, false);
+    if (e == cudaSuccess) e = launch_near_pairs(h, st, x64, posm, F64, frcm, false);
+    prof_end(h, SD_KERNEL_NEAR, st);
+    return e;
 }
 
 // ---------------------------------------------------------------- epilogue

@@ -143,8 +143,7 @@ struct CellList {
     int nblk = 0;          // scan blocks
     int4 *cell = nullptr;  // [n] integer cell coordinates (w unused)
     uint32_t *key = nullptr;  // [n] bucket of each particle
-    int *cnt = nullptr;    // [H] occupancy, then fill counters
-    int *fill = nullptr;   // [H]
+    int *cnt = nullptr;    // [H] occupancy (zero between builds)
     int *start = nullptr;  // [H+1]
     int *bsum = nullptr;   // [nblk]
     int *sorted = nullptr; // [n]
@@ -176,6 +175,7 @@ struct Profiler {
     int kind[kMaxPending] = {};
     int npending = 0;
     int nevents = 0;  // created event pairs
+    bool open = false;   // a range is open (ranges do not nest: an inner one is ignored)
 };
 
 struct Allocator {
@@ -258,6 +258,14 @@ struct sd_handle {
     int64_t launches = 0;
     bool capturing = false;
     int part_kind = 0;   // 1: sd_mobility_apply_part done, 2: sd_step_part done (their combine may follow)
+
+    // Verlet neighbour lists of sd_step (constant forces only): the near-pair list holds
+    // the pairs within r_near + skin of the positions xref it was built from
+    bool verlet = false;
+    double skin = 0.0;
+    double *xref = nullptr;        // [n*3] positions of the last build
+    int *d_vl = nullptr;           // [0] rebuild request, [1] blocks done (check kernel)
+    cudaStream_t cap2 = nullptr;   // captures the rebuild body of a conditional graph node
 };
 
 namespace sd {
@@ -288,7 +296,15 @@ void prof_end(sd_handle *h, int kind, cudaStream_t st);
 cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm);
 cudaError_t launch_stage_forces(sd_handle *h, cudaStream_t st, const void *src, int src_dtype, int add_ext,
                                 double *dst64, Mirror dstm);
-cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm);
+// xref != nullptr: a Verlet-list build (copies x64 to xref and clears the rebuild
+// request); otherwise any build requests a rebuild of the step's list.
+cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm,
+                               double *xref = nullptr);
+// Verlet step: the mirror of x64, the clamp flag reset, and the rebuild decision
+// (displacements relative to particle 0 since xref; list overflow), handed to the
+// conditional graph node `cond` when `use_cond`.
+cudaError_t launch_verlet_check(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm,
+                                cudaGraphConditionalHandle cond, bool use_cond);
 cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64);
 cudaError_t launch_pad_mirror(sd_handle *h, cudaStream_t st, Mirror m);
 // dense.cu
@@ -296,8 +312,17 @@ cudaError_t dense_setup(sd_handle *h);
 cudaError_t launch_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, double *part,
                          const TileWin *win = nullptr);
 // epilogue.cu
+// count_zeroed: the list counter is already zero (launch_build_cells zeroes it), so
+// the pass needs no memset of its own.
 cudaError_t launch_near(sd_handle *h, cudaStream_t st, const double *x64, const void *posm, const double *F64,
-                        const void *frcm);
+                        const void *frcm, bool count_zeroed = false);
+// The two halves of the near pass: the candidate list (cutoff r_near, or r_near + skin
+// for a Verlet list, which is then sorted by partner within each particle) and the
+// FP64 terms of the listed pairs.
+cudaError_t launch_near_collect(sd_handle *h, cudaStream_t st, const double *x64, const void *posm,
+                                const double *F64, const void *frcm, bool count_zeroed, bool verlet_list);
+cudaError_t launch_near_pairs(sd_handle *h, cudaStream_t st, const double *x64, const void *posm, const double *F64,
+                              const void *frcm, bool verlet_step = false);
 cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double *x64, const void *posm,
                             const double *F64, const void *frcm, void *vout, double dt, double *x64n, int row0 = 0,
                             int row1 = -1, const EpiShard *shard = nullptr);

@@ -47,6 +47,7 @@ def test_config_defaults(sd):
     assert cfg.tensor == sd.SD_TENSOR_RPY and cfg.prec == sd.SD_PREC_FP32C
     assert cfg.r_near == 2.5 and cfg.rep_eps == 0.0
     assert list(cfg.box) == [0.0, 0.0, 0.0]
+    assert cfg.verlet_skin == 0.5
     assert "sm_103a" in sd.sd_version()
 
 

@@ -155,3 +155,61 @@ def test_checkpoint_resume_is_exact():
         s2.set_positions(mid)
         s2.step(0.02, 23)
         np.testing.assert_array_equal(s2.get_positions(), full)
+
+
+def _verlet_case(n=1500, seed=61):
+    """A loose packing under strong random forces: relative displacements pass half
+    the skin every few steps, so lists are both reused and rebuilt."""
+    x0, _ = inputs.cube_rsa(n, 0.08, seed)
+    fe = 40.0 * inputs.normal_forces(n, seed + 1)
+    return x0, fe
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_verlet_lists_graph_eager_and_no_reuse_agree(prec):
+    """Neighbour lists reused across steps (graph replays with the conditional rebuild)
+    equal eager steps (which rebuild every step) bit for bit, and agree with lists
+    built every step without a skin to the last bits; against the oracle as usual."""
+    x0, fe = _verlet_case()
+    n, steps, dt = x0.shape[0], 48, 0.01
+    with sd.System(n, prec=prec, gravity=(0, 0, -1.0)) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(dt, steps)                 # three 16-step graph replays
+        a = s.get_positions()
+        s.set_positions(x0)
+        for _ in range(steps):
+            s.step(dt, 1)                 # single-step graph replays
+        b = s.get_positions()
+        s.set_positions(x0)
+        s.profile(True)                   # eager launches
+        s.step(dt, steps)
+        s.profile(False)
+        e = s.get_positions()
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, e)
+    with sd.System(n, prec=prec, gravity=(0, 0, -1.0), verlet_skin=0) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(dt, steps)
+        c = s.get_positions()
+    disp = np.abs(a - x0).max()
+    rel = (a - x0) - (a[0] - x0[0])
+    assert np.linalg.norm(rel, axis=1).max() > 1.0   # relative motion of several half skins
+    assert np.abs(a - c).max() <= (1e-13 if prec == "fp64" else 1e-6) * disp
+    ref = oracle.euler(x0, steps, dt, fext=fe, gravity=(0, 0, -1.0), nthreads=8)
+    assert np.abs(a - ref).max() <= (1e-10 if prec == "fp64" else 1e-5) * np.abs(ref - x0).max()
+
+
+def test_verlet_lists_periodic_box():
+    x0, L = inputs.cube_rsa(2000, 0.08, 71)
+    L = L + 2.5
+    box = (L, L, L)
+    fe = 10.0 * inputs.normal_forces(2000, 72)
+    with sd.System(2000, prec="fp64", box=box) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(0.01, 32)
+        xT = s.get_positions()
+    ref = oracle.euler(x0, 32, 0.01, fext=fe, box=box, nthreads=8)
+    assert np.abs(xT - ref).max() <= 1e-10 * np.abs(ref - x0).max()
