@@ -272,8 +272,10 @@ def run_ours(args):
     world, rank, local = _dist()
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        torch.cuda.set_device(local % torch.cuda.device_count())
+        # NCCL between GPUs; SD_BENCH_BACKEND=gloo runs the same multi-rank logic with the
+        # exchange staged through host memory (e.g. several ranks sharing one GPU)
+        dist.init_process_group(os.environ.get("SD_BENCH_BACKEND", "nccl"))
     dev = torch.cuda.current_device()
     props = torch.cuda.get_device_properties(dev)
     stream = torch.cuda.current_stream(dev)
@@ -382,13 +384,15 @@ def _leg_tile_sharded(args, x, F, stream, world, rank):
     s = sd.System(n, prec="fp32c", stream="torch", torch_allocator=True, device=torch.cuda.current_device())
     s.set_positions(x)
     s.set_forces(F)
-    tile_sharded_steps(s, DT, max(args.warmup, 3), rank, world)
+    import torch.distributed as dist
+    via_host = dist.get_backend() != "nccl"
+    tile_sharded_steps(s, DT, max(args.warmup, 3), rank, world, via_host=via_host)
     torch.cuda.synchronize()
     _barrier(world)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    tile_sharded_steps(s, DT, args.steps, rank, world)
+    tile_sharded_steps(s, DT, args.steps, rank, world, via_host=via_host)
     e1.record(stream)
     torch.cuda.synchronize()
     _barrier(world)
@@ -398,7 +402,8 @@ def _leg_tile_sharded(args, x, F, stream, world, rank):
     ms = t_ms / args.steps
     return {"tile_sharded": {"value": float(n) * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                              "scaling": "strong", "ranks": world, "n": n, "all_pairs_kernel": kind,
-                             "exchange": "NCCL all-gather of 24 B per particle and rank per step"}}
+                             "exchange": "%s all-gather of 24 B per particle and rank per step"
+                                         % ("host-staged gloo" if via_host else "NCCL")}}
 
 
 def run_leg(args):

@@ -47,3 +47,27 @@ def test_single_rank_is_identity():
     import bench
     assert bench._max_over_ranks(3.5, 1) == 3.5
     bench._barrier(1)
+
+
+@pytest.mark.gpu
+def test_bench_two_ranks_sharing_the_gpu():
+    """bench.py launched as the driver launches it for N > 1 (torchrun, one process per
+    rank), here two ranks on one GPU with the exchange staged through host memory
+    (gloo): rank 0 prints one JSON line for both ranks, with the replicas' value and
+    the tile-sharded system's."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SD_BENCH_BACKEND="gloo")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--gpus", "2", "--steps", "3", "--warmup",
+           "3", "--quick"]
+    r = subprocess.run(cmd, cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
+    lines = [json.loads(ln) for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = lines[0]
+    assert line["n_gpus"] == 2 and line["value"] > 0 and line["config"]["parallelism"] == "replicas"
+    ts = line["tile_sharded"]
+    assert ts["ranks"] == 2 and ts["value"] > 0 and ts["scaling"] == "strong"
