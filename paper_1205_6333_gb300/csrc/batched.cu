@@ -579,11 +579,17 @@ __global__ void __launch_bounds__(BT, R == 2 ? SD_BATCH_R2_MINB * 128 / BT : 0) 
 //     complete after its row (every tile that reaches it has run) and is finalised
 //     at once: + F_i (the self term mu_ii = mu0 I), v = mu0 V, x <- x + dt v in FP64.
 //   * r^2 is clamped to (2a)^2; the smallest unclamped r^2 of each tile is tracked,
-//     and a tile that met a pair with r < 2a is walked again: each such pair's
-//     clamped terms (bit-identical, recomputed) are replaced by the exact ones, in
-//     both directions.
+//     and in a tile that met a pair with r < 2a the warp screens the targets of the
+//     lanes that met one against the tile's sources, in parallel, listing each such
+//     pair.  Before a row pair is finalised, the lanes take the listed pairs one each
+//     and replace their clamped terms (bit-identical, recomputed) by the exact ones,
+//     in both directions.
 constexpr int kSymSlots = kMaxCluster;                 // particles per cluster half (8 blocks of 32)
-constexpr size_t kSymWarpSmem = 9 * static_cast<size_t>(kSymSlots) * sizeof(f2);   // 6 staged + 3 sum arrays
+constexpr int kSymFixCap = 128;                       // entries of a warp's list of pairs closer than 2a
+constexpr int kSymTileCap = 16;                       // flagged tiles of a row pair (at most 9 walks)
+constexpr size_t kSymWarpSmem = 9 * static_cast<size_t>(kSymSlots) * sizeof(f2)    // 6 staged + 3 sum arrays
+                                + kSymFixCap * sizeof(int)                           // + the pair list
+                                + kSymTileCap * sizeof(int2);                        // + the flagged tiles
 
 // One pair of each half, both directions, with the unclamped r^2 of each half
 // tracked (the order of operations of pair_sym_f32x2 with CLAMP).
@@ -698,55 +704,175 @@ __device__ __forceinline__ void bsym_tile2(const f2 *__restrict__ S, f2 *__restr
     __syncwarp();
 }
 
-// Second walk of a tile that met a pair closer than 2a: such pairs' clamped terms
-// are replaced by the exact ones (Yamakawa form for RPY), in both directions.  The
-// target side goes to FIX (this lane's target), the source side to the shared sums
-// (distinct sources per step; steps ordered by __syncwarp).
-template <int TENSOR, bool DIAG>
-__device__ void bsym_fix(const f2 *__restrict__ S, f2 *__restrict__ SUM, int p, int q, int lane, const int (&nh)[2],
-                         const PairConst &pc, float (&FIX)[2][3], bool &coincident) {
+// Pairs closer than 2a.  The walk only records the tiles that met one (with the
+// lanes that did); one out-of-line call per row pair (bsym_rowfix) screens those
+// tiles and fixes the pairs found, so the walk's code stays as it would be without
+// them.
+// The exact pair term (overlap branch included) for the fix below, without divides:
+// 1/r from one SFU reciprocal square root.  inv32a = 1 / (32 a).
+template <int TENSOR>
+__device__ __forceinline__ void exact_pair_sfu(float dx, float dy, float dz, float fx, float fy, float fz,
+                                               const PairConst &c, float inv32a, float &ox, float &oy, float &oz,
+                                               bool &coincident) {
+    const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    if (r2 == 0.0f) {
+        if (TENSOR != T_RPY) coincident = true;
+        ox = TENSOR == T_RPY ? fx : 0.0f;   // T^(0) = I for the RPY overlap form
+        oy = TENSOR == T_RPY ? fy : 0.0f;
+        oz = TENSOR == T_RPY ? fz : 0.0f;
+        return;
+    }
+    const float ri = rsqrt_sfu(r2), ri2 = __fmul_rn(ri, ri);
+    float A, B;
+    if (TENSOR == T_RPY && r2 < c.r2min_f) {   // r < 2a: 1 - 9 r / (32 a), 3 / (32 a r)
+        A = __fmaf_rn(-9.0f * inv32a, __fmul_rn(r2, ri), 1.0f);
+        B = __fmul_rn(3.0f * inv32a, ri);
+    } else if (TENSOR == T_OSEEN) {
+        A = __fmul_rn(c.c1_f, ri);
+        B = __fmul_rn(A, ri2);
+    } else {
+        A = __fmul_rn(ri, __fmaf_rn(c.c3_f, ri2, c.c1_f));
+        B = __fmul_rn(__fmul_rn(ri, ri2), __fmaf_rn(c.m3c3_f, ri2, c.c1_f));
+    }
+    const float s = __fmul_rn(B, __fmaf_rn(dz, fz, __fmaf_rn(dy, fy, __fmul_rn(dx, fx))));
+    ox = __fmaf_rn(s, dx, __fmul_rn(A, fx));
+    oy = __fmaf_rn(s, dy, __fmul_rn(A, fy));
+    oz = __fmaf_rn(s, dz, __fmul_rn(A, fz));
+}
+
+// Adds v (3 dims, half h) to the shared sum of slot `to` for every lane whose `on` is
+// set: in parallel when the lanes' slots are distinct, else one entry at a time in
+// lane order (each sum by the lane that owns its slot, slot mod 32).
+__device__ __forceinline__ void bsym_add_sums(f2 *__restrict__ SUM, bool on, int to, int h, const float (&v)[3],
+                                              int lane) {
+    const unsigned grp = __match_any_sync(0xffffffffu, on ? to : -1 - lane);
+    if (__all_sync(0xffffffffu, __popc(grp) == 1)) {
+        if (on)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) SUM[d * kSymSlots + to] = add_half(SUM[d * kSymSlots + to], h, v[d]);
+    } else {
+        unsigned act = __ballot_sync(0xffffffffu, on);
+        while (act) {
+            const int u = __ffs(act) - 1;
+            act &= act - 1;
+            const int tu = __shfl_sync(0xffffffffu, to, u), hu = __shfl_sync(0xffffffffu, h, u);
+            float vu[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) vu[d] = __shfl_sync(0xffffffffu, v[d], u);
+            if (lane == (tu & 31))
+#pragma unroll
+                for (int d = 0; d < 3; ++d) SUM[d * kSymSlots + tu] = add_half(SUM[d * kSymSlots + tu], hu, vu[d]);
+        }
+    }
+    __syncwarp();
+}
+
+// Fix (bsym_fix_list): in place of the clamped terms of the nfix listed pairs, the
+// exact ones (Yamakawa form for RPY), in both directions.  Each lane computes the
+// corrections of one entry: the exact term minus the clamped one, the latter
+// recomputed bit for bit.  The target sides are then added to the targets' shared
+// sums, then the source sides to the sources' (bsym_add_sums).
+template <int TENSOR>
+__device__ __forceinline__ void bsym_fix_list(const f2 *__restrict__ S, f2 *__restrict__ SUM,
+                                              const int *__restrict__ FL, int nfix, int lane, const PairConst &pc,
+                                              int *err) {
     constexpr int TD = (TENSOR == T_OSEEN) ? T_OSEEN : T_RP;
-    constexpr int M0 = DIAG ? 1 : 0, M1 = DIAG ? 16 : 31;
-    const int i = 32 * p + lane;
-    for (int m = M0; m <= M1; ++m) {
-        const int j = 32 * q + ((lane + m) & 31);
-        if (!(DIAG && m == 16 && lane >= 16)) {
-            for (int h = 0; h < 2; ++h) {
-                if (i >= nh[h] || j >= nh[h]) continue;
-                const float4 pi = make_float4(half_of(S[i], h), half_of(S[kSymSlots + i], h),
-                                              half_of(S[2 * kSymSlots + i], h), 0.0f);
-                const float4 fi = make_float4(half_of(S[3 * kSymSlots + i], h), half_of(S[4 * kSymSlots + i], h),
-                                              half_of(S[5 * kSymSlots + i], h), 0.0f);
-                const float4 pj = make_float4(half_of(S[j], h), half_of(S[kSymSlots + j], h),
-                                              half_of(S[2 * kSymSlots + j], h), 0.0f);
-                const float4 fj = make_float4(half_of(S[3 * kSymSlots + j], h), half_of(S[4 * kSymSlots + j], h),
-                                              half_of(S[5 * kSymSlots + j], h), 0.0f);
-                const float dx = __fsub_rn(pi.x, pj.x), dy = __fsub_rn(pi.y, pj.y), dz = __fsub_rn(pi.z, pj.z);
-                if (!(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < pc.r2min_f)) continue;
-                float cx = 0.0f, cy = 0.0f, cz = 0.0f, ex, ey, ez;
-                pair_f32<TD, true>(pi.x, pi.y, pi.z, pj, fj, pc, cx, cy, cz);
-                exact_pair<TENSOR, float>(dx, dy, dz, fj.x, fj.y, fj.z, pc, ex, ey, ez, coincident);
-                FIX[h][0] = __fadd_rn(FIX[h][0], __fsub_rn(ex, cx));
-                FIX[h][1] = __fadd_rn(FIX[h][1], __fsub_rn(ey, cy));
-                FIX[h][2] = __fadd_rn(FIX[h][2], __fsub_rn(ez, cz));
-                float bx = 0.0f, by = 0.0f, bz = 0.0f;
-                pair_f32<TD, true>(pj.x, pj.y, pj.z, pi, fi, pc, bx, by, bz);
-                exact_pair<TENSOR, float>(-dx, -dy, -dz, fi.x, fi.y, fi.z, pc, ex, ey, ez, coincident);
-                SUM[j] = add_half(SUM[j], h, __fsub_rn(ex, bx));
-                SUM[kSymSlots + j] = add_half(SUM[kSymSlots + j], h, __fsub_rn(ey, by));
-                SUM[2 * kSymSlots + j] = add_half(SUM[2 * kSymSlots + j], h, __fsub_rn(ez, bz));
+    const float inv32a = 1.0f / (32.0f * static_cast<float>(pc.a));
+    bool coincident = false;
+    __syncwarp();   // the list and the walks' shared sums are visible
+    for (int e0 = 0; e0 < nfix; e0 += 32) {
+        float ct[3] = {0.0f, 0.0f, 0.0f}, cs[3] = {0.0f, 0.0f, 0.0f};
+        const bool on = e0 + lane < nfix;
+        int i = 0, k = 0, h = 0;
+        if (on) {
+            const int ent = FL[e0 + lane];
+            i = ent >> 9;
+            k = (ent >> 1) & 255;
+            h = ent & 1;
+            const float4 pi = make_float4(half_of(S[i], h), half_of(S[kSymSlots + i], h),
+                                          half_of(S[2 * kSymSlots + i], h), 0.0f);
+            const float4 fi = make_float4(half_of(S[3 * kSymSlots + i], h), half_of(S[4 * kSymSlots + i], h),
+                                          half_of(S[5 * kSymSlots + i], h), 0.0f);
+            const float4 pj = make_float4(half_of(S[k], h), half_of(S[kSymSlots + k], h),
+                                          half_of(S[2 * kSymSlots + k], h), 0.0f);
+            const float4 fj = make_float4(half_of(S[3 * kSymSlots + k], h), half_of(S[4 * kSymSlots + k], h),
+                                          half_of(S[5 * kSymSlots + k], h), 0.0f);
+            const float dx = __fsub_rn(pi.x, pj.x), dy = __fsub_rn(pi.y, pj.y), dz = __fsub_rn(pi.z, pj.z);
+            float cx = 0.0f, cy = 0.0f, cz = 0.0f, ex, ey, ez;
+            pair_f32<TD, true>(pi.x, pi.y, pi.z, pj, fj, pc, cx, cy, cz);
+            exact_pair_sfu<TENSOR>(dx, dy, dz, fj.x, fj.y, fj.z, pc, inv32a, ex, ey, ez, coincident);
+            ct[0] = __fsub_rn(ex, cx);
+            ct[1] = __fsub_rn(ey, cy);
+            ct[2] = __fsub_rn(ez, cz);
+            float bx = 0.0f, by = 0.0f, bz = 0.0f;
+            pair_f32<TD, true>(pj.x, pj.y, pj.z, pi, fi, pc, bx, by, bz);
+            exact_pair_sfu<TENSOR>(-dx, -dy, -dz, fi.x, fi.y, fi.z, pc, inv32a, ex, ey, ez, coincident);
+            cs[0] = __fsub_rn(ex, bx);
+            cs[1] = __fsub_rn(ey, by);
+            cs[2] = __fsub_rn(ez, bz);
+        }
+        bsym_add_sums(SUM, on, i, h, ct, lane);
+        bsym_add_sums(SUM, on, k, h, cs, lane);
+    }
+    if (coincident) atomicOr(err, DEV_ERR_COINCIDENT);
+}
+
+// Screening, then fix (bsym_rowfix), for the row blocks p, p + 1: TL holds ntl flagged
+// walks, each (source block q | rows << 8 | diagonal << 10, lanes).  rows = r for the
+// tile (p + r, q) alone, 2 for the walk of both rows.  For each lane L that met a pair
+// closer than 2a the warp tests L's target against the tile's 32 sources, one
+// source per lane: the walk's r^2, recomputed bit for bit, and only the pairs the
+// walk gave lane L.  Each pair found goes to the warp's list FL as (target slot,
+// source slot, half); a list that could overflow is fixed and emptied first.
+template <int TENSOR>
+__device__ __noinline__ void bsym_rowfix(const f2 *__restrict__ S, f2 *__restrict__ SUM, int *__restrict__ FL,
+                                         const int2 *__restrict__ TL, int ntl, int p, int lane, int nh0, int nh1,
+                                         const PairConst &pc, int *err) {
+    __syncwarp();   // the recorded walks are visible
+    const unsigned below = (1u << lane) - 1u;
+    int nfix = 0;
+    for (int t = 0; t < ntl; ++t) {
+        const int2 w = TL[t];
+        const int q = w.x & 255, rows = (w.x >> 8) & 3;
+        const bool diag = (w.x >> 10) & 1;
+        const int j = 32 * q + lane;
+        const f2 PX = S[j], PY = S[kSymSlots + j], PZ = S[2 * kSymSlots + j];
+        for (int r = (rows == 1 ? 1 : 0); r <= (rows == 0 ? 0 : 1); ++r) {
+            unsigned who = static_cast<unsigned>(w.y);
+            while (who) {
+                const int L = __ffs(who) - 1;
+                who &= who - 1;
+                if (nfix > kSymFixCap - 64) {   // room for one target's 32 sources x 2 halves
+                    bsym_fix_list<TENSOR>(S, SUM, FL, nfix, lane, pc, err);
+                    nfix = 0;
+                }
+                const int i = 32 * (p + r) + L;
+                const int m = (lane - L) & 31;   // the step of the walk at which lane L met this lane's source
+                const bool mine = !diag || (m >= 1 && m <= 15) || (m == 16 && L < 16);
+                const f2 dx = sub2(S[i], PX), dy = sub2(S[kSymSlots + i], PY), dz = sub2(S[2 * kSymSlots + i], PZ);
+                const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                float ra, rb;
+                upk2(r2, ra, rb);
+                const unsigned h0 = __ballot_sync(0xffffffffu, mine && i < nh0 && j < nh0 && ra < pc.r2min_f);
+                if ((h0 >> lane) & 1u) FL[nfix + __popc(h0 & below)] = (i << 9) | (j << 1);
+                nfix += __popc(h0);
+                const unsigned h1 = __ballot_sync(0xffffffffu, mine && i < nh1 && j < nh1 && rb < pc.r2min_f);
+                if ((h1 >> lane) & 1u) FL[nfix + __popc(h1 & below)] = (i << 9) | (j << 1) | 1;
+                nfix += __popc(h1);
             }
         }
-        __syncwarp();
     }
+    if (nfix) bsym_fix_list<TENSOR>(S, SUM, FL, nfix, lane, pc, err);
 }
 
 template <int TENSOR>
-__global__ void __launch_bounds__(128) batched_sym_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(128, 3) batched_sym_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    f2 *S = reinterpret_cast<f2 *>(smem) + static_cast<size_t>(wid) * 9 * kSymSlots;   // x y z Fx Fy Fz
+    f2 *S = reinterpret_cast<f2 *>(smem + static_cast<size_t>(wid) * kSymWarpSmem);    // x y z Fx Fy Fz
     f2 *SUM = S + 6 * kSymSlots;                                                         // sums x y z
+    int *FL = reinterpret_cast<int *>(SUM + 3 * kSymSlots);                              // pair list
+    int2 *TL = reinterpret_cast<int2 *>(FL + kSymFixCap);                                // flagged walks
     const float4 *frcm = static_cast<const float4 *>(a.frcm);
     PairConst2 c2{};
     c2.c1 = pk2(a.pc.c1_f, a.pc.c1_f);
@@ -785,7 +911,6 @@ __global__ void __launch_bounds__(128) batched_sym_kernel(BatchArgs a) {
             for (int d = 0; d < 3; ++d) SUM[d * kSymSlots + k] = 0ull;
         }
         __syncwarp();
-        bool coincident = false;
         // the block rows in pairs (p, p + 1): their tiles against the blocks q > p + 1
         // share each walk of q (bsym_tile2); the rest run one row at a time
         for (int p = 0; p < nb; p += 2) {
@@ -795,9 +920,8 @@ __global__ void __launch_bounds__(128) batched_sym_kernel(BatchArgs a) {
                 const int i = 32 * (p + r) + lane;   // (a padding row when !two: never used)
                 for (int d = 0; d < 6; ++d) T[r][d] = S[d * kSymSlots + i];
             }
-            // (hi, lo) sums of the rows' targets [row][half][dim], and exact-term fixes
+            // (hi, lo) sums of the rows' targets [row][half][dim]
             float hs[2][2][3] = {}, ls[2][2][3] = {};
-            float FIX[2][2][3] = {};
             auto fold = [&](int r, const f2 (&A)[3]) {
                 for (int d = 0; d < 3; ++d) {
                     float v0, v1;
@@ -805,6 +929,11 @@ __global__ void __launch_bounds__(128) batched_sym_kernel(BatchArgs a) {
                     fold2(hs[r][0][d], ls[r][0][d], v0);
                     fold2(hs[r][1][d], ls[r][1][d], v1);
                 }
+            };
+            int ntl = 0;   // walks of rows p, p + 1 that met a pair closer than 2a
+            auto record = [&](int rows, int q, bool diag, unsigned who) {
+                if (lane == 0) TL[ntl] = make_int2(q | (rows << 8) | (diag ? 1 << 10 : 0), static_cast<int>(who));
+                ++ntl;
             };
             auto one = [&](int r, int q) {   // tile (p + r, q) alone
                 f2 A[3] = {0ull, 0ull, 0ull};
@@ -816,12 +945,8 @@ __global__ void __launch_bounds__(128) batched_sym_kernel(BatchArgs a) {
                     bsym_tile<TENSOR, false>(S, SUM, q, lane, T[r][0], T[r][1], T[r][2], T[r][3], T[r][4], T[r][5],
                                              c2, A[0], A[1], A[2], mn0, mn1);
                 fold(r, A);
-                if (__any_sync(0xffffffffu, fminf(mn0, mn1) < c2.r2min)) {   // rare: pairs closer than 2a
-                    if (q == p + r)
-                        bsym_fix<TENSOR, true>(S, SUM, p + r, q, lane, nh, a.pc, FIX[r], coincident);
-                    else
-                        bsym_fix<TENSOR, false>(S, SUM, p + r, q, lane, nh, a.pc, FIX[r], coincident);
-                }
+                const unsigned who = __ballot_sync(0xffffffffu, fminf(mn0, mn1) < c2.r2min);
+                if (who) record(r, q, q == p + r, who);   // rare: pairs closer than 2a
             };
             one(0, p);
             if (two) {
@@ -838,11 +963,10 @@ __global__ void __launch_bounds__(128) batched_sym_kernel(BatchArgs a) {
                 bsym_tile2<TENSOR>(S, SUM, q, lane, T[0], T[1], c2, A0, A1, mn0, mn1);
                 fold(0, A0);
                 fold(1, A1);
-                if (__any_sync(0xffffffffu, fminf(mn0, mn1) < c2.r2min)) {
-                    bsym_fix<TENSOR, false>(S, SUM, p, q, lane, nh, a.pc, FIX[0], coincident);
-                    bsym_fix<TENSOR, false>(S, SUM, p + 1, q, lane, nh, a.pc, FIX[1], coincident);
-                }
+                const unsigned who = __ballot_sync(0xffffffffu, fminf(mn0, mn1) < c2.r2min);
+                if (who) record(2, q, false, who);   // (a lane's flag covers both of its targets)
             }
+            if (ntl) bsym_rowfix<TENSOR>(S, SUM, FL, TL, ntl, p, lane, nh[0], nh[1], a.pc, a.err);
             // rows p (and p + 1) are complete: finalise their particles
             for (int r = 0; r < (two ? 2 : 1); ++r)
             for (int h = 0; h < 2; ++h) {
@@ -852,7 +976,6 @@ __global__ void __launch_bounds__(128) batched_sym_kernel(BatchArgs a) {
                 for (int d = 0; d < 3; ++d) {
                     float hh = hs[r][h][d], ll = ls[r][h][d];
                     fold2(hh, ll, half_of(SUM[d * kSymSlots + i], h));
-                    fold2(hh, ll, FIX[r][h][d]);
                     fold2(hh, ll, half_of(S[(3 + d) * kSymSlots + i], h));   // mu_ii F_i / mu0 = F_i
                     V[d] = __fadd_rn(hh, ll);
                 }
@@ -870,7 +993,6 @@ __global__ void __launch_bounds__(128) batched_sym_kernel(BatchArgs a) {
                                         static_cast<float>(nz - a.x64[3 * an + 2]), 0.0f);
             }
         }
-        if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
         __syncwarp();   // the warp's shared memory is free for the next task
     }
 }

@@ -226,3 +226,48 @@ def test_batched_symmetric_kernel_overlaps_and_coincident(tensor):
         a, e = off[c], off[c + 1]
         disp = max(np.abs(ref[a:e] - x[a:e]).max(), 1e-300)
         assert np.abs(got[a:e] - ref[a:e]).max() <= 1e-5 * disp, (c, sizes[c])
+
+
+def _crowded_cluster(n, side, dmin, rng):
+    """n centres uniform in a cube of the given side, none closer than dmin to another
+    (random sequential addition): every sphere overlaps several others."""
+    pts = []
+    while len(pts) < n:
+        q = rng.uniform(0.0, side, 3)
+        if all(np.sum((q - p) ** 2) >= dmin * dmin for p in pts):
+            pts.append(q)
+    return np.array(pts)
+
+
+@pytest.mark.parametrize("tensor", ["rpy", "oseen"])
+def test_batched_symmetric_kernel_crowded_clusters(tensor):
+    """The symmetric kernel pinned on crowded clusters (about eight overlapping
+    partners per sphere, none closer than 0.3a): most tiles meet pairs closer than 2a,
+    many lanes of a warp at once and several pairs per target in one tile, in both
+    halves of the packed registers, in diagonal and off-diagonal tiles; the two halves
+    pair crowded with crowded and crowded with dilute clusters.  3 steps against the
+    oracle."""
+    rng = np.random.default_rng(21)
+    sizes = [256, 256, 250, 249, 200, 64, 33, 32, 31, 2]
+    xs = []
+    for c, n in enumerate(sizes):
+        if c in (3, 6):   # dilute partners for a crowded cluster of (nearly) the same size
+            p, _ = inputs.cube_rsa(n, 0.05, int(rng.integers(1 << 30)))
+        else:
+            p = _crowded_cluster(n, (n / 0.25) ** (1.0 / 3.0), 0.3, rng)
+        xs.append(p)
+    x = np.concatenate(xs)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    F = inputs.normal_forces(x.shape[0], 22)
+    ref = _oracle_batch(x, off, F, 3, 0.002, tensor)
+    b = sd.Batch(off, tensor=tensor)
+    b.set_shape(next(k for k, sh in enumerate(b.shapes()) if sh["targets_per_thread"] == 0))
+    b.set_positions(x)
+    b.set_forces(F)
+    b.step(0.002, 3)
+    got = b.get_positions()
+    b.close()
+    for c in range(len(sizes)):
+        a, e = off[c], off[c + 1]
+        disp = max(np.abs(ref[a:e] - x[a:e]).max(), 1e-300)
+        assert np.abs(got[a:e] - ref[a:e]).max() <= 1e-5 * disp, (c, sizes[c])
