@@ -131,60 +131,21 @@ static sd_status launch_check(cudaError_t e, const char *what) {
 
 // ---------------------------------------------------------------- one Euler step
 
-// The neighbour-list rebuild of a Verlet step: cell list (and xref = x_in), the
-// candidate list within r_near + skin, sorted by partner.
-static cudaError_t verlet_rebuild(sd_handle *h, cudaStream_t st, const double *x_in) {
-    cudaError_t e = launch_build_cells(h, st, x_in, h->posm, h->xref);
-    if (e == cudaSuccess) e = launch_near_collect(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true, true);
-    return e;
-}
-
-// A Verlet step (constant forces): check kernel (mirror, rebuild decision), the
-// rebuild only when needed, FP64 terms of the listed pairs (which clear the request),
-// all-pairs kernel, Euler epilogue.  Under graph capture the rebuild is the body of a
-// conditional node set by the check kernel; launched eagerly its kernels read the
-// request and return at once without one.  A fresh and a reused list give the same
-// result bit for bit: each particle's list is sorted by partner and entries beyond
-// r_near add exact zeros.
+// A Verlet step (constant forces): the check kernel (mirror, rebuild decision), the
+// rebuild kernels (cell list and xref = x_in; the candidate list within r_near + skin,
+// each particle's run sorted by partner), which read the decision and return at once
+// when no rebuild is due, the FP64 terms of the listed pairs (which clear the
+// request), the all-pairs kernel and the Euler epilogue.  A fresh and a reused list
+// give the same result bit for bit: each particle's list is sorted by partner and
+// entries beyond r_near add exact zeros.
 static cudaError_t launch_verlet_step(sd_handle *h, cudaStream_t st, double dt, const double *x_in, double *x_out) {
-    cudaError_t e = cudaSuccess;
-    if (h->capturing) {
-        cudaStreamCaptureStatus cs;
-        cudaGraph_t g = nullptr;
-        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g);
-        cudaGraphConditionalHandle cond = 0;
-        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault);
-        if (e == cudaSuccess) e = launch_verlet_check(h, st, x_in, h->posm, cond, true);
-        const cudaGraphNode_t *deps = nullptr;
-        size_t ndeps = 0;
-        if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &ndeps);
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = cond;
-        cp.conditional.type = cudaGraphCondTypeIf;
-        cp.conditional.size = 1;
-        cudaGraphNode_t node = nullptr;
-        if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp);
-        if (e == cudaSuccess) {
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            e = cudaStreamBeginCaptureToGraph(h->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                cudaError_t eb = verlet_rebuild(h, h->cap2, x_in);
-                cudaGraph_t out = nullptr;
-                e = cudaStreamEndCapture(h->cap2, &out);
-                if (eb != cudaSuccess) e = eb;
-            }
-        }
-        if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-        if (e == cudaSuccess) e = launch_near_pairs(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true);
-    } else {   // (profiler event pairs do not nest: cells, then the near pass)
-        e = launch_verlet_check(h, st, x_in, h->posm, 0, false);
-        if (e == cudaSuccess) e = launch_build_cells(h, st, x_in, h->posm, h->xref);
-        prof_begin(h, SD_KERNEL_NEAR, st);
-        if (e == cudaSuccess) e = launch_near_collect(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true, true);
-        if (e == cudaSuccess) e = launch_near_pairs(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true);
-        prof_end(h, SD_KERNEL_NEAR, st);
-    }
+    // (profiler event pairs do not nest: cells, then the near pass)
+    cudaError_t e = launch_verlet_check(h, st, x_in, h->posm);
+    if (e == cudaSuccess) e = launch_build_cells(h, st, x_in, h->posm, h->xref);
+    prof_begin(h, SD_KERNEL_NEAR, st);
+    if (e == cudaSuccess) e = launch_near_collect(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true, true);
+    if (e == cudaSuccess) e = launch_near_pairs(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true);
+    prof_end(h, SD_KERNEL_NEAR, st);
     if (e == cudaSuccess) e = launch_dense(h, st, h->posm, h->frcm, h->part);
     if (e == cudaSuccess)
         e = launch_epilogue(h, st, OUT_EULER, x_in, h->posm.aos, h->F64, h->frcm.aos, nullptr, dt, x_out);
@@ -480,7 +441,6 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return fail(SD_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
     e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking);
     if (e != cudaSuccess) return fail(SD_ERR_CUDA, "stream creation");
 
     const size_t n3 = 3 * static_cast<size_t>(std::max(h->n, 1));
@@ -587,7 +547,6 @@ void sd_destroy(sd_handle *h) {
                     h->near_ent, h->near_out, h->near_n, h->near_off, h->near_cnt, h->vlag, h->xref, h->d_vl};
     for (void *p : bufs) dfree(h, p);
     if (h->cap) cudaStreamDestroy(h->cap);
-    if (h->cap2) cudaStreamDestroy(h->cap2);
     delete h;
 }
 

@@ -76,13 +76,12 @@ cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, M
 // particle's displacement since the build, relative to particle 0's, is below
 // skin / 2 (pair distances then changed by less than the skin; a uniform
 // translation moves no pair).  A list that overflowed (its particles corrected in
-// place at build time) is rebuilt every step.  The last block to finish hands the
-// decision to the conditional graph node.
+// place at build time) is rebuilt every step.  The rebuild kernels that follow read
+// the decision (vl[0]).
 template <typename V4>
 __global__ void verlet_check_kernel(const double *__restrict__ x, const double *__restrict__ xref, int n, int npad,
                                     Box b, double half_skin2, V4 *__restrict__ m, float *__restrict__ soa, int *flag,
-                                    int *vl, const unsigned long long *near_n, int cap,
-                                    cudaGraphConditionalHandle cond, int use_cond, int *err) {
+                                    int *vl, const unsigned long long *near_n, int cap, int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
@@ -97,21 +96,9 @@ __global__ void verlet_check_kernel(const double *__restrict__ x, const double *
             if (*near_n > static_cast<unsigned long long>(cap)) atomicOr(&vl[0], 1);
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const int done = atomicAdd(&vl[1], 1);
-        if (done == static_cast<int>(gridDim.x) - 1) {   // every block's decision is in
-            __threadfence();
-            const int rebuild = atomicOr(&vl[0], 0);
-            vl[1] = 0;
-            if (use_cond) cudaGraphSetConditional(cond, rebuild != 0 ? 1u : 0u);
-        }
-    }
 }
 
-cudaError_t launch_verlet_check(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm,
-                                cudaGraphConditionalHandle cond, bool use_cond) {
+cudaError_t launch_verlet_check(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm) {
     if (h->n == 0) return cudaSuccess;
     const int nb = (h->n + 255) / 256;
     const double hs2 = 0.25 * h->skin * h->skin;
@@ -119,11 +106,11 @@ cudaError_t launch_verlet_check(sd_handle *h, cudaStream_t st, const double *x64
     if (h->mode == MODE_FP64)
         verlet_check_kernel<dbl4><<<nb, 256, 0, st>>>(x64, h->xref, h->n, h->npad, h->cl.box, hs2,
                                                       static_cast<dbl4 *>(posm.aos), posm.soa, h->d_flag, h->d_vl,
-                                                      h->near_n, h->near_cap, cond, use_cond ? 1 : 0, h->d_err);
+                                                      h->near_n, h->near_cap, h->d_err);
     else
         verlet_check_kernel<float4><<<nb, 256, 0, st>>>(x64, h->xref, h->n, h->npad, h->cl.box, hs2,
                                                         static_cast<float4 *>(posm.aos), posm.soa, h->d_flag, h->d_vl,
-                                                        h->near_n, h->near_cap, cond, use_cond ? 1 : 0, h->d_err);
+                                                        h->near_n, h->near_cap, h->d_err);
     prof_end(h, SD_KERNEL_CELLS, st);
     ++h->launches;
     return cudaGetLastError();
@@ -369,8 +356,8 @@ __global__ void cells_sort_kernel(const int *__restrict__ start, int *__restrict
 cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm, double *xref) {
     CellList &c = h->cl;
     if (h->n == 0) return cudaSuccess;
-    // a Verlet build runs only when the step's check asked for it (graph: the conditional
-    // node; launched eagerly: every kernel reads the request and returns at once without it)
+    // a Verlet build runs only when the step's check asked for it: every kernel reads
+    // the request and returns at once without it
     const int *gate = xref ? h->d_vl : nullptr;
     prof_begin(h, SD_KERNEL_CELLS, st);
     // (the bucket counters are zero: zeroed at creation, counted back to zero by

@@ -267,6 +267,22 @@ __global__ void __launch_bounds__(128) near_collect_kernel(NearArgs a) {
         if (active && sub == 0) a.ncnt[i] = -1;
         near_direct<TENSOR, MODE>(a, i, sub, active);
     }
+    // A Verlet list (a.gate set): each particle's run in ascending partner index, so
+    // that the epilogue adds a particle's near terms in an order that does not depend
+    // on when, or from which cell list, the list was built (entries beyond r_near add
+    // exact zeros).  The run was written by this warp's lanes of the particle.
+    __syncwarp();
+    if (a.gate && fits && active && sub == 0 && pcnt > 1) {
+        for (int p = pfirst + 1; p < pfirst + pcnt; ++p) {
+            const int2 v = a.ent[p];
+            int q = p - 1;
+            while (q >= pfirst && a.ent[q].y > v.y) {
+                a.ent[q + 1] = a.ent[q];
+                --q;
+            }
+            a.ent[q + 1] = v;
+        }
+    }
 }
 
 // Step 2: one thread per listed pair: the FP64 test r < r_near, the flags, and the
@@ -298,29 +314,6 @@ __global__ void __launch_bounds__(128) near_pair_kernel(NearArgs a) {
     }
     if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
     if (close) atomicOr(a.flag, 1);
-}
-
-// A Verlet list: each particle's run of entries in ascending partner index, so that the
-// epilogue adds a particle's near terms in an order that does not depend on when, or
-// from which cell list, the list was built (entries beyond r_near add exact zeros).
-__global__ void near_sort_kernel(int2 *__restrict__ ent, const int *__restrict__ noff, const int *__restrict__ ncnt,
-                                 int n, int cap, const int *gate) {
-    if (gate && *gate == 0) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int cnt = ncnt[i];
-    if (cnt < 2) return;   // (cnt < 0: corrected in place)
-    const int e0 = noff[i];
-    if (e0 < 0 || e0 + cnt > cap) return;
-    for (int p = e0 + 1; p < e0 + cnt; ++p) {
-        const int2 v = ent[p];
-        int q = p - 1;
-        while (q >= e0 && ent[q].y > v.y) {
-            ent[q + 1] = ent[q];
-            --q;
-        }
-        ent[q + 1] = v;
-    }
 }
 
 template <int TENSOR, int MODE>
@@ -382,10 +375,7 @@ cudaError_t launch_near_collect(sd_handle *h, cudaStream_t st, const double *x64
     }
     SD_NEAR_DISPATCH(near_launch_collect, nb);
     ++h->launches;
-    if (verlet_list) {
-        near_sort_kernel<<<(h->n + 127) / 128, 128, 0, st>>>(a.ent, a.noff, a.ncnt, h->n, a.cap, a.gate);
-        ++h->launches;
-    } else if (h->verlet) {
+    if (!verlet_list && h->verlet) {
         // a list the steps cannot reuse (no skin, unsorted): their next step rebuilds
         cudaError_t e = cudaMemsetAsync(h->d_vl, 0xff, sizeof(int), st);
         if (e != cudaSuccess) return e;

@@ -264,8 +264,7 @@ struct sd_handle {
     bool verlet = false;
     double skin = 0.0;
     double *xref = nullptr;        // [n*3] positions of the last build
-    int *d_vl = nullptr;           // [0] rebuild request, [1] blocks done (check kernel)
-    cudaStream_t cap2 = nullptr;   // captures the rebuild body of a conditional graph node
+    int *d_vl = nullptr;           // [0] rebuild request
 };
 
 namespace sd {
@@ -301,10 +300,8 @@ cudaError_t launch_stage_forces(sd_handle *h, cudaStream_t st, const void *src, 
 cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm,
                                double *xref = nullptr);
 // Verlet step: the mirror of x64, the clamp flag reset, and the rebuild decision
-// (displacements relative to particle 0 since xref; list overflow), handed to the
-// conditional graph node `cond` when `use_cond`.
-cudaError_t launch_verlet_check(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm,
-                                cudaGraphConditionalHandle cond, bool use_cond);
+// (displacements relative to particle 0 since xref; list overflow) in d_vl[0].
+cudaError_t launch_verlet_check(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm);
 cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64);
 cudaError_t launch_pad_mirror(sd_handle *h, cudaStream_t st, Mirror m);
 // dense.cu
