@@ -3,8 +3,9 @@
 One JSON line on rank 0.  A step is one explicit Euler step (Sec. 3.1) of the
 N = 65,536 system at volume fraction 0.05 with per-particle N(0,1) forces,
 float32 inputs, RPY tensor, FP32-compensated pair sums, FP64 positions:
-cell-list build + FP32 mirror, all-pairs kernel, FP64 near/self terms and split
-reduction, Euler update.  value = N^2 pair interactions per second (self pairs
+Verlet-list check + FP32 mirror, then the all-pairs kernel beside the list rebuild
+(when due) and the FP64 near terms, then the split reduction with the self term
+and the Euler update.  value = N^2 pair interactions per second (self pairs
 included, as the paper counts them).
 
 Extra legs on rank 0 (reported in the same line): the plain FP64 GPU path on the
@@ -226,7 +227,8 @@ def cpu_baseline(x, F, target_s=10.0):
 def _config(L, world):
     return {"workload": "rpy_euler_step_N65536_phi0.05_cube_fp32c", "n": N_MAIN, "phi": PHI,
             "box_side": L, "tensor": "rpy", "precision": "fp32 pair terms, compensated sums, fp64 state",
-            "step": "cells+mirror, all-pairs, fp64 near/self + reduction, Euler", "dt": DT,
+            "step": "Verlet check + mirror; all-pairs kernel beside (list rebuild when due, fp64 near terms); "
+                    "reduction + self, Euler", "dt": DT,
             "l2": "flushed (512 MiB write) before every timed step",
             "parallelism": "replicas" if world > 1 else "single"}
 
@@ -363,7 +365,10 @@ def run_ours(args):
                      "peak_source": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz, %s)"
                                     % (sms, FP32_LANES_PER_SM, peaks.get("sm_max_mhz", 2070.0), peak_src)},
         "kernel_ms_per_step": {"dense": dense_ms / args.steps, "near": near_ms / args.steps,
-                               "epilogue": epi_ms / args.steps, "cells": cells_ms / args.steps},
+                               "epilogue": epi_ms / args.steps, "cells": cells_ms / args.steps,
+                               "note": "CUDA-event ranges per kernel class; with Verlet lists the rebuild "
+                                       "(cells) and the near pass run on a side stream beside the all-pairs "
+                                       "kernel, and their ranges include time spent waiting for free SMs"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 24 * n},
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -417,8 +422,8 @@ def run_leg(args):
 
 def legs(args, x, F, stream, flush, only=None, workloads=True):
     """FP64 path, batched workload, Oseen variant and the CPU oracle baseline (rank 0
-    only); with `workloads` (single-GPU runs) also the trajectory drift of workload 3
-    and the adjoint of workload 5."""
+    only); with `workloads` (single-GPU runs) also the trajectory drift of workload 3,
+    the adjoint of workload 5 and the N sweep 2^10 .. 2^18."""
     out = {}
     if only in (None, "fp64"):
         out.update(_leg_fp64(args, x, F, stream, flush))
@@ -429,6 +434,7 @@ def legs(args, x, F, stream, flush, only=None, workloads=True):
     if only is None and workloads:
         out.update(leg_drift(args))
         out.update(leg_adjoint(args))
+        out.update(leg_sweep(args, forced=False))
     if only is None:
         out["cpu_baseline"] = cpu_baseline(x, F, target_s=args.cpu_seconds)
     return out
@@ -477,10 +483,10 @@ def _leg_oseen(args, x, F, stream, flush):
                       "flops_per_pair": {"rpy": 34, "oseen": 30}}}
 
 
-def leg_sweep(args):
+def leg_sweep(args, forced=True):
     """N = 2^10 .. 2^18 at phi = 0.05: FP32C and FP64 step times, the all-pairs kernel's
     fraction of the FP32 peak, and the FP32C / FP64 velocity error against the oracle
-    on sampled rows."""
+    on sampled rows; with `forced`, also both all-pairs kernels forced in turn."""
     import torch
     import oracle
     import paper_1205_6333_gb300 as sd
@@ -518,7 +524,7 @@ def leg_sweep(args):
                 rec["frac_fp32_peak"] = FLOPS_PER_PAIR * float(n) * n / (dms * 1e-3) / peak
             s.close()
         # both all-pairs kernels forced, for the automatic choice between them
-        for dense in ("directed", "symmetric"):
+        for dense in (("directed", "symmetric") if forced else ()):
             s = sd.System(n, prec="fp32c", stream="torch", torch_allocator=True, dense=dense)
             s.set_positions(x)
             s.set_forces(F)

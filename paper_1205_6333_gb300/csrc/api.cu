@@ -131,24 +131,30 @@ static sd_status launch_check(cudaError_t e, const char *what) {
 
 // ---------------------------------------------------------------- one Euler step
 
-// A Verlet step (constant forces): the check kernel (mirror, rebuild decision), the
-// rebuild kernels (cell list and xref = x_in; the candidate list within r_near + skin,
-// each particle's run sorted by partner), which read the decision and return at once
-// when no rebuild is due, the FP64 terms of the listed pairs (which clear the
-// request), the all-pairs kernel and the Euler epilogue.  A fresh and a reused list
-// give the same result bit for bit: each particle's list is sorted by partner and
-// entries beyond r_near add exact zeros.
+// A Verlet step (constant forces).  The check kernel writes the mirror, the rebuild
+// decision and the clamp flag.  Then two branches run side by side: the all-pairs
+// kernel on st, and on the side stream the rebuild kernels (cell list and
+// xref = x_in; the candidate list within r_near + skin, each particle's run sorted by
+// partner), which read the decision and return at once when no rebuild is due,
+// followed by the FP64 terms of the listed pairs.  The Euler epilogue joins them.
+// Neither branch writes what the other reads.  A fresh and a reused list give the
+// same result bit for bit: each particle's list is sorted by partner and entries
+// beyond r_near add exact zeros.
 static cudaError_t launch_verlet_step(sd_handle *h, cudaStream_t st, double dt, const double *x_in, double *x_out) {
-    // (profiler event pairs do not nest: cells, then the near pass)
     cudaError_t e = launch_verlet_check(h, st, x_in, h->posm);
-    if (e == cudaSuccess) e = launch_build_cells(h, st, x_in, h->posm, h->xref);
-    prof_begin(h, SD_KERNEL_NEAR, st);
-    if (e == cudaSuccess) e = launch_near_collect(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true, true);
-    if (e == cudaSuccess) e = launch_near_pairs(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true);
-    prof_end(h, SD_KERNEL_NEAR, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_build_cells(h, h->side, x_in, h->posm, h->xref);
+    prof_begin(h, SD_KERNEL_NEAR, h->side);
+    if (e == cudaSuccess) e = launch_near_collect(h, h->side, x_in, h->posm.aos, h->F64, h->frcm.aos, true, true);
+    if (e == cudaSuccess) e = launch_near_pairs(h, h->side, x_in, h->posm.aos, h->F64, h->frcm.aos, true);
+    prof_end(h, SD_KERNEL_NEAR, h->side);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side);
     if (e == cudaSuccess) e = launch_dense(h, st, h->posm, h->frcm, h->part);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_join, 0);
     if (e == cudaSuccess)
-        e = launch_epilogue(h, st, OUT_EULER, x_in, h->posm.aos, h->F64, h->frcm.aos, nullptr, dt, x_out);
+        e = launch_epilogue(h, st, OUT_EULER, x_in, h->posm.aos, h->F64, h->frcm.aos, nullptr, dt, x_out, 0, -1,
+                            nullptr, true);
     return e;
 }
 
@@ -442,19 +448,27 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     if (e != cudaSuccess) return fail(SD_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
     e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return fail(SD_ERR_CUDA, "stream creation");
+    if (h->verlet) {   // the side branch of a Verlet step
+        e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(SD_ERR_CUDA, "stream creation");
+    }
 
     const size_t n3 = 3 * static_cast<size_t>(std::max(h->n, 1));
     const size_t np = static_cast<size_t>(std::max(h->npad, kPadTo));
     const size_t vb = v4size(h);
     h->near_cap = static_cast<int>(std::min<long long>(static_cast<long long>(kNearPerParticle) * h->n + 1024,
                                                         1LL << 30));
-    bool ok = dalloc_t(h, h->d_err, 1) && dalloc_t(h, h->d_flag, 1) && dalloc_t(h, h->d_vl, 2) &&
+    bool ok = dalloc_t(h, h->d_err, 1) && dalloc_t(h, h->d_flag, 1) && dalloc_t(h, h->d_vl, 3) &&
               dalloc_t(h, h->near64, 2 * n3) &&
               dalloc_t(h, h->near_ent, h->near_cap) && dalloc_t(h, h->near_out, 6 * static_cast<size_t>(h->near_cap)) &&
               dalloc_t(h, h->near_n, 1) && dalloc_t(h, h->near_off, n3 / 3 + 1) && dalloc_t(h, h->near_cnt, n3 / 3 + 1);
     for (int b = 0; b < 2 && ok; ++b) ok = dalloc_t(h, h->x64[b], n3);
     if (ok && h->lub) ok = dalloc_t(h, h->vlag, n3);
-    if (ok && h->verlet) ok = dalloc_t(h, h->xref, n3);
+    if (ok && h->verlet)
+        ok = dalloc_t(h, h->xref, n3) && dalloc_t(h, h->vent, h->near_cap) && dalloc_t(h, h->voff, n3 / 3 + 1) &&
+             dalloc_t(h, h->vcnt, n3 / 3 + 1) && dalloc_t(h, h->vn, 1);
     ok = ok && dalloc_t(h, h->fext64, n3) && dalloc_t(h, h->F64, n3) && dalloc_t(h, h->Fa64, n3) &&
          dalloc_t(h, h->Wa64, n3);
     const bool soa = h->mode != MODE_FP64;
@@ -512,8 +526,9 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     cudaStream_t st = h->stream;
     e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_vl, 0, 2 * sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_vl, 0xff, sizeof(int), st);   // the first step builds
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_vl, 0, 3 * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_vl, 0xff, sizeof(int), st);   // no list until positions are set
+    if (e == cudaSuccess && h->vn) e = cudaMemsetAsync(h->vn, 0, sizeof(*h->vn), st);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(h->x64[b], 0, n3 * sizeof(double), st);
     for (Mirror *m : {&h->posm, &h->frcm, &h->frcam, &h->wam}) {
         if (e == cudaSuccess) e = cudaMemsetAsync(m->aos, 0, np * vb, st);
@@ -544,9 +559,13 @@ void sd_destroy(sd_handle *h) {
     void *bufs[] = {h->fext64, h->F64, h->Fa64, h->Wa64, h->part, h->part2, h->jpart,
                     h->cl.cell, h->cl.key, h->cl.cnt, h->cl.start, h->cl.bsum, h->cl.sorted,
                     h->ckpt, h->seg, h->lam, h->gFacc, h->near64, h->d_flag, h->d_err,
-                    h->near_ent, h->near_out, h->near_n, h->near_off, h->near_cnt, h->vlag, h->xref, h->d_vl};
+                    h->near_ent, h->near_out, h->near_n, h->near_off, h->near_cnt, h->vlag, h->xref, h->d_vl,
+                    h->vent, h->voff, h->vcnt, h->vn};
     for (void *p : bufs) dfree(h, p);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
 }
 
@@ -587,9 +606,19 @@ sd_status sd_set_positions(sd_handle *h, const double *xyz, int on_device) {
         sd_status s = launch_check(launch_stage_pos(h, h->stream, h->x64[h->cur], h->posm), "stage positions");
         if (s != SD_OK) return s;
         // new positions: the previous step's velocities no longer apply (lubrication),
-        // and the next step builds its neighbour list afresh
+        // and the steps' neighbour list is built afresh around them, so that a
+        // trajectory resumed from positions read back continues bit for bit
         if (h->vlag) SD_CUDA(cudaMemsetAsync(h->vlag, 0, 3 * sizeof(double) * h->n, h->stream));
-        if (h->verlet) SD_CUDA(cudaMemsetAsync(h->d_vl, 0xff, sizeof(int), h->stream));
+        if (h->verlet) {
+            SD_CUDA(cudaMemsetAsync(h->d_vl, 0, sizeof(int), h->stream));
+            SD_CUDA(cudaMemsetAsync(h->d_vl, 1, 1, h->stream));   // a rebuild request (bit 2 clear)
+            s = launch_check(launch_build_cells(h, h->stream, h->x64[h->cur], h->posm, h->xref), "neighbour list");
+            if (s == SD_OK)
+                s = launch_check(launch_near_collect(h, h->stream, h->x64[h->cur], h->posm.aos, h->F64,
+                                                     h->frcm.aos, true, true),
+                                 "neighbour list");
+            if (s != SD_OK) return s;
+        }
     }
     h->pos_set = true;
     h->cells_valid = false;

@@ -72,17 +72,32 @@ cudaError_t launch_stage_pos(sd_handle *h, cudaStream_t st, const double *x64, M
 }
 
 // The Verlet step's first kernel: the mirror of x (as the cell-list build writes it),
-// the clamp flag reset, and the rebuild decision.  The list stays valid while every
-// particle's displacement since the build, relative to particle 0's, is below
-// skin / 2 (pair distances then changed by less than the skin; a uniform
-// translation moves no pair).  A list that overflowed (its particles corrected in
-// place at build time) is rebuilt every step.  The rebuild kernels that follow read
-// the decision (vl[0]).
+// the rebuild decision and the clamp flag of the step, both written by the last block
+// to finish (vl[0] and *flag; vl[1] counts the blocks, vl[2] gathers their bits).
+//   * The list holds the pairs within r_near + skin of the positions xref it was
+//     built from.  While every particle's displacement since then, relative to
+//     particle 0's, stays below skin / 2, pair distances have changed by less than
+//     the skin (a uniform translation moves no pair), so the list still holds every
+//     pair within r_near.  It is rebuilt early, from skin / 4 on, so that this holds
+//     in the step that rebuilds it too.
+//   * The clamp flag (some pair closer than r_safe: the all-pairs kernel then clamps
+//     every tile) comes from the pairs of that list, in FP64 exactly as the near pass
+//     tests them, so the all-pairs kernel need not wait for the near pass.  It is
+//     raised outright when the list may miss pairs: no list yet (bit 2 of vl[0]:
+//     positions never set), overflowed (its particles corrected in place), or a
+//     displacement of skin / 2 or more.  (The list is the steps' own, built when the
+//     positions are set and by the steps' rebuilds; no other pass touches it.)
 template <typename V4>
 __global__ void verlet_check_kernel(const double *__restrict__ x, const double *__restrict__ xref, int n, int npad,
-                                    Box b, double half_skin2, V4 *__restrict__ m, float *__restrict__ soa, int *flag,
-                                    int *vl, const unsigned long long *near_n, int cap, int *err) {
+                                    Box b, double quarter_skin2, double half_skin2, double rsafe2,
+                                    V4 *__restrict__ m, float *__restrict__ soa, int *flag, int *vl,
+                                    const unsigned long long *near_n, int cap, const int2 *__restrict__ ent,
+                                    const int *__restrict__ noff, const int *__restrict__ ncnt, int *err) {
+    __shared__ int s_invalid;
+    if (threadIdx.x == 0) s_invalid = (vl[0] & 2) != 0;
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int bits = s_invalid ? 3 : 0;   // 1: rebuild; 2: clamp every tile
     if (i < n) {
         const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
         if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicOr(err, DEV_ERR_NONFINITE);
@@ -90,10 +105,36 @@ __global__ void verlet_check_kernel(const double *__restrict__ x, const double *
         const double ux = (px - xref[3 * i]) - (x[0] - xref[0]);
         const double uy = (py - xref[3 * i + 1]) - (x[1] - xref[1]);
         const double uz = (pz - xref[3 * i + 2]) - (x[2] - xref[2]);
-        if (!(ux * ux + uy * uy + uz * uz < half_skin2)) atomicOr(&vl[0], 1);   // (also NaN)
-        if (i == 0) {
-            *flag = 0;   // the near pass of these positions raises it again if needed
-            if (*near_n > static_cast<unsigned long long>(cap)) atomicOr(&vl[0], 1);
+        const double u2 = ux * ux + uy * uy + uz * uz;
+        if (!(u2 < quarter_skin2)) bits |= 1;   // (also NaN)
+        if (!(u2 < half_skin2)) bits |= 3;
+        if (i == 0 && *near_n > static_cast<unsigned long long>(cap)) bits |= 3;
+        if (!(bits & 2)) {   // the list is complete around i: its pairs closer than r_safe
+            const int c = ncnt[i];
+            if (c < 0) {
+                bits |= 3;
+            } else {
+                const long long e0 = dbg_index(noff[i], static_cast<long long>(cap) - c + 1, err);
+                for (int k = 0; k < c; ++k) {
+                    const int j = static_cast<int>(dbg_index(ent[e0 + k].y, n, err));
+                    double dx = px - x[3 * j], dy = py - x[3 * j + 1], dz = pz - x[3 * j + 2];
+                    box_image(b, dx, dy, dz);
+                    if (dx * dx + dy * dy + dz * dz < rsafe2) bits |= 2;
+                }
+            }
+        }
+    }
+    const int any = (__syncthreads_or(bits & 1) ? 1 : 0) | (__syncthreads_or(bits & 2) ? 2 : 0);
+    if (threadIdx.x == 0) {
+        if (any) atomicOr(&vl[2], any);
+        __threadfence();
+        const int done = atomicAdd(&vl[1], 1);
+        if (done == static_cast<int>(gridDim.x) - 1) {   // every block's bits are in
+            __threadfence();
+            const int all = atomicExch(&vl[2], 0);
+            *flag = (all & 2) ? 1 : 0;
+            vl[0] = all & 1;
+            vl[1] = 0;
         }
     }
 }
@@ -101,16 +142,18 @@ __global__ void verlet_check_kernel(const double *__restrict__ x, const double *
 cudaError_t launch_verlet_check(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm) {
     if (h->n == 0) return cudaSuccess;
     const int nb = (h->n + 255) / 256;
-    const double hs2 = 0.25 * h->skin * h->skin;
+    const double hs2 = 0.25 * h->skin * h->skin, qs2 = 0.0625 * h->skin * h->skin;
+    const double rs2 = kRSafe * kRSafe * h->pc.a * h->pc.a;
     prof_begin(h, SD_KERNEL_CELLS, st);
     if (h->mode == MODE_FP64)
-        verlet_check_kernel<dbl4><<<nb, 256, 0, st>>>(x64, h->xref, h->n, h->npad, h->cl.box, hs2,
+        verlet_check_kernel<dbl4><<<nb, 256, 0, st>>>(x64, h->xref, h->n, h->npad, h->cl.box, qs2, hs2, rs2,
                                                       static_cast<dbl4 *>(posm.aos), posm.soa, h->d_flag, h->d_vl,
-                                                      h->near_n, h->near_cap, h->d_err);
+                                                      h->vn, h->near_cap, h->vent, h->voff, h->vcnt, h->d_err);
     else
-        verlet_check_kernel<float4><<<nb, 256, 0, st>>>(x64, h->xref, h->n, h->npad, h->cl.box, hs2,
-                                                        static_cast<float4 *>(posm.aos), posm.soa, h->d_flag, h->d_vl,
-                                                        h->near_n, h->near_cap, h->d_err);
+        verlet_check_kernel<float4><<<nb, 256, 0, st>>>(x64, h->xref, h->n, h->npad, h->cl.box, qs2, hs2, rs2,
+                                                        static_cast<float4 *>(posm.aos), posm.soa, h->d_flag,
+                                                        h->d_vl, h->vn, h->near_cap, h->vent, h->voff, h->vcnt,
+                                                        h->d_err);
     prof_end(h, SD_KERNEL_CELLS, st);
     ++h->launches;
     return cudaGetLastError();
@@ -204,31 +247,31 @@ __device__ __forceinline__ int cell_coord_d(const CellList &c, int d, double x) 
 }
 
 // Bins particle i and writes its mirror (position relative to particle 0, in the
-// dense kernels' precision), so the mirror is a pure function of the FP64 state.
+// dense kernels' precision), so the mirror is a pure function of the FP64 state.  A
+// Verlet list build (xref given) records the positions in xref instead and leaves
+// the mirror and the clamp flag to the step's check kernel.
 template <typename V4>
 __global__ void cells_hash_kernel(const double *__restrict__ x, int n, CellList c, int4 *__restrict__ cell,
                                   uint32_t *__restrict__ key, int *__restrict__ cnt, V4 *__restrict__ m,
                                   float *__restrict__ soa, int npad, int *flag, unsigned long long *near_n,
-                                  double *__restrict__ xref, int *rebuild, const int *gate, int *err) {
+                                  double *__restrict__ xref, const int *gate, int *err) {
     if (gate && *gate == 0) return;   // a Verlet step without a rebuild request
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (i == 0) {
-        *flag = 0;     // the near pass of these positions raises it again if needed
-        *near_n = 0;   // ... and fills its candidate list from the start
-        // any build outside a Verlet step replaces the near-pair list with one the
-        // steps cannot reuse (a Verlet step's request is cleared by its near pass)
-        if (rebuild && !xref) *rebuild = 1;
-    }
-    if (xref) {
-        xref[3 * i] = x[3 * i];
-        xref[3 * i + 1] = x[3 * i + 1];
-        xref[3 * i + 2] = x[3 * i + 2];
+        *near_n = 0;                // the near pass fills its candidate list from the start
+        if (!xref) *flag = 0;       // ... and raises the flag again if needed
     }
     const int H = c.H;
     const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
-    if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicOr(err, DEV_ERR_NONFINITE);
-    put_pos_mirror(m, soa, npad, i, x, c.box);
+    if (xref) {   // a Verlet step's rebuild: the flag and the mirror are its check kernel's
+        xref[3 * i] = px;
+        xref[3 * i + 1] = py;
+        xref[3 * i + 2] = pz;
+    } else {
+        if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) atomicOr(err, DEV_ERR_NONFINITE);
+        put_pos_mirror(m, soa, npad, i, x, c.box);
+    }
     const int cx = cell_coord_d(c, 0, px);
     const int cy = cell_coord_d(c, 1, py);
     const int cz = cell_coord_d(c, 2, pz);
@@ -366,11 +409,11 @@ cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64,
     if (h->mode == MODE_FP64)
         cells_hash_kernel<dbl4><<<nb, 256, 0, st>>>(x64, h->n, c, c.cell, c.key, c.cnt,
                                                     static_cast<dbl4 *>(posm.aos), posm.soa, h->npad, h->d_flag,
-                                                    h->near_n, xref, h->d_vl, gate, h->d_err);
+                                                    xref ? h->vn : h->near_n, xref, gate, h->d_err);
     else
         cells_hash_kernel<float4><<<nb, 256, 0, st>>>(x64, h->n, c, c.cell, c.key, c.cnt,
                                                       static_cast<float4 *>(posm.aos), posm.soa, h->npad,
-                                                      h->d_flag, h->near_n, xref, h->d_vl, gate, h->d_err);
+                                                      h->d_flag, xref ? h->vn : h->near_n, xref, gate, h->d_err);
     scan_blocks_kernel<<<c.nblk, kScanThreads, 0, st>>>(c.cnt, c.start, c.bsum, c.H, gate);
     if (c.nblk > 1) {
         scan_top_kernel<<<1, kScanThreads, 0, st>>>(c.bsum, c.nblk, c.start, c.H, gate);

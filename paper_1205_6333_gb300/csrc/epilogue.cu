@@ -6,6 +6,8 @@
 //     for both variants of Tdense (r^2 clamped to (2a)^2, and unclamped), and a
 //     device flag raised when some pair is closer than r_safe (then the
 //     all-pairs kernel clamps every tile, else only the tiles holding self pairs);
+//     in a Verlet step the flag comes from the step's check kernel instead, and the
+//     near pass runs beside the all-pairs kernel;
 //   epilogue (after it):
 //     V_i = sum over the CTA slots of the dense partial sums (and, after the
 //           symmetric kernel, over the source-side slots of the particle's block
@@ -106,7 +108,6 @@ struct NearArgs {
     int *noff, *ncnt; // per particle: first entry and count; ncnt = -1: correction is in near[i]
     int cap;
     const int *gate;  // Verlet list build: run only when the step's check asked for a rebuild
-    int *gate_reset;  // the step's FP64 pass clears that request once the list is (re)built
 };
 
 // The correction of one near pair (FP64 r^2 < r_near^2), added to c6: the exact
@@ -181,7 +182,7 @@ __device__ void near_direct(const NearArgs &a, int i, int sub, bool active) {
     close = walk_any(close);
     if (!active || sub != writer) return;
     if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
-    if (close) atomicOr(a.flag, 1);
+    if (close && a.flag) atomicOr(a.flag, 1);
     double *o = a.near + 6 * static_cast<size_t>(i);
     for (int d = 0; d < 3; ++d) {
         o[d] = c6[d];                 // correction when every tile is clamped
@@ -289,7 +290,6 @@ __global__ void __launch_bounds__(128) near_collect_kernel(NearArgs a) {
 // two correction variants of the pair, written to its entry.
 template <int TENSOR, int MODE>
 __global__ void __launch_bounds__(128) near_pair_kernel(NearArgs a) {
-    if (a.gate_reset && blockIdx.x == 0 && threadIdx.x == 0) *a.gate_reset = 0;   // the list is current
     const int total = static_cast<int>(min(*a.ent_n, static_cast<unsigned long long>(a.cap)));
     bool coincident = false, close = false;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(128) near_pair_kernel(NearArgs a) {
         }
     }
     if (coincident) atomicOr(a.err, DEV_ERR_COINCIDENT);
-    if (close) atomicOr(a.flag, 1);
+    if (close && a.flag) atomicOr(a.flag, 1);
 }
 
 template <int TENSOR, int MODE>
@@ -326,7 +326,7 @@ static void near_launch_pairs(int np, cudaStream_t st, const NearArgs &a) {
 }
 
 static NearArgs near_args(sd_handle *h, const double *x64, const void *posm, const double *F64, const void *frcm,
-                          double screen) {
+                          double screen, bool vlist = false) {
     NearArgs a;
     a.x64 = x64;
     a.posm = posm;
@@ -342,14 +342,13 @@ static NearArgs near_args(sd_handle *h, const double *x64, const void *posm, con
     a.flag = h->d_flag;
     a.err = h->d_err;
     a.g = h->geom;
-    a.ent = h->near_ent;
+    a.ent = vlist ? h->vent : h->near_ent;   // (the Verlet steps' own list)
     a.ent_out = h->near_out;
-    a.ent_n = h->near_n;
-    a.noff = h->near_off;
-    a.ncnt = h->near_cnt;
+    a.ent_n = vlist ? h->vn : h->near_n;
+    a.noff = vlist ? h->voff : h->near_off;
+    a.ncnt = vlist ? h->vcnt : h->near_cnt;
     a.cap = h->near_cap;
     a.gate = nullptr;
-    a.gate_reset = nullptr;
     return a;
 }
 
@@ -366,8 +365,11 @@ static NearArgs near_args(sd_handle *h, const double *x64, const void *posm, con
 cudaError_t launch_near_collect(sd_handle *h, cudaStream_t st, const double *x64, const void *posm,
                                 const double *F64, const void *frcm, bool count_zeroed, bool verlet_list) {
     if (h->n == 0) return cudaSuccess;
-    NearArgs a = near_args(h, x64, posm, F64, frcm, verlet_list ? h->r_near + h->skin : h->r_near);
-    if (verlet_list) a.gate = h->d_vl;
+    NearArgs a = near_args(h, x64, posm, F64, frcm, verlet_list ? h->r_near + h->skin : h->r_near, verlet_list);
+    if (verlet_list) {   // a Verlet step's rebuild: the clamp flag is its check kernel's
+        a.gate = h->d_vl;
+        a.flag = nullptr;
+    }
     const int nb = static_cast<int>((static_cast<long long>(h->n) * kWalkLanes + 127) / 128);
     if (!count_zeroed) {
         cudaError_t e = cudaMemsetAsync(a.ent_n, 0, sizeof(*a.ent_n), st);
@@ -375,19 +377,14 @@ cudaError_t launch_near_collect(sd_handle *h, cudaStream_t st, const double *x64
     }
     SD_NEAR_DISPATCH(near_launch_collect, nb);
     ++h->launches;
-    if (!verlet_list && h->verlet) {
-        // a list the steps cannot reuse (no skin, unsorted): their next step rebuilds
-        cudaError_t e = cudaMemsetAsync(h->d_vl, 0xff, sizeof(int), st);
-        if (e != cudaSuccess) return e;
-    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_near_pairs(sd_handle *h, cudaStream_t st, const double *x64, const void *posm, const double *F64,
                               const void *frcm, bool verlet_step) {
     if (h->n == 0) return cudaSuccess;
-    NearArgs a = near_args(h, x64, posm, F64, frcm, h->r_near);
-    if (verlet_step) a.gate_reset = h->d_vl;
+    NearArgs a = near_args(h, x64, posm, F64, frcm, h->r_near, verlet_step);
+    if (verlet_step) a.flag = nullptr;   // (the check kernel's; the all-pairs kernel may be reading it)
     const int np = static_cast<int>(std::min<long long>((static_cast<long long>(a.cap) + 127) / 128,
                                                         8LL * h->num_sms));
     SD_NEAR_DISPATCH(near_launch_pairs, np);
@@ -629,15 +626,15 @@ static void epi_launch_mode(int mode, int out, int nb, cudaStream_t st, const Ep
 
 cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double *x64, const void *posm,
                             const double *F64, const void *frcm, void *vout, double dt, double *x64n, int row0,
-                            int row1, const EpiShard *shard) {
+                            int row1, const EpiShard *shard, bool vlist) {
     if (h->n == 0) return cudaSuccess;
     if (row1 < 0 || row1 > h->n) row1 = h->n;
     if (row0 < 0) row0 = 0;
     if (row0 >= row1) return cudaSuccess;
     EpiArgs a;
     a.ent_out = h->near_out;
-    a.noff = h->near_off;
-    a.ncnt = h->near_cnt;
+    a.noff = vlist ? h->voff : h->near_off;   // (a Verlet step: its own candidate list)
+    a.ncnt = vlist ? h->vcnt : h->near_cnt;
     a.part = h->part;
     a.jpart = h->mode == MODE_FP64 ? nullptr : static_cast<const float *>(h->jpart);
     a.jpart64 = h->mode == MODE_FP64 ? static_cast<const double *>(h->jpart) : nullptr;

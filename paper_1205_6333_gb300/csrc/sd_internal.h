@@ -264,7 +264,14 @@ struct sd_handle {
     bool verlet = false;
     double skin = 0.0;
     double *xref = nullptr;        // [n*3] positions of the last build
-    int *d_vl = nullptr;           // [0] rebuild request
+    int *d_vl = nullptr;           // [0] rebuild request (bit 2: no list yet), [1] [2] check kernel's
+    // the Verlet steps' own candidate list, kept across steps (every other near pass
+    // uses near_ent / near_off / near_cnt / near_n): entries, each particle's run, count
+    int2 *vent = nullptr;
+    int *voff = nullptr, *vcnt = nullptr;
+    unsigned long long *vn = nullptr;
+    cudaStream_t side = nullptr;   // the rebuild and the near pass, beside the all-pairs kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace sd {
@@ -322,7 +329,7 @@ cudaError_t launch_near_pairs(sd_handle *h, cudaStream_t st, const double *x64, 
                               const void *frcm, bool verlet_step = false);
 cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double *x64, const void *posm,
                             const double *F64, const void *frcm, void *vout, double dt, double *x64n, int row0 = 0,
-                            int row1 = -1, const EpiShard *shard = nullptr);
+                            int row1 = -1, const EpiShard *shard = nullptr, bool vlist = false);
 // vjp.cu
 cudaError_t vjp_setup(sd_handle *h);
 cudaError_t launch_vjp_dense(sd_handle *h, cudaStream_t st, const void *posm, const void *frcm, const void *wm,

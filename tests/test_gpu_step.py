@@ -167,9 +167,9 @@ def _verlet_case(n=1500, seed=61):
 
 @pytest.mark.parametrize("prec", ["fp32c", "fp64"])
 def test_verlet_lists_graph_eager_and_no_reuse_agree(prec):
-    """Neighbour lists reused across steps (graph replays with the conditional rebuild)
-    equal eager steps (which rebuild every step) bit for bit, and agree with lists
-    built every step without a skin to the last bits; against the oracle as usual."""
+    """Neighbour lists reused across steps give the same trajectory bit for bit in graph
+    replays, single steps and eager steps, and agree with lists built every step
+    without a skin to the last bits; against the oracle as usual."""
     x0, fe = _verlet_case()
     n, steps, dt = x0.shape[0], 48, 0.01
     with sd.System(n, prec=prec, gravity=(0, 0, -1.0)) as s:
@@ -198,6 +198,51 @@ def test_verlet_lists_graph_eager_and_no_reuse_agree(prec):
     assert np.linalg.norm(rel, axis=1).max() > 1.0   # relative motion of several half skins
     assert np.abs(a - c).max() <= (1e-13 if prec == "fp64" else 1e-6) * disp
     ref = oracle.euler(x0, steps, dt, fext=fe, gravity=(0, 0, -1.0), nthreads=8)
+    assert np.abs(a - ref).max() <= (1e-10 if prec == "fp64" else 1e-5) * np.abs(ref - x0).max()
+
+
+@pytest.mark.parametrize("dense", ["directed", "symmetric"])
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_verlet_clamp_flag_from_the_list(prec, dense):
+    """A pair driven past each other comes closer than r_safe = 1a and separates again,
+    so the all-pairs kernel's clamp-every-tile flag turns on and off during the run.
+    In a Verlet step that flag comes from the step's check kernel, which scans the
+    last list, while the near pass runs beside the all-pairs kernel.  Graph replays,
+    single steps and eager steps agree bit for bit; the lists rebuilt every step
+    without a skin and the oracle agree as usual."""
+    n, steps, dt = 600, 64, 0.01
+    x0, _ = inputs.cube_rsa(n, 0.05, 81)
+    x0[1] = x0[0] + np.array([2.0, 0.3, 0.0])   # closer than 1a in steps 14 .. 53 (oracle)
+    fe = inputs.normal_forces(n, 82)
+    fe[0] = [250.0, 0.0, 0.0]
+    fe[1] = [-250.0, 0.0, 0.0]
+    runs = []
+    with sd.System(n, prec=prec, dense=dense) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(dt, steps)
+        runs.append(s.get_positions())
+        s.set_positions(x0)
+        for _ in range(steps):
+            s.step(dt, 1)
+        runs.append(s.get_positions())
+        s.set_positions(x0)
+        s.profile(True)
+        s.step(dt, steps)
+        s.profile(False)
+        runs.append(s.get_positions())
+    np.testing.assert_array_equal(runs[0], runs[1])
+    np.testing.assert_array_equal(runs[0], runs[2])
+    a = runs[0]
+    assert np.linalg.norm(a[0] - a[1]) > 1.2 and a[0, 0] - a[1, 0] > 1.0   # passed and apart again
+    with sd.System(n, prec=prec, dense=dense, verlet_skin=0) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(dt, steps)
+        c = s.get_positions()
+    disp = np.abs(a - x0).max()
+    assert np.abs(a - c).max() <= (1e-13 if prec == "fp64" else 1e-6) * disp
+    ref = oracle.euler(x0, steps, dt, fext=fe, nthreads=8)
     assert np.abs(a - ref).max() <= (1e-10 if prec == "fp64" else 1e-5) * np.abs(ref - x0).max()
 
 
