@@ -11,8 +11,9 @@
 //   * FP32C: each tile's FP32 partial sum is folded into a two-float (hi, lo)
 //     accumulator with TwoSum (Sec. 3.2: single-precision pair terms, higher-precision
 //     accumulation); FP64: plain FP64 sums; FP32: plain FP32 sums (ablation);
-//   * each CTA writes its partial sum for every i-block it touched into a fixed slot;
-//     the epilogue adds the slots in ascending order (deterministic result).
+//   * each CTA writes its partial sum for every i-block it touched into a fixed slot
+//     (FP32C: the (hi, lo) float pair; FP64, FP32: one double); the epilogue adds the
+//     slots in ascending order (deterministic result).
 // Self and overlapping pairs take r^2 clamped to (2a)^2 here; the FP64 epilogue
 // replaces them (and every pair closer than r_near) by their exact terms.
 #include <algorithm>
@@ -287,16 +288,15 @@ __global__ void __launch_bounds__(kNT) dense2_kernel(const float *__restrict__ p
             const size_t i = static_cast<size_t>(ib) * g.I + tid + k * kNT;
             const f2 acc[3] = {AX[k], AY[k], AZ[k]};
             for (int d = 0; d < 3; ++d) {
-                double v;
-                if constexpr (COMP) {
+                if constexpr (COMP) {   // the (hi, lo) pair itself, for the epilogue's FP32 TwoSum
                     const float *q = s_acc + (k * 6) * kNT + tid;
-                    v = static_cast<double>(q[d * kNT]) + static_cast<double>(q[(3 + d) * kNT]);
+                    reinterpret_cast<float2 *>(dst)[d * static_cast<size_t>(npad) + i] =
+                        make_float2(q[d * kNT], q[(3 + d) * kNT]);
                 } else {
                     float lo, hi;
                     upk2(acc[d], lo, hi);
-                    v = static_cast<double>(__fadd_rn(lo, hi));
+                    dst[d * static_cast<size_t>(npad) + i] = static_cast<double>(__fadd_rn(lo, hi));
                 }
-                dst[d * static_cast<size_t>(npad) + i] = v;
             }
         }
     };
@@ -516,16 +516,15 @@ __global__ void __launch_bounds__(NT, SD_SYM_MINB) dense_sym_kernel(const float 
             const size_t i = static_cast<size_t>(ib) * B + tid + k * NT;
             const f2 acc[3] = {AX[k], AY[k], AZ[k]};
             for (int d = 0; d < 3; ++d) {
-                double v;
-                if constexpr (COMP) {
+                if constexpr (COMP) {   // the (hi, lo) pair itself, for the epilogue's FP32 TwoSum
                     const float *qa = s_acc + (k * 6) * NT + tid;
-                    v = static_cast<double>(qa[d * NT]) + static_cast<double>(qa[(3 + d) * NT]);
+                    reinterpret_cast<float2 *>(dst)[d * static_cast<size_t>(npad) + i] =
+                        make_float2(qa[d * NT], qa[(3 + d) * NT]);
                 } else {
                     float lo, hi;
                     upk2(acc[d], lo, hi);
-                    v = static_cast<double>(__fadd_rn(lo, hi));
+                    dst[d * static_cast<size_t>(npad) + i] = static_cast<double>(__fadd_rn(lo, hi));
                 }
-                dst[d * static_cast<size_t>(npad) + i] = v;
             }
         }
     };

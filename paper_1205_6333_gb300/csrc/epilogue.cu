@@ -448,9 +448,12 @@ __device__ __forceinline__ int first_row_at(const DenseGeom &g, int ib, long lon
 // symmetric kernel, the source-side tiles r = w, w + kEpiWarps, ... of the
 // particle's block column); lane l reads particle 32 b + l, so every warp load is
 // one coalesced 128-byte row.  Warp 0 adds the warps' results in ascending w
-// (fixed order: deterministic) and applies the FP64 terms.
+// (fixed order: deterministic) and applies the FP64 terms.  Four warps per 32
+// particles measured best at N = 65,536 (40 us against 45 for 8, 51 for 2, 79 for 16):
+// the kernel waits on DRAM latency, and fewer warps per group leave fewer idle
+// during warp 0's FP64 tail.
 #ifndef SD_EPI_WARPS
-#define SD_EPI_WARPS 8
+#define SD_EPI_WARPS 4
 #endif
 #ifndef SD_EPI_UNROLL
 #define SD_EPI_UNROLL 2
@@ -471,8 +474,8 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
 
     // This warp's share of the dense sum: the CTA slots of the particle's i-block,
     // then (symmetric kernel) the source-side slots of the tiles (r, ib), r < ib.
-    // The column holds up to N/256 FP32 values per component: it is summed with
-    // TwoSum in FP32 (hi, lo), because FP64 issues at 1/64 the FP32 rate on GB300.
+    // FP32C sums both with TwoSum in FP32 (hi, lo) -- the slots are (hi, lo) pairs
+    // themselves -- because FP64 issues at 1/64 the FP32 rate on GB300.
     {
         double v[3] = {0.0, 0.0, 0.0};
         float hi[3] = {0.0f, 0.0f, 0.0f}, lo[3] = {0.0f, 0.0f, 0.0f};
@@ -512,9 +515,15 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
                     const double *src = a.jpart64 + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
                     for (int d = 0; d < 3; ++d) v[d] += src[d * J];
                 }
-            } else {
+            } else {   // FP32C: each slot is a (hi, lo) float pair
+                const float2 *pp = reinterpret_cast<const float2 *>(a.part);
+#pragma unroll 4
                 for (int s = s0 + w; s < ns; s += kEpiWarps)
-                    for (int d = 0; d < 3; ++d) v[d] += a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+                    for (int d = 0; d < 3; ++d) {
+                        const float2 q = pp[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+                        fold2(hi[d], lo[d], q.x);
+                        lo[d] = __fadd_rn(lo[d], q.y);
+                    }
 #pragma unroll kEpiUnroll
                 for (int r = r0 + w; r < nc; r += kEpiWarps) {
                     const float *src = a.jpart + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
