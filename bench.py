@@ -10,7 +10,9 @@ included, as the paper counts them).
 
 Extra legs on rank 0 (reported in the same line): the plain FP64 GPU path on the
 same system, the batched workload (16,384 clusters, N per cluster U{4..256}),
-and the CPU oracle on a bounded sample (cpu_baseline).
+the Oseen variant and the CPU oracle on a bounded sample (cpu_baseline); on a
+single GPU also the other workloads (four spheres, drift, adjoint), the N sweep,
+the paper's fcc benchmark and the lubrication lattice.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -422,8 +424,9 @@ def run_leg(args):
 
 def legs(args, x, F, stream, flush, only=None, workloads=True):
     """FP64 path, batched workload, Oseen variant and the CPU oracle baseline (rank 0
-    only); with `workloads` (single-GPU runs) also the trajectory drift of workload 3,
-    the adjoint of workload 5 and the N sweep 2^10 .. 2^18."""
+    only); with `workloads` (single-GPU runs) also the four-sphere runs of workload 1,
+    the trajectory drift of workload 3, the adjoint of workload 5, the N sweep
+    2^10 .. 2^18, the paper's fcc benchmark and the lubrication lattice."""
     out = {}
     if only in (None, "fp64"):
         out.update(_leg_fp64(args, x, F, stream, flush))
@@ -432,9 +435,12 @@ def legs(args, x, F, stream, flush, only=None, workloads=True):
     if only in (None, "oseen"):
         out.update(_leg_oseen(args, x, F, stream, flush))
     if only is None and workloads:
+        out.update(leg_workload1(args))
         out.update(leg_drift(args))
         out.update(leg_adjoint(args))
         out.update(leg_sweep(args, forced=False))
+        out.update(leg_fcc(args))
+        out.update(leg_lubrication(args))
     if only is None:
         out["cpu_baseline"] = cpu_baseline(x, F, target_s=args.cpu_seconds)
     return out
@@ -536,6 +542,61 @@ def leg_sweep(args, forced=True):
         rows_out.append(rec)
         print(json.dumps(rec), file=sys.stderr, flush=True)
     return {"sweep": rows_out}
+
+
+def leg_workload1(args):
+    """Config 1 (Sec. 4): four spheres on a horizontal square of side 4a (+-0.01a
+    seeded jitter), F = (0, 0, -1), RPY, 20,000 Euler steps at dt = 0.01 tau_s: the
+    FP64 and FP32C GPU paths against the FP64 oracle, and steps/s.  Then the paper's
+    symmetric start (RP tensor) for 1,000 tau_s: the orbit's period and amplitude
+    (from the maxima of particle 1's x) and the drift of particles 1 and 3 out of the
+    xz plane."""
+    import torch
+    import oracle
+    import paper_1205_6333_gb300 as sd
+    from paper_1205_6333_gb300 import inputs
+    x0 = inputs.config_inputs(1)["x"]
+    tau = 1.0 / oracle.mu0()
+    dt = 0.01 * tau
+    nsteps = 20000
+    t0 = time.perf_counter()
+    ref = oracle.euler(x0, nsteps, dt, gravity=(0, 0, -1.0))
+    out = {"n": 4, "steps": nsteps, "dt_tau_s": 0.01, "oracle_s": time.perf_counter() - t0}
+    disp = float(np.abs(ref - x0).max())
+    for prec in ("fp64", "fp32c"):
+        with sd.System(4, prec=prec, gravity=(0, 0, -1.0), stream="torch") as s:
+            s.set_positions(x0)
+            s.step(dt, 16)
+            s.set_positions(x0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.step(dt, nsteps)
+            xt = s.get_positions()
+            el = time.perf_counter() - t0
+        d = float(np.abs(xt - ref).max())
+        out[prec] = {"max_abs_diff": d, "rel_to_max_displacement": d / disp, "steps_per_s": nsteps / el}
+    with open(os.path.join(ROOT, "tests", "golden", "four_sphere_orbit.json")) as f:
+        g = json.load(f)
+    dto = g["dt_tau_s"] * tau
+    chunk = 100
+    for prec in ("fp64", "fp32c"):
+        traj = []
+        with sd.System(4, prec=prec, tensor="rp", gravity=g["force"], stream="torch") as s:
+            s.set_positions(np.array(g["start"]))
+            for _ in range(int(1000.0 / g["dt_tau_s"]) // chunk):
+                s.step(dto, chunk)
+                traj.append(s.get_positions())
+        traj = np.array(traj)
+        x1 = traj[:, 0, 0]
+        k = np.nonzero((x1[1:-1] > x1[:-2]) & (x1[1:-1] >= x1[2:]))[0] + 1
+        t = (k + 1) * chunk * g["dt_tau_s"]
+        out["orbit_" + prec] = {
+            "period_tau_s": float(np.mean(np.diff(t))) if len(t) > 1 else None,
+            "paper_period_tau_s": g["period_tau_s"],
+            "amplitude_x1": float(0.5 * (x1.max() - x1.min())),
+            "y_drift_particles_1_3": float(np.abs(traj[:, [0, 2], 1]).max()),
+            "time_tau_s": 1000.0}
+    return {"workload1": out}
 
 
 def leg_drift(args):
@@ -895,7 +956,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="main leg only")
     ap.add_argument("--leg", default="all", choices=["all", "main", "fp64", "batched", "oseen", "sweep", "drift",
-                                                     "adjoint", "lubrication", "fcc", "access"],
+                                                     "adjoint", "lubrication", "fcc", "access", "workload1"],
                     help="run one leg alone and print its numbers (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--batched-shape", default="auto", choices=["auto", "sym", "blocks"],
@@ -921,6 +982,8 @@ def main():
         print(json.dumps(leg_fcc(args)), flush=True)
     elif args.leg == "access":
         print(json.dumps(leg_access(args)), flush=True)
+    elif args.leg == "workload1":
+        print(json.dumps(leg_workload1(args)), flush=True)
     else:
         if args.leg == "main":
             args.quick = True
