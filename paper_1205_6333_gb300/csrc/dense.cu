@@ -873,20 +873,26 @@ cudaError_t dense_setup(sd_handle *h) {
     const int R = (h->mode == MODE_FP64) ? kR64 : kR32;
     DenseGeom g{};
     g.I = kNT * R;
-    g.nIB = h->npad / g.I;
+    // Blocks and tiles cover the n particles, not the padded arrays (the slots past n
+    // hold far-away particles with zero force, so a partly filled block or tile is
+    // harmless): at small n the padding would otherwise be most of the work, which
+    // matters in FP64 (GB300 issues FP64 at 1/64 the FP32 rate).
+    const int nreal = std::max(h->n, 1);
+    g.nIB = (nreal + g.I - 1) / g.I;
     void *fn = pick_dense(h->tensor, h->mode, h->pc.periodic != 0);
-    const int Jcand[3] = {kJmax, 128, 64};
+    const int Jcand[4] = {kJmax, 128, 64, 32};
     int occ = 0;
-    for (int ci = 0; ci < 3; ++ci) {
+    for (int ci = 0; ci < 4; ++ci) {
         const int J = Jcand[ci];
         if (h->mode == MODE_FP64 && J > 128) continue;
+        if (h->mode != MODE_FP64 && J < 64) continue;   // (32-source tiles: FP64 only)
         const size_t smem = dense_smem(h->mode, J);
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kNT, smem);
         if (e != cudaSuccess) return e;
         g.J = J;
-        g.nJT = h->npad / J;
+        g.nJT = (nreal + J - 1) / J;
         const long long T = static_cast<long long>(g.nIB) * g.nJT;
         if (T >= 4LL * h->num_sms * std::max(occ, 1)) break;
     }
@@ -926,7 +932,7 @@ cudaError_t dense_setup(sd_handle *h) {
         DenseGeom s{};
         s.sym = 1;
         s.I = s.J = kB64;
-        s.nIB = s.nJT = h->npad / kB64;
+        s.nIB = s.nJT = (nreal + kB64 - 1) / kB64;
         s.nT = static_cast<long long>(s.nIB) * (s.nIB + 1) / 2;
         if (want_sym == SD_DENSE_SYMMETRIC || s.nT * SD_DENSE_SYM_SMS_PER_TILE >= h->num_sms) {
             const long long swant = static_cast<long long>(h->num_sms) * socc * SD_DENSE_SYM_CTA_SCALE;
@@ -949,7 +955,7 @@ cudaError_t dense_setup(sd_handle *h) {
         DenseGeom s{};
         s.sym = 1;
         s.I = s.J = B;
-        s.nIB = s.nJT = h->npad / B;
+        s.nIB = s.nJT = (nreal + B - 1) / B;
         s.nT = static_cast<long long>(s.nIB) * (s.nIB + 1) / 2;
         // (blocks of 128: four times as many, and smaller, tiles are needed to beat the
         // directed kernel: measured directed faster at n = 2048, symmetric at 4096)
