@@ -347,6 +347,7 @@ def run_ours(args):
     extra = {}
     if world > 1:
         extra.update(_leg_tile_sharded(args, x, F, stream, world, rank))
+        extra.update(_leg_batched_sharded(args, stream, world, rank))
     if rank == 0 and not args.quick:
         extra.update(legs(args, x, F, stream, flush, workloads=(world == 1)))
 
@@ -411,6 +412,36 @@ def _leg_tile_sharded(args, x, F, stream, world, rank):
                              "scaling": "strong", "ranks": world, "n": n, "all_pairs_kernel": kind,
                              "exchange": "%s all-gather of 24 B per particle and rank per step"
                                          % ("host-staged gloo" if via_host else "NCCL")}}
+
+
+def _leg_batched_sharded(args, stream, world, rank):
+    """The batched workload (16,384 clusters) split over the ranks by cluster shards
+    balanced by pair work; no data moves between ranks.  Steps/s of the whole batch
+    from the slowest rank (strong scaling)."""
+    import torch
+    from paper_1205_6333_gb300 import inputs
+    from paper_1205_6333_gb300.distributed import ShardedBatch
+    w = inputs.config_inputs(4)
+    off = w["offsets"]
+    sb = ShardedBatch(off, rank, world, prec="fp32c", stream="torch", torch_allocator=True)
+    sb.set_positions(w["x"])
+    sb.set_forces(w["F"])
+    sb.step(0.01, 16)   # (autotune, graph capture)
+    torch.cuda.synchronize()
+    _barrier(world)
+    k = max(args.steps, 32)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sb.step(0.01, k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(world)
+    ms = _max_over_ranks(e0.elapsed_time(e1) / k, world)
+    sb.close()
+    return {"batched_sharded": {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "scaling": "strong", "ranks": world,
+                                "clusters_this_rank_0": None if rank else sb.c1 - sb.c0,
+                                "split": "contiguous clusters balanced by the sum of N_c^2, no exchange"}}
 
 
 def run_leg(args):

@@ -15,6 +15,10 @@ Row shards (the directed kernel only):
   Rank r computes the velocities of its own rows (``sd_*_rows``) and an all-gather
   of those rows (24 B per particle) restores the replicated state.
 
+Cluster shards (batched workloads): the clusters are independent, so rank r simply
+steps a contiguous run of them (``shard_clusters``, ``ShardedBatch``), balanced by
+pair work (the sum of N_c^2); no data moves between ranks.
+
 This module only partitions the work and moves data (the collective and nothing
 else); every step of the method runs in the library's kernels.  Collectives run on
 the default process group unless ``group`` is given (NCCL between GPUs; gloo with
@@ -113,3 +117,84 @@ def sharded_steps(system, dt: float, nsteps: int, rank: int, world: int, x=None,
         _gather_rows(x, rank, world, group)
         system.set_positions(x)
     return x
+
+
+def shard_clusters(offsets, rank: int, world: int):
+    """Contiguous clusters [c0, c1) of `rank`, cut where the running pair work (the sum
+    of N_c^2 over the clusters before the cut) first reaches rank / world of the total,
+    so every rank gets about the same work (up to one cluster's)."""
+    import numpy as np
+    off = np.asarray(offsets, dtype=np.int64)
+    nc = off.size - 1
+    work = np.cumsum(np.diff(off) ** 2)
+    total = int(work[-1]) if nc > 0 else 0
+
+    def cut(r):
+        if r <= 0 or nc == 0:
+            return 0
+        if r >= world:
+            return nc
+        return int(np.searchsorted(work, total * r / world, side="left")) + 1
+
+    c0, c1 = cut(rank), cut(rank + 1)
+    return min(c0, nc), min(max(c1, c0), nc)
+
+
+class ShardedBatch:
+    """This rank's share of a batch of independent clusters: the clusters
+    [c0, c1) of ``shard_clusters`` as one ``Batch``.  Positions and forces are given and
+    returned for the whole batch (n_total x 3); only this rank's rows are used or
+    written."""
+
+    def __init__(self, offsets, rank: int, world: int, **kw):
+        import numpy as np
+        from . import Batch
+        off = np.asarray(offsets, dtype=np.int64)
+        self.c0, self.c1 = shard_clusters(off, rank, world)
+        self.p0, self.p1 = int(off[self.c0]), int(off[self.c1])
+        # (more ranks than clusters: an empty share, no batch)
+        self.batch = Batch((off[self.c0:self.c1 + 1] - self.p0).astype(np.int32), **kw) if self.c1 > self.c0 else None
+
+    def set_positions(self, x):
+        if self.batch:
+            self.batch.set_positions(x[self.p0:self.p1])
+
+    def set_forces(self, f):
+        if self.batch:
+            self.batch.set_forces(f[self.p0:self.p1])
+
+    def step(self, dt, nsteps=1):
+        if self.batch:
+            self.batch.step(dt, nsteps)
+
+    def get_positions(self, out):
+        """Writes this rank's rows of `out` (the whole batch's n_total x 3 array)."""
+        if self.batch:
+            out[self.p0:self.p1] = self.batch.get_positions()
+        return out
+
+    def close(self):
+        if self.batch:
+            self.batch.close()
+
+
+def gather_cluster_rows(x_local, offsets, rank: int, world: int, group=None):
+    """The whole batch's n_total x 3 positions on every rank, from each rank's rows of
+    its ``shard_clusters`` share (x_local, a CPU tensor or array): one all-gather of
+    equal-size padded blocks."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    off = np.asarray(offsets, dtype=np.int64)
+    ranges = [shard_clusters(off, r, world) for r in range(world)]
+    rows = [(int(off[a]), int(off[b])) for a, b in ranges]
+    chunk = max(max(b - a for a, b in rows), 1)
+    send = torch.zeros((chunk, 3), dtype=torch.float64)
+    p0, p1 = rows[rank]
+    send[: p1 - p0] = torch.as_tensor(np.asarray(x_local), dtype=torch.float64)[: p1 - p0]
+    recv = [torch.empty_like(send) for _ in range(world)]
+    dist.all_gather(recv, send, group=group)
+    out = np.empty((int(off[-1]), 3))
+    for r, (a, b) in enumerate(rows):
+        out[a:b] = recv[r][: b - a].numpy()
+    return out

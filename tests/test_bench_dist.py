@@ -53,8 +53,8 @@ def test_single_rank_is_identity():
 def test_bench_two_ranks_sharing_the_gpu():
     """bench.py launched as the driver launches it for N > 1 (torchrun, one process per
     rank), here two ranks on one GPU with the exchange staged through host memory
-    (gloo): rank 0 prints one JSON line for both ranks, with the replicas' value and
-    the tile-sharded system's."""
+    (gloo): rank 0 prints one JSON line for both ranks, with the replicas' value, the
+    tile-sharded system's and the cluster-sharded batch's."""
     import json
     import subprocess
     import sys
@@ -71,3 +71,5 @@ def test_bench_two_ranks_sharing_the_gpu():
     assert line["n_gpus"] == 2 and line["value"] > 0 and line["config"]["parallelism"] == "replicas"
     ts = line["tile_sharded"]
     assert ts["ranks"] == 2 and ts["value"] > 0 and ts["scaling"] == "strong"
+    bs = line["batched_sharded"]
+    assert bs["ranks"] == 2 and bs["steps_per_s"] > 0 and 0 < bs["clusters_this_rank_0"] < 16384

@@ -7,7 +7,10 @@ Tile shards (the all-pairs sum divided by pairs, either kernel, every precision)
     FP64 oracle element by element, for the apply and for Euler steps;
   * two processes sharing one GPU run the real kernels and exchange their shares
     over gloo (host staging), as distributed.tile_sharded_steps does between GPUs.
-Row shards (directed kernel): the same on CPU, and bit-identical logical shards."""
+Row shards (directed kernel): the same on CPU, and bit-identical logical shards.
+Cluster shards (batched workloads): the work-balanced partition, gloo ranks that
+gather their clusters' results, and logical shards on one GPU equal to the whole
+batch bit for bit."""
 import os
 import socket
 
@@ -404,3 +407,111 @@ def test_tile_sharded_two_processes_one_gpu():
     assert rel_err(V0, oracle.mobility_apply(x0, fe, nthreads=8)) <= 1e-5
     ref = oracle.euler(x0, 4, 0.05, fe, (0.0, 0.0, -1.0), nthreads=8)
     assert np.linalg.norm(X0 - ref, axis=1).max() <= 1e-5 * np.linalg.norm(ref - x0, axis=1).max()
+
+# ---------------------------------------------------------------- cluster shards (batched)
+
+def _cluster_case():
+    sizes = np.array([0, 5, 256, 3, 130, 0, 77, 200, 1, 64, 33, 150], dtype=np.int64)
+    x, off = inputs.ball_rsa_batch(sizes, 0.05, 931)
+    F = inputs.normal_forces(x.shape[0], 932)
+    return x, off, F
+
+
+def test_shard_clusters_partition():
+    from paper_1205_6333_gb300.distributed import shard_clusters
+    x, off, F = _cluster_case()
+    sizes = np.diff(off)
+    for world in [1, 2, 3, 5, 12, 20]:
+        ranges = [shard_clusters(off, r, world) for r in range(world)]
+        assert ranges[0][0] == 0 and ranges[-1][1] == len(sizes)
+        for (a0, b0), (a1, b1) in zip(ranges, ranges[1:]):
+            assert b0 == a1 and a0 <= b0
+        work = [int((sizes[a:b] ** 2).sum()) for a, b in ranges]
+        # every rank is within one cluster's work of an equal share
+        assert max(work) <= (sizes ** 2).sum() / world + (sizes ** 2).max()
+    sizes = inputs.cluster_sizes(16384, 4, 256, 933)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    work = [int((sizes[a:b] ** 2).sum()) for a, b in (shard_clusters(off, r, 8) for r in range(8))]
+    assert max(work) / (sum(work) / 8) < 1.005
+
+
+def _cluster_worker(rank, world, port, out):
+    import torch.distributed as dist
+    from paper_1205_6333_gb300.distributed import gather_cluster_rows, shard_clusters
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    x, off, F = _cluster_case()
+    c0, c1 = shard_clusters(off, rank, world)
+    local = []
+    for c in range(c0, c1):   # the oracle stands in for this rank's batch
+        a, b = off[c], off[c + 1]
+        local.append(oracle.euler(x[a:b], 3, 0.01, fext=F[a:b]) if b > a else np.empty((0, 3)))
+    xl = np.concatenate(local) if local else np.empty((0, 3))
+    out[rank] = gather_cluster_rows(xl, off, rank, world).tobytes()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_cluster_shards_gloo(world):
+    """Each rank steps its clusters; one all-gather gives every rank the whole batch,
+    equal bit for bit to stepping all clusters in one place."""
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_cluster_worker, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(180)
+        assert p.exitcode == 0
+    x, off, F = _cluster_case()
+    ref = np.concatenate([oracle.euler(x[off[c]:off[c + 1]], 3, 0.01, fext=F[off[c]:off[c + 1]])
+                          for c in range(len(off) - 1) if off[c + 1] > off[c]])
+    for r in range(world):
+        np.testing.assert_array_equal(np.frombuffer(out[r]).reshape(-1, 3), ref)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", ["sym", "blocks"])
+def test_cluster_shards_logical_gpu(shape):
+    """Two cluster shards on one GPU, each its own Batch with the same kernel pinned,
+    give the whole batch's positions and match the oracle.  With the symmetric kernel
+    bit for bit (a cluster's result does not depend on which clusters share its
+    launch); the block kernel aligns its four-source steps to where a cluster lands in
+    a CTA's staging area, which its neighbours decide, so there the shards agree to
+    FP32 rounding."""
+    from paper_1205_6333_gb300.distributed import ShardedBatch
+    import paper_1205_6333_gb300 as sd
+    x, off, F = _cluster_case()
+    r = 0 if shape == "sym" else 1
+
+    def pin(b):
+        b.set_shape(next(k for k, sh in enumerate(b.shapes()) if sh["targets_per_thread"] == r and sh["threads"] == 128))
+
+    full = sd.Batch(off.astype(np.int32))
+    pin(full)
+    full.set_positions(x)
+    full.set_forces(F)
+    full.step(0.01, 5)
+    xf = full.get_positions()
+    full.close()
+    xs = np.zeros_like(x)
+    for rank in range(2):
+        sb = ShardedBatch(off, rank, 2)
+        pin(sb.batch)
+        sb.set_positions(x)
+        sb.set_forces(F)
+        sb.step(0.01, 5)
+        sb.get_positions(xs)
+        sb.close()
+    if shape == "sym":
+        np.testing.assert_array_equal(xs, xf)
+    else:
+        assert np.abs(xs - xf).max() <= 1e-7 * np.abs(xf - x).max()
+    for c in range(len(off) - 1):
+        a, b = off[c], off[c + 1]
+        if b > a:
+            ref = oracle.euler(x[a:b], 5, 0.01, fext=F[a:b])
+            assert np.abs(xs[a:b] - ref).max() <= 1e-5 * max(np.abs(ref - x[a:b]).max(), 1e-300)
