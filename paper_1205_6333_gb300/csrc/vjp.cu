@@ -98,10 +98,10 @@ __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const size_t i = static_cast<size_t>(ib) * g.I + tid + k * kNT;
-            if constexpr (COMP) {
+            if constexpr (COMP) {   // the (hi, lo) pairs themselves, for the epilogue's FP32 TwoSum
                 for (int d = 0; d < 3; ++d) {
-                    dM[d * static_cast<size_t>(npad) + i] = static_cast<double>(mh[k][d]) + ml[k][d];
-                    dG[d * static_cast<size_t>(npad) + i] = static_cast<double>(gh[k][d]) + gl[k][d];
+                    reinterpret_cast<float2 *>(dM)[d * static_cast<size_t>(npad) + i] = make_float2(mh[k][d], ml[k][d]);
+                    reinterpret_cast<float2 *>(dG)[d * static_cast<size_t>(npad) + i] = make_float2(gh[k][d], gl[k][d]);
                 }
             } else {
                 dM[i] = m[k].x;
@@ -192,6 +192,14 @@ static void *pick_vjp(int tensor, int mode, bool per) {
     return dt == T_OSEEN ? vjp_fn<T_OSEEN, MODE_FP32C>(per) : vjp_fn<T_RP, MODE_FP32C>(per);
 }
 
+// The grid holds SD_VJP_CTA_SCALE times as many CTAs as fit at once, so the block
+// scheduler evens out the SMs' shares (N = 4,096: 57 -> 51 us; 8x gave the same).
+#ifndef SD_VJP_CTA_SCALE
+#define SD_VJP_CTA_SCALE 2
+#endif
+#ifndef SD_VJP_JMIN
+#define SD_VJP_JMIN 64   // smallest j-tile (32 measured slower at N = 4,096)
+#endif
 cudaError_t vjp_setup(sd_handle *h) {
     DenseGeom g{};
     g.I = kNT * kRV;
@@ -199,8 +207,8 @@ cudaError_t vjp_setup(sd_handle *h) {
     const int mode = (h->mode == MODE_FP64) ? MODE_FP64 : MODE_FP32C;
     void *fn = pick_vjp(h->tensor, mode, h->pc.periodic != 0);
     int occ = 0;
-    const int Jc[3] = {kJmax, 128, 64};
-    for (int ci = 0; ci < 3; ++ci) {
+    const int Jc[4] = {kJmax, 128, 64, SD_VJP_JMIN};
+    for (int ci = 0; ci < 4; ++ci) {
         const int J = Jc[ci];
         if (mode == MODE_FP64 && J > 128) continue;
         const size_t smem = 6 * static_cast<size_t>(J) * v4b(mode);
@@ -214,7 +222,7 @@ cudaError_t vjp_setup(sd_handle *h) {
     }
     occ = std::max(occ, 1);
     const long long T = static_cast<long long>(g.nIB) * g.nJT;
-    const long long want = static_cast<long long>(h->num_sms) * occ;
+    const long long want = static_cast<long long>(h->num_sms) * occ * SD_VJP_CTA_SCALE;
     g.chunk = std::max(1LL, (T + want - 1) / want);
     g.grid = static_cast<int>((T + g.chunk - 1) / g.chunk);
     int ms = 0;
@@ -293,11 +301,27 @@ __device__ __forceinline__ void vjp_epilogue_lane(const VjpEpiArgs &a, int i, in
     {
         const int ib = i / a.g.I;
         const int ns = geom_last(a.g, ib) - geom_first(a.g, ib) + 1;
-        for (int s = sub; s < ns; s += kWalkLanes)
-            for (int d = 0; d < 3; ++d) {
-                MG[d] += a.partM[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
-                MG[3 + d] += a.partG[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
-            }
+        if constexpr (MODE == MODE_FP64) {
+            for (int s = sub; s < ns; s += kWalkLanes)
+                for (int d = 0; d < 3; ++d) {
+                    MG[d] += a.partM[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+                    MG[3 + d] += a.partG[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+                }
+        } else {   // (hi, lo) float pairs, summed with FP32 TwoSum (FP64 issues at 1/64 the rate)
+            const float2 *pM = reinterpret_cast<const float2 *>(a.partM);
+            const float2 *pG = reinterpret_cast<const float2 *>(a.partG);
+            float hi[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, lo[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            for (int s = sub; s < ns; s += kWalkLanes)
+                for (int d = 0; d < 3; ++d) {
+                    const float2 qm = pM[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+                    const float2 qg = pG[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+                    fold2(hi[d], lo[d], qm.x);
+                    lo[d] = __fadd_rn(lo[d], qm.y);
+                    fold2(hi[3 + d], lo[3 + d], qg.x);
+                    lo[3 + d] = __fadd_rn(lo[3 + d], qg.y);
+                }
+            for (int d = 0; d < 6; ++d) MG[d] += static_cast<double>(hi[d]) + static_cast<double>(lo[d]);
+        }
     }
     const V4 pi = pm[i], fi4 = fm[i], wi4 = wm[i];
     V3 Fi, Wi;
