@@ -119,13 +119,15 @@ typedef struct sd_config {
                                 (SD_ERR_UNSUPPORTED). */
     double verlet_skin;      /* neighbour-list skin of sd_step (Sec. 3.1 step 2, Verlet lists): 0 = default
                                 0.5a, < 0 = off.  With constant forces (no repulsion, no lubrication),
-                                the FP64 near-pair list holds the pairs within r_near + skin and is
-                                rebuilt only when some particle has moved more than skin / 2 relative
-                                to particle 0 since the last build (a uniform translation never forces
-                                one); each particle's list is in ascending partner order, so a step
-                                gives the same result bit for bit from a fresh or a reused list.  Off
-                                automatically when forces are not constant or a periodic side is
-                                below 3 (max cutoff + skin). */
+                                the steps keep an FP64 near-pair list of the pairs within r_near + skin,
+                                built by sd_set_positions and rebuilt once some particle has moved
+                                skin / 4 relative to particle 0 since the last build (a uniform
+                                translation never forces one; up to skin / 2 the list still holds
+                                every pair within r_near).  The rebuild and the near terms run beside
+                                the all-pairs kernel.  Each particle's list is in ascending partner
+                                order, so a step gives the same result bit for bit from a fresh or a
+                                reused list.  Off automatically when forces are not constant or a
+                                periodic side is below 3 (max cutoff + skin). */
 } sd_config;
 
 typedef struct sd_handle sd_handle;
@@ -142,7 +144,9 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out);
 void sd_destroy(sd_handle *h);
 
 /* Positions r_i (n x 3 doubles), copied into the handle's FP64 state; also
- * refreshes the FP32 mirror the all-pairs kernel reads.  Non-finite values give
+ * refreshes the FP32 mirror the all-pairs kernel reads; with Verlet lists it also
+ * builds the steps' near-pair list around the new positions, so a trajectory
+ * resumed from positions read back continues bit for bit.  Non-finite values give
  * SD_ERR_NONFINITE (host pointers: from this call; device pointers: deferred). */
 sd_status sd_set_positions(sd_handle *h, const double *xyz, int on_device);
 sd_status sd_get_positions(sd_handle *h, double *xyz, int on_device);
