@@ -283,7 +283,7 @@ static cudaError_t adjoint_segment(sd_handle *h, cudaStream_t st, double dt, int
     for (int64_t k = len - 1; k >= 0 && e == cudaSuccess; --k) {
         e = launch_stage_forces(h, st, h->lam, SD_DTYPE_F64, 0, h->Wa64, h->wam);
         if (e == cudaSuccess) e = launch_build_cells(h, st, segx(k), h->posm);
-        if (e == cudaSuccess) e = launch_vjp_dense(h, st, h->posm.aos, h->frcm.aos, h->wam.aos, h->part, h->part2);
+        if (e == cudaSuccess) e = launch_vjp_dense(h, st, h->posm, h->frcm, h->wam, h->part, h->part2);
         if (e == cudaSuccess)
             e = launch_vjp_epilogue(h, st, segx(k), h->posm.aos, h->F64, h->frcm.aos, h->Wa64, h->wam.aos, -1,
                                     nullptr, nullptr, dt, h->lam, h->gFacc);
@@ -476,7 +476,7 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
         if (!ok) break;
         m->aos = dalloc(h, np * vb);
         ok = m->aos != nullptr;
-        if (ok && soa && m != &h->wam) {
+        if (ok && soa) {   // (the cotangents' too: the packed FP32C VJP kernel stages SoA tiles)
             m->soa = static_cast<float *>(dalloc(h, 3 * np * sizeof(float)));
             ok = m->soa != nullptr;
         }
@@ -971,7 +971,7 @@ sd_status sd_mobility_vjp(sd_handle *h, const void *F, const void *W, void *gX, 
     if (s == SD_OK) s = launch_check(launch_stage_forces(h, h->stream, Wd, dtype, 0, h->Wa64, h->wam), "stage W");
     if (s == SD_OK) s = ensure_cells(h);
     if (s == SD_OK)
-        s = launch_check(launch_vjp_dense(h, h->stream, h->posm.aos, h->frcam.aos, h->wam.aos, h->part, h->part2),
+        s = launch_check(launch_vjp_dense(h, h->stream, h->posm, h->frcam, h->wam, h->part, h->part2),
                          "vjp kernel");
     if (s == SD_OK)
         s = launch_check(launch_vjp_epilogue(h, h->stream, h->x64[h->cur], h->posm.aos, h->Fa64, h->frcam.aos,

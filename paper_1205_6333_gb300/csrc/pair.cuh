@@ -418,6 +418,68 @@ __device__ __forceinline__ void vjp_pair_f32(float xi, float yi, float zi, float
     m.z = __fmaf_rn(bWj, dz, __fmaf_rn(A, w.z, m.z));
 }
 
+// Packed constants of vjp_pair_f32x2: the values vjp_pair_f32 forms from PairConst,
+// each as a (c, c) pair (products such as -5 m3c3 rounded in FP32 as there).
+struct VjpConst2 {
+    f2 c1, c3, m3c3, nc1, n5m3c3, n3c1;   // c1, c3, m3c3, -c1, -5 m3c3, -3 c1
+    float r2min;
+    f2 negL[3], invL[3];
+};
+
+// Two pairs at once, (i, j0) and (i, j1): XI.. FI.. WI.. = the target's values in both
+// lanes, P* F* W* = (source j0, source j1).  Lane by lane the operation sequence of
+// vjp_pair_f32, so each lane's terms are bit-identical to it (the epilogue subtracts
+// vjp_pair_f32's value for the pairs closer than r_near).
+template <int TENSOR, bool PER = false>
+__device__ __forceinline__ void vjp_pair_f32x2(f2 XI, f2 YI, f2 ZI, f2 FIx, f2 FIy, f2 FIz, f2 WIx, f2 WIy, f2 WIz,
+                                               f2 PX, f2 PY, f2 PZ, f2 FX, f2 FY, f2 FZ, f2 WX, f2 WY, f2 WZ,
+                                               const VjpConst2 &c, f2 (&M)[3], f2 (&G)[3]) {
+    f2 dx = sub2(XI, PX);
+    f2 dy = sub2(YI, PY);
+    f2 dz = sub2(ZI, PZ);
+    if (PER) {
+        dx = min_image2(dx, c.negL[0], c.invL[0]);
+        dy = min_image2(dy, c.negL[1], c.invL[1]);
+        dz = min_image2(dz, c.negL[2], c.invL[2]);
+    }
+    const f2 r2p = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    float ra, rb;
+    upk2(r2p, ra, rb);
+    ra = fmaxf(ra, c.r2min);
+    rb = fmaxf(rb, c.r2min);
+    const f2 ri = pk2(rsqrt_sfu(ra), rsqrt_sfu(rb));
+    const f2 ri2 = mul2(ri, ri);
+    const f2 ri3 = mul2(ri, ri2);
+    const f2 ri5 = mul2(ri3, ri2);
+    f2 A, B, dA, dB;
+    if (TENSOR == T_OSEEN) {
+        A = mul2(c.c1, ri);
+        B = mul2(c.c1, ri3);
+        dA = mul2(c.nc1, ri3);
+        dB = mul2(c.n3c1, ri5);
+    } else {
+        A = mul2(ri, fma2(c.c3, ri2, c.c1));
+        B = mul2(ri3, fma2(c.m3c3, ri2, c.c1));
+        dA = mul2(ri3, fma2(c.m3c3, ri2, c.nc1));
+        dB = mul2(ri5, fma2(c.n5m3c3, ri2, c.n3c1));
+    }
+    const f2 Wir = fma2(dz, WIz, fma2(dy, WIy, mul2(dx, WIx)));
+    const f2 Fir = fma2(dz, FIz, fma2(dy, FIy, mul2(dx, FIx)));
+    const f2 Wjr = fma2(dz, WZ, fma2(dy, WY, mul2(dx, WX)));
+    const f2 Fjr = fma2(dz, FZ, fma2(dy, FY, mul2(dx, FX)));
+    const f2 WiFj = fma2(WIz, FZ, fma2(WIy, FY, mul2(WIx, FX)));
+    const f2 U = fma2(WZ, FIz, fma2(WY, FIy, fma2(WX, FIx, WiFj)));
+    const f2 Q = fma2(Wjr, Fir, mul2(Wir, Fjr));
+    const f2 cr = fma2(dB, Q, mul2(dA, U));
+    const f2 bFj = mul2(B, Fjr), bWi = mul2(B, Wir), bFi = mul2(B, Fir), bWj = mul2(B, Wjr);
+    G[0] = fma2(cr, dx, fma2(WIx, bFj, fma2(FX, bWi, fma2(WX, bFi, fma2(FIx, bWj, G[0])))));
+    G[1] = fma2(cr, dy, fma2(WIy, bFj, fma2(FY, bWi, fma2(WY, bFi, fma2(FIy, bWj, G[1])))));
+    G[2] = fma2(cr, dz, fma2(WIz, bFj, fma2(FZ, bWi, fma2(WZ, bFi, fma2(FIz, bWj, G[2])))));
+    M[0] = fma2(bWj, dx, fma2(A, WX, M[0]));
+    M[1] = fma2(bWj, dy, fma2(A, WY, M[1]));
+    M[2] = fma2(bWj, dz, fma2(A, WZ, M[2]));
+}
+
 // The same pair in FP64 with the clamp (what the FP64 dense VJP kernel adds).
 template <int TENSOR, bool PER = false>
 __device__ __forceinline__ void vjp_pair_f64(double xi, double yi, double zi, double3 Fi, double3 Wi, dbl4 p,

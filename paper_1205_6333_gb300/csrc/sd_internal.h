@@ -332,8 +332,8 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
                             int row1 = -1, const EpiShard *shard = nullptr, bool vlist = false);
 // vjp.cu
 cudaError_t vjp_setup(sd_handle *h);
-cudaError_t launch_vjp_dense(sd_handle *h, cudaStream_t st, const void *posm, const void *frcm, const void *wm,
-                             double *partM, double *partG);
+cudaError_t launch_vjp_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, Mirror wm, double *partM,
+                             double *partG);
 cudaError_t launch_vjp_epilogue(sd_handle *h, cudaStream_t st, const double *x64, const void *posm,
                                 const double *F64, const void *frcm, const double *W64, const void *wm,
                                 int out_dtype, void *gx_out, void *gF_out, double dt, double *lam_acc,

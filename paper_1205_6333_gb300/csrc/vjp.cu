@@ -178,7 +178,166 @@ __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 
     }
 }
 
-static size_t v4b(int mode) { return mode == MODE_FP64 ? sizeof(dbl4) : sizeof(float4); }
+// FP32C: the same sums with the pair terms packed over pairs of sources.  The j-tiles
+// are staged as nine float arrays (x, y, z, Fx, Fy, Fz, Wx, Wy, Wz: nine bulk copies),
+// so two consecutive j's form one 64-bit operand and every instruction of
+// vjp_pair_f32x2 evaluates (i, j) and (i, j + 1): half the issued instructions of the
+// scalar loop (N = 4,096: 45 us against 48).  Each thread owns R targets, duplicated
+// into both lanes; its packed
+// accumulators sum even and odd j's separately, and both lanes are folded into (hi, lo)
+// TwoSum accumulators in shared memory after every tile.  Slots are (hi, lo) float
+// pairs, as the FP32C epilogue reads them.
+// Targets per thread of the packed FP32C VJP kernel.  One keeps it at about 120
+// registers (4 CTAs per SM); two took 140 and were slower at N = 4,096 (50 against 45 us).
+#ifndef SD_VJP2_R
+#define SD_VJP2_R 1
+#endif
+constexpr int kRV2 = SD_VJP2_R;
+
+template <int TENSOR, bool PER>
+__global__ void __launch_bounds__(kNT) vjp2_kernel(const float *__restrict__ pos, const float *__restrict__ frc,
+                                                   const float *__restrict__ wv, double *__restrict__ partM,
+                                                   double *__restrict__ partG, int npad, DenseGeom g, VjpConst2 c,
+                                                   int *__restrict__ err, long long wd) {
+    constexpr int R = kRV2;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+    float *s_tile = reinterpret_cast<float *>(smem);   // [2 stages][9 arrays][J]
+    float *s_acc = s_tile + 18 * g.J;                   // [R][12][kNT]: M hi(3) lo(3), G hi(3) lo(3)
+
+    const int tid = threadIdx.x;
+    const long long T = static_cast<long long>(g.nIB) * g.nJT;
+    const long long t0 = static_cast<long long>(blockIdx.x) * g.chunk;
+    const long long t1 = (t0 + g.chunk < T) ? t0 + g.chunk : T;
+    if (t0 >= t1) return;
+    const uint32_t arr_bytes = static_cast<uint32_t>(g.J * sizeof(float));
+
+    int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0;   // bookkeeping of thread 0 only
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    auto issue = [&](long long t, int stg) {
+        const size_t j0 = static_cast<size_t>(t % g.nJT) * g.J;
+        float *dst = s_tile + stg * 9 * g.J;
+        mbar_arrive_expect_tx(&bars[stg], 9 * arr_bytes);
+        for (int a = 0; a < 3; ++a) {
+            bulk_g2s(dst + a * g.J, pos + a * static_cast<size_t>(npad) + j0, arr_bytes, &bars[stg]);
+            bulk_g2s(dst + (3 + a) * g.J, frc + a * static_cast<size_t>(npad) + j0, arr_bytes, &bars[stg]);
+            bulk_g2s(dst + (6 + a) * g.J, wv + a * static_cast<size_t>(npad) + j0, arr_bytes, &bars[stg]);
+        }
+        if (stg == 0) ++issued0; else ++issued1;
+    };
+    if (tid == 0)
+        for (int q = 0; q < 2 && t0 + q < t1; ++q) issue(t0 + q, q);
+
+    f2 XI[R], YI[R], ZI[R], FI[R][3], WI[R][3];
+    int cur_ib = -1;
+    bool aborted = false;
+
+    auto flush = [&](int ib) {
+        const int slot = static_cast<int>(blockIdx.x) - geom_first(g, ib);
+        float2 *dM = reinterpret_cast<float2 *>(partM) + static_cast<size_t>(slot) * 3 * npad;
+        float2 *dG = reinterpret_cast<float2 *>(partG) + static_cast<size_t>(slot) * 3 * npad;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const size_t i = static_cast<size_t>(ib) * g.I + tid + k * kNT;
+            const float *q = s_acc + k * 12 * kNT + tid;
+            for (int d = 0; d < 3; ++d) {
+                dM[d * static_cast<size_t>(npad) + i] = make_float2(q[d * kNT], q[(3 + d) * kNT]);
+                dG[d * static_cast<size_t>(npad) + i] = make_float2(q[(6 + d) * kNT], q[(9 + d) * kNT]);
+            }
+        }
+    };
+
+    for (long long t = t0; t < t1; ++t) {
+        const int ib = static_cast<int>(t / g.nJT);
+        if (ib != cur_ib) {
+            if (cur_ib >= 0) flush(cur_ib);
+            cur_ib = ib;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const size_t i = static_cast<size_t>(ib) * g.I + tid + k * kNT;
+                const float x = pos[i], y = pos[npad + i], z = pos[2 * static_cast<size_t>(npad) + i];
+                XI[k] = pk2(x, x);
+                YI[k] = pk2(y, y);
+                ZI[k] = pk2(z, z);
+                for (int d = 0; d < 3; ++d) {
+                    const float fv = frc[d * static_cast<size_t>(npad) + i], wvv = wv[d * static_cast<size_t>(npad) + i];
+                    FI[k][d] = pk2(fv, fv);
+                    WI[k][d] = pk2(wvv, wvv);
+                }
+                for (int e = 0; e < 12; ++e) s_acc[(k * 12 + e) * kNT + tid] = 0.0f;
+            }
+        }
+        const int q = static_cast<int>(t - t0);
+        const int st = q & 1;
+        if (!aborted) {
+            if (mbar_wait_bounded(&bars[st], (q >> 1) & 1, wd)) {
+                if (tid == 0) { if (st == 0) ++waited0; else ++waited1; }
+            } else {
+                atomicOr(err, DEV_ERR_TIMEOUT);
+                s_abort = 1;
+            }
+        }
+        const float *src = s_tile + st * 9 * g.J;
+        f2 M[R][3], G[R][3];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            for (int d = 0; d < 3; ++d) M[k][d] = G[k][d] = 0ull;
+#pragma unroll 2
+        for (int jj = 0; jj < g.J; jj += 4) {
+            f2 P[9][2];   // four sources: two packed pairs per array
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(src + a * g.J + jj);
+                P[a][0] = v.x;
+                P[a][1] = v.y;
+            }
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+                    vjp_pair_f32x2<TENSOR, PER>(XI[k], YI[k], ZI[k], FI[k][0], FI[k][1], FI[k][2], WI[k][0], WI[k][1],
+                                                WI[k][2], P[0][h2], P[1][h2], P[2][h2], P[3][h2], P[4][h2], P[5][h2],
+                                                P[6][h2], P[7][h2], P[8][h2], c, M[k], G[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            for (int d = 0; d < 3; ++d) {
+                float lo, hi;
+                float *q0 = s_acc + (k * 12 + d) * kNT + tid;   // M hi; M lo at +3 kNT
+                upk2(M[k][d], lo, hi);
+                float h = q0[0], l = q0[3 * kNT];
+                fold2(h, l, lo);
+                fold2(h, l, hi);
+                q0[0] = h;
+                q0[3 * kNT] = l;
+                float *q1 = s_acc + (k * 12 + 6 + d) * kNT + tid;   // G hi; G lo at +3 kNT
+                upk2(G[k][d], lo, hi);
+                h = q1[0];
+                l = q1[3 * kNT];
+                fold2(h, l, lo);
+                fold2(h, l, hi);
+                q1[0] = h;
+                q1[3 * kNT] = l;
+            }
+        __syncthreads();   // every thread is done with stage st
+        aborted = s_abort != 0;
+        if (tid == 0 && !aborted && t + 2 < t1) issue(t + 2, st);
+    }
+    flush(cur_ib);
+    if (tid == 0) {
+        for (int k = waited0; k < issued0; ++k)
+            if (!mbar_wait_bounded(&bars[0], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+        for (int k = waited1; k < issued1; ++k)
+            if (!mbar_wait_bounded(&bars[1], k & 1, drain_limit(wd))) atomicOr(err, DEV_ERR_TIMEOUT);
+    }
+}
 
 template <int TT, int MM>
 static void *vjp_fn(bool per) {
@@ -186,10 +345,22 @@ static void *vjp_fn(bool per) {
                : reinterpret_cast<void *>(&vjp_kernel<TT, MM, false>);
 }
 
+template <int TT>
+static void *vjp2_fn(bool per) {
+    return per ? reinterpret_cast<void *>(&vjp2_kernel<TT, true>) : reinterpret_cast<void *>(&vjp2_kernel<TT, false>);
+}
+
 static void *pick_vjp(int tensor, int mode, bool per) {
     const int dt = (tensor == T_OSEEN) ? T_OSEEN : T_RP;
     if (mode == MODE_FP64) return dt == T_OSEEN ? vjp_fn<T_OSEEN, MODE_FP64>(per) : vjp_fn<T_RP, MODE_FP64>(per);
-    return dt == T_OSEEN ? vjp_fn<T_OSEEN, MODE_FP32C>(per) : vjp_fn<T_RP, MODE_FP32C>(per);
+    return dt == T_OSEEN ? vjp2_fn<T_OSEEN>(per) : vjp2_fn<T_RP>(per);
+}
+
+// Dynamic shared memory: FP64, two stages of three dbl4 arrays; FP32C, two stages of
+// nine float arrays and the (hi, lo) accumulators.
+static size_t vjp_smem(int mode, int J) {
+    if (mode == MODE_FP64) return 6 * static_cast<size_t>(J) * sizeof(dbl4);
+    return 18 * static_cast<size_t>(J) * sizeof(float) + static_cast<size_t>(kRV2) * 12 * kNT * sizeof(float);
 }
 
 // The grid holds SD_VJP_CTA_SCALE times as many CTAs as fit at once, so the block
@@ -202,16 +373,16 @@ static void *pick_vjp(int tensor, int mode, bool per) {
 #endif
 cudaError_t vjp_setup(sd_handle *h) {
     DenseGeom g{};
-    g.I = kNT * kRV;
-    g.nIB = h->npad / g.I;
     const int mode = (h->mode == MODE_FP64) ? MODE_FP64 : MODE_FP32C;
+    g.I = kNT * (mode == MODE_FP64 ? kRV : kRV2);
+    g.nIB = h->npad / g.I;
     void *fn = pick_vjp(h->tensor, mode, h->pc.periodic != 0);
     int occ = 0;
     const int Jc[4] = {kJmax, 128, 64, SD_VJP_JMIN};
     for (int ci = 0; ci < 4; ++ci) {
         const int J = Jc[ci];
         if (mode == MODE_FP64 && J > 128) continue;
-        const size_t smem = 6 * static_cast<size_t>(J) * v4b(mode);
+        const size_t smem = vjp_smem(mode, J);
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kNT, smem);
@@ -233,28 +404,49 @@ cudaError_t vjp_setup(sd_handle *h) {
     return cudaSuccess;
 }
 
-cudaError_t launch_vjp_dense(sd_handle *h, cudaStream_t st, const void *posm, const void *frcm, const void *wm,
-                             double *partM, double *partG) {
+cudaError_t launch_vjp_dense(sd_handle *h, cudaStream_t st, Mirror posm, Mirror frcm, Mirror wm, double *partM,
+                             double *partG) {
     const DenseGeom &g = h->geomv;
     const bool f64 = h->mode == MODE_FP64;
-    const size_t smem = 6 * static_cast<size_t>(g.J) * v4b(f64 ? MODE_FP64 : MODE_FP32C);
+    const size_t smem = vjp_smem(f64 ? MODE_FP64 : MODE_FP32C, g.J);
     const bool oseen = h->tensor == T_OSEEN;
+    const bool per = h->pc.periodic != 0;
     prof_begin(h, SD_KERNEL_VJP, st);
-#define SD_VJP_LAUNCH(TT, MM, PP)                                                                             \
-    vjp_kernel<TT, MM, PP><<<g.grid, kNT, smem, st>>>(                                                        \
-        static_cast<const typename VjpT<MM>::V4 *>(posm), static_cast<const typename VjpT<MM>::V4 *>(frcm),   \
-        static_cast<const typename VjpT<MM>::V4 *>(wm), partM, partG, h->npad, g, h->pc, h->d_err, h->watchdog)
-#define SD_VJP_PER(TT, MM)                                                                                    \
-    do {                                                                                                      \
-        if (h->pc.periodic) SD_VJP_LAUNCH(TT, MM, true); else SD_VJP_LAUNCH(TT, MM, false);                  \
-    } while (0)
     if (f64) {
-        if (oseen) SD_VJP_PER(T_OSEEN, MODE_FP64); else SD_VJP_PER(T_RP, MODE_FP64);
-    } else {
-        if (oseen) SD_VJP_PER(T_OSEEN, MODE_FP32C); else SD_VJP_PER(T_RP, MODE_FP32C);
-    }
-#undef SD_VJP_PER
+#define SD_VJP_LAUNCH(TT, PP)                                                                                 \
+    vjp_kernel<TT, MODE_FP64, PP><<<g.grid, kNT, smem, st>>>(                                                 \
+        static_cast<const dbl4 *>(posm.aos), static_cast<const dbl4 *>(frcm.aos),                            \
+        static_cast<const dbl4 *>(wm.aos), partM, partG, h->npad, g, h->pc, h->d_err, h->watchdog)
+        if (oseen) {
+            if (per) SD_VJP_LAUNCH(T_OSEEN, true); else SD_VJP_LAUNCH(T_OSEEN, false);
+        } else {
+            if (per) SD_VJP_LAUNCH(T_RP, true); else SD_VJP_LAUNCH(T_RP, false);
+        }
 #undef SD_VJP_LAUNCH
+    } else {
+        const PairConst &pc = h->pc;
+        VjpConst2 c{};
+        c.c1 = pk2_host(pc.c1_f);
+        c.c3 = pk2_host(pc.c3_f);
+        c.m3c3 = pk2_host(pc.m3c3_f);
+        c.nc1 = pk2_host(-pc.c1_f);
+        c.n5m3c3 = pk2_host(-5.0f * pc.m3c3_f);   // (rounded in FP32, as vjp_pair_f32 forms them)
+        c.n3c1 = pk2_host(-3.0f * pc.c1_f);
+        c.r2min = pc.r2min_f;
+        for (int d = 0; d < 3; ++d) {
+            c.negL[d] = pk2_host(-pc.Lf[d]);
+            c.invL[d] = pk2_host(pc.invLf[d]);
+        }
+#define SD_VJP2_LAUNCH(TT, PP)                                                                                \
+    vjp2_kernel<TT, PP><<<g.grid, kNT, smem, st>>>(posm.soa, frcm.soa, wm.soa, partM, partG, h->npad, g, c,   \
+                                                    h->d_err, h->watchdog)
+        if (oseen) {
+            if (per) SD_VJP2_LAUNCH(T_OSEEN, true); else SD_VJP2_LAUNCH(T_OSEEN, false);
+        } else {
+            if (per) SD_VJP2_LAUNCH(T_RP, true); else SD_VJP2_LAUNCH(T_RP, false);
+        }
+#undef SD_VJP2_LAUNCH
+    }
     prof_end(h, SD_KERNEL_VJP, st);
     ++h->launches;
     return cudaGetLastError();
