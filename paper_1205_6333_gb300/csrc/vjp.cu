@@ -41,6 +41,7 @@ __device__ __forceinline__ void vjp_term(typename VjpT<MODE>::S xi, typename Vjp
         vjp_pair_f32<TENSOR, PER>(xi, yi, zi, Fi, Wi, p, f, w, c, m, g);
 }
 
+// The FP64 VJP kernel (the FP32C path runs vjp2_kernel below): plain FP64 sums.
 template <int TENSOR, int MODE, bool PER>
 __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 *__restrict__ pos,
                                                   const typename VjpT<MODE>::V4 *__restrict__ frc,
@@ -51,7 +52,6 @@ __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 
     using V3 = typename VjpT<MODE>::V3;
     using S = typename VjpT<MODE>::S;
     constexpr int R = kRV;
-    constexpr bool COMP = (MODE != MODE_FP64);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_abort;
@@ -87,7 +87,6 @@ __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 
 
     S xi[R], yi[R], zi[R];
     V3 Fi[R], Wi[R], m[R], gg[R];
-    float mh[R][3], ml[R][3], gh[R][3], gl[R][3];
     int cur_ib = -1;
     bool aborted = false;
 
@@ -98,19 +97,12 @@ __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const size_t i = static_cast<size_t>(ib) * g.I + tid + k * kNT;
-            if constexpr (COMP) {   // the (hi, lo) pairs themselves, for the epilogue's FP32 TwoSum
-                for (int d = 0; d < 3; ++d) {
-                    reinterpret_cast<float2 *>(dM)[d * static_cast<size_t>(npad) + i] = make_float2(mh[k][d], ml[k][d]);
-                    reinterpret_cast<float2 *>(dG)[d * static_cast<size_t>(npad) + i] = make_float2(gh[k][d], gl[k][d]);
-                }
-            } else {
-                dM[i] = m[k].x;
-                dM[npad + i] = m[k].y;
-                dM[2 * static_cast<size_t>(npad) + i] = m[k].z;
-                dG[i] = gg[k].x;
-                dG[npad + i] = gg[k].y;
-                dG[2 * static_cast<size_t>(npad) + i] = gg[k].z;
-            }
+            dM[i] = m[k].x;
+            dM[npad + i] = m[k].y;
+            dM[2 * static_cast<size_t>(npad) + i] = m[k].z;
+            dG[i] = gg[k].x;
+            dG[npad + i] = gg[k].y;
+            dG[2 * static_cast<size_t>(npad) + i] = gg[k].z;
         }
     };
 
@@ -130,7 +122,6 @@ __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 
                 Wi[k].x = w.x; Wi[k].y = w.y; Wi[k].z = w.z;
                 m[k].x = m[k].y = m[k].z = S(0);
                 gg[k].x = gg[k].y = gg[k].z = S(0);
-                for (int d = 0; d < 3; ++d) mh[k][d] = ml[k][d] = gh[k][d] = gl[k][d] = 0.0f;
             }
         }
         const int q = static_cast<int>(t - t0);
@@ -151,19 +142,6 @@ __global__ void __launch_bounds__(kNT) vjp_kernel(const typename VjpT<MODE>::V4 
 #pragma unroll
             for (int k = 0; k < R; ++k)
                 vjp_term<TENSOR, MODE, PER>(xi[k], yi[k], zi[k], Fi[k], Wi[k], p, f, w, c, m[k], gg[k]);
-        }
-        if constexpr (COMP) {
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                fold2(mh[k][0], ml[k][0], m[k].x);
-                fold2(mh[k][1], ml[k][1], m[k].y);
-                fold2(mh[k][2], ml[k][2], m[k].z);
-                fold2(gh[k][0], gl[k][0], gg[k].x);
-                fold2(gh[k][1], gl[k][1], gg[k].y);
-                fold2(gh[k][2], gl[k][2], gg[k].z);
-                m[k].x = m[k].y = m[k].z = S(0);
-                gg[k].x = gg[k].y = gg[k].z = S(0);
-            }
         }
         __syncthreads();
         aborted = s_abort != 0;
