@@ -142,11 +142,19 @@ static sd_status launch_check(cudaError_t e, const char *what) {
 // beyond r_near add exact zeros.
 static cudaError_t launch_verlet_step(sd_handle *h, cudaStream_t st, double dt, const double *x_in, double *x_out) {
     cudaError_t e = launch_verlet_check(h, st, x_in, h->posm);
+    // with soft repulsion the forces need the list: rebuild (when due) and forces first
+    cudaStream_t rb = h->forces_const ? h->side : st;
+    if (!h->forces_const) {
+        if (e == cudaSuccess) e = launch_build_cells(h, st, x_in, h->posm, h->xref);
+        if (e == cudaSuccess) e = launch_near_collect(h, st, x_in, h->posm.aos, h->F64, h->frcm.aos, true, true);
+        if (e == cudaSuccess) e = launch_forces_list(h, st, x_in);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-    if (e == cudaSuccess) e = launch_build_cells(h, h->side, x_in, h->posm, h->xref);
+    if (h->forces_const && e == cudaSuccess) e = launch_build_cells(h, rb, x_in, h->posm, h->xref);
     prof_begin(h, SD_KERNEL_NEAR, h->side);
-    if (e == cudaSuccess) e = launch_near_collect(h, h->side, x_in, h->posm.aos, h->F64, h->frcm.aos, true, true);
+    if (h->forces_const && e == cudaSuccess)
+        e = launch_near_collect(h, rb, x_in, h->posm.aos, h->F64, h->frcm.aos, true, true);
     if (e == cudaSuccess) e = launch_near_pairs(h, h->side, x_in, h->posm.aos, h->F64, h->frcm.aos, true);
     prof_end(h, SD_KERNEL_NEAR, h->side);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side);
@@ -385,10 +393,11 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
             return set_error(SD_ERR_ARG, "a periodic box side must be at least 3 max(r_near, rep_rc, 3a if "
                                          "lubrication)");
     if (!std::isfinite(cfg->verlet_skin)) return set_error(SD_ERR_ARG, "verlet_skin must be finite");
-    // Verlet lists for the steps of a system with constant forces, when the box allows
-    // cells of side cutoff + skin
+    // Verlet lists for the steps, when the box allows cells of side cutoff + skin:
+    // constant forces, or soft repulsion within r_near (its pairs then come from the
+    // list too); not with lubrication
     double skin = cfg->verlet_skin == 0.0 ? 0.5 * a : cfg->verlet_skin;
-    bool verlet = skin > 0.0 && cfg->rep_eps == 0.0 && cfg->lubrication == 0;
+    bool verlet = skin > 0.0 && cfg->lubrication == 0 && (cfg->rep_eps == 0.0 || rep_rc <= r_near);
     for (int d = 0; d < 3 && verlet; ++d)
         if (cfg->box[d] > 0.0 && cfg->box[d] < 3.0 * (cutoff + skin)) verlet = false;
     if (!verlet) skin = 0.0;

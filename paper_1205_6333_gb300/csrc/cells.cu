@@ -512,6 +512,76 @@ __global__ void forces_rep_kernel(const double *__restrict__ x, const double *__
     put_mirror(m, soa, npad, i, f0, f1, f2v);
 }
 
+// Forces of a Verlet step with soft repulsion (Sec. 3.1, step 2): the pairs closer
+// than r_c come from the steps' near-pair list (it holds every pair within r_near >= r_c
+// while the list is valid), one thread per particle over its run in ascending partner
+// order, in FP64; plus F_ext and gravity.  Writes F64 and the force mirror.
+template <typename V4>
+__global__ void forces_list_kernel(const double *__restrict__ x, const double *__restrict__ fext, double gx,
+                                   double gy, double gz, double eps, double rc2, double s12, CellList c,
+                                   const int2 *__restrict__ ent, const int *__restrict__ noff,
+                                   const int *__restrict__ ncnt, int cap, int n, int npad, double *__restrict__ F,
+                                   V4 *__restrict__ m, float *__restrict__ soa, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
+    double f[3] = {0.0, 0.0, 0.0};
+    bool coincident = false;
+    auto pair = [&](int j) {
+        double dx = xi - x[3 * j], dy = yi - x[3 * j + 1], dz = zi - x[3 * j + 2];
+        box_image(c.box, dx, dy, dz);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= rc2) return;
+        if (r2 == 0.0) {
+            coincident = true;
+            return;
+        }
+        const double ri = rsqrt_nr64(r2);
+        const double ir2 = ri * ri;
+        const double ir6 = ir2 * ir2 * ir2;
+        const double coef = 12.0 * eps * s12 * ir6 * ir6 * ir2;
+        f[0] += coef * dx;
+        f[1] += coef * dy;
+        f[2] += coef * dz;
+    };
+    const int cnt = ncnt[i];
+    if (cnt < 0) {   // a particle the overflowed list corrects in place: the cell list (rebuilt
+                     // every step while the list overflows) gives its pairs
+        for_each_neighbour_part(c, i, c.cell[i], 0, 1, pair);
+    } else {
+        const long long e0 = dbg_index(noff[i], static_cast<long long>(cap) - cnt + 1, err);
+        for (int k = 0; k < cnt; ++k) pair(static_cast<int>(dbg_index(ent[e0 + k].y, n, err)));
+    }
+    const double f0 = f[0] + fext[3 * i] + gx, f1 = f[1] + fext[3 * i + 1] + gy, f2v = f[2] + fext[3 * i + 2] + gz;
+    if (coincident) atomicOr(err, DEV_ERR_COINCIDENT);
+    if (!isfinite(f0) || !isfinite(f1) || !isfinite(f2v)) atomicOr(err, DEV_ERR_NONFINITE);
+    F[3 * i] = f0;
+    F[3 * i + 1] = f1;
+    F[3 * i + 2] = f2v;
+    put_mirror(m, soa, npad, i, f0, f1, f2v);
+}
+
+cudaError_t launch_forces_list(sd_handle *h, cudaStream_t st, const double *x64) {
+    if (h->n == 0) return cudaSuccess;
+    const int nb = (h->n + 127) / 128;
+    const double *g = h->cfg.gravity;
+    const double s12 = pow(2.0 * h->cfg.a, 12.0), rc2 = h->rep_rc * h->rep_rc;
+    prof_begin(h, SD_KERNEL_FORCES, st);
+    if (h->mode == MODE_FP64)
+        forces_list_kernel<dbl4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, rc2, s12,
+                                                     h->cl, h->vent, h->voff, h->vcnt, h->near_cap, h->n,
+                                                     h->npad, h->F64, static_cast<dbl4 *>(h->frcm.aos), h->frcm.soa,
+                                                     h->d_err);
+    else
+        forces_list_kernel<float4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, rc2, s12,
+                                                       h->cl, h->vent, h->voff, h->vcnt, h->near_cap, h->n,
+                                                       h->npad, h->F64, static_cast<float4 *>(h->frcm.aos),
+                                                       h->frcm.soa, h->d_err);
+    prof_end(h, SD_KERNEL_FORCES, st);
+    ++h->launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64) {
     if (h->n == 0) return cudaSuccess;
     const int nb = static_cast<int>((static_cast<long long>(h->n) * kWalkLanes + 127) / 128);

@@ -310,6 +310,8 @@ cudaError_t launch_build_cells(sd_handle *h, cudaStream_t st, const double *x64,
 // (displacements relative to particle 0 since xref; list overflow) in d_vl[0].
 cudaError_t launch_verlet_check(sd_handle *h, cudaStream_t st, const double *x64, Mirror posm);
 cudaError_t launch_forces_rep(sd_handle *h, cudaStream_t st, const double *x64);
+// Verlet step with soft repulsion: the forces from the steps' near-pair list.
+cudaError_t launch_forces_list(sd_handle *h, cudaStream_t st, const double *x64);
 cudaError_t launch_pad_mirror(sd_handle *h, cudaStream_t st, Mirror m);
 // dense.cu
 cudaError_t dense_setup(sd_handle *h);

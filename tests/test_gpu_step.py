@@ -246,6 +246,46 @@ def test_verlet_clamp_flag_from_the_list(prec, dense):
     assert np.abs(a - ref).max() <= (1e-10 if prec == "fp64" else 1e-5) * np.abs(ref - x0).max()
 
 
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_verlet_lists_with_repulsion(prec):
+    """Soft repulsion with Verlet lists: the repulsive pairs come from the near-pair list
+    (their cutoff 2.5a equals r_near).  A dense packing under gravity and strong random
+    forces, so pairs enter and leave the cutoff and the list is rebuilt.  Graph replays,
+    single steps and eager steps agree bit for bit; the cell-list forces of steps
+    without a skin and the oracle agree to rounding."""
+    n, steps, dt = 1500, 48, 0.005
+    x0, _ = inputs.cube_rsa(n, 0.15, 63)
+    fe = 20.0 * inputs.normal_forces(n, 64)
+    kw = dict(prec=prec, gravity=(0, 0, -1.0), rep_eps=1.0, rep_rc=2.5)
+    runs = []
+    with sd.System(n, **kw) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(dt, steps)
+        runs.append(s.get_positions())
+        s.set_positions(x0)
+        for _ in range(steps):
+            s.step(dt, 1)
+        runs.append(s.get_positions())
+        s.set_positions(x0)
+        s.profile(True)
+        s.step(dt, steps)
+        s.profile(False)
+        runs.append(s.get_positions())
+    np.testing.assert_array_equal(runs[0], runs[1])
+    np.testing.assert_array_equal(runs[0], runs[2])
+    a = runs[0]
+    with sd.System(n, verlet_skin=0, **kw) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(dt, steps)
+        c = s.get_positions()
+    disp = np.abs(a - x0).max()
+    assert np.abs(a - c).max() <= (1e-12 if prec == "fp64" else 1e-6) * disp
+    ref = oracle.euler(x0, steps, dt, fext=fe, gravity=(0, 0, -1.0), rep_eps=1.0, rep_rc=2.5, nthreads=8)
+    assert np.abs(a - ref).max() <= (1e-10 if prec == "fp64" else 1e-5) * np.abs(ref - x0).max()
+
+
 def test_verlet_lists_periodic_box():
     x0, L = inputs.cube_rsa(2000, 0.08, 71)
     L = L + 2.5
