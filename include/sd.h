@@ -119,17 +119,17 @@ typedef struct sd_config {
                                 (SD_ERR_UNSUPPORTED). */
     double verlet_skin;      /* neighbour-list skin of sd_step (Sec. 3.1 step 2, Verlet lists): 0 = default
                                 0.5a, < 0 = off.  The steps keep an FP64 near-pair list of the pairs
-                                within r_near + skin, built by sd_set_positions and rebuilt once some
+                                within its cutoff + skin, built by sd_set_positions and rebuilt once some
                                 particle has moved skin / 4 relative to particle 0 since the last
                                 build (a uniform translation never forces one; up to skin / 2 the
-                                list still holds every pair within r_near).  With constant forces the
-                                rebuild and the near terms run beside the all-pairs kernel; with soft
-                                repulsion (rep_rc <= r_near) the repulsive pairs come from the same
-                                list, and the near terms alone run beside it.  Each particle's list is
-                                in ascending partner order, so a step gives the same result bit for
-                                bit from a fresh or a reused list.  Off automatically with lubrication,
-                                with rep_rc > r_near, or when a periodic side is below
-                                3 (max cutoff + skin). */
+                                list still holds every pair within its cutoff, the largest of r_near,
+                                rep_rc with repulsion and 3a with lubrication).  With constant forces
+                                the rebuild and the near terms run beside the all-pairs kernel; with
+                                repulsion or lubrication their pairs come from the same list, and the
+                                near terms alone run beside it.  Each particle's list is in ascending
+                                partner order, so a step gives the same result bit for bit from a
+                                fresh or a reused list.  Off automatically when a periodic side is
+                                below 3 (max cutoff + skin). */
 } sd_config;
 
 typedef struct sd_handle sd_handle;

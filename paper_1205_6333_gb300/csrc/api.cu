@@ -393,11 +393,11 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
             return set_error(SD_ERR_ARG, "a periodic box side must be at least 3 max(r_near, rep_rc, 3a if "
                                          "lubrication)");
     if (!std::isfinite(cfg->verlet_skin)) return set_error(SD_ERR_ARG, "verlet_skin must be finite");
-    // Verlet lists for the steps, when the box allows cells of side cutoff + skin:
-    // constant forces, or soft repulsion within r_near (its pairs then come from the
-    // list too); not with lubrication
+    // Verlet lists for the steps, when the box allows cells of side cutoff + skin: the
+    // list holds every pair within the largest cutoff, so the repulsive and lubricated
+    // pairs come from it too
     double skin = cfg->verlet_skin == 0.0 ? 0.5 * a : cfg->verlet_skin;
-    bool verlet = skin > 0.0 && cfg->lubrication == 0 && (cfg->rep_eps == 0.0 || rep_rc <= r_near);
+    bool verlet = skin > 0.0;
     for (int d = 0; d < 3 && verlet; ++d)
         if (cfg->box[d] > 0.0 && cfg->box[d] < 3.0 * (cutoff + skin)) verlet = false;
     if (!verlet) skin = 0.0;
@@ -421,6 +421,7 @@ sd_status sd_create(const sd_config *cfg, sd_handle **out) {
     h->forces_const = (cfg->rep_eps == 0.0) && !h->lub;
     h->verlet = verlet;
     h->skin = skin;
+    h->list_cut = cutoff;
 
     PairConst &pc = h->pc;
     pc.a = a;

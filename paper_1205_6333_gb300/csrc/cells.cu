@@ -512,18 +512,24 @@ __global__ void forces_rep_kernel(const double *__restrict__ x, const double *__
     put_mirror(m, soa, npad, i, f0, f1, f2v);
 }
 
-// Forces of a Verlet step with soft repulsion (Sec. 3.1, step 2): the pairs closer
-// than r_c come from the steps' near-pair list (it holds every pair within r_near >= r_c
-// while the list is valid), one thread per particle over its run in ascending partner
-// order, in FP64; plus F_ext and gravity.  Writes F64 and the force mirror.
+// Forces of a Verlet step (Sec. 3.1, step 2) with soft repulsion and/or lubrication:
+// the pairs come from the steps' near-pair list (it holds every pair within the
+// largest cutoff while the list is valid), one thread per particle over its run in
+// ascending partner order, in FP64; the terms are forces_rep_kernel's.  Plus F_ext and
+// gravity.  Writes F64 and the force mirror.
 template <typename V4>
 __global__ void forces_list_kernel(const double *__restrict__ x, const double *__restrict__ fext, double gx,
-                                   double gy, double gz, double eps, double rc2, double s12, CellList c,
+                                   double gy, double gz, double eps, double rc, double s12,
+                                   const double *__restrict__ vlag, double inv_a, double inv_mu0, CellList c,
                                    const int2 *__restrict__ ent, const int *__restrict__ noff,
                                    const int *__restrict__ ncnt, int cap, int n, int npad, double *__restrict__ F,
                                    V4 *__restrict__ m, float *__restrict__ soa, int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const bool rep = eps != 0.0, lub = vlag != nullptr;
+    const double rc2 = rep ? rc * rc : 0.0;
+    const double rl2 = lub ? 9.0 / (inv_a * inv_a) : 0.0;   // (3a)^2
+    const double rmax2 = rc2 > rl2 ? rc2 : rl2;
     const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
     double f[3] = {0.0, 0.0, 0.0};
     bool coincident = false;
@@ -531,18 +537,43 @@ __global__ void forces_list_kernel(const double *__restrict__ x, const double *_
         double dx = xi - x[3 * j], dy = yi - x[3 * j + 1], dz = zi - x[3 * j + 2];
         box_image(c.box, dx, dy, dz);
         const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= rc2) return;
+        if (r2 >= rmax2) return;
         if (r2 == 0.0) {
-            coincident = true;
+            if (rep) coincident = true;   // s = -2: no lubrication term
             return;
         }
         const double ri = rsqrt_nr64(r2);
-        const double ir2 = ri * ri;
-        const double ir6 = ir2 * ir2 * ir2;
-        const double coef = 12.0 * eps * s12 * ir6 * ir6 * ir2;
-        f[0] += coef * dx;
-        f[1] += coef * dy;
-        f[2] += coef * dz;
+        if (r2 < rc2) {
+            const double ir2 = ri * ri;
+            const double ir6 = ir2 * ir2 * ir2;
+            const double coef = 12.0 * eps * s12 * ir6 * ir6 * ir2;
+            f[0] += coef * dx;
+            f[1] += coef * dy;
+            f[2] += coef * dz;
+        }
+        if (lub) {
+            const double sg = r2 * ri * inv_a - 2.0;
+            if (sg > 0.0 && sg < 1.0) {
+                double zn, zt;
+                if constexpr (std::is_same<V4, float4>::value) {
+                    const float sf = static_cast<float>(sg), ls = logf(sf);
+                    zn = __fsub_rn(__fdiv_rn(0.25f, sf), __fmul_rn(0.225f, ls));
+                    zt = __fmul_rn(ls, -1.0f / 6.0f);
+                } else {
+                    const double ls = log(sg);
+                    zn = 0.25 / sg - 0.225 * ls;
+                    zt = -ls / 6.0;
+                }
+                const double ex = dx * ri, ey = dy * ri, ez = dz * ri;
+                const double wx = vlag[3 * i] - vlag[3 * j], wy = vlag[3 * i + 1] - vlag[3 * j + 1],
+                             wz = vlag[3 * i + 2] - vlag[3 * j + 2];
+                const double en = ex * wx + ey * wy + ez * wz;
+                const double kn = (zn - zt) * en;
+                f[0] -= inv_mu0 * (kn * ex + zt * wx);
+                f[1] -= inv_mu0 * (kn * ey + zt * wy);
+                f[2] -= inv_mu0 * (kn * ez + zt * wz);
+            }
+        }
     };
     const int cnt = ncnt[i];
     if (cnt < 0) {   // a particle the overflowed list corrects in place: the cell list (rebuilt
@@ -565,18 +596,20 @@ cudaError_t launch_forces_list(sd_handle *h, cudaStream_t st, const double *x64)
     if (h->n == 0) return cudaSuccess;
     const int nb = (h->n + 127) / 128;
     const double *g = h->cfg.gravity;
-    const double s12 = pow(2.0 * h->cfg.a, 12.0), rc2 = h->rep_rc * h->rep_rc;
+    const double s12 = pow(2.0 * h->cfg.a, 12.0);
+    const double *vlag = h->lub ? h->vlag : nullptr;
+    const double inv_a = 1.0 / h->pc.a, inv_mu0 = 1.0 / h->pc.mu0;
     prof_begin(h, SD_KERNEL_FORCES, st);
     if (h->mode == MODE_FP64)
-        forces_list_kernel<dbl4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, rc2, s12,
-                                                     h->cl, h->vent, h->voff, h->vcnt, h->near_cap, h->n,
-                                                     h->npad, h->F64, static_cast<dbl4 *>(h->frcm.aos), h->frcm.soa,
-                                                     h->d_err);
+        forces_list_kernel<dbl4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, h->rep_rc,
+                                                     s12, vlag, inv_a, inv_mu0, h->cl, h->vent, h->voff, h->vcnt,
+                                                     h->near_cap, h->n, h->npad, h->F64,
+                                                     static_cast<dbl4 *>(h->frcm.aos), h->frcm.soa, h->d_err);
     else
-        forces_list_kernel<float4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, rc2, s12,
-                                                       h->cl, h->vent, h->voff, h->vcnt, h->near_cap, h->n,
-                                                       h->npad, h->F64, static_cast<float4 *>(h->frcm.aos),
-                                                       h->frcm.soa, h->d_err);
+        forces_list_kernel<float4><<<nb, 128, 0, st>>>(x64, h->fext64, g[0], g[1], g[2], h->cfg.rep_eps, h->rep_rc,
+                                                       s12, vlag, inv_a, inv_mu0, h->cl, h->vent, h->voff, h->vcnt,
+                                                       h->near_cap, h->n, h->npad, h->F64,
+                                                       static_cast<float4 *>(h->frcm.aos), h->frcm.soa, h->d_err);
     prof_end(h, SD_KERNEL_FORCES, st);
     ++h->launches;
     return cudaGetLastError();

@@ -365,7 +365,7 @@ static NearArgs near_args(sd_handle *h, const double *x64, const void *posm, con
 cudaError_t launch_near_collect(sd_handle *h, cudaStream_t st, const double *x64, const void *posm,
                                 const double *F64, const void *frcm, bool count_zeroed, bool verlet_list) {
     if (h->n == 0) return cudaSuccess;
-    NearArgs a = near_args(h, x64, posm, F64, frcm, verlet_list ? h->r_near + h->skin : h->r_near, verlet_list);
+    NearArgs a = near_args(h, x64, posm, F64, frcm, verlet_list ? h->list_cut + h->skin : h->r_near, verlet_list);
     if (verlet_list) {   // a Verlet step's rebuild: the clamp flag is its check kernel's
         a.gate = h->d_vl;
         a.flag = nullptr;

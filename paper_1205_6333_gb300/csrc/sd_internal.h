@@ -74,7 +74,8 @@ constexpr int kRV = 2;           // i-particles per thread, VJP dense kernel
 constexpr int kJmax = 256;       // largest j-tile
 constexpr double kRSafe = 1.0;   // pairs closer than kRSafe * a make the FP32 kernel clamp every tile
 constexpr long long kDefaultWatchdog = 1LL << 22;
-constexpr int kNearPerParticle = 16;  // near-pass list capacity per particle (overflow: in-place path)
+constexpr int kNearPerParticle = 32;  // near-pass list capacity per particle (overflow: in-place path); an fcc
+                                      // lattice at the paper's density lists 18 partners within 3a + skin
 
 // Partition of the (i-block, j-tile) plane over a persistent grid: CTA b takes
 // the row-major tile range [b*chunk, min((b+1)*chunk, nIB*nJT)).  The CTAs that
@@ -263,6 +264,7 @@ struct sd_handle {
     // the pairs within r_near + skin of the positions xref it was built from
     bool verlet = false;
     double skin = 0.0;
+    double list_cut = 0.0;         // cutoff of the Verlet list: max(r_near, r_c with repulsion, 3a with lubrication)
     double *xref = nullptr;        // [n*3] positions of the last build
     int *d_vl = nullptr;           // [0] rebuild request (bit 2: no list yet), [1] [2] check kernel's
     // the Verlet steps' own candidate list, kept across steps (every other near pass

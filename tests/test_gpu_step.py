@@ -286,6 +286,45 @@ def test_verlet_lists_with_repulsion(prec):
     assert np.abs(a - ref).max() <= (1e-10 if prec == "fp64" else 1e-5) * np.abs(ref - x0).max()
 
 
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_verlet_lists_with_lubrication(prec):
+    """Lubrication with Verlet lists: the lubricated pairs (s < 1, r < 3a) come from the
+    near-pair list, whose cutoff is then 3a + skin.  A jittered lattice of spacing 2.9a
+    (every nearest-neighbour gap inside the friction window) under random forces and
+    gravity, dt = 0.02, with the previous step's velocities.  Graph replays and eager
+    steps agree bit for bit; the cell-list forces of steps without a skin and the oracle
+    agree to rounding."""
+    m, spacing, steps, dt = 10, 2.9, 24, 0.02
+    rng = np.random.default_rng(65)
+    g = np.arange(m) * spacing
+    x0 = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) + rng.uniform(-0.05, 0.05, (m ** 3, 3))
+    n = x0.shape[0]
+    fe = inputs.normal_forces(n, 66)
+    kw = dict(prec=prec, gravity=(0, 0, -1.0), lubrication=True)
+    runs = []
+    with sd.System(n, **kw) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(dt, steps)
+        runs.append(s.get_positions())
+        s.set_positions(x0)
+        s.profile(True)
+        s.step(dt, steps)
+        s.profile(False)
+        runs.append(s.get_positions())
+    np.testing.assert_array_equal(runs[0], runs[1])
+    a = runs[0]
+    with sd.System(n, verlet_skin=0, **kw) as s:
+        s.set_positions(x0)
+        s.set_forces(fe)
+        s.step(dt, steps)
+        c = s.get_positions()
+    disp = np.abs(a - x0).max()
+    assert np.abs(a - c).max() <= (1e-12 if prec == "fp64" else 1e-6) * disp
+    ref = oracle.euler(x0, steps, dt, fext=fe, gravity=(0, 0, -1.0), lubrication=True, nthreads=8)
+    assert np.abs(a - ref).max() <= (1e-10 if prec == "fp64" else 1e-4) * np.abs(ref - x0).max()
+
+
 def test_verlet_lists_periodic_box():
     x0, L = inputs.cube_rsa(2000, 0.08, 71)
     L = L + 2.5
