@@ -862,10 +862,11 @@ static constexpr size_t sym_smem(int B, int NT) {
 #define SD_DENSE_SYM_SMALL_N 8192
 #endif
 // CTA oversubscription of the symmetric kernel's grid (see SD_DENSE_CTA_SCALE).  At
-// N = 65,536: all-pairs + epilogue 2.265 ms at 8, 2.251 at 16, 2.251 at 32 (more
-// CTAs balance the SMs better but leave more partial rows for the epilogue).
+// N = 65,536 (8,256 tiles of 512, 2 CTAs per SM) 16 gives runs of 2 tiles and 32 one
+// tile per CTA: the step fell from 2.281 to 2.265 ms (all-pairs 2.209 -> 2.179 ms,
+// epilogue 0.041 -> 0.053 ms, since more CTAs leave more partial rows to sum).
 #ifndef SD_DENSE_SYM_CTA_SCALE
-#define SD_DENSE_SYM_CTA_SCALE 16
+#define SD_DENSE_SYM_CTA_SCALE 32
 #endif
 
 // Choose the tile J and the persistent grid for h->npad, and size the partials.
