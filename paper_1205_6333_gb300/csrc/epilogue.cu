@@ -451,7 +451,10 @@ __device__ __forceinline__ int first_row_at(const DenseGeom &g, int ib, long lon
 // (fixed order: deterministic) and applies the FP64 terms.  Four warps per 32
 // particles measured best at N = 65,536 (40 us against 45 for 8, 51 for 2, 79 for 16):
 // the kernel waits on DRAM latency, and fewer warps per group leave fewer idle
-// during warp 0's FP64 tail.
+// during warp 0's FP64 tail.  With one tile per all-pairs CTA (twice the target-side
+// slots): 53 us at 4 warps, 55 at 8; source loop unrolled 1 / 2 / 4: 52.6 / 53.0 /
+// 70 us; launch bounds for 16 or 12 resident CTAs per SM (32 or 40 registers, all
+// CTAs in one wave): 53 / 61 us.
 #ifndef SD_EPI_WARPS
 #define SD_EPI_WARPS 4
 #endif
