@@ -559,6 +559,7 @@ void sd_destroy(sd_handle *h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->side) cudaStreamSynchronize(h->side);   // (a step that failed before its join)
     drop_graphs(h);
     prof_destroy(h->prof);
     for (int b = 0; b < 2; ++b) dfree(h, h->x64[b]);
