@@ -861,13 +861,26 @@ static constexpr size_t sym_smem(int B, int NT) {
 #ifndef SD_DENSE_SYM_SMALL_N
 #define SD_DENSE_SYM_SMALL_N 8192
 #endif
-// CTA oversubscription of the symmetric kernel's grid (see SD_DENSE_CTA_SCALE).  At
-// N = 65,536 (8,256 tiles of 512, 2 CTAs per SM) 16 gives runs of 2 tiles and 32 one
-// tile per CTA: the step fell from 2.281 to 2.265 ms (all-pairs 2.209 -> 2.179 ms,
-// epilogue 0.041 -> 0.053 ms, since more CTAs leave more partial rows to sum).
+// CTA oversubscription of the symmetric kernel's grid (see SD_DENSE_CTA_SCALE): runs
+// of ceil(tiles / (SD_DENSE_SYM_CTA_SCALE x resident CTAs)) tiles, or one tile per CTA
+// while the tiles number at most SD_DENSE_SYM_ONE_TILE x the resident CTAs.  Measured
+// all-pairs kernel (blocks of 512, 2 CTAs per SM):
+//   N = 65,536 (8,256 tiles): one tile per CTA 2.179 ms, runs of 2 (16x) 2.209 ms;
+//   N = 131,072: runs of 7 (16x) 8.571 ms, runs of 4 (32x) 8.646 ms;
+//   N = 262,144: runs of 27 (16x) 34.07 ms, runs of 14 (32x) 34.19 ms.
+// Longer runs write fewer target-side partial rows; at N = 65,536 the shorter work
+// units balance the SMs better.
 #ifndef SD_DENSE_SYM_CTA_SCALE
-#define SD_DENSE_SYM_CTA_SCALE 32
+#define SD_DENSE_SYM_CTA_SCALE 16
 #endif
+#ifndef SD_DENSE_SYM_ONE_TILE
+#define SD_DENSE_SYM_ONE_TILE 32
+#endif
+static long long sym_chunk(long long nT, long long resident) {
+    if (nT <= resident * SD_DENSE_SYM_ONE_TILE) return 1;
+    const long long want = resident * SD_DENSE_SYM_CTA_SCALE;
+    return (nT + want - 1) / want;
+}
 
 // Choose the tile J and the persistent grid for h->npad, and size the partials.
 cudaError_t dense_setup(sd_handle *h) {
@@ -936,8 +949,7 @@ cudaError_t dense_setup(sd_handle *h) {
         s.nIB = s.nJT = (nreal + kB64 - 1) / kB64;
         s.nT = static_cast<long long>(s.nIB) * (s.nIB + 1) / 2;
         if (want_sym == SD_DENSE_SYMMETRIC || s.nT * SD_DENSE_SYM_SMS_PER_TILE >= h->num_sms) {
-            const long long swant = static_cast<long long>(h->num_sms) * socc * SD_DENSE_SYM_CTA_SCALE;
-            s.chunk = std::max(1LL, (s.nT + swant - 1) / swant);
+            s.chunk = sym_chunk(s.nT, static_cast<long long>(h->num_sms) * socc);
             s.grid = static_cast<int>((s.nT + s.chunk - 1) / s.chunk);
             g = s;
             occ = socc;
@@ -962,8 +974,7 @@ cudaError_t dense_setup(sd_handle *h) {
         // directed kernel: measured directed faster at n = 2048, symmetric at 4096)
         const long long need = static_cast<long long>(h->num_sms) * (B == 128 ? 4 : 1);
         if (want_sym == SD_DENSE_SYMMETRIC || s.nT * SD_DENSE_SYM_SMS_PER_TILE >= need) {
-            const long long swant = static_cast<long long>(h->num_sms) * socc * SD_DENSE_SYM_CTA_SCALE;
-            s.chunk = std::max(1LL, (s.nT + swant - 1) / swant);
+            s.chunk = sym_chunk(s.nT, static_cast<long long>(h->num_sms) * socc);
             s.grid = static_cast<int>((s.nT + s.chunk - 1) / s.chunk);
             g = s;
             occ = socc;
