@@ -106,7 +106,10 @@ typedef struct sd_config {
     double gravity[3];       /* uniform force added to every particle                       */
     int32_t device;          /* CUDA device ordinal                                         */
     void *stream;            /* cudaStream_t to run on; NULL = the legacy default stream    */
-    void *(*alloc)(size_t bytes, void *ctx);   /* optional device allocator              */
+    void *(*alloc)(size_t bytes, void *ctx);   /* optional device allocator; it must return
+                                                  memory aligned to 256 bytes, as cudaMalloc
+                                                  does (the kernels use 16-byte vector loads
+                                                  and bulk copies)                          */
     void (*free)(void *ptr, void *ctx);        /* its matching free                      */
     void *alloc_ctx;
     int32_t dense_kernel;    /* sd_dense_kernel                                             */

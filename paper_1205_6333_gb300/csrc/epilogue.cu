@@ -454,39 +454,58 @@ __device__ __forceinline__ int first_row_at(const DenseGeom &g, int ib, long lon
 // during warp 0's FP64 tail.  With one tile per all-pairs CTA (twice the target-side
 // slots): 53 us at 4 warps, 55 at 8; source loop unrolled 1 / 2 / 4: 52.6 / 53.0 /
 // 70 us; launch bounds for 16 or 12 resident CTAs per SM (32 or 40 registers, all
-// CTAs in one wave): 53 / 61 us.
+// CTAs in one wave): 53 / 61 us.  Two particles per lane (one 16-byte load for both
+// particles' (hi, lo) pairs): 43 us, the loads then reaching 63% of the HBM copy
+// rate instead of 50%.
 #ifndef SD_EPI_WARPS
 #define SD_EPI_WARPS 4
 #endif
 #ifndef SD_EPI_UNROLL
 #define SD_EPI_UNROLL 2
 #endif
+#ifndef SD_EPI_PAIRS
+#define SD_EPI_PAIRS 1
+#endif
 constexpr int kEpiWarps = SD_EPI_WARPS;
 constexpr int kEpiUnroll = SD_EPI_UNROLL;
+constexpr bool kEpiPairs = SD_EPI_PAIRS != 0;   // FP32C: two particles per lane in the sums
 
-template <int TDENSE, int MODE, int OUT>
+// P particles per lane in the sums (P = 2: FP32C without shard shares, row0 even):
+// a lane then reads the (hi, lo) pairs of particles i0, i0 + 1 as one 16-byte load
+// and their source-side partials as one 8-byte load, so each load instruction
+// carries twice the bytes; every particle's sums take the same operations in the
+// same order as with P = 1.
+template <int TDENSE, int MODE, int OUT, int P>
 __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
     using V4 = typename EpiT<MODE>::V4;
-    __shared__ double s_v[kEpiWarps][3][32];
-    __shared__ float s_h[kEpiWarps][3][32], s_l[kEpiWarps][3][32];
+    constexpr int NP = 32 * P;   // particles per CTA
+    static_assert(P == 1 || (P == 2 && MODE == MODE_FP32C), "two particles per lane: FP32C only");
+    __shared__ double s_v[kEpiWarps][3][NP];
+    __shared__ float s_h[kEpiWarps][3][NP], s_l[kEpiWarps][3][NP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // CTAs in reverse particle order: the last blocks have the longest source-side
     // columns, so they start first instead of forming the tail
-    const int i = a.row0 + (gridDim.x - 1 - blockIdx.x) * 32 + lane;
-    const bool active = i < a.row1;
+    const int base = a.row0 + (gridDim.x - 1 - blockIdx.x) * NP;
 
     // This warp's share of the dense sum: the CTA slots of the particle's i-block,
     // then (symmetric kernel) the source-side slots of the tiles (r, ib), r < ib.
     // FP32C sums both with TwoSum in FP32 (hi, lo) -- the slots are (hi, lo) pairs
     // themselves -- because FP64 issues at 1/64 the FP32 rate on GB300.
     {
-        double v[3] = {0.0, 0.0, 0.0};
-        float hi[3] = {0.0f, 0.0f, 0.0f}, lo[3] = {0.0f, 0.0f, 0.0f};
-        if (active && a.sh.pall) {
+        const int i = base + P * lane;   // this lane's particles: i .. i + P - 1 (one i-block)
+        const bool active = i < a.row1;
+        double v[P][3];
+        float hi[P][3], lo[P][3];
+        for (int k = 0; k < P; ++k)
+            for (int d = 0; d < 3; ++d) {
+                v[k][d] = 0.0;
+                hi[k][d] = lo[k][d] = 0.0f;
+            }
+        if (active && a.sh.pall) {   // (P = 1)
             // the shards' results, added in shard order (warp 0)
             if (w == 0)
                 for (int q = 0; q < a.sh.nparts; ++q)
-                    for (int d = 0; d < 3; ++d) v[d] += a.sh.pall[(static_cast<size_t>(q) * a.n + i) * 3 + d];
+                    for (int d = 0; d < 3; ++d) v[0][d] += a.sh.pall[(static_cast<size_t>(q) * a.n + i) * 3 + d];
         } else if (active) {
             const int ib = i / a.g.I;
             const int first = geom_first(a.g, ib);
@@ -505,58 +524,84 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
             if constexpr (MODE == MODE_FP32) {
                 for (int s = s0 + w; s < ns; s += kEpiWarps)
                     for (int d = 0; d < 3; ++d)
-                        hi[d] = __fadd_rn(hi[d],
-                                          static_cast<float>(a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i]));
+                        hi[0][d] = __fadd_rn(hi[0][d], static_cast<float>(
+                                                           a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i]));
                 for (int r = r0 + w; r < nc; r += kEpiWarps) {
                     const float *src = a.jpart + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
-                    for (int d = 0; d < 3; ++d) hi[d] = __fadd_rn(hi[d], src[d * J]);
+                    for (int d = 0; d < 3; ++d) hi[0][d] = __fadd_rn(hi[0][d], src[d * J]);
                 }
             } else if constexpr (MODE == MODE_FP64) {
                 for (int s = s0 + w; s < ns; s += kEpiWarps)
-                    for (int d = 0; d < 3; ++d) v[d] += a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
+                    for (int d = 0; d < 3; ++d) v[0][d] += a.part[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
                 for (int r = r0 + w; r < nc; r += kEpiWarps) {
                     const double *src = a.jpart64 + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
-                    for (int d = 0; d < 3; ++d) v[d] += src[d * J];
+                    for (int d = 0; d < 3; ++d) v[0][d] += src[d * J];
                 }
-            } else {   // FP32C: each slot is a (hi, lo) float pair
+            } else if constexpr (P == 1) {   // FP32C: each slot is a (hi, lo) float pair
                 const float2 *pp = reinterpret_cast<const float2 *>(a.part);
 #pragma unroll 4
                 for (int s = s0 + w; s < ns; s += kEpiWarps)
                     for (int d = 0; d < 3; ++d) {
                         const float2 q = pp[(static_cast<size_t>(s) * 3 + d) * a.npad + i];
-                        fold2(hi[d], lo[d], q.x);
-                        lo[d] = __fadd_rn(lo[d], q.y);
+                        fold2(hi[0][d], lo[0][d], q.x);
+                        lo[0][d] = __fadd_rn(lo[0][d], q.y);
                     }
 #pragma unroll kEpiUnroll
                 for (int r = r0 + w; r < nc; r += kEpiWarps) {
                     const float *src = a.jpart + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
-                    for (int d = 0; d < 3; ++d) fold2(hi[d], lo[d], src[d * J]);
+                    for (int d = 0; d < 3; ++d) fold2(hi[0][d], lo[0][d], src[d * J]);
+                }
+            } else {   // FP32C, two particles: i even, npad, I and J even, so both loads are aligned
+                const float2 *pp = reinterpret_cast<const float2 *>(a.part);
+#pragma unroll 4
+                for (int s = s0 + w; s < ns; s += kEpiWarps)
+                    for (int d = 0; d < 3; ++d) {
+                        const float4 q =
+                            *reinterpret_cast<const float4 *>(pp + (static_cast<size_t>(s) * 3 + d) * a.npad + i);
+                        fold2(hi[0][d], lo[0][d], q.x);
+                        lo[0][d] = __fadd_rn(lo[0][d], q.y);
+                        fold2(hi[1][d], lo[1][d], q.z);
+                        lo[1][d] = __fadd_rn(lo[1][d], q.w);
+                    }
+#pragma unroll kEpiUnroll
+                for (int r = r0 + w; r < nc; r += kEpiWarps) {
+                    const float *src = a.jpart + static_cast<size_t>(geom_rowstart(a.g, r) + (ib - r)) * cs + o;
+                    for (int d = 0; d < 3; ++d) {
+                        const float2 q = *reinterpret_cast<const float2 *>(src + d * J);
+                        fold2(hi[0][d], lo[0][d], q.x);
+                        fold2(hi[1][d], lo[1][d], q.y);
+                    }
                 }
             }
         }
-        for (int d = 0; d < 3; ++d) {
-            s_v[w][d][lane] = v[d];
-            s_h[w][d][lane] = hi[d];
-            s_l[w][d][lane] = lo[d];
-        }
+        for (int k = 0; k < P; ++k)
+            for (int d = 0; d < 3; ++d) {
+                s_v[w][d][P * lane + k] = v[k][d];
+                s_h[w][d][P * lane + k] = hi[k][d];
+                s_l[w][d][P * lane + k] = lo[k][d];
+            }
     }
     __syncthreads();
-    if (w != 0 || !active) return;
+    // one particle per lane from here: warps 0 .. P - 1
+    if (w >= P) return;
+    const int j = 32 * w + lane;   // the particle's place in the CTA's sums
+    const int i = base + j;
+    if (i >= a.row1) return;
     const V4 *pm = static_cast<const V4 *>(a.posm);
     const V4 *fm = static_cast<const V4 *>(a.frcm);
     double V[3];
     for (int d = 0; d < 3; ++d) {
         if constexpr (MODE == MODE_FP32) {
-            float f = s_h[0][d][lane];
-            for (int q = 1; q < kEpiWarps; ++q) f = __fadd_rn(f, s_h[q][d][lane]);
+            float f = s_h[0][d][j];
+            for (int q = 1; q < kEpiWarps; ++q) f = __fadd_rn(f, s_h[q][d][j]);
             V[d] = f;
         } else {
-            double v = s_v[0][d][lane];
-            float h = s_h[0][d][lane], l = s_l[0][d][lane];
+            double v = s_v[0][d][j];
+            float h = s_h[0][d][j], l = s_l[0][d][j];
             for (int q = 1; q < kEpiWarps; ++q) {
-                v += s_v[q][d][lane];
-                fold2(h, l, s_h[q][d][lane]);
-                l = __fadd_rn(l, s_l[q][d][lane]);
+                v += s_v[q][d][j];
+                fold2(h, l, s_h[q][d][j]);
+                l = __fadd_rn(l, s_l[q][d][j]);
             }
             V[d] = v + (static_cast<double>(h) + static_cast<double>(l));
         }
@@ -617,22 +662,29 @@ __global__ void __launch_bounds__(32 * kEpiWarps) epilogue_kernel(EpiArgs a) {
     }
 }
 
-template <int TDENSE, int MODE>
-static void epi_launch(int out, int nb, cudaStream_t st, const EpiArgs &a) {
+template <int TDENSE, int MODE, int P>
+static void epi_launch(int out, cudaStream_t st, const EpiArgs &a) {
+    const int nb = (a.row1 - a.row0 + 32 * P - 1) / (32 * P);
     switch (out) {
-        case OUT_F32: epilogue_kernel<TDENSE, MODE, OUT_F32><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
-        case OUT_F64: epilogue_kernel<TDENSE, MODE, OUT_F64><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
-        case OUT_PART: epilogue_kernel<TDENSE, MODE, OUT_PART><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
-        default: epilogue_kernel<TDENSE, MODE, OUT_EULER><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
+        case OUT_F32: epilogue_kernel<TDENSE, MODE, OUT_F32, P><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
+        case OUT_F64: epilogue_kernel<TDENSE, MODE, OUT_F64, P><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
+        case OUT_PART: epilogue_kernel<TDENSE, MODE, OUT_PART, P><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
+        default: epilogue_kernel<TDENSE, MODE, OUT_EULER, P><<<nb, 32 * kEpiWarps, 0, st>>>(a); break;
     }
 }
 
 template <int TDENSE>
-static void epi_launch_mode(int mode, int out, int nb, cudaStream_t st, const EpiArgs &a) {
+static void epi_launch_mode(int mode, int out, cudaStream_t st, const EpiArgs &a) {
     switch (mode) {
-        case MODE_FP32C: epi_launch<TDENSE, MODE_FP32C>(out, nb, st, a); break;
-        case MODE_FP64: epi_launch<TDENSE, MODE_FP64>(out, nb, st, a); break;
-        default: epi_launch<TDENSE, MODE_FP32>(out, nb, st, a); break;
+        case MODE_FP32C:
+            // two particles per lane needs an even first row (aligned loads) and no shard shares
+            if (kEpiPairs && (a.row0 & 1) == 0 && !a.sh.pall)
+                epi_launch<TDENSE, MODE_FP32C, 2>(out, st, a);
+            else
+                epi_launch<TDENSE, MODE_FP32C, 1>(out, st, a);
+            break;
+        case MODE_FP64: epi_launch<TDENSE, MODE_FP64, 1>(out, st, a); break;
+        default: epi_launch<TDENSE, MODE_FP32, 1>(out, st, a); break;
     }
 }
 
@@ -669,12 +721,11 @@ cudaError_t launch_epilogue(sd_handle *h, cudaStream_t st, int out, const double
     a.row0 = row0;
     a.row1 = row1;
     if (shard) a.sh = *shard;
-    const int nb = (row1 - row0 + 31) / 32;
     prof_begin(h, SD_KERNEL_EPILOGUE, st);
     if (h->tensor == T_OSEEN)
-        epi_launch_mode<T_OSEEN>(h->mode, out, nb, st, a);
+        epi_launch_mode<T_OSEEN>(h->mode, out, st, a);
     else
-        epi_launch_mode<T_RP>(h->mode, out, nb, st, a);
+        epi_launch_mode<T_RP>(h->mode, out, st, a);
     prof_end(h, SD_KERNEL_EPILOGUE, st);
     ++h->launches;
     return cudaGetLastError();
